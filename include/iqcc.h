@@ -1,0 +1,231 @@
+/*
+ * iqcc.h - C ABI of libiqcc.so, the GB300 (sm_103a) hot path of iterative
+ * qubit coupled cluster (iQCC, arXiv 2603.08883).
+ *
+ * One opaque context owns one qubit Hamiltonian H = sum_k C_k P_k (Eq. 2 /
+ * Eq. 9, real C_k) resident in GPU memory, and every operation below runs as
+ * CUDA kernels on the context's stream.  No PyTorch type appears here.
+ *
+ * Pauli keys.  A string on n qubits is stored as two bit vectors x and z of
+ * W = ceil(n/64) little-endian 64-bit words (qubit j = bit j%64 of word j/64);
+ * the letter of qubit j is (x,z) = (0,0) I, (1,0) X, (1,1) Y, (0,1) Z, and
+ * P(x,z) = i^{popcount(x&z)} X^x Z^z is Hermitian.  Arrays of keys are
+ * row-major [count][W]; bits at qubits >= n must be zero.  This is the
+ * "binary strings of X and Z components" of the paper's GPU section.
+ *
+ * Sign convention.  iqcc_dress(P, tau) maps H to e^{-i tau P/2} H e^{+i tau P/2}:
+ * a string T that anticommutes with P becomes cos(tau) T + sin(tau) (i T P),
+ * one that commutes is kept.  This is Eq. 5 with tau = -tau_paper; energies and
+ * their minima are the same, gradients flip sign:
+ * dE/dtau = -Im<Omega|H P|Omega> (Eq. 7 gives +Im for tau_paper).
+ *
+ * Canonical key order (export, DIS ties, compression ties): x as an unsigned
+ * integer of W words (word W-1 most significant), then z the same way.
+ *
+ * Memory and calls.  All pointer arguments are HOST memory unless stated.
+ * Inputs are copied; the library never keeps or frees caller memory.  Calls
+ * are ordered on opts.stream and return after their outputs are written
+ * (they synchronise that stream).  A context is used by one host thread at a
+ * time.  Device memory comes from opts.alloc/opts.free when given (e.g. a
+ * framework's caching allocator), else cudaMalloc/cudaFree; it grows on demand
+ * up to opts.capacity rows.
+ *
+ * Errors.  Every entry point returns an iqcc_status; iqcc_last_error() gives a
+ * one-line message.  On IQCC_ERR_ARG nothing was changed.  On
+ * IQCC_ERR_CAPACITY the Hamiltonian is exactly as before the generator that
+ * would have overflowed (n_applied says how many were applied).  After
+ * IQCC_ERR_CUDA, IQCC_ERR_HASH_FULL or IQCC_ERR_TIMEOUT the context is marked
+ * broken and later calls return IQCC_ERR_STATE; only iqcc_free() is valid.
+ */
+#ifndef IQCC_H
+#define IQCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct iqcc_ctx iqcc_ctx;
+
+typedef enum {
+    IQCC_OK = 0,
+    IQCC_ERR_ARG = 1,       /* invalid argument; nothing changed */
+    IQCC_ERR_CUDA = 2,      /* CUDA runtime error (context broken) */
+    IQCC_ERR_OOM = 3,       /* device allocation failed; H unchanged */
+    IQCC_ERR_CAPACITY = 4,  /* a dress would exceed opts.capacity rows; H unchanged */
+    IQCC_ERR_HASH_FULL = 5, /* hash probe bound exceeded (context broken) */
+    IQCC_ERR_TIMEOUT = 6,   /* a bounded device wait gave up (context broken) */
+    IQCC_ERR_STATE = 7      /* context broken by an earlier error */
+} iqcc_status;
+
+typedef struct {
+    int n_qubits;          /* 1..256 */
+    int64_t capacity;      /* maximum number of terms held; 0 -> 1<<30; at most 4294967294 */
+    int max_probe;         /* hash buckets probed per lookup before IQCC_ERR_HASH_FULL; 0 -> 64 */
+    void* stream;          /* cudaStream_t to run on; NULL -> the legacy default stream */
+    void* (*alloc)(size_t bytes, void* user); /* device allocator or NULL (cudaMalloc) */
+    void (*free)(void* ptr, void* user);      /* matching free or NULL (cudaFree) */
+    void* alloc_user;      /* passed to alloc/free */
+} iqcc_opts;
+
+/*
+ * Create a context holding H = sum_k coef[k] P(x[k], z[k]) (Eq. 2).
+ * x, z: host [n_terms][W]; coef: host [n_terms].  Repeated keys are summed in
+ * input order, exact zeros are dropped, and the rows are stored in canonical
+ * order (device radix sort + segmented sum).  n_terms may be 0.
+ * On success *out owns the context (free with iqcc_free); on failure *out is
+ * NULL and iqcc_last_error(NULL) describes the error.
+ */
+iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t n_terms,
+                                  const uint64_t* x, const uint64_t* z, const double* coef);
+
+/*
+ * Dress H in place with n_gen generators, in order k = 0..n_gen-1 (Eq. 5,
+ * Eq. 6; App. A procedure step 4), each the Hermitian string P(gx[k], gz[k])
+ * with amplitude tau[k] in the convention above.  gx, gz: host [n_gen][W];
+ * tau: host [n_gen].  A string T anticommuting with P_k and its partner
+ * Q = T xor P_k (i T P_k = s Q, s = +-1) are rotated as a pair when both are
+ * present; when Q is absent, T is scaled by cos and Q is appended with
+ * s sin(tau) C_T.  Commuting strings are untouched.  Nothing is pruned: exact
+ * zeros stay until iqcc_prune.  *n_applied (may be NULL) receives the number
+ * of generators applied.
+ */
+iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
+                       const double* tau, int* n_applied);
+
+/*
+ * Compress H (App. A procedure step 5; the "Maximum Terms" limit of the
+ * paper's Tables 2-3): remove every term with |C| < eps (eps <= 0 removes
+ * nothing); then, when max_terms > 0 and more terms remain, keep the max_terms
+ * largest |C|, ties at the threshold kept in ascending canonical key order.
+ * Surviving terms keep their relative order.  *n_removed may be NULL.
+ */
+iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_removed);
+
+/*
+ * QMF energy E = sum_k C_k <Omega|P_k|Omega> for the product state of Eq. 3
+ * (Eq. 10), theta/phi: host [n_qubits].  <X> = sin(th) cos(ph),
+ * <Y> = sin(th) sin(ph), <Z> = cos(th) per qubit.  When every theta_j is
+ * exactly 0 or pi (a computational basis state) only strings without X/Y
+ * contribute and no sines are evaluated (sin(pi) is taken as 0).
+ */
+iqcc_status iqcc_qmf_energy(iqcc_ctx* ctx, const double* theta, const double* phi, double* energy);
+
+/*
+ * Closed-form energy along one generator: E(tau) = A + B cos(tau) + C sin(tau)
+ * for the dressed energy <Omega|e^{-i tau P/2} H e^{i tau P/2}|Omega>
+ * (Eq. 5 inserted into Eq. 12).  A: commuting strings; B: anticommuting
+ * strings; C: sum over anticommuting T of C_T <i T P>.  abc: host double[3].
+ * The minimiser is tau* = atan2(-C, -B); dE/dtau at 0 equals C.
+ */
+iqcc_status iqcc_generator_abc(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz,
+                               const double* theta, const double* phi, double abc[3]);
+
+/*
+ * Energy gradients of candidate generators at tau = 0 (Eq. 7 / Eq. 13, sign as
+ * above: g = dE/dtau = C of iqcc_generator_abc).
+ * n_cand > 0: gradients of the given candidates cx, cz [n_cand][W]; grad[k]
+ *   for candidate k (grad: host [n_cand]); ox, oz, cap are ignored and
+ *   *n_out = n_cand.
+ * n_cand == 0: the Direct Interaction Space of App. A: one candidate per
+ *   distinct non-empty flip set F (the x vector) of the terms of H, with Y on
+ *   the lowest qubit of F and X on the rest (odd Y count, matching flip set).
+ *   When Omega is a basis state (all theta in {0, pi}) only terms with flip
+ *   set F contribute (Eq. 14-15) and the pass is one stream over H; otherwise
+ *   every term is summed for every candidate (cost M x G).  Candidates are
+ *   ordered by |g| with its 20 low mantissa bits cleared (relative tie
+ *   tolerance 2^-32), descending, then canonical key ascending.  *n_out = G
+ *   (the total); min(cap, G) candidates are written to ox, oz [cap][W] and grad
+ *   [cap].  cap = 0 is a size query.
+ */
+iqcc_status iqcc_dis_gradients(iqcc_ctx* ctx, const double* theta, const double* phi,
+                               int64_t n_cand, const uint64_t* cx, const uint64_t* cz,
+                               int64_t cap, int64_t* n_out, uint64_t* ox, uint64_t* oz,
+                               double* grad);
+
+/* Options and record of one iQCC iteration (App. A procedure steps 1-5). */
+typedef struct {
+    int n_gen;                 /* generators per iteration (<= 64) */
+    double eps;                /* compression threshold, as iqcc_prune */
+    int64_t max_terms;         /* term cap, as iqcc_prune (<= 0: none) */
+    double min_gradient;       /* candidates need |g| > this; 0 -> 1e-12 */
+    int n_forced;              /* > 0: use these generators instead of screening */
+    const uint64_t* forced_x;  /* host [n_forced][W] */
+    const uint64_t* forced_z;  /* host [n_forced][W] */
+    const double* forced_tau;  /* host [n_forced] or NULL: amplitudes to use */
+} iqcc_iter_opts;
+
+typedef struct {
+    int n_applied;             /* generators applied */
+    uint64_t gx[64 * 4];       /* [n_applied][W] generators, in order */
+    uint64_t gz[64 * 4];
+    double grad[64];           /* their screening gradients */
+    double tau[64];            /* amplitudes used */
+    double abc[64][3];         /* A, B, C of each, on the H it dressed */
+    int64_t n_terms_before;    /* M at the start of the iteration */
+    int64_t n_terms_peak;      /* largest M during the iteration */
+    int64_t n_removed;         /* removed by compression */
+    int64_t n_terms;           /* M at the end */
+    int64_t dressed_terms;     /* sum over generators of M at its dress */
+    double energy;             /* QMF energy after compression */
+} iqcc_iter_result;
+
+/*
+ * One iQCC iteration on the device (App. A steps 1-5; Fig. 1 loop 2a-2c):
+ * DIS screening (iqcc_dis_gradients with n_cand = 0) and the top n_gen
+ * candidates with |g| > min_gradient (or the forced list); for each in order,
+ * A, B, C on the current H, tau = atan2(-C, -B) (0 when B = C = 0; or the
+ * forced amplitude), and the dress; then iqcc_prune(eps, max_terms) and the
+ * energy.  The generators of one iteration come from one screening.
+ */
+iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi,
+                         const iqcc_iter_opts* opts, iqcc_iter_result* out);
+
+/* Number of terms currently held. */
+iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms);
+
+/*
+ * Copy H to the host in canonical order: *n = M; min(cap, M) rows written to
+ * x, z [cap][W] and coef [cap].  cap = 0 is a size query.
+ */
+iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z,
+                        double* coef);
+
+/* Running counters of the context (reset by iqcc_reset_stats). */
+typedef struct {
+    int64_t n_dress;           /* generators applied */
+    int64_t dressed_terms;     /* sum of M over applied generators */
+    int64_t anticommuting;     /* sum of anticommuting terms seen */
+    int64_t appended;          /* sum of appended terms */
+    double dress_kernel_ms;    /* device time of the dress kernels (CUDA events) */
+    double dress_bytes;        /* algorithmic bytes of those kernels: 16W M + 16 M_anti + (16W+8) M_new */
+    int64_t n_energy;          /* energy / A,B,C passes */
+    double energy_kernel_ms;
+    double energy_bytes;       /* (16W+8) M per pass */
+    double prune_ms;           /* device time of compression incl. hash rebuild */
+    double dis_ms;             /* device time of DIS screening */
+    double hash_ms;            /* device time of hash inserts and rebuilds */
+    int64_t hash_rebuilds;
+    int64_t rows_allocated;    /* rows currently allocated on the device */
+    int64_t hash_slots;        /* active hash slots */
+    int words;                 /* device words per x or z vector (1, 2 or 4) */
+    int pad;
+} iqcc_stats;
+
+iqcc_status iqcc_get_stats(const iqcc_ctx* ctx, iqcc_stats* out);
+iqcc_status iqcc_reset_stats(iqcc_ctx* ctx);
+
+/* One-line description of the last error of ctx (or of the calling thread's
+   last failed iqcc_load_hamiltonian when ctx is NULL).  Never NULL. */
+const char* iqcc_last_error(const iqcc_ctx* ctx);
+
+/* Release the context and all its device memory (NULL is allowed). */
+void iqcc_free(iqcc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IQCC_H */

@@ -1,0 +1,942 @@
+// C ABI of libiqcc: context management and the host-side sequencing of the
+// kernels in k_dress.cu, k_expect.cu and k_sort.cu.  Declarations and the
+// contract of every entry point are in include/iqcc.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "iqcc_internal.cuh"
+
+using namespace iqcc;
+
+namespace {
+
+thread_local std::string g_last_error = "no error";
+
+constexpr double kPi = 3.141592653589793;
+
+iqcc_status fail(iqcc_ctx* ctx, iqcc_status st, const std::string& msg) {
+    if (ctx) {
+        ctx->err = msg;
+        if (st == IQCC_ERR_CUDA || st == IQCC_ERR_HASH_FULL || st == IQCC_ERR_TIMEOUT) ctx->broken = true;
+    } else {
+        g_last_error = msg;
+    }
+    return st;
+}
+
+iqcc_status fail_cuda(iqcc_ctx* ctx, cudaError_t e, const char* what, int line) {
+    char buf[512];
+    snprintf(buf, sizeof buf, "CUDA error %d (%s) in %s at abi.cu:%d", (int)e, cudaGetErrorString(e), what, line);
+    return fail(ctx, IQCC_ERR_CUDA, buf);
+}
+
+#define CK(call)                                                        \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return fail_cuda(ctx, e_, #call, __LINE__); \
+    } while (0)
+
+#define CK_LAUNCH() CK(cudaGetLastError())
+
+#define GUARD(ctx)                                                                 \
+    do {                                                                           \
+        if (!(ctx)) return fail(nullptr, IQCC_ERR_ARG, "null context");            \
+        if ((ctx)->broken) return IQCC_ERR_STATE;                                  \
+    } while (0)
+
+void* dalloc(iqcc_ctx* ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    void* p = nullptr;
+    if (ctx->alloc) {
+        p = ctx->alloc(bytes, ctx->alloc_user);
+    } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        p = nullptr;
+    }
+    return p;
+}
+
+void dfree(iqcc_ctx* ctx, void* p) {
+    if (!p) return;
+    if (ctx->dfree) ctx->dfree(p, ctx->alloc_user);
+    else cudaFree(p);
+}
+
+void release(iqcc_ctx* ctx, Buf& b) {
+    dfree(ctx, b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+// Make b hold at least `bytes`; contents are not kept.
+bool ensure(iqcc_ctx* ctx, Buf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.p) return true;
+    size_t want = std::max(bytes, b.bytes + b.bytes / 2);
+    cudaStreamSynchronize(ctx->stream);
+    void* p = dalloc(ctx, want);
+    if (!p) {
+        p = dalloc(ctx, bytes);
+        want = bytes;
+    }
+    if (!p) return false;
+    release(ctx, b);
+    b.p = p;
+    b.bytes = want;
+    return true;
+}
+
+// Grow b to at least `bytes`, keeping the first `keep` bytes.
+bool grow_keep(iqcc_ctx* ctx, Buf& b, size_t bytes, size_t keep) {
+    if (b.bytes >= bytes && b.p) return true;
+    void* p = dalloc(ctx, bytes);
+    if (!p) return false;
+    if (keep && b.p) {
+        if (cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, ctx->stream) != cudaSuccess) {
+            cudaGetLastError();
+            dfree(ctx, p);
+            return false;
+        }
+    }
+    cudaStreamSynchronize(ctx->stream);
+    release(ctx, b);
+    b.p = p;
+    b.bytes = bytes;
+    return true;
+}
+
+size_t align256(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Bump allocator over ctx->scratch: first compute the total with a dry run of
+// take(), then ensure() and carve.
+struct Carver {
+    char* base = nullptr;
+    size_t off = 0;
+    template <class T>
+    T* take(size_t count) {
+        T* p = (T*)(base ? base + off : nullptr);
+        off += align256(count * sizeof(T) + 1);
+        return p;
+    }
+};
+
+size_t row_bytes(const iqcc_ctx* ctx) { return (size_t)16 * ctx->Wd; }
+
+HashView hash_view(const iqcc_ctx* ctx) {
+    HashView h;
+    h.slots = (uint64_t*)ctx->hash.p;
+    h.bucket_mask = ctx->hash_slots / kBucketSlots - 1;
+    h.max_probe = ctx->max_probe;
+    return h;
+}
+
+DevCounters* dctr(iqcc_ctx* ctx) { return (DevCounters*)ctx->counters.p; }
+
+iqcc_status read_counters(iqcc_ctx* ctx) {
+    CK(cudaMemcpyAsync(ctx->h_counters, ctx->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const DevCounters& c = *ctx->h_counters;
+    if (c.err) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "device error %d raised by kernel site %d", c.err, c.err_where);
+        return fail(ctx, (iqcc_status)c.err, buf);
+    }
+    return IQCC_OK;
+}
+
+uint64_t pow2_at_least(uint64_t v) {
+    uint64_t p = 1024;
+    while (p < v) p <<= 1;
+    return p;
+}
+
+// (Re)build the index over rows [0, M) with `slots` slots.
+iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
+    if (slots != ctx->hash_slots || !ctx->hash.p) {
+        release(ctx, ctx->hash);
+        ctx->hash_slots = 0;
+        if (!ensure(ctx, ctx->hash, slots * sizeof(uint64_t))) return fail(ctx, IQCC_ERR_OOM, "hash allocation failed");
+        ctx->hash_slots = slots;
+    }
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    HashView h = hash_view(ctx);
+    launch_hash_clear(h, ctx->hash_slots, ctx->stream);
+    CK_LAUNCH();
+    launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.hash_ms += ms;
+    ctx->stats.hash_rebuilds++;
+    ctx->stats.hash_slots = (int64_t)ctx->hash_slots;
+    return read_counters(ctx);
+}
+
+// Rows and index able to hold `rows_needed` rows (current rows kept).
+iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
+    if (rows_needed > ctx->rows_alloc) {
+        int64_t want = std::max<int64_t>(rows_needed, ctx->rows_alloc + ctx->rows_alloc / 2);
+        want = std::min<int64_t>(want, ctx->capacity);
+        want = std::max<int64_t>(want, rows_needed);
+        const size_t rb = row_bytes(ctx);
+        if (!grow_keep(ctx, ctx->keys[ctx->cur], (size_t)want * rb, (size_t)ctx->M * rb) ||
+            !grow_keep(ctx, ctx->coef[ctx->cur], (size_t)want * 8, (size_t)ctx->M * 8))
+            return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
+        release(ctx, ctx->keys[ctx->cur ^ 1]);
+        release(ctx, ctx->coef[ctx->cur ^ 1]);
+        if (!ensure(ctx, ctx->keys[ctx->cur ^ 1], (size_t)want * rb) ||
+            !ensure(ctx, ctx->coef[ctx->cur ^ 1], (size_t)want * 8))
+            return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
+        ctx->rows_alloc = want;
+        ctx->stats.rows_allocated = want;
+    }
+    // load factor <= 1/2 after the rows are inserted
+    if ((uint64_t)rows_needed * 2 > ctx->hash_slots) {
+        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 4));
+        if (st) return st;
+    }
+    return IQCC_OK;
+}
+
+bool bits_above_n(const iqcc_ctx* ctx, const uint64_t* w) {
+    int r = ctx->n - 64 * (ctx->W - 1);
+    if (r >= 64) return false;
+    return (w[ctx->W - 1] >> r) != 0;
+}
+
+// Device layout of one key: x[Wd] then z[Wd].
+void pad_key(const iqcc_ctx* ctx, const uint64_t* x, const uint64_t* z, uint64_t* out) {
+    for (int w = 0; w < ctx->Wd; ++w) {
+        out[w] = w < ctx->W ? x[w] : 0;
+        out[ctx->Wd + w] = w < ctx->W ? z[w] : 0;
+    }
+}
+
+SortPlan canonical_plan(const iqcc_ctx* ctx) {
+    SortPlan p{};
+    p.n_words = 2 * ctx->Wd;
+    p.n_order = 0;
+    for (int w = ctx->Wd - 1; w >= 0; --w) p.order[p.n_order++] = w;            // x, most significant first
+    for (int w = ctx->Wd - 1; w >= 0; --w) p.order[p.n_order++] = ctx->Wd + w;  // then z
+    return p;
+}
+
+bool is_basis(const iqcc_ctx* ctx, const double* theta) {
+    for (int j = 0; j < ctx->n; ++j)
+        if (!(theta[j] == 0.0 || theta[j] == kPi)) return false;
+    return true;
+}
+
+void occ_words(const iqcc_ctx* ctx, const double* theta, uint64_t* occ) {
+    for (int w = 0; w < 4; ++w) occ[w] = 0;
+    for (int j = 0; j < ctx->n; ++j)
+        if (theta[j] == kPi) occ[j / 64] |= 1ull << (j % 64);
+}
+
+int n_groups(const iqcc_ctx* ctx) { return (ctx->n + 3) / 4; }
+
+// QMF tables for general angles, into `tables` (device), from host angles.
+iqcc_status upload_tables(iqcc_ctx* ctx, const double* theta, const double* phi, double* d_angles, double* tables) {
+    CK(cudaMemcpyAsync(d_angles, theta, sizeof(double) * ctx->n, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_angles + ctx->n, phi, sizeof(double) * ctx->n, cudaMemcpyHostToDevice, ctx->stream));
+    launch_qmf_tables(d_angles, d_angles + ctx->n, ctx->n, n_groups(ctx), tables, ctx->stream);
+    CK_LAUNCH();
+    return IQCC_OK;
+}
+
+// A, B, C of padded device-layout generator pkey (all zero: energy).
+iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, const double* phi, double* abc) {
+    const bool basis = is_basis(ctx, theta);
+    uint64_t occ[4];
+    occ_words(ctx, theta, occ);
+    const int nb = expect_blocks();
+    Carver cv;
+    cv.take<double>(nb * 3);
+    cv.take<double>(4);
+    cv.take<double>(2 * ctx->n);
+    cv.take<double>((size_t)n_groups(ctx) * 256);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    double* partials = cv.take<double>(nb * 3);
+    double* out3 = cv.take<double>(4);
+    double* angles = cv.take<double>(2 * ctx->n);
+    double* tables = cv.take<double>((size_t)n_groups(ctx) * 256);
+    if (!basis) {
+        iqcc_status st = upload_tables(ctx, theta, phi, angles, tables);
+        if (st) return st;
+    }
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    launch_abc(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pkey, basis, occ, tables, n_groups(ctx), partials,
+               ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    launch_reduce3(partials, nb, out3, ctx->stream);
+    CK_LAUNCH();
+    double h3[3];
+    CK(cudaMemcpyAsync(h3, out3, sizeof h3, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.n_energy++;
+    ctx->stats.energy_kernel_ms += ms;
+    ctx->stats.energy_bytes += (double)ctx->M * (16.0 * ctx->Wd + 8.0);
+    abc[0] = h3[0];
+    abc[1] = h3[1];
+    abc[2] = h3[2];
+    return IQCC_OK;
+}
+
+// One generator (device-layout key); on IQCC_ERR_CAPACITY / OOM H is unchanged.
+iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
+    if (ctx->M == 0) {
+        ctx->stats.n_dress++;
+        return IQCC_OK;
+    }
+    const int64_t M = ctx->M;
+    int64_t upper = 2 * M;
+    DevCounters* c = dctr(ctx);
+    if (upper > ctx->capacity) {
+        // exact admission count (probe only)
+        CK(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), ctx->stream));
+        launch_dress_count(ctx->Wd, ctx->rows(), M, pkey, hash_view(ctx), c, ctx->stream);
+        CK_LAUNCH();
+        iqcc_status st = read_counters(ctx);
+        if (st) return st;
+        upper = M + (int64_t)ctx->h_counters->n_new;
+        if (upper > ctx->capacity) {
+            char buf[200];
+            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)upper,
+                     (long long)ctx->capacity);
+            return fail(ctx, IQCC_ERR_CAPACITY, buf);
+        }
+    }
+    iqcc_status st = reserve_rows(ctx, upper);
+    if (st) return st;
+    CK(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    launch_dress(ctx->Wd, ctx->rows(), ctx->rows(), ctx->c(), M, pkey, std::cos(tau), std::sin(tau),
+                 hash_view(ctx), c, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    st = read_counters(ctx);
+    if (st) return st;
+    const int64_t n_new = (int64_t)ctx->h_counters->n_new;
+    const int64_t n_anti = (int64_t)ctx->h_counters->n_anti;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    // index the appended rows
+    cudaEvent_t h0 = ctx->ev0, h1 = ctx->ev1;
+    CK(cudaEventRecord(h0, ctx->stream));
+    launch_hash_insert(ctx->Wd, ctx->rows(), M, M + n_new, hash_view(ctx), c, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(h1, ctx->stream));
+    ctx->M = M + n_new;
+    iqcc_stats& s = ctx->stats;
+    s.n_dress++;
+    s.dressed_terms += M;
+    s.anticommuting += n_anti;
+    s.appended += n_new;
+    s.dress_kernel_ms += ms;
+    s.dress_bytes += 16.0 * ctx->Wd * (double)M + 16.0 * (double)n_anti + (16.0 * ctx->Wd + 8.0) * (double)n_new;
+    st = read_counters(ctx);
+    if (st) return st;
+    float hms = 0;
+    cudaEventElapsedTime(&hms, h0, h1);
+    s.hash_ms += hms;
+    return IQCC_OK;
+}
+
+// Indirect sort of rows [0, n) (or of the listed subset) in canonical order.
+// Returns the sorted permutation in *out (device, inside scratch region `sc`).
+struct SortArea {
+    uint32_t* a;
+    uint32_t* b;
+    void* tmp;
+    size_t tmp_bytes;
+};
+
+size_t sort_area_bytes(int64_t n) {
+    return align256((size_t)n * 4 + 1) * 2 + align256(radix_sort_scratch_bytes(n));
+}
+
+SortArea carve_sort(Carver& cv, int64_t n) {
+    SortArea s;
+    s.a = cv.take<uint32_t>(n);
+    s.b = cv.take<uint32_t>(n);
+    s.tmp_bytes = radix_sort_scratch_bytes(n);
+    s.tmp = cv.take<char>(s.tmp_bytes);
+    return s;
+}
+
+iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed) {
+    const int64_t M = ctx->M;
+    *removed = 0;
+    if (M == 0) return IQCC_OK;
+    Carver cv;
+    cv.take<uint8_t>(M);
+    cv.take<unsigned long long>(256);
+    cv.take<char>(compact_scratch_bytes(M));
+    cv.take<uint32_t>(M);  // tie list
+    cv.off += sort_area_bytes(M);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint8_t* flags = cv.take<uint8_t>(M);
+    unsigned long long* hist = cv.take<unsigned long long>(256);
+    char* cscratch = cv.take<char>(compact_scratch_bytes(M));
+    uint32_t* ties = cv.take<uint32_t>(M);
+    SortArea sa = carve_sort(cv, M);
+
+    DevCounters* c = dctr(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    const int64_t kept = (int64_t)ctx->h_counters->aux;
+    if (max_terms > 0 && kept > max_terms) {
+        // radix select of the max_terms-th largest |C| bit pattern, 8 bits at a time
+        int64_t need = max_terms;
+        uint64_t prefix = 0, pmask = 0;
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), ctx->stream));
+            launch_abs_digit_hist(ctx->c(), flags, M, shift, prefix, pmask, hist, ctx->stream);
+            CK_LAUNCH();
+            unsigned long long h[256];
+            CK(cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            int64_t cum = 0;
+            int sel = 0;
+            for (int d = 255; d >= 0; --d) {
+                if (cum + (int64_t)h[d] >= need) { sel = d; break; }
+                cum += (int64_t)h[d];
+            }
+            need -= cum;
+            prefix |= (uint64_t)sel << shift;
+            pmask |= (uint64_t)255 << shift;
+        }
+        // strictly larger kept; the `need` smallest keys among the ties kept
+        CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+        launch_budget_flags(ctx->c(), flags, M, prefix, ties, &c->aux, ctx->stream);
+        CK_LAUNCH();
+        st = read_counters(ctx);
+        if (st) return st;
+        const int64_t n_ties = (int64_t)ctx->h_counters->aux;
+        if (need >= n_ties) {
+            launch_set_flags(ties, n_ties, flags, ctx->stream);
+        } else {
+            CK(cudaMemcpyAsync(sa.a, ties, (size_t)n_ties * 4, cudaMemcpyDeviceToDevice, ctx->stream));
+            uint32_t* sorted = nullptr;
+            radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, n_ties, &sorted, sa.tmp,
+                                sa.tmp_bytes, ctx->stream);
+            CK_LAUNCH();
+            launch_set_flags(sorted, need, flags, ctx->stream);
+        }
+        CK_LAUNCH();
+    }
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_compact_rows(ctx->Wd, flags, ctx->rows(), ctx->c(), ctx->rows_alt(), ctx->c_alt(), M, cscratch, &c->aux,
+                        ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    st = read_counters(ctx);
+    if (st) return st;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.prune_ms += ms;
+    const int64_t newM = (int64_t)ctx->h_counters->aux;
+    ctx->cur ^= 1;
+    ctx->M = newM;
+    *removed = M - newM;
+    // rows moved: rebuild the index (same size)
+    return rebuild_hash(ctx, ctx->hash_slots ? ctx->hash_slots : pow2_at_least((uint64_t)newM * 4));
+}
+
+// DIS candidates and gradients (n_cand == 0 path).  Leaves the ordered
+// candidates in scratch and returns G; copies min(cap, G) to the host.
+iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi, int64_t cap, int64_t* n_out,
+                          uint64_t* ox, uint64_t* oz, double* og) {
+    const int64_t M = ctx->M;
+    const int Wd = ctx->Wd, W = ctx->W;
+    const bool basis = is_basis(ctx, theta);
+    uint64_t occ[4];
+    occ_words(ctx, theta, occ);
+    const uint64_t gslots = pow2_at_least((uint64_t)std::max<int64_t>(M, 1) * 2);
+    const int nblk = expect_blocks();
+    const int64_t Mg = std::max<int64_t>(M, 1);
+    Carver cv;
+    cv.take<uint64_t>(gslots);
+    cv.take<uint64_t>((size_t)Mg * Wd);
+    cv.take<double>(Mg);
+    cv.take<uint64_t>((size_t)Mg * (Wd + 1));
+    cv.off += sort_area_bytes(Mg);
+    cv.take<uint64_t>((size_t)Mg * W * 2);
+    cv.take<double>(Mg);
+    cv.take<double>(2 * ctx->n);
+    cv.take<double>((size_t)n_groups(ctx) * 256);
+    cv.take<uint64_t>(16 * 2 * 4);
+    cv.take<double>((size_t)nblk * 16);
+    cv.take<double>(16);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint64_t* slots = cv.take<uint64_t>(gslots);
+    uint64_t* gkeys = cv.take<uint64_t>((size_t)Mg * Wd);
+    double* gsum = cv.take<double>(Mg);
+    uint64_t* skeys = cv.take<uint64_t>((size_t)Mg * (Wd + 1));
+    SortArea sa = carve_sort(cv, Mg);
+    uint64_t* stage_x = cv.take<uint64_t>((size_t)Mg * W * 2);
+    double* stage_g = cv.take<double>(Mg);
+    double* angles = cv.take<double>(2 * ctx->n);
+    double* tables = cv.take<double>((size_t)n_groups(ctx) * 256);
+    uint64_t* cand = cv.take<uint64_t>(16 * 2 * 4);
+    double* partials = cv.take<double>((size_t)nblk * 16);
+    double* colsum = cv.take<double>(16);
+
+    DevCounters* c = dctr(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    HashView gh{slots, gslots / kBucketSlots - 1, ctx->max_probe};
+    launch_hash_clear(gh, gslots, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    launch_dis_group(Wd, ctx->rows(), ctx->c(), M, occ, basis, slots, gh.bucket_mask, ctx->max_probe, gkeys, gsum, c,
+                     ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    const int64_t G = (int64_t)ctx->h_counters->n_groups;
+    if (!basis && G > 0) {
+        // general angles: every term against every candidate, 16 candidates per pass
+        st = upload_tables(ctx, theta, phi, angles, tables);
+        if (st) return st;
+        std::vector<uint64_t> hk((size_t)G * Wd);
+        CK(cudaMemcpyAsync(hk.data(), gkeys, hk.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        for (int64_t g0 = 0; g0 < G; g0 += 16) {
+            const int K = (int)std::min<int64_t>(16, G - g0);
+            uint64_t hc[16 * 8] = {0};
+            for (int k = 0; k < K; ++k) {
+                bool found = false;
+                for (int w = 0; w < Wd; ++w) {
+                    uint64_t x = hk[(size_t)(g0 + k) * Wd + w];
+                    hc[k * 2 * Wd + w] = x;
+                    hc[k * 2 * Wd + Wd + w] = found ? 0 : (x & (~x + 1));
+                    found |= x != 0;
+                }
+            }
+            CK(cudaMemcpyAsync(cand, hc, sizeof(uint64_t) * 2 * Wd * K, cudaMemcpyHostToDevice, ctx->stream));
+            launch_grad_general(Wd, ctx->rows(), ctx->c(), M, cand, K, tables, n_groups(ctx), partials, nblk,
+                                ctx->stream);
+            CK_LAUNCH();
+            launch_reduce_cols(partials, nblk, 16, colsum, ctx->stream);
+            CK_LAUNCH();
+            CK(cudaMemcpyAsync(gsum + g0, colsum, sizeof(double) * K, cudaMemcpyDeviceToDevice, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));  // hc is reused
+        }
+    }
+    *n_out = G;
+    if (cap > 0 && G > 0) {
+        launch_dis_sort_keys(Wd, gkeys, gsum, G, skeys, ctx->stream);
+        CK_LAUNCH();
+        launch_iota(sa.a, G, ctx->stream);
+        CK_LAUNCH();
+        SortPlan plan{};
+        plan.n_words = Wd + 1;
+        plan.n_order = Wd + 1;
+        for (int w = 0; w <= Wd; ++w) plan.order[w] = w;
+        uint32_t* sorted = nullptr;
+        radix_sort_indirect(skeys, Wd + 1, plan, sa.a, sa.b, G, &sorted, sa.tmp, sa.tmp_bytes, ctx->stream);
+        CK_LAUNCH();
+        const int64_t k = std::min(cap, G);
+        launch_dis_export(W, Wd, gkeys, gsum, sorted, k, stage_x, stage_x + (size_t)k * W, stage_g, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(ox, stage_x, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(oz, stage_x + (size_t)k * W, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(og, stage_g, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.dis_ms += ms;
+    return IQCC_OK;
+}
+
+iqcc_status gradients_given(iqcc_ctx* ctx, const double* theta, const double* phi, int64_t K, const uint64_t* cx,
+                            const uint64_t* cz, double* grad) {
+    const int Wd = ctx->Wd;
+    const int nblk = expect_blocks();
+    Carver cv;
+    cv.take<double>(2 * ctx->n);
+    cv.take<double>((size_t)n_groups(ctx) * 256);
+    cv.take<uint64_t>(16 * 2 * 4);
+    cv.take<double>((size_t)nblk * 16);
+    cv.take<double>(16);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    double* angles = cv.take<double>(2 * ctx->n);
+    double* tables = cv.take<double>((size_t)n_groups(ctx) * 256);
+    uint64_t* cand = cv.take<uint64_t>(16 * 2 * 4);
+    double* partials = cv.take<double>((size_t)nblk * 16);
+    double* colsum = cv.take<double>(16);
+    iqcc_status st = upload_tables(ctx, theta, phi, angles, tables);
+    if (st) return st;
+    for (int64_t k0 = 0; k0 < K; k0 += 16) {
+        const int k = (int)std::min<int64_t>(16, K - k0);
+        uint64_t hc[16 * 8] = {0};
+        for (int i = 0; i < k; ++i) pad_key(ctx, cx + (k0 + i) * ctx->W, cz + (k0 + i) * ctx->W, hc + i * 2 * Wd);
+        CK(cudaMemcpyAsync(cand, hc, sizeof(uint64_t) * 2 * Wd * k, cudaMemcpyHostToDevice, ctx->stream));
+        launch_grad_general(Wd, ctx->rows(), ctx->c(), ctx->M, cand, k, tables, n_groups(ctx), partials, nblk,
+                            ctx->stream);
+        CK_LAUNCH();
+        launch_reduce_cols(partials, nblk, 16, colsum, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(grad + k0, colsum, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return IQCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t n_terms, const uint64_t* x,
+                                  const uint64_t* z, const double* coef) {
+    if (!out) return fail(nullptr, IQCC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!opts) return fail(nullptr, IQCC_ERR_ARG, "opts is NULL");
+    if (opts->n_qubits < 1 || opts->n_qubits > 256) return fail(nullptr, IQCC_ERR_ARG, "n_qubits must be in 1..256");
+    if (n_terms < 0) return fail(nullptr, IQCC_ERR_ARG, "n_terms < 0");
+    if (n_terms > 0 && (!x || !z || !coef)) return fail(nullptr, IQCC_ERR_ARG, "null input array");
+    if (opts->capacity < 0 || opts->capacity > 0xFFFFFFFEll) return fail(nullptr, IQCC_ERR_ARG, "capacity out of range");
+    if ((opts->alloc == nullptr) != (opts->free == nullptr))
+        return fail(nullptr, IQCC_ERR_ARG, "alloc and free must be given together");
+    iqcc_ctx* ctx = new iqcc_ctx();
+    ctx->n = opts->n_qubits;
+    ctx->W = (ctx->n + 63) / 64;
+    ctx->Wd = device_words(ctx->n);
+    ctx->capacity = opts->capacity ? opts->capacity : (int64_t)1 << 30;
+    ctx->max_probe = opts->max_probe > 0 ? opts->max_probe : 64;
+    ctx->stream = (cudaStream_t)opts->stream;
+    ctx->alloc = opts->alloc;
+    ctx->dfree = opts->free;
+    ctx->alloc_user = opts->alloc_user;
+    ctx->stats.words = ctx->Wd;
+    auto bail = [&](iqcc_status st) {
+        g_last_error = ctx->err;
+        iqcc_free(ctx);
+        return st;
+    };
+    for (int64_t k = 0; k < n_terms; ++k)
+        if (bits_above_n(ctx, x + k * ctx->W) || bits_above_n(ctx, z + k * ctx->W)) {
+            fail(ctx, IQCC_ERR_ARG, "key bits set above n_qubits");
+            return bail(IQCC_ERR_ARG);
+        }
+    if (n_terms > ctx->capacity) {
+        fail(ctx, IQCC_ERR_CAPACITY, "more input terms than capacity");
+        return bail(IQCC_ERR_CAPACITY);
+    }
+    if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess ||
+        cudaMallocHost((void**)&ctx->h_counters, sizeof(DevCounters)) != cudaSuccess) {
+        cudaGetLastError();
+        fail(ctx, IQCC_ERR_CUDA, "event / pinned allocation failed (is a CUDA device visible?)");
+        return bail(IQCC_ERR_CUDA);
+    }
+    if (!ensure(ctx, ctx->counters, sizeof(DevCounters))) {
+        fail(ctx, IQCC_ERR_OOM, "counter allocation failed");
+        return bail(IQCC_ERR_OOM);
+    }
+    if (cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream) != cudaSuccess) {
+        fail_cuda(ctx, cudaGetLastError(), "memset", __LINE__);
+        return bail(IQCC_ERR_CUDA);
+    }
+    const int64_t rows0 = std::min<int64_t>(ctx->capacity, std::max<int64_t>(1024, 2 * n_terms));
+    const size_t rb = row_bytes(ctx);
+    for (int b = 0; b < 2; ++b)
+        if (!ensure(ctx, ctx->keys[b], (size_t)rows0 * rb) || !ensure(ctx, ctx->coef[b], (size_t)rows0 * 8)) {
+            fail(ctx, IQCC_ERR_OOM, "row allocation failed");
+            return bail(IQCC_ERR_OOM);
+        }
+    ctx->rows_alloc = rows0;
+    ctx->stats.rows_allocated = rows0;
+    const int64_t n = n_terms;
+    if (n > 0) {
+        const int W = ctx->W, Wd = ctx->Wd;
+        Carver cv;
+        cv.take<uint64_t>((size_t)n * W);
+        cv.take<uint64_t>((size_t)n * W);
+        cv.take<uint8_t>(n);
+        cv.take<char>(compact_scratch_bytes(n));
+        cv.off += sort_area_bytes(n);
+        if (!ensure(ctx, ctx->scratch, cv.off)) {
+            fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+            return bail(IQCC_ERR_OOM);
+        }
+        cv = Carver{(char*)ctx->scratch.p, 0};
+        uint64_t* dx = cv.take<uint64_t>((size_t)n * W);
+        uint64_t* dz = cv.take<uint64_t>((size_t)n * W);
+        uint8_t* flags = cv.take<uint8_t>(n);
+        char* cscratch = cv.take<char>(compact_scratch_bytes(n));
+        SortArea sa = carve_sort(cv, n);
+        cudaStream_t s = ctx->stream;
+        uint64_t* staged = ctx->rows_alt();
+        double* c_staged = ctx->c_alt();
+        iqcc_status st = IQCC_OK;
+        do {
+            if (cudaMemcpyAsync(dx, x, sizeof(uint64_t) * n * W, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(dz, z, sizeof(uint64_t) * n * W, cudaMemcpyHostToDevice, s) ||
+                cudaMemcpyAsync(c_staged, coef, sizeof(double) * n, cudaMemcpyHostToDevice, s)) {
+                st = fail_cuda(ctx, cudaGetLastError(), "input copy", __LINE__);
+                break;
+            }
+            launch_pack_rows(W, Wd, dx, dz, staged, n, s);
+            launch_iota(sa.a, n, s);
+            uint32_t* sorted = nullptr;
+            radix_sort_indirect(staged, 2 * Wd, canonical_plan(ctx), sa.a, sa.b, n, &sorted, sa.tmp, sa.tmp_bytes, s);
+            // run sums land in the current buffers at sorted positions, then compact back into the alternate
+            launch_sum_runs(Wd, staged, c_staged, sorted, n, flags, ctx->rows(), ctx->c(), s);
+            DevCounters* c = dctr(ctx);
+            launch_compact_rows(Wd, flags, ctx->rows(), ctx->c(), staged, c_staged, n, cscratch, &c->aux, s);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) { st = fail_cuda(ctx, e, "load kernels", __LINE__); break; }
+            st = read_counters(ctx);
+            if (st) break;
+            ctx->cur ^= 1;
+            ctx->M = (int64_t)ctx->h_counters->aux;
+        } while (0);
+        if (st) return bail(st);
+    }
+    iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
+    if (st) return bail(st);
+    ctx->stats.hash_rebuilds = 0;
+    ctx->stats.hash_ms = 0;
+    *out = ctx;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* tau,
+                       int* n_applied) {
+    if (n_applied) *n_applied = 0;
+    GUARD(ctx);
+    if (n_gen < 0) return fail(ctx, IQCC_ERR_ARG, "n_gen < 0");
+    if (n_gen > 0 && (!gx || !gz || !tau)) return fail(ctx, IQCC_ERR_ARG, "null generator array");
+    for (int k = 0; k < n_gen; ++k) {
+        if (bits_above_n(ctx, gx + k * ctx->W) || bits_above_n(ctx, gz + k * ctx->W))
+            return fail(ctx, IQCC_ERR_ARG, "generator bits set above n_qubits");
+        if (!std::isfinite(tau[k])) return fail(ctx, IQCC_ERR_ARG, "non-finite amplitude");
+    }
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    for (int k = 0; k < n_gen; ++k) {
+        uint64_t pk[8];
+        pad_key(ctx, gx + k * ctx->W, gz + k * ctx->W, pk);
+        iqcc_status st = dress_one(ctx, pk, tau[k]);
+        if (st) return st;
+        if (n_applied) *n_applied = k + 1;
+    }
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_removed) {
+    if (n_removed) *n_removed = 0;
+    GUARD(ctx);
+    if (std::isnan(eps)) return fail(ctx, IQCC_ERR_ARG, "eps is NaN");
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    int64_t removed = 0;
+    iqcc_status st = compress(ctx, eps, max_terms, &removed);
+    if (st) return st;
+    if (n_removed) *n_removed = removed;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_qmf_energy(iqcc_ctx* ctx, const double* theta, const double* phi, double* energy) {
+    GUARD(ctx);
+    if (!theta || !phi || !energy) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    uint64_t zero[8] = {0};
+    double abc[3];
+    iqcc_status st = abc_impl(ctx, zero, theta, phi, abc);
+    if (st) return st;
+    *energy = abc[0];
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_generator_abc(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, const double* theta,
+                               const double* phi, double abc[3]) {
+    GUARD(ctx);
+    if (!gx || !gz || !theta || !phi || !abc) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    if (bits_above_n(ctx, gx) || bits_above_n(ctx, gz)) return fail(ctx, IQCC_ERR_ARG, "generator bits above n_qubits");
+    uint64_t pk[8];
+    pad_key(ctx, gx, gz, pk);
+    return abc_impl(ctx, pk, theta, phi, abc);
+}
+
+iqcc_status iqcc_dis_gradients(iqcc_ctx* ctx, const double* theta, const double* phi, int64_t n_cand,
+                               const uint64_t* cx, const uint64_t* cz, int64_t cap, int64_t* n_out, uint64_t* ox,
+                               uint64_t* oz, double* grad) {
+    GUARD(ctx);
+    if (!theta || !phi || !n_out) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    *n_out = 0;
+    if (n_cand < 0 || cap < 0) return fail(ctx, IQCC_ERR_ARG, "negative count");
+    if (n_cand > 0) {
+        if (!cx || !cz || !grad) return fail(ctx, IQCC_ERR_ARG, "null candidate array");
+        for (int64_t k = 0; k < n_cand; ++k)
+            if (bits_above_n(ctx, cx + k * ctx->W) || bits_above_n(ctx, cz + k * ctx->W))
+                return fail(ctx, IQCC_ERR_ARG, "candidate bits above n_qubits");
+        iqcc_status st = gradients_given(ctx, theta, phi, n_cand, cx, cz, grad);
+        if (st) return st;
+        *n_out = n_cand;
+        return IQCC_OK;
+    }
+    if (cap > 0 && (!ox || !oz || !grad)) return fail(ctx, IQCC_ERR_ARG, "null output array");
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    return dis_enumerate(ctx, theta, phi, cap, n_out, ox, oz, grad);
+}
+
+iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, const iqcc_iter_opts* o,
+                         iqcc_iter_result* out) {
+    GUARD(ctx);
+    if (!theta || !phi || !o || !out) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    const int W = ctx->W;
+    const int n_gen = o->n_forced > 0 ? o->n_forced : o->n_gen;
+    if (n_gen < 0 || n_gen > 64) return fail(ctx, IQCC_ERR_ARG, "n_gen must be in 0..64");
+    if (o->n_forced > 0 && (!o->forced_x || !o->forced_z)) return fail(ctx, IQCC_ERR_ARG, "null forced generators");
+    std::memset(out, 0, sizeof *out);
+    out->n_terms_before = ctx->M;
+    out->n_terms_peak = ctx->M;
+    const double gmin = o->min_gradient > 0 ? o->min_gradient : 1e-12;
+    std::vector<uint64_t> gx((size_t)64 * W), gz((size_t)64 * W);
+    std::vector<double> g(64);
+    int used = 0;
+    if (o->n_forced > 0) {
+        used = o->n_forced;
+        std::memcpy(gx.data(), o->forced_x, sizeof(uint64_t) * used * W);
+        std::memcpy(gz.data(), o->forced_z, sizeof(uint64_t) * used * W);
+        int64_t nn = 0;
+        iqcc_status st = iqcc_dis_gradients(ctx, theta, phi, used, gx.data(), gz.data(), 0, &nn, nullptr, nullptr,
+                                            g.data());
+        if (st) return st;
+    } else if (n_gen > 0) {
+        int64_t G = 0;
+        iqcc_status st = iqcc_dis_gradients(ctx, theta, phi, 0, nullptr, nullptr, n_gen, &G, gx.data(), gz.data(),
+                                            g.data());
+        if (st) return st;
+        const int64_t avail = std::min<int64_t>(G, n_gen);
+        while (used < avail && std::fabs(g[used]) > gmin) ++used;
+    }
+    for (int k = 0; k < used; ++k) {
+        double abc[3];
+        iqcc_status st = iqcc_generator_abc(ctx, gx.data() + k * W, gz.data() + k * W, theta, phi, abc);
+        if (st) return st;
+        double tau;
+        if (o->n_forced > 0 && o->forced_tau) tau = o->forced_tau[k];
+        else tau = (abc[1] == 0.0 && abc[2] == 0.0) ? 0.0 : std::atan2(-abc[2], -abc[1]);
+        out->dressed_terms += ctx->M;
+        int applied = 0;
+        st = iqcc_dress(ctx, 1, gx.data() + k * W, gz.data() + k * W, &tau, &applied);
+        if (st) {
+            out->n_applied = k;
+            return st;
+        }
+        std::memcpy(out->gx + k * W, gx.data() + k * W, sizeof(uint64_t) * W);
+        std::memcpy(out->gz + k * W, gz.data() + k * W, sizeof(uint64_t) * W);
+        out->grad[k] = g[k];
+        out->tau[k] = tau;
+        for (int i = 0; i < 3; ++i) out->abc[k][i] = abc[i];
+        out->n_applied = k + 1;
+        out->n_terms_peak = std::max(out->n_terms_peak, ctx->M);
+    }
+    int64_t removed = 0;
+    iqcc_status st = iqcc_prune(ctx, o->eps, o->max_terms, &removed);
+    if (st) return st;
+    out->n_removed = removed;
+    out->n_terms = ctx->M;
+    return iqcc_qmf_energy(ctx, theta, phi, &out->energy);
+}
+
+iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms) {
+    if (!ctx || !n_terms) return fail(nullptr, IQCC_ERR_ARG, "null argument");
+    if (ctx->broken) return IQCC_ERR_STATE;
+    *n_terms = ctx->M;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z, double* coef) {
+    GUARD(ctx);
+    if (!n) return fail(ctx, IQCC_ERR_ARG, "n is NULL");
+    if (cap < 0) return fail(ctx, IQCC_ERR_ARG, "cap < 0");
+    *n = ctx->M;
+    const int64_t k = std::min(cap, ctx->M);
+    if (k == 0) return IQCC_OK;
+    if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
+    const int64_t M = ctx->M;
+    const int W = ctx->W;
+    Carver cv;
+    cv.off += sort_area_bytes(M);
+    cv.take<uint64_t>((size_t)k * W);
+    cv.take<uint64_t>((size_t)k * W);
+    cv.take<double>(k);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    SortArea sa = carve_sort(cv, M);
+    uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
+    uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
+    double* sc = cv.take<double>(k);
+    launch_iota(sa.a, M, ctx->stream);
+    uint32_t* sorted = nullptr;
+    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, M, &sorted, sa.tmp, sa.tmp_bytes,
+                        ctx->stream);
+    CK_LAUNCH();
+    launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), sorted, sx, sz, sc, k, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_get_stats(const iqcc_ctx* ctx, iqcc_stats* out) {
+    if (!ctx || !out) return fail(nullptr, IQCC_ERR_ARG, "null argument");
+    *out = ctx->stats;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_reset_stats(iqcc_ctx* ctx) {
+    if (!ctx) return fail(nullptr, IQCC_ERR_ARG, "null context");
+    iqcc_stats s{};
+    s.rows_allocated = ctx->rows_alloc;
+    s.hash_slots = (int64_t)ctx->hash_slots;
+    s.words = ctx->Wd;
+    ctx->stats = s;
+    return IQCC_OK;
+}
+
+const char* iqcc_last_error(const iqcc_ctx* ctx) {
+    if (!ctx) return g_last_error.c_str();
+    return ctx->err.empty() ? "no error" : ctx->err.c_str();
+}
+
+void iqcc_free(iqcc_ctx* ctx) {
+    if (!ctx) return;
+    cudaStreamSynchronize(ctx->stream);
+    for (int b = 0; b < 2; ++b) {
+        release(ctx, ctx->keys[b]);
+        release(ctx, ctx->coef[b]);
+    }
+    release(ctx, ctx->hash);
+    release(ctx, ctx->counters);
+    release(ctx, ctx->scratch);
+    if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    cudaGetLastError();
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Internal declarations of libiqcc: device key helpers, the context, and the
+// host-side launchers of every kernel.  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/iqcc.h"
+
+namespace iqcc {
+
+// ----------------------------------------------------------------------------
+// Keys on the device: a row is x[Wd] then z[Wd] (Wd = 1, 2 or 4 words, padded
+// with zeros above the input's W), 16*Wd bytes, 16-byte aligned.
+// ----------------------------------------------------------------------------
+
+constexpr uint64_t kEmptySlot = ~0ull;        // hash slot never used
+constexpr uint32_t kPendingGroup = 0xFFFFFFFEu;  // group slot claimed, key not yet published
+constexpr int kBucketSlots = 4;               // 4 x 8-byte slots = one 32-byte sector
+
+template <int W>
+struct Key {
+    uint64_t x[W];
+    uint64_t z[W];
+};
+
+template <int W>
+__device__ __forceinline__ Key<W> load_key(const uint64_t* __restrict__ rows, int64_t i) {
+    Key<W> k;
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(rows + (size_t)i * 2 * W);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        ulonglong2 v = __ldg(p + j);
+        uint64_t a = v.x, b = v.y;
+        // words 2j and 2j+1 of the row
+        int w0 = 2 * j, w1 = 2 * j + 1;
+        if (w0 < W) k.x[w0] = a; else k.z[w0 - W] = a;
+        if (w1 < W) k.x[w1] = b; else k.z[w1 - W] = b;
+    }
+    return k;
+}
+
+template <>
+__device__ __forceinline__ Key<1> load_key<1>(const uint64_t* __restrict__ rows, int64_t i) {
+    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(rows) + i);
+    Key<1> k;
+    k.x[0] = v.x;
+    k.z[0] = v.y;
+    return k;
+}
+
+template <int W>
+__device__ __forceinline__ void store_key(uint64_t* rows, int64_t i, const Key<W>& k) {
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(rows + (size_t)i * 2 * W);
+    uint64_t w[2 * W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) { w[j] = k.x[j]; w[W + j] = k.z[j]; }
+#pragma unroll
+    for (int j = 0; j < W; ++j) p[j] = make_ulonglong2(w[2 * j], w[2 * j + 1]);
+}
+
+template <int W>
+__device__ __forceinline__ bool key_equal(const Key<W>& a, const Key<W>& b) {
+    uint64_t d = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) d |= (a.x[j] ^ b.x[j]) | (a.z[j] ^ b.z[j]);
+    return d == 0;
+}
+
+template <int W>
+__device__ __forceinline__ Key<W> key_xor(const Key<W>& a, const Key<W>& b) {
+    Key<W> r;
+#pragma unroll
+    for (int j = 0; j < W; ++j) { r.x[j] = a.x[j] ^ b.x[j]; r.z[j] = a.z[j] ^ b.z[j]; }
+    return r;
+}
+
+template <int W>
+__device__ __forceinline__ int popc_and(const uint64_t* a, const uint64_t* b) {
+    int s = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) s += __popcll(a[j] & b[j]);
+    return s;
+}
+
+// Symplectic form: 1 when P(a) and P(b) anticommute.
+template <int W>
+__device__ __forceinline__ int anticommutes(const Key<W>& a, const Key<W>& b) {
+    uint64_t v = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) v ^= (a.x[j] & b.z[j]) ^ (a.z[j] & b.x[j]);
+    return __popcll(v) & 1;
+}
+
+// For anticommuting Hermitian strings T and P with Q = T xor P:
+//   i T P = s Q, s = +1 when e = 3 and -1 when e = 1, where
+//   e = popc(xT&zT) + popc(xP&zP) + 2 popc(zT&xP) - popc(xQ&zQ)  (mod 4).
+// (From P(x,z) = i^{popc(x&z)} X^x Z^z and Z^a X^b = (-1)^{popc(a&b)} X^b Z^a.)
+template <int W>
+__device__ __forceinline__ int product_sign(const Key<W>& t, int yP, const Key<W>& p, const Key<W>& q) {
+    int e = popc_and<W>(t.x, t.z) + yP + 2 * popc_and<W>(t.z, p.x) - popc_and<W>(q.x, q.z);
+    return ((e & 3) == 3) ? 1 : -1;
+}
+
+// Key hash: a multiply-xorshift chain over the 2W words, finished with the
+// 64-bit fmix of MurmurHash3.  Low bits pick the bucket, high 32 bits are the
+// fingerprint kept in the slot.
+template <int W>
+__device__ __forceinline__ uint64_t hash_key(const Key<W>& k) {
+    uint64_t h = 0x9E3779B97F4A7C15ull;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        h = (h ^ k.x[j]) * 0xBF58476D1CE4E5B9ull;
+        h ^= h >> 31;
+        h = (h ^ k.z[j]) * 0x94D049BB133111EBull;
+        h ^= h >> 29;
+    }
+    h ^= h >> 33;
+    h *= 0xFF51AFD7ED558CCDull;
+    h ^= h >> 33;
+    h *= 0xC4CEB9FE1A85EC53ull;
+    h ^= h >> 33;
+    return h;
+}
+
+// Device-side counters shared by the kernels of one call.
+struct DevCounters {
+    unsigned long long n_new;      // rows appended by a dress
+    unsigned long long n_anti;     // anticommuting rows seen by a dress
+    unsigned long long n_groups;   // DIS groups / compaction output
+    unsigned long long aux;        // scratch counter
+    int err;                       // iqcc_status set by a kernel (first error wins)
+    int err_where;                 // which kernel
+};
+
+// Hash table view.
+struct HashView {
+    uint64_t* slots;
+    uint64_t bucket_mask;  // number of buckets - 1 (buckets are 4 slots)
+    int max_probe;
+};
+
+// Generator of one dress / A,B,C pass.
+template <int W>
+struct Gen {
+    Key<W> p;
+    int yP;          // popc(xP & zP) mod 4
+    int top_word;    // word index (0..2W-1, x words first) of P's highest set bit
+    uint64_t top_mask;
+    double cos_t, sin_t;
+};
+
+// ----------------------------------------------------------------------------
+// Context
+// ----------------------------------------------------------------------------
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace iqcc
+
+struct iqcc_ctx {
+    int n = 0;            // qubits
+    int W = 0;            // host words per x / z vector
+    int Wd = 0;           // device words (1, 2, 4)
+    int64_t capacity = 0; // admission limit (rows)
+    int max_probe = 64;
+    cudaStream_t stream = nullptr;
+    void* (*alloc)(size_t, void*) = nullptr;
+    void (*dfree)(void*, void*) = nullptr;
+    void* alloc_user = nullptr;
+
+    int64_t M = 0;                 // live rows
+    int64_t rows_alloc = 0;        // rows allocated in each key/coef buffer
+    int cur = 0;                   // current buffer (0/1)
+    iqcc::Buf keys[2], coef[2];
+    iqcc::Buf hash;                // slots
+    uint64_t hash_slots = 0;       // active slots (power of two)
+    iqcc::Buf counters;            // DevCounters
+    iqcc::DevCounters* h_counters = nullptr;  // pinned host mirror
+    iqcc::Buf scratch;             // general scratch (grows)
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+    bool broken = false;
+    std::string err;
+    iqcc_stats stats{};
+
+    uint64_t* rows() const { return (uint64_t*)keys[cur].p; }
+    double* c() const { return (double*)coef[cur].p; }
+    uint64_t* rows_alt() const { return (uint64_t*)keys[cur ^ 1].p; }
+    double* c_alt() const { return (double*)coef[cur ^ 1].p; }
+};
+
+namespace iqcc {
+
+// ----------------------------------------------------------------------------
+// Host launchers (defined in the k_*.cu files).  All run on ctx->stream.
+// ----------------------------------------------------------------------------
+
+int device_words(int n);
+int sm_count();
+
+// k_hash.cu / k_dress.cu
+void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
+void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
+                        DevCounters* ctr, cudaStream_t s);
+void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
+                  const uint64_t* pkey, double cos_t, double sin_t, HashView h, DevCounters* ctr,
+                  cudaStream_t s);
+void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,
+                        DevCounters* ctr, cudaStream_t s);
+
+// k_expect.cu
+int expect_blocks();
+// Fills partials[block][3] with (A, B, C) sums; pkey may be all-zero (energy).
+void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,
+                bool basis, const uint64_t* occ, const double* tables, int n_groups, double* partials,
+                cudaStream_t s);
+void launch_reduce3(const double* partials, int n, double* out3, cudaStream_t s);
+void launch_qmf_tables(const double* theta, const double* phi, int n, int n_groups, double* tables,
+                       cudaStream_t s);
+// DIS basis path: group by x, sum signed contributions.
+void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ,
+                      bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe,
+                      uint64_t* gkeys, double* gsum, DevCounters* ctr, cudaStream_t s);
+// General-angle gradients of K candidates: partials[block][K].
+void launch_grad_general(int Wd, const uint64_t* rows, const double* coef, int64_t M,
+                         const uint64_t* cand, int K, const double* tables, int n_groups,
+                         double* partials, int n_blocks, cudaStream_t s);
+void launch_reduce_cols(const double* partials, int rows, int cols, double* out, cudaStream_t s);
+
+// k_sort.cu
+struct SortPlan {
+    int n_words;          // key words per element (stride in the key array)
+    int order[9];         // word indices from most to least significant
+    int n_order;
+};
+// Indirect stable LSD radix sort of perm[0..n) by keys[perm[i]*stride + order[..]].
+// perm_alt is scratch of the same size; the result ends in *result (one of the two).
+void radix_sort_indirect(const uint64_t* keys, int stride, const SortPlan& plan, uint32_t* perm,
+                         uint32_t* perm_alt, int64_t n, uint32_t** result, void* scratch,
+                         size_t scratch_bytes, cudaStream_t s);
+size_t radix_sort_scratch_bytes(int64_t n);
+void launch_iota(uint32_t* p, int64_t n, cudaStream_t s);
+
+// compaction: out[rank] = in[i] for flags[i] != 0 (stable); count to *ctr_count (device).
+size_t compact_scratch_bytes(int64_t n);
+void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, const double* c_in,
+                         uint64_t* rows_out, double* c_out, int64_t n, void* scratch,
+                         unsigned long long* count, cudaStream_t s);
+
+// load: pack host-layout x/z into rows, sum runs after the sort
+void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n,
+                      cudaStream_t s);
+void launch_unpack_rows(int W, int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
+                        uint64_t* x, uint64_t* z, double* c, int64_t n, cudaStream_t s);
+void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,
+                     uint8_t* flags, uint64_t* rows_out_gather, double* c_out_gather, cudaStream_t s);
+void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
+                        int64_t n, uint64_t* rows_out, double* c_out, cudaStream_t s);
+
+// prune
+void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags,
+                        unsigned long long* count, cudaStream_t s);
+// histogram of one 8-bit digit of |c| bits among kept rows whose higher digits equal prefix
+void launch_abs_digit_hist(const double* coef, const uint8_t* flags, int64_t n, int shift,
+                           uint64_t prefix, uint64_t prefix_mask, unsigned long long* hist,
+                           cudaStream_t s);
+// flags: 1 if |c| bits > t; ties (== t) are listed into tie_idx (count in *tie_count)
+void launch_budget_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t t_bits,
+                         uint32_t* tie_idx, unsigned long long* tie_count, cudaStream_t s);
+void launch_set_flags(const uint32_t* idx, int64_t k, uint8_t* flags, cudaStream_t s);
+
+// DIS candidate keys for the sort: [coarse |g| complement, x words...]
+void launch_dis_sort_keys(int Wd, const uint64_t* gkeys, const double* gsum, int64_t G, uint64_t* skeys,
+                          cudaStream_t s);
+void launch_dis_export(int W, int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* perm,
+                       int64_t k, uint64_t* ox, uint64_t* oz, double* og, cudaStream_t s);
+
+}  // namespace iqcc

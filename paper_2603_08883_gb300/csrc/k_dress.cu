@@ -1,0 +1,265 @@
+// Dressing of the resident Hamiltonian by one generator (Eq. 5 in the
+// library convention, Eq. 6) and the open-addressing index it relies on.
+//
+// Index: 2^k buckets of 4 eight-byte slots (one 32-byte sector); a slot holds
+// (fingerprint32 << 32) | row32, ~0 when empty.  Rows are never deleted from
+// the index; compression rebuilds it.  Lookups stop at the first empty slot.
+//
+// Dress: one streaming pass over the M rows.  For a row T that anticommutes
+// with P (popcount parity of (xT & zP) ^ (zT & xP)), its partner Q = T xor P is
+// looked up.  Exactly one member of each present pair - the one with a zero at
+// P's lowest set bit - rotates both coefficients; a row whose partner is
+// absent scales itself by cos(tau) and appends (Q, s sin(tau) C_T) behind the
+// M input rows.  q -> q xor P is a bijection, so appended keys are distinct and
+// absent from H: no duplicate merge is needed within one generator (the
+// "insert if unique, else add" merge of App. D, Eq. 18, done as a lookup).
+#include <cuda_runtime.h>
+
+#include "iqcc_internal.cuh"
+
+namespace iqcc {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+__device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where) {
+    if (atomicCAS(&ctr->err, 0, code) == 0) ctr->err_where = where;
+}
+
+// Row index of key q in the index, -1 when absent, -2 when the probe bound
+// was reached.  Read-only use of the table (no inserts run concurrently).
+template <int W>
+__device__ __forceinline__ int64_t lookup(const Key<W>& q, const HashView& h,
+                                          const uint64_t* __restrict__ rows) {
+    uint64_t hv = hash_key<W>(q);
+    uint32_t fp = (uint32_t)(hv >> 32);
+    uint64_t b = hv & h.bucket_mask;
+    for (int p = 0; p < h.max_probe; ++p) {
+        const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
+        ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
+        uint64_t sl[4] = {s01.x, s01.y, s23.x, s23.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sl[k] == kEmptySlot) return -1;
+            if ((uint32_t)(sl[k] >> 32) == fp) {
+                uint32_t idx = (uint32_t)sl[k];
+                Key<W> r = load_key<W>(rows, idx);
+                if (key_equal<W>(r, q)) return (int64_t)idx;
+            }
+        }
+        b = (b + 1) & h.bucket_mask;
+    }
+    return -2;
+}
+
+template <int W>
+__device__ __forceinline__ bool insert(const Key<W>& k, uint32_t row, const HashView& h) {
+    uint64_t hv = hash_key<W>(k);
+    uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)row;
+    uint64_t b = hv & h.bucket_mask;
+    for (int p = 0; p < h.max_probe; ++p) {
+        unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) {
+            if (s[k2] == kEmptySlot &&
+                atomicCAS(s + k2, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot)
+                return true;
+        }
+        b = (b + 1) & h.bucket_mask;
+    }
+    return false;
+}
+
+template <int W>
+__device__ __forceinline__ bool bit_of(const Key<W>& k, int word, uint64_t mask) {
+    uint64_t v = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        if (word == j) v = k.x[j];
+        if (word == W + j) v = k.z[j];
+    }
+    return (v & mask) != 0;
+}
+
+__global__ void k_hash_clear(uint64_t* slots, uint64_t n) {
+    uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(slots);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n / 2; i += stride)
+        p[i] = make_ulonglong2(kEmptySlot, kEmptySlot);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_hash_insert(const uint64_t* __restrict__ rows, int64_t lo,
+                                                          int64_t hi, HashView h, DevCounters* ctr) {
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += stride) {
+        Key<W> k = load_key<W>(rows, i);
+        if (!insert<W>(k, (uint32_t)i, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
+    }
+}
+
+// One pass of Eq. 5 over rows [0, M).  rows_app is the same buffer as rows;
+// appended rows land at M + slot and are not visited by this pass.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_dress(const uint64_t* __restrict__ rows, uint64_t* rows_app,
+                                                    double* coef, int64_t M, Gen<W> g, HashView h,
+                                                    DevCounters* ctr) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned n_anti = 0;
+    for (int64_t base = warp * 32; base < M; base += n_warps * 32) {
+        const int64_t i = base + lane;
+        bool append = false;
+        Key<W> q;
+        double c_new = 0.0;
+        if (i < M) {
+            Key<W> t = load_key<W>(rows, i);
+            if (anticommutes<W>(t, g.p)) {
+                ++n_anti;
+                q = key_xor<W>(t, g.p);
+                const double s = (double)product_sign<W>(t, g.yP, g.p, q);
+                const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
+                const int64_t j = lookup<W>(q, h, rows);
+                if (j == -1) {
+                    const double c = coef[i];
+                    coef[i] = c * g.cos_t;
+                    c_new = s * c * g.sin_t;
+                    append = true;
+                } else if (j >= 0) {
+                    if (!upper) {
+                        const double ct = coef[i], cq = coef[j];
+                        coef[i] = ct * g.cos_t - s * cq * g.sin_t;
+                        coef[j] = cq * g.cos_t + s * ct * g.sin_t;
+                    }
+                } else {
+                    set_error(ctr, IQCC_ERR_HASH_FULL, 2);
+                }
+            }
+        }
+        const unsigned need = __ballot_sync(FULL, append);
+        if (need) {
+            const int leader = __ffs(need) - 1;
+            unsigned long long slot0 = 0;
+            if (lane == leader) slot0 = atomicAdd(&ctr->n_new, (unsigned long long)__popc(need));
+            slot0 = __shfl_sync(FULL, slot0, leader);
+            if (append) {
+                const int64_t r = M + (int64_t)slot0 + __popc(need & ((1u << lane) - 1u));
+                store_key<W>(rows_app, r, q);
+                coef[r] = c_new;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(FULL, n_anti, o);
+    if (lane == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
+}
+
+// Admission count: how many partners a dress would append (no writes to H).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_dress_count(const uint64_t* __restrict__ rows, int64_t M,
+                                                          Gen<W> g, HashView h, DevCounters* ctr) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    unsigned cnt = 0;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        Key<W> t = load_key<W>(rows, i);
+        if (anticommutes<W>(t, g.p)) {
+            Key<W> q = key_xor<W>(t, g.p);
+            int64_t j = lookup<W>(q, h, rows);
+            if (j == -1) ++cnt;
+            else if (j == -2) set_error(ctr, IQCC_ERR_HASH_FULL, 3);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(FULL, cnt, o);
+    if (lane == 0 && cnt) atomicAdd(&ctr->n_new, (unsigned long long)cnt);
+}
+
+template <int W>
+Gen<W> make_gen(const uint64_t* pkey, double cos_t, double sin_t) {
+    Gen<W> g{};
+    int y = 0;
+    g.top_word = -1;
+    for (int j = 0; j < W; ++j) {
+        g.p.x[j] = pkey[j];
+        g.p.z[j] = pkey[W + j];
+        y += __builtin_popcountll(pkey[j] & pkey[W + j]);
+    }
+    for (int w = 0; w < 2 * W && g.top_word < 0; ++w)
+        if (pkey[w]) { g.top_word = w; g.top_mask = pkey[w] & (~pkey[w] + 1); }
+    if (g.top_word < 0) { g.top_word = 0; g.top_mask = 0; }
+    g.yP = y & 3;
+    g.cos_t = cos_t;
+    g.sin_t = sin_t;
+    return g;
+}
+
+int grid_for(int64_t n, int per_sm) {
+    int64_t want = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)sm_count() * per_sm;
+    if (want > cap) want = cap;
+    return (int)(want < 1 ? 1 : want);
+}
+
+}  // namespace
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+int device_words(int n) { return n <= 64 ? 1 : (n <= 128 ? 2 : 4); }
+
+void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s) {
+    int grid = (int)((slots / 2 + kThreads - 1) / kThreads);
+    int cap = sm_count() * 8;
+    if (grid > cap) grid = cap;
+    if (grid < 1) grid = 1;
+    k_hash_clear<<<grid, kThreads, 0, s>>>(h.slots, slots);
+}
+
+void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
+                        DevCounters* ctr, cudaStream_t s) {
+    if (hi <= lo) return;
+    int grid = grid_for(hi - lo, 8);
+    switch (Wd) {
+        case 1: k_hash_insert<1><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); break;
+        case 2: k_hash_insert<2><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); break;
+        default: k_hash_insert<4><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); break;
+    }
+}
+
+void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
+                  const uint64_t* pkey, double cos_t, double sin_t, HashView h, DevCounters* ctr,
+                  cudaStream_t s) {
+    if (M <= 0) return;
+    int grid = grid_for(M, 8);
+    switch (Wd) {
+        case 1: k_dress<1><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<1>(pkey, cos_t, sin_t), h, ctr); break;
+        case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr); break;
+        default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr); break;
+    }
+}
+
+void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,
+                        DevCounters* ctr, cudaStream_t s) {
+    if (M <= 0) return;
+    int grid = grid_for(M, 8);
+    switch (Wd) {
+        case 1: k_dress_count<1><<<grid, kThreads, 0, s>>>(rows, M, make_gen<1>(pkey, 1, 0), h, ctr); break;
+        case 2: k_dress_count<2><<<grid, kThreads, 0, s>>>(rows, M, make_gen<2>(pkey, 1, 0), h, ctr); break;
+        default: k_dress_count<4><<<grid, kThreads, 0, s>>>(rows, M, make_gen<4>(pkey, 1, 0), h, ctr); break;
+    }
+}
+
+}  // namespace iqcc

@@ -1,0 +1,469 @@
+// Reordering kernels: indirect stable LSD radix sort on multi-word keys,
+// stable stream compaction, load-time canonicalisation (sort + segmented sum
+// of repeated keys, Eq. 2), export in canonical order, compression flags
+// (magnitude threshold and term budget by radix select on the |C| bit
+// pattern), and the DIS candidate ordering.
+#include <cuda_runtime.h>
+
+#include "iqcc_internal.cuh"
+
+namespace iqcc {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = 16;
+constexpr int kTile = kThreads * kItems;  // elements per block in sort / compaction
+
+int64_t n_tiles(int64_t n) { return (n + kTile - 1) / kTile; }
+
+// ---------------------------------------------------------------- radix sort
+
+__global__ void k_word_orand(const uint64_t* __restrict__ keys, int stride, const uint32_t* __restrict__ perm,
+                             int64_t n, unsigned long long* orand /* [2*stride] */) {
+    // per-word OR and AND over the listed elements (to skip constant digits)
+    extern __shared__ unsigned long long sh[];
+    for (int w = threadIdx.x; w < 2 * stride; w += blockDim.x) sh[w] = (w < stride) ? 0ull : ~0ull;
+    __syncthreads();
+    unsigned long long o[9], a[9];
+    for (int w = 0; w < stride; ++w) { o[w] = 0ull; a[w] = ~0ull; }
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const uint64_t* k = keys + (size_t)perm[i] * stride;
+        for (int w = 0; w < stride; ++w) { o[w] |= k[w]; a[w] &= k[w]; }
+    }
+    for (int w = 0; w < stride; ++w) {
+        atomicOr(sh + w, o[w]);
+        atomicAnd(sh + stride + w, a[w]);
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < 2 * stride; w += blockDim.x) {
+        if (w < stride) atomicOr(orand + w, sh[w]);
+        else atomicAnd(orand + w, sh[w]);
+    }
+}
+
+__global__ void k_sort_hist(const uint64_t* __restrict__ keys, int stride, int word, int shift,
+                            const uint32_t* __restrict__ perm, int64_t n, uint32_t* hist, int64_t nblocks) {
+    __shared__ uint32_t h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        if (i < n) {
+            uint32_t d = (uint32_t)(keys[(size_t)perm[i] * stride + word] >> shift) & 255u;
+            atomicAdd(&h[d], 1u);
+        }
+    }
+    __syncthreads();
+    hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Exclusive scan of a u32 array in place by one block (n up to a few million).
+__global__ void k_scan_u32(uint32_t* data, int64_t n) {
+    __shared__ uint32_t sums[1024];
+    const int T = blockDim.x;
+    const int64_t chunk = (n + T - 1) / T;
+    const int64_t lo = threadIdx.x * chunk, hi = min(n, lo + chunk);
+    uint32_t s = 0;
+    for (int64_t i = lo; i < hi; ++i) s += data[i];
+    sums[threadIdx.x] = s;
+    __syncthreads();
+    for (int off = 1; off < T; off <<= 1) {
+        uint32_t v = threadIdx.x >= off ? sums[threadIdx.x - off] : 0u;
+        __syncthreads();
+        sums[threadIdx.x] += v;
+        __syncthreads();
+    }
+    uint32_t run = threadIdx.x ? sums[threadIdx.x - 1] : 0u;
+    for (int64_t i = lo; i < hi; ++i) {
+        uint32_t v = data[i];
+        data[i] = run;
+        run += v;
+    }
+}
+
+// Stable scatter of one digit: rounds of 256 elements in index order; within a
+// round warps in order and lanes in order (match_any gives the same-digit peers).
+__global__ void k_sort_scatter(const uint64_t* __restrict__ keys, int stride, int word, int shift,
+                               const uint32_t* __restrict__ perm_in, uint32_t* perm_out, int64_t n,
+                               const uint32_t* __restrict__ offsets, int64_t nblocks) {
+    __shared__ uint32_t s_off[256];
+    __shared__ uint32_t s_cnt[kThreads / 32][256];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    s_off[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+        for (int w = 0; w < kThreads / 32; ++w) s_cnt[w][threadIdx.x] = 0;
+        __syncthreads();
+        const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        const bool valid = i < n;
+        uint32_t src = 0, d = 256;
+        if (valid) {
+            src = perm_in[i];
+            d = (uint32_t)(keys[(size_t)src * stride + word] >> shift) & 255u;
+        }
+        const unsigned peers = __match_any_sync(0xFFFFFFFFu, d);
+        const int rank = __popc(peers & ((1u << lane) - 1u));
+        if (valid && rank == 0) s_cnt[wid][d] = __popc(peers);
+        __syncthreads();
+        if (valid) {
+            uint32_t pos = s_off[d] + rank;
+            for (int w = 0; w < wid; ++w) pos += s_cnt[w][d];
+            perm_out[pos] = src;
+        }
+        __syncthreads();
+        uint32_t tot = 0;
+        for (int w = 0; w < kThreads / 32; ++w) tot += s_cnt[w][threadIdx.x];
+        s_off[threadIdx.x] += tot;
+        __syncthreads();
+    }
+}
+
+__global__ void k_iota(uint32_t* p, int64_t n) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) p[i] = (uint32_t)i;
+}
+
+// ---------------------------------------------------------------- compaction
+
+__global__ void k_flag_count(const uint8_t* __restrict__ flags, int64_t n, uint32_t* counts) {
+    __shared__ uint32_t s;
+    if (threadIdx.x == 0) s = 0;
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    uint32_t c = 0;
+    for (int r = 0; r < kItems; ++r) {
+        int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        if (i < n && flags[i]) ++c;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&s, c);
+    __syncthreads();
+    if (threadIdx.x == 0) counts[blockIdx.x] = s;
+}
+
+__global__ void k_total(const uint32_t* scanned, const uint32_t* counts_last, int64_t nb,
+                        unsigned long long* total) {
+    *total = (unsigned long long)scanned[nb - 1] + (unsigned long long)*counts_last;
+}
+
+template <int W>
+__global__ void k_compact_scatter(const uint8_t* __restrict__ flags, const uint64_t* __restrict__ rows_in,
+                                  const double* __restrict__ c_in, uint64_t* rows_out, double* c_out, int64_t n,
+                                  const uint32_t* __restrict__ offsets) {
+    __shared__ uint32_t s_w[kThreads / 32];
+    __shared__ uint32_t s_base;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) s_base = offsets[blockIdx.x];
+    __syncthreads();
+    const int64_t base = (int64_t)blockIdx.x * kTile;
+    for (int r = 0; r < kItems; ++r) {
+        const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        const bool f = i < n && flags[i];
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
+        if (lane == 0) s_w[wid] = __popc(b);
+        __syncthreads();
+        uint32_t pos = s_base + __popc(b & ((1u << lane) - 1u));
+        for (int w = 0; w < wid; ++w) pos += s_w[w];
+        if (f) {
+            Key<W> k = load_key<W>(rows_in, i);
+            store_key<W>(rows_out, pos, k);
+            c_out[pos] = c_in[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t t = 0;
+            for (int w = 0; w < kThreads / 32; ++w) t += s_w[w];
+            s_base += t;
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------- load / export
+
+__global__ void k_pack_rows(int W, int Wd, const uint64_t* __restrict__ x, const uint64_t* __restrict__ z,
+                            uint64_t* rows, int64_t n) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        for (int w = 0; w < Wd; ++w) {
+            rows[(size_t)i * 2 * Wd + w] = w < W ? x[(size_t)i * W + w] : 0ull;
+            rows[(size_t)i * 2 * Wd + Wd + w] = w < W ? z[(size_t)i * W + w] : 0ull;
+        }
+    }
+}
+
+__global__ void k_unpack_rows(int W, int Wd, const uint64_t* __restrict__ rows, const double* __restrict__ coef,
+                              const uint32_t* __restrict__ perm, uint64_t* x, uint64_t* z, double* c, int64_t n) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const uint32_t r = perm ? perm[i] : (uint32_t)i;
+        for (int w = 0; w < W; ++w) {
+            x[(size_t)i * W + w] = rows[(size_t)r * 2 * Wd + w];
+            z[(size_t)i * W + w] = rows[(size_t)r * 2 * Wd + Wd + w];
+        }
+        c[i] = coef[r];
+    }
+}
+
+template <int W>
+__device__ __forceinline__ bool same_key_rows(const uint64_t* rows, uint32_t a, uint32_t b) {
+    Key<W> ka = load_key<W>(rows, a), kb = load_key<W>(rows, b);
+    return key_equal<W>(ka, kb);
+}
+
+// After the sort: position i starts a run when its key differs from position
+// i-1.  The run head sums the run in sorted (= stable input) order and writes
+// the key and sum to position i of the gathered output; flags[i] = sum != 0.
+template <int W>
+__global__ void k_sum_runs(const uint64_t* __restrict__ rows, const double* __restrict__ coef,
+                           const uint32_t* __restrict__ perm, int64_t n, uint8_t* flags, uint64_t* rows_out,
+                           double* c_out) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const uint32_t r = perm[i];
+        const bool head = (i == 0) || !same_key_rows<W>(rows, perm[i - 1], r);
+        if (!head) { flags[i] = 0; continue; }
+        double sum = coef[r];
+        for (int64_t j = i + 1; j < n && same_key_rows<W>(rows, perm[j], r); ++j) sum += coef[perm[j]];
+        Key<W> k = load_key<W>(rows, r);
+        store_key<W>(rows_out, i, k);
+        c_out[i] = sum;
+        flags[i] = (sum != 0.0);
+    }
+}
+
+template <int W>
+__global__ void k_gather_rows(const uint64_t* __restrict__ rows, const double* __restrict__ coef,
+                              const uint32_t* __restrict__ perm, int64_t n, uint64_t* rows_out, double* c_out) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const uint32_t r = perm[i];
+        store_key<W>(rows_out, i, load_key<W>(rows, r));
+        c_out[i] = coef[r];
+    }
+}
+
+// ---------------------------------------------------------------- compression
+
+__device__ __forceinline__ uint64_t abs_bits(double c) {
+    return (uint64_t)__double_as_longlong(c) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+__global__ void k_prune_flags(const double* __restrict__ coef, int64_t n, double eps, uint8_t* flags,
+                              unsigned long long* count) {
+    unsigned c = 0;
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const bool keep = !(fabs(coef[i]) < eps);
+        flags[i] = keep;
+        c += keep;
+    }
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+__global__ void k_abs_digit_hist(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
+                                 int shift, uint64_t prefix, uint64_t prefix_mask, unsigned long long* hist) {
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        if (!flags[i]) continue;
+        const uint64_t b = abs_bits(coef[i]);
+        if ((b & prefix_mask) != prefix) continue;
+        atomicAdd(&h[(b >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
+__global__ void k_budget_flags(const double* __restrict__ coef, uint8_t* flags, int64_t n, uint64_t t,
+                               uint32_t* tie_idx, unsigned long long* tie_count) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        if (!flags[i]) continue;
+        const uint64_t b = abs_bits(coef[i]);
+        if (b > t) continue;
+        flags[i] = 0;
+        if (b == t) tie_idx[atomicAdd(tie_count, 1ull)] = (uint32_t)i;
+    }
+}
+
+__global__ void k_set_flags(const uint32_t* __restrict__ idx, int64_t k, uint8_t* flags) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) flags[idx[i]] = 1;
+}
+
+// ---------------------------------------------------------------- DIS ordering
+
+// skeys[g] = [~coarse(|g|), x[Wd-1], ..., x[0]]: ascending order of these words
+// is |g| (20 low mantissa bits cleared) descending, then x ascending.
+__global__ void k_dis_sort_keys(int Wd, const uint64_t* __restrict__ gkeys, const double* __restrict__ gsum,
+                                int64_t G, uint64_t* skeys) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += s) {
+        uint64_t a = abs_bits(gsum[g]) & ~((1ull << 20) - 1ull);
+        skeys[(size_t)g * (Wd + 1)] = ~a;
+        for (int w = 0; w < Wd; ++w) skeys[(size_t)g * (Wd + 1) + 1 + w] = gkeys[(size_t)g * Wd + (Wd - 1 - w)];
+    }
+}
+
+__global__ void k_dis_export(int W, int Wd, const uint64_t* __restrict__ gkeys, const double* __restrict__ gsum,
+                             const uint32_t* __restrict__ perm, int64_t k, uint64_t* ox, uint64_t* oz, double* og) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) {
+        const uint32_t g = perm[i];
+        bool found = false;
+        for (int w = 0; w < W; ++w) {
+            const uint64_t x = gkeys[(size_t)g * Wd + w];
+            ox[(size_t)i * W + w] = x;
+            oz[(size_t)i * W + w] = found ? 0ull : (x & (~x + 1ull));
+            found |= (x != 0);
+        }
+        og[i] = gsum[g];
+    }
+}
+
+int grid_stride_blocks(int64_t n) {
+    int64_t want = (n + kThreads - 1) / kThreads;
+    int64_t cap = (int64_t)sm_count() * 8;
+    if (want > cap) want = cap;
+    return (int)(want < 1 ? 1 : want);
+}
+
+}  // namespace
+
+size_t radix_sort_scratch_bytes(int64_t n) {
+    // hist [256][nblocks] + orand
+    return (size_t)256 * (size_t)n_tiles(n) * sizeof(uint32_t) + 32 * sizeof(unsigned long long) + 256;
+}
+
+void launch_iota(uint32_t* p, int64_t n, cudaStream_t s) {
+    if (n > 0) k_iota<<<grid_stride_blocks(n), kThreads, 0, s>>>(p, n);
+}
+
+void radix_sort_indirect(const uint64_t* keys, int stride, const SortPlan& plan, uint32_t* perm,
+                         uint32_t* perm_alt, int64_t n, uint32_t** result, void* scratch, size_t scratch_bytes,
+                         cudaStream_t s) {
+    *result = perm;
+    if (n <= 1) return;
+    const int64_t nb = n_tiles(n);
+    uint32_t* hist = (uint32_t*)scratch;
+    unsigned long long* orand =
+        (unsigned long long*)((char*)scratch + (((size_t)256 * nb * sizeof(uint32_t) + 255) & ~(size_t)255));
+    (void)scratch_bytes;
+    // constant digits are skipped: OR and AND of each word over all elements
+    unsigned long long init[18];
+    for (int w = 0; w < stride; ++w) { init[w] = 0ull; init[stride + w] = ~0ull; }
+    cudaMemcpyAsync(orand, init, sizeof(unsigned long long) * 2 * stride, cudaMemcpyHostToDevice, s);
+    k_word_orand<<<grid_stride_blocks(n), kThreads, 2 * stride * sizeof(unsigned long long), s>>>(keys, stride, perm,
+                                                                                                 n, orand);
+    unsigned long long host_orand[18];
+    cudaMemcpyAsync(host_orand, orand, sizeof(unsigned long long) * 2 * stride, cudaMemcpyDeviceToHost, s);
+    cudaStreamSynchronize(s);
+    uint32_t* a = perm;
+    uint32_t* b = perm_alt;
+    for (int oi = plan.n_order - 1; oi >= 0; --oi) {
+        const int word = plan.order[oi];
+        const uint64_t varying = host_orand[word] ^ host_orand[stride + word];
+        for (int shift = 0; shift < 64; shift += 8) {
+            if (((varying >> shift) & 255ull) == 0) continue;
+            k_sort_hist<<<(unsigned)nb, kThreads, 0, s>>>(keys, stride, word, shift, a, n, hist, nb);
+            k_scan_u32<<<1, 1024, 0, s>>>(hist, 256 * nb);
+            k_sort_scatter<<<(unsigned)nb, kThreads, 0, s>>>(keys, stride, word, shift, a, b, n, hist, nb);
+            uint32_t* t = a; a = b; b = t;
+        }
+    }
+    *result = a;
+}
+
+size_t compact_scratch_bytes(int64_t n) { return (size_t)n_tiles(n) * 2 * sizeof(uint32_t) + 512; }
+
+void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, const double* c_in,
+                         uint64_t* rows_out, double* c_out, int64_t n, void* scratch, unsigned long long* count,
+                         cudaStream_t s) {
+    if (n <= 0) {
+        cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+        return;
+    }
+    const int64_t nb = n_tiles(n);
+    uint32_t* counts = (uint32_t*)scratch;
+    uint32_t* offsets = counts + nb;
+    k_flag_count<<<(unsigned)nb, kThreads, 0, s>>>(flags, n, counts);
+    cudaMemcpyAsync(offsets, counts, nb * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
+    k_scan_u32<<<1, 1024, 0, s>>>(offsets, nb);
+    k_total<<<1, 1, 0, s>>>(offsets, counts + nb - 1, nb, count);
+    switch (Wd) {
+        case 1: k_compact_scatter<1><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); break;
+        case 2: k_compact_scatter<2><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); break;
+        default: k_compact_scatter<4><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); break;
+    }
+}
+
+void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n,
+                      cudaStream_t s) {
+    if (n > 0) k_pack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, x, z, rows, n);
+}
+
+void launch_unpack_rows(int W, int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
+                        uint64_t* x, uint64_t* z, double* c, int64_t n, cudaStream_t s) {
+    if (n > 0) k_unpack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, rows, coef, perm, x, z, c, n);
+}
+
+void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,
+                     uint8_t* flags, uint64_t* rows_out, double* c_out, cudaStream_t s) {
+    if (n <= 0) return;
+    int g = grid_stride_blocks(n);
+    switch (Wd) {
+        case 1: k_sum_runs<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); break;
+        case 2: k_sum_runs<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); break;
+        default: k_sum_runs<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); break;
+    }
+}
+
+void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,
+                        uint64_t* rows_out, double* c_out, cudaStream_t s) {
+    if (n <= 0) return;
+    int g = grid_stride_blocks(n);
+    switch (Wd) {
+        case 1: k_gather_rows<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); break;
+        case 2: k_gather_rows<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); break;
+        default: k_gather_rows<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); break;
+    }
+}
+
+void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags, unsigned long long* count,
+                        cudaStream_t s) {
+    if (n > 0) k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count);
+}
+
+void launch_abs_digit_hist(const double* coef, const uint8_t* flags, int64_t n, int shift, uint64_t prefix,
+                           uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s) {
+    if (n > 0)
+        k_abs_digit_hist<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift, prefix, prefix_mask, hist);
+}
+
+void launch_budget_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t t_bits, uint32_t* tie_idx,
+                         unsigned long long* tie_count, cudaStream_t s) {
+    if (n > 0) k_budget_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, t_bits, tie_idx, tie_count);
+}
+
+void launch_set_flags(const uint32_t* idx, int64_t k, uint8_t* flags, cudaStream_t s) {
+    if (k > 0) k_set_flags<<<grid_stride_blocks(k), kThreads, 0, s>>>(idx, k, flags);
+}
+
+void launch_dis_sort_keys(int Wd, const uint64_t* gkeys, const double* gsum, int64_t G, uint64_t* skeys,
+                          cudaStream_t s) {
+    if (G > 0) k_dis_sort_keys<<<grid_stride_blocks(G), kThreads, 0, s>>>(Wd, gkeys, gsum, G, skeys);
+}
+
+void launch_dis_export(int W, int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* perm, int64_t k,
+                       uint64_t* ox, uint64_t* oz, double* og, cudaStream_t s) {
+    if (k > 0) k_dis_export<<<grid_stride_blocks(k), kThreads, 0, s>>>(W, Wd, gkeys, gsum, perm, k, ox, oz, og);
+}
+
+}  // namespace iqcc

@@ -1,0 +1,309 @@
+"""Python binding of libiqcc.so (ctypes; argument marshalling only).
+
+Every function below has the name of the C entry point it calls (see
+``include/iqcc.h``) and does no arithmetic of the method itself.  PyTorch, when
+present, supplies the CUDA stream and the device allocator (its caching
+allocator) to the library.  There is no CPU fallback: importing this module
+raises when the compiled library is missing, and creating a Hamiltonian raises
+when no CUDA device is visible.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libiqcc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2603_08883_gb300.build` "
+                      "(the iQCC path has no CPU fallback)")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_vp = ctypes.c_void_p
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+STATUS = {0: "IQCC_OK", 1: "IQCC_ERR_ARG", 2: "IQCC_ERR_CUDA", 3: "IQCC_ERR_OOM", 4: "IQCC_ERR_CAPACITY",
+          5: "IQCC_ERR_HASH_FULL", 6: "IQCC_ERR_TIMEOUT", 7: "IQCC_ERR_STATE"}
+
+
+class IqccError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class iqcc_opts(ctypes.Structure):
+    _fields_ = [("n_qubits", ctypes.c_int), ("capacity", ctypes.c_int64), ("max_probe", ctypes.c_int),
+                ("stream", ctypes.c_void_p), ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p)]
+
+
+class iqcc_iter_opts(ctypes.Structure):
+    _fields_ = [("n_gen", ctypes.c_int), ("eps", ctypes.c_double), ("max_terms", ctypes.c_int64),
+                ("min_gradient", ctypes.c_double), ("n_forced", ctypes.c_int), ("forced_x", _u64p),
+                ("forced_z", _u64p), ("forced_tau", _f64p)]
+
+
+class iqcc_iter_result(ctypes.Structure):
+    _fields_ = [("n_applied", ctypes.c_int), ("gx", ctypes.c_uint64 * 256), ("gz", ctypes.c_uint64 * 256),
+                ("grad", ctypes.c_double * 64), ("tau", ctypes.c_double * 64), ("abc", (ctypes.c_double * 3) * 64),
+                ("n_terms_before", ctypes.c_int64), ("n_terms_peak", ctypes.c_int64), ("n_removed", ctypes.c_int64),
+                ("n_terms", ctypes.c_int64), ("dressed_terms", ctypes.c_int64), ("energy", ctypes.c_double)]
+
+
+class iqcc_stats(ctypes.Structure):
+    _fields_ = [("n_dress", ctypes.c_int64), ("dressed_terms", ctypes.c_int64), ("anticommuting", ctypes.c_int64),
+                ("appended", ctypes.c_int64), ("dress_kernel_ms", ctypes.c_double), ("dress_bytes", ctypes.c_double),
+                ("n_energy", ctypes.c_int64), ("energy_kernel_ms", ctypes.c_double),
+                ("energy_bytes", ctypes.c_double), ("prune_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
+                ("hash_ms", ctypes.c_double), ("hash_rebuilds", ctypes.c_int64), ("rows_allocated", ctypes.c_int64),
+                ("hash_slots", ctypes.c_int64), ("words", ctypes.c_int), ("pad", ctypes.c_int)]
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+_c = ctypes.c_int
+_load = _sig("iqcc_load_hamiltonian", _c, [ctypes.POINTER(_vp), ctypes.POINTER(iqcc_opts), ctypes.c_int64, _u64p,
+                                           _u64p, _f64p])
+_dress = _sig("iqcc_dress", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.POINTER(ctypes.c_int)])
+_prune = _sig("iqcc_prune", _c, [_vp, ctypes.c_double, ctypes.c_int64, _i64p])
+_energy = _sig("iqcc_qmf_energy", _c, [_vp, _f64p, _f64p, _f64p])
+_abc = _sig("iqcc_generator_abc", _c, [_vp, _u64p, _u64p, _f64p, _f64p, _f64p])
+_dis = _sig("iqcc_dis_gradients", _c, [_vp, _f64p, _f64p, ctypes.c_int64, _u64p, _u64p, ctypes.c_int64, _i64p,
+                                       _u64p, _u64p, _f64p])
+_iterate = _sig("iqcc_iterate", _c, [_vp, _f64p, _f64p, ctypes.POINTER(iqcc_iter_opts),
+                                     ctypes.POINTER(iqcc_iter_result)])
+_num = _sig("iqcc_num_terms", _c, [_vp, _i64p])
+_export = _sig("iqcc_export", _c, [_vp, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
+_stats = _sig("iqcc_get_stats", _c, [_vp, ctypes.POINTER(iqcc_stats)])
+_reset = _sig("iqcc_reset_stats", _c, [_vp])
+_err = _sig("iqcc_last_error", ctypes.c_char_p, [_vp])
+_free = _sig("iqcc_free", None, [_vp])
+
+
+def _u64(a, shape=None):
+    a = np.ascontiguousarray(a, dtype=np.uint64)
+    if shape is not None:
+        a = a.reshape(shape)
+    return a, a.ctypes.data_as(_u64p)
+
+
+def _f64(a, n=None):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if n is not None and a.size != n:
+        raise ValueError(f"expected {n} values, got {a.size}")
+    return a, a.ctypes.data_as(_f64p)
+
+
+def _torch_hooks(device):
+    """(stream handle, alloc callback, free callback) from PyTorch, or Nones."""
+    try:
+        import torch
+    except ImportError:
+        return None, None, None
+    if not torch.cuda.is_available():
+        return None, None, None
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+
+    def _alloc(size, _user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(size), dev.index, stream)
+        except Exception:  # out of memory -> NULL, the library reports IQCC_ERR_OOM
+            return None
+
+    def _free(ptr, _user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    return stream.cuda_stream, ALLOC_FN(_alloc), FREE_FN(_free)
+
+
+class Hamiltonian:
+    """A Hamiltonian resident on the GPU (an ``iqcc_ctx``)."""
+
+    def __init__(self, handle, n, keepalive):
+        self._h = handle
+        self.n = n
+        self.W = (n + 63) // 64
+        self._keepalive = keepalive
+
+    def _check(self, st):
+        if st != 0:
+            raise IqccError(st, _err(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _free(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __len__(self):
+        return iqcc_num_terms(self)
+
+    @property
+    def handle(self):
+        return self._h
+
+
+def iqcc_load_hamiltonian(n_qubits: int, x, z, coef, capacity: int = 0, max_probe: int = 0,
+                          use_torch: bool = True, device=None) -> Hamiltonian:
+    """Load H = sum_k coef[k] P(x[k], z[k]) onto the GPU (iqcc_load_hamiltonian)."""
+    W = (n_qubits + 63) // 64
+    xa, xp = _u64(x, (-1, W))
+    za, zp = _u64(z, (-1, W))
+    ca, cp = _f64(coef)
+    if not (len(xa) == len(za) == len(ca)):
+        raise ValueError("x, z and coef lengths differ")
+    stream, alloc, free = _torch_hooks(device) if use_torch else (None, None, None)
+    opts = iqcc_opts(n_qubits, capacity, max_probe, stream, alloc or ALLOC_FN(), free or FREE_FN(), None)
+    h = _vp()
+    st = _load(ctypes.byref(h), ctypes.byref(opts), len(ca), xp, zp, cp)
+    if st != 0:
+        raise IqccError(st, _err(None).decode())
+    return Hamiltonian(h, n_qubits, (alloc, free, opts))
+
+
+def iqcc_dress(H: Hamiltonian, gx, gz, tau) -> int:
+    gxa, gxp = _u64(gx, (-1, H.W))
+    gza, gzp = _u64(gz, (-1, H.W))
+    ta, tp = _f64(np.atleast_1d(tau), len(gxa))
+    applied = ctypes.c_int(0)
+    H._check(_dress(H._h, len(gxa), gxp, gzp, tp, ctypes.byref(applied)))
+    return applied.value
+
+
+def iqcc_prune(H: Hamiltonian, eps: float, max_terms: int = 0) -> int:
+    removed = ctypes.c_int64(0)
+    H._check(_prune(H._h, float(eps), int(max_terms), ctypes.byref(removed)))
+    return removed.value
+
+
+def iqcc_qmf_energy(H: Hamiltonian, theta, phi) -> float:
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    e = ctypes.c_double(0.0)
+    H._check(_energy(H._h, tp, pp, ctypes.byref(e)))
+    return e.value
+
+
+def iqcc_generator_abc(H: Hamiltonian, gx, gz, theta, phi):
+    gxa, gxp = _u64(gx, (H.W,))
+    gza, gzp = _u64(gz, (H.W,))
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    out = np.zeros(3)
+    H._check(_abc(H._h, gxp, gzp, tp, pp, out.ctypes.data_as(_f64p)))
+    return out
+
+
+def iqcc_dis_gradients(H: Hamiltonian, theta, phi, cx=None, cz=None, cap: int | None = None):
+    """With candidates: their gradients.  Without: the ordered DIS (cx, cz, g),
+    at most ``cap`` of them (all when cap is None)."""
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    n_out = ctypes.c_int64(0)
+    if cx is not None:
+        cxa, cxp = _u64(cx, (-1, H.W))
+        cza, czp = _u64(cz, (-1, H.W))
+        g = np.zeros(max(len(cxa), 1))
+        H._check(_dis(H._h, tp, pp, len(cxa), cxp, czp, 0, ctypes.byref(n_out), None, None,
+                      g.ctypes.data_as(_f64p)))
+        return g[: len(cxa)]
+    if cap is None:
+        H._check(_dis(H._h, tp, pp, 0, None, None, 0, ctypes.byref(n_out), None, None, None))
+        cap = n_out.value
+    k = max(int(cap), 1)
+    ox = np.zeros((k, H.W), np.uint64)
+    oz = np.zeros((k, H.W), np.uint64)
+    og = np.zeros(k)
+    H._check(_dis(H._h, tp, pp, 0, None, None, int(cap), ctypes.byref(n_out), ox.ctypes.data_as(_u64p),
+                  oz.ctypes.data_as(_u64p), og.ctypes.data_as(_f64p)))
+    m = min(int(cap), n_out.value)
+    return ox[:m], oz[:m], og[:m]
+
+
+def iqcc_iterate(H: Hamiltonian, theta, phi, n_gen: int, eps: float = 0.0, max_terms: int = 0,
+                 min_gradient: float = 0.0, forced_x=None, forced_z=None, forced_tau=None) -> dict:
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    keep = []
+    o = iqcc_iter_opts(n_gen, eps, max_terms, min_gradient, 0, None, None, None)
+    if forced_x is not None:
+        fxa, fxp = _u64(forced_x, (-1, H.W))
+        fza, fzp = _u64(forced_z, (-1, H.W))
+        keep += [fxa, fza]
+        o.n_forced, o.forced_x, o.forced_z = len(fxa), fxp, fzp
+        if forced_tau is not None:
+            fta, ftp = _f64(forced_tau, len(fxa))
+            keep.append(fta)
+            o.forced_tau = ftp
+    r = iqcc_iter_result()
+    H._check(_iterate(H._h, tp, pp, ctypes.byref(o), ctypes.byref(r)))
+    k, W = r.n_applied, H.W
+    return {"gx": np.array(r.gx[: k * W], np.uint64).reshape(k, W),
+            "gz": np.array(r.gz[: k * W], np.uint64).reshape(k, W),
+            "g": np.array(r.grad[:k]), "tau": np.array(r.tau[:k]),
+            "abc": np.array([list(r.abc[i]) for i in range(k)]).reshape(k, 3),
+            "removed": r.n_removed, "energy": r.energy, "M": r.n_terms, "M_before": r.n_terms_before,
+            "M_peak": r.n_terms_peak, "dressed_terms": r.dressed_terms}
+
+
+def iqcc_num_terms(H: Hamiltonian) -> int:
+    m = ctypes.c_int64(0)
+    H._check(_num(H._h, ctypes.byref(m)))
+    return m.value
+
+
+def iqcc_export(H: Hamiltonian, out=None):
+    """(x, z, c) in canonical order; ``out`` = preallocated (x, z, c) host arrays
+    (e.g. pinned), filled in place."""
+    n = ctypes.c_int64(0)
+    H._check(_export(H._h, 0, ctypes.byref(n), None, None, None))
+    m = n.value
+    if out is None:
+        x = np.zeros((max(m, 1), H.W), np.uint64)
+        z = np.zeros((max(m, 1), H.W), np.uint64)
+        c = np.zeros(max(m, 1))
+    else:
+        x, z, c = out
+    H._check(_export(H._h, m, ctypes.byref(n), x.ctypes.data_as(_u64p), z.ctypes.data_as(_u64p),
+                     c.ctypes.data_as(_f64p)))
+    return x[:m], z[:m], c[:m]
+
+
+def iqcc_get_stats(H: Hamiltonian) -> dict:
+    s = iqcc_stats()
+    H._check(_stats(H._h, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in iqcc_stats._fields_ if name != "pad"}
+
+
+def iqcc_reset_stats(H: Hamiltonian) -> None:
+    H._check(_reset(H._h))
+
+
+def iqcc_last_error(H: Hamiltonian | None = None) -> str:
+    return _err(H._h if H is not None else None).decode()
+
+
+def iqcc_free(H: Hamiltonian) -> None:
+    H.close()
+
+
+def exported_symbols():
+    """Names of the C entry points this binding resolves."""
+    return sorted(n for n in globals() if n.startswith("iqcc_") and callable(globals()[n]))

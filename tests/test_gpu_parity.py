@@ -1,0 +1,279 @@
+"""GPU parity: every entry point of the C ABI against the CPU oracle on the
+same seeded inputs (sizes the oracle finishes in seconds, several tiles and a
+ragged tail; word counts 1, 2, 3 and 4; the degenerate cases)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_08883_gb300 import synth
+from tests.compare import ABS, REL, compare
+
+pytestmark = pytest.mark.gpu
+
+iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc")
+
+SIZES = [(1, 3, 1), (7, 3000, 2), (24, 40_037, 3), (64, 20_011, 4), (65, 30_029, 5), (100, 50_021, 6),
+         (130, 20_003, 7), (200, 12_007, 8)]
+
+
+def _with_dups(n, m, seed):
+    """Random H plus repeated keys and an exact cancellation, shuffled."""
+    n_, x, z, c = synth.random_hamiltonian(n, m, seed)
+    rng = np.random.Generator(np.random.PCG64(seed + 99))
+    k = max(1, len(c) // 10)
+    pick = rng.integers(0, len(c), k)
+    x = np.vstack([x, x[pick]])
+    z = np.vstack([z, z[pick]])
+    c = np.concatenate([c, rng.standard_normal(k)])
+    if len(c) > 2:                      # one key cancels exactly to zero
+        x = np.vstack([x, x[:1]])
+        z = np.vstack([z, z[:1]])
+        c = np.append(c, -np.sum(c[np.all(x[:-1] == x[0], 1) & np.all(z[:-1] == z[0], 1)]))
+    perm = rng.permutation(len(c))
+    return x[perm], z[perm], c[perm]
+
+
+@pytest.mark.parametrize("n,m,seed", SIZES)
+def test_load_and_export_canonical(n, m, seed):
+    x, z, c = _with_dups(n, m, seed)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    gx, gz, gc = iqcc.iqcc_export(H)
+    ox, oz, oc = o.export()
+    assert len(gc) == len(oc) == len(H)
+    assert np.array_equal(gx, ox) and np.array_equal(gz, oz)      # same keys, same canonical order
+    assert np.array_equal(gc, oc)                                   # sums in input order: bit-exact
+
+
+@pytest.mark.parametrize("n,m,seed", SIZES)
+def test_dress_matches_oracle(n, m, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    _, x, z, c = synth.random_hamiltonian(n, m, seed)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    gens = [synth.random_generator(n, rng) for _ in range(4)]
+    taus = rng.uniform(-math.pi, math.pi, 4)
+    for (gx, gz), t in zip(gens, taus):
+        o.dress(gx, gz, t)
+    assert iqcc.iqcc_dress(H, np.array([g[0] for g in gens]), np.array([g[1] for g in gens]), taus) == 4
+    bad = compare(iqcc.iqcc_export(H), o.export())
+    assert not bad, bad[:5]
+    assert len(H) == len(o)                      # eps = 0: no key is dropped on either side
+
+
+def test_dress_pairs_present_and_absent():
+    """A generator whose partners are all present (pure rotations) and one whose
+    partners are all absent (pure appends), with the exact key count."""
+    n = 10
+    _, x, z, c = synth.random_hamiltonian(n, 500, 17)
+    P = (np.array([0b11], np.uint64), np.array([0b01], np.uint64))   # Y0 X1
+    x2 = np.vstack([x, x ^ P[0]])
+    z2 = np.vstack([z, z ^ P[1]])
+    c2 = np.concatenate([c, c[::-1]])
+    o = oracle.Oracle(n, x2, z2, c2)
+    H = iqcc.iqcc_load_hamiltonian(n, x2, z2, c2)
+    m0 = len(H)
+    iqcc.iqcc_dress(H, P[0], P[1], [0.7])
+    o.dress(P[0], P[1], 0.7)
+    assert len(H) == m0                          # every partner present: no append
+    assert not compare(iqcc.iqcc_export(H), o.export())
+
+
+@pytest.mark.parametrize("n,seed", [(8, 1), (64, 2), (100, 3), (130, 4)])
+@pytest.mark.parametrize("angles", ["basis", "uniform"])
+def test_energy_and_abc_match_oracle(n, seed, angles):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    _, x, z, c = synth.random_hamiltonian(n, 30_000 if angles == "basis" else 5_000, seed, density=0.3)
+    # plenty of diagonal and generator-matching strings
+    x[: len(x) // 3] = 0
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    th, ph = synth.qmf_angles(n, angles, seed)
+    if angles == "basis":
+        th = np.where(rng.random(n) < 0.5, np.pi, 0.0)
+    e = iqcc.iqcc_qmf_energy(H, th, ph)
+    assert e == pytest.approx(o.energy(th, ph), abs=1e-9)
+    for k in range(3):
+        gx, gz = synth.random_generator(n, rng)
+        if k == 0 and len(x) > 10:                # a generator with the flip set of existing terms
+            gx = x[len(x) // 2].copy()
+            if not gx.any():
+                gx[0] = np.uint64(3)
+            gz = np.zeros_like(gx)
+            low = int(np.nonzero(gx)[0][0])
+            gz[low] = gx[low] & (~gx[low] + np.uint64(1))
+        a = iqcc.iqcc_generator_abc(H, gx, gz, th, ph)
+        b = o.abc(gx, gz, th, ph)
+        assert np.allclose(a, b, rtol=0, atol=1e-9), (a, b)
+
+
+@pytest.mark.parametrize("n,seed", [(6, 1), (24, 2), (100, 3)])
+def test_dis_basis_matches_oracle(n, seed):
+    _, x, z, c = synth.random_hamiltonian(n, 20_000, seed, density=0.15)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    th, ph = synth.qmf_angles(n, "basis")
+    ox, oz, og = o.dis(th, ph)
+    gx, gz, gg = iqcc.iqcc_dis_gradients(H, th, ph)
+    assert len(gg) == len(og)
+    ref = {(a.tobytes(), b.tobytes()): v for a, b, v in zip(ox, oz, og)}
+    got = {(a.tobytes(), b.tobytes()): v for a, b, v in zip(gx, gz, gg)}
+    assert ref.keys() == got.keys()
+    for k in ref:
+        assert got[k] == pytest.approx(ref[k], abs=1e-12 + 1e-12 * abs(ref[k]))
+    # ordering: identical wherever the oracle's coarse |g| values are distinct
+    top = min(len(og), 50)
+    mag = np.abs(og)
+
+    def separated(i, j):
+        return j < 0 or j >= len(mag) or abs(mag[i] - mag[j]) > 1e-9 * mag[i]
+
+    for i in range(top):
+        if separated(i, i - 1) and separated(i, i + 1):
+            assert (gx[i].tobytes(), gz[i].tobytes()) == (ox[i].tobytes(), oz[i].tobytes())
+    # the capped query returns the head of the same order
+    hx, hz, hg = iqcc.iqcc_dis_gradients(H, th, ph, cap=5)
+    assert np.array_equal(hx, gx[:5]) and np.array_equal(hg, gg[:5])
+
+
+@pytest.mark.parametrize("n,seed", [(5, 1), (12, 2), (70, 3)])
+def test_dis_general_angles_and_given_candidates(n, seed):
+    _, x, z, c = synth.random_hamiltonian(n, 300, seed, density=0.3)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    th, ph = synth.qmf_angles(n, "uniform", seed)
+    ox, oz, og = o.dis(th, ph)
+    gx, gz, gg = iqcc.iqcc_dis_gradients(H, th, ph)
+    ref = {(a.tobytes(), b.tobytes()): v for a, b, v in zip(ox, oz, og)}
+    got = {(a.tobytes(), b.tobytes()): v for a, b, v in zip(gx, gz, gg)}
+    assert ref.keys() == got.keys()
+    for k in ref:
+        assert got[k] == pytest.approx(ref[k], abs=1e-10)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cand = [synth.random_generator(n, rng) for _ in range(37)]
+    cx = np.array([a for a, b in cand])
+    cz = np.array([b for a, b in cand])
+    g = iqcc.iqcc_dis_gradients(H, th, ph, cx=cx, cz=cz)
+    for i in range(len(cand)):
+        assert g[i] == pytest.approx(o.gradient(cx[i], cz[i], th, ph), abs=1e-10)
+
+
+@pytest.mark.parametrize("eps,cap", [(0.0, 0), (1e-3, 0), (0.0, 777), (1e-4, 5000), (0.0, 1), (10.0, 0)])
+def test_prune_matches_oracle(eps, cap):
+    n = 100
+    _, x, z, c = synth.random_hamiltonian(n, 60_013, 31)
+    rng = np.random.Generator(np.random.PCG64(5))
+    c[: len(c) // 4] = np.round(c[: len(c) // 4], 3)            # exact |c| ties, some zeros
+    c[len(c) // 4: len(c) // 2] = -c[: len(c) // 4][: len(c) // 2 - len(c) // 4]
+    c = c * rng.choice([-1.0, 1.0], len(c))
+    c[c == 0] = 1e-3
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    removed = iqcc.iqcc_prune(H, eps, cap)
+    r_o = o.prune(eps, cap)
+    assert removed == r_o
+    gx, gz, gc = iqcc.iqcc_export(H)
+    ox, oz, oc = o.export()
+    assert np.array_equal(gx, ox) and np.array_equal(gz, oz) and np.array_equal(gc, oc)
+
+
+def test_empty_and_degenerate_cases():
+    n = 9
+    e = np.zeros((0, 1), np.uint64)
+    H = iqcc.iqcc_load_hamiltonian(n, e, e, np.zeros(0))
+    assert len(H) == 0
+    assert iqcc.iqcc_dress(H, [3], [1], [0.5]) == 1
+    assert iqcc.iqcc_prune(H, 1e-3, 5) == 0
+    assert iqcc.iqcc_qmf_energy(H, np.zeros(n), np.zeros(n)) == 0.0
+    x, z, c = iqcc.iqcc_export(H)
+    assert len(c) == 0
+    assert len(iqcc.iqcc_dis_gradients(H, np.zeros(n), np.zeros(n))[2]) == 0
+    # all-zero input collapses to an empty Hamiltonian
+    H = iqcc.iqcc_load_hamiltonian(n, np.ones((3, 1), np.uint64), np.zeros((3, 1), np.uint64), np.zeros(3))
+    assert len(H) == 0
+    # identity only; a generator commutes with it; tau = 0 and tau = 2 pi
+    H = iqcc.iqcc_load_hamiltonian(n, np.zeros((1, 1), np.uint64), np.zeros((1, 1), np.uint64), np.array([2.5]))
+    iqcc.iqcc_dress(H, [5], [4], [1.3])
+    assert len(H) == 1 and iqcc.iqcc_export(H)[2][0] == 2.5
+    _, x, z, c = synth.random_hamiltonian(n, 200, 3)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    iqcc.iqcc_dress(H, [1], [1], [0.0])
+    o.dress([1], [1], 0.0)
+    assert not compare(iqcc.iqcc_export(H), o.export())
+    iqcc.iqcc_dress(H, [1], [1], [2 * math.pi])
+    o.dress([1], [1], 2 * math.pi)
+    assert not compare(iqcc.iqcc_export(H), o.export())
+
+
+def test_capacity_error_leaves_h_unchanged():
+    n = 20
+    _, x, z, c = synth.random_hamiltonian(n, 3000, 8)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=len(c) + 10)
+    before = iqcc.iqcc_export(H)
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_dress(H, [0b111], [0b001], [0.3])   # anticommutes with about half, partners absent
+    assert e.value.status == 4
+    after = iqcc.iqcc_export(H)
+    for a, b in zip(before, after):
+        assert np.array_equal(a, b)
+    iqcc.iqcc_prune(H, 1.0)                           # still usable
+
+
+def test_arguments_rejected():
+    n = 5
+    _, x, z, c = synth.random_hamiltonian(n, 50, 1)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_dress(H, [1 << 7], [0], [0.1])
+    assert e.value.status == 1
+    with pytest.raises(iqcc.IqccError):
+        iqcc.iqcc_dress(H, [1], [0], [float("nan")])
+    assert len(H) == len(oracle.Oracle(n, x, z, c))
+
+
+# ------------------------------------------------------------------ whole iterations
+
+
+def test_jw8_iterations_free_running():
+    """Configuration of the 8-qubit workload: 3 iterations x 2 generators with
+    random QMF angles and no compression; the GPU screens, optimises and dresses
+    on its own and must reproduce the oracle's choices and energies."""
+    w = synth.WORKLOADS["jw8"]
+    n, x, z, c = synth.workload_hamiltonian(w)
+    th, ph = synth.workload_angles(w)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    for it in range(w.n_iter):
+        ro = o.iterate(th, ph, w.n_gen, w.eps, w.max_terms)
+        rg = iqcc.iqcc_iterate(H, th, ph, w.n_gen, w.eps, w.max_terms)
+        assert np.array_equal(rg["gx"], ro["gx"]) and np.array_equal(rg["gz"], ro["gz"])
+        assert np.allclose(rg["g"], ro["g"], rtol=1e-12, atol=1e-12)
+        assert np.allclose(rg["tau"], ro["tau"], rtol=0, atol=1e-12)
+        assert rg["energy"] == pytest.approx(ro["energy"], abs=1e-9)
+        assert not compare(iqcc.iqcc_export(H), o.export())
+
+
+def test_jw24_iterations_teacher_forced_and_free():
+    """24-qubit workload: the GPU is given the oracle's generators and
+    amplitudes (teacher forcing) and must reproduce the dressed Hamiltonian after
+    every iteration; the free-running GPU energies of the same iterations must
+    match too."""
+    w = synth.WORKLOADS["jw24"]
+    n, x, z, c = synth.workload_hamiltonian(w)
+    th, ph = synth.workload_angles(w)
+    o = oracle.Oracle(n, x, z, c)
+    Hf = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    Hs = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    for it in range(3):
+        ro = o.iterate(th, ph, w.n_gen, w.eps, w.max_terms)
+        rf = iqcc.iqcc_iterate(Hf, th, ph, w.n_gen, w.eps, w.max_terms, forced_x=ro["gx"], forced_z=ro["gz"],
+                               forced_tau=ro["tau"])
+        assert rf["removed"] == ro["removed"] or abs(rf["removed"] - ro["removed"]) <= 2
+        bad = compare(iqcc.iqcc_export(Hf), o.export(), eps=w.eps)
+        assert not bad, bad[:5]
+        assert rf["energy"] == pytest.approx(ro["energy"], abs=1e-9)
+        rs = iqcc.iqcc_iterate(Hs, th, ph, w.n_gen, w.eps, w.max_terms)
+        assert rs["energy"] == pytest.approx(ro["energy"], abs=1e-9)
