@@ -1,0 +1,352 @@
+#!/usr/bin/env python3
+"""Benchmark of the iQCC dressing path on GB300.
+
+One step = one iQCC iteration (App. A steps 1-5) of the 100-qubit workload:
+DIS screening, 8 x (A, B, C; dress; term limit), compression, energy.  The run
+is the workload's own iteration sequence: W warm-up iterations, then K timed
+ones on the Hamiltonian those produced, all resident in HBM.
+
+Metric: dressed Pauli terms per second = sum over the timed iterations of M at
+each generator's dress, divided by the device time of those iterations (max
+over ranks).  N > 1 ranks run independent seeded Hamiltonians (weak scaling;
+the path has no cross-rank exchange in this configuration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gpu|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L2_BYTES = 129 * 1024 * 1024
+METRIC = "dressed Pauli terms/s, 100-qubit iQCC iteration"
+UNIT = "terms/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gpu", "reference"], default="gpu")
+    ap.add_argument("--workload", default="jw100")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload_config(w, extra):
+    cfg = {"workload": f"{w.name}: {w.notes}", "n_qubits": w.n_qubits, "orbitals": w.norb, "integrals": w.integrals,
+           "reference_state": w.angles, "generators_per_iteration": w.n_gen, "eps": w.eps,
+           "max_terms": w.max_terms, "capacity_rows": w.capacity, "seed": w.seed}
+    cfg.update(extra)
+    return cfg
+
+
+def oracle_dressed(w, n, x, z, c, th, ph, rows):
+    """Dressed-term count of one oracle iteration on the sample (same
+    definition as the GPU metric) and its wall time."""
+    import oracle
+    o = oracle.Oracle(n, x[:rows], z[:rows], c[:rows])
+    t0 = time.perf_counter()
+    cx, cz, g = o.dis(th, ph)
+    sel = [i for i in range(len(g)) if abs(g[i]) > 1e-12][: w.n_gen]
+    dressed = 0
+    for i in sel:
+        a, b, cc = o.abc(cx[i], cz[i], th, ph)
+        tau = 0.0 if (b == 0.0 and cc == 0.0) else float(np.arctan2(-cc, -b))
+        dressed += len(o)
+        o.dress(cx[i], cz[i], tau)
+        if w.max_terms > 0 and len(o) > w.max_terms:
+            o.prune(0.0, w.max_terms)
+    o.prune(w.eps, w.max_terms)
+    o.energy(th, ph)
+    return dressed, time.perf_counter() - t0
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        self.out = ""
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "out", "").splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def profile_traffic(avg_rows):
+    """DRAM bytes per dressed term of the dress kernel from the committed ncu
+    summary (profiles/dress_kernel_jw100.md, line 'dram_bytes_per_dressed_term:'),
+    scaled to a launch of avg_rows rows; None when absent."""
+    path = os.path.join(ROOT, "profiles", "dress_kernel_jw100.md")
+    try:
+        for line in open(path):
+            if line.startswith("dram_bytes_per_dressed_term:"):
+                return float(line.split(":")[1].split()[0]) * avg_rows
+    except OSError:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return
+    from paper_2603_08883_gb300 import synth
+    w = synth.WORKLOADS[args.workload]
+    n, x, z, c = synth.workload_hamiltonian(w)
+    th, ph = synth.workload_angles(w)
+    rows = 4000
+    for _ in range(args.warmup):
+        oracle_dressed(w, n, x, z, c, th, ph, rows)
+    tot, dt = 0, 0.0
+    for _ in range(args.steps):
+        d, t = oracle_dressed(w, n, x, z, c, th, ph, rows)
+        tot += d
+        dt += t
+    value = tot / dt
+    sample = (f"each step: one oracle iteration (DIS, {w.n_gen} x (A,B,C + dress + term limit), compression, "
+              f"energy) on the first {rows} of the {len(c)} strings of the {w.n_qubits}-qubit Hamiltonian")
+    print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+                      "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True,
+                      "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                      "impl": "reference",
+                      "config": workload_config(w, {"sample_rows": rows}),
+                      "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+                      "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+          flush=True)
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+
+def run_gpu(args):
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_2603_08883_gb300 import iqcc, synth
+    import dataclasses
+
+    w = synth.WORKLOADS[args.workload]
+    if world > 1:
+        w = dataclasses.replace(w, seed=w.seed + 1000 * rank)
+    n, x, z, c = synth.workload_hamiltonian(w)
+    th, ph = synth.workload_angles(w)
+    M0 = len(c)
+    stream = torch.cuda.current_stream()
+    capacity = w.capacity
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---------------- device-resident run
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=capacity)
+    for _ in range(args.warmup):
+        iqcc.iqcc_iterate(H, th, ph, w.n_gen, w.eps, w.max_terms)
+    M_start = len(H)
+    flush = M_start * (16 * ((n + 63) // 64) + 8) < 2 * L2_BYTES
+    scratch = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda") if flush else None
+    iqcc.iqcc_reset_stats(H)
+    recs = []
+    barrier()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        t0 = time.perf_counter()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            if scratch is not None:
+                scratch.zero_()
+            recs.append(iqcc.iqcc_iterate(H, th, ph, w.n_gen, w.eps, w.max_terms))
+        ev1.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+    dev_s = ev0.elapsed_time(ev1) / 1e3
+    stats = iqcc.iqcc_get_stats(H)
+    dressed = sum(r["dressed_terms"] for r in recs)
+    t_max = dev_s
+    total_dressed = dressed
+    if dist is not None:
+        tt = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max = float(tt.item())
+        dd = torch.tensor([dressed], dtype=torch.float64, device="cuda")
+        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
+        total_dressed = float(dd.item())
+
+    # ---------------- end to end through host buffers (pinned), N = 1 path of a user
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        hx, hz, hc = iqcc.iqcc_export(H)
+        W = hx.shape[1]
+        cap_rows = max(w.max_terms if w.max_terms > 0 else 0, len(hc)) + 1
+
+        def pinned(shape, dtype):
+            nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
+            t = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+            return t.numpy().view(dtype).reshape(shape)
+
+        bufs = [(pinned((cap_rows, W), np.uint64), pinned((cap_rows, W), np.uint64), pinned((cap_rows,), np.float64))
+                for _ in range(2)]
+        m = len(hc)
+        bufs[0][0][:m], bufs[0][1][:m], bufs[0][2][:m] = hx, hz, hc
+        del hx, hz, hc
+        H.close()
+        h2d = d2h = 0
+        e_dressed = 0
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.e2e_steps):
+            src, dst = bufs[k % 2], bufs[(k + 1) % 2]
+            Hk = iqcc.iqcc_load_hamiltonian(n, src[0][:m], src[1][:m], src[2][:m], capacity=capacity)
+            r = iqcc.iqcc_iterate(Hk, th, ph, w.n_gen, w.eps, w.max_terms)
+            ox, oz, oc = iqcc.iqcc_export(Hk, out=dst)
+            h2d += m * (2 * W * 8 + 8) + 2 * n * 8
+            d2h += len(oc) * (2 * W * 8 + 8) + 8
+            m = len(oc)
+            e_dressed += r["dressed_terms"]
+            Hk.close()
+        barrier()
+        e_wall = time.perf_counter() - t0
+        e2e = {"value": e_dressed / e_wall, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
+               "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps,
+               "path": "per step: iqcc_load_hamiltonian from pinned host arrays, iqcc_iterate, iqcc_export to "
+                       "pinned host arrays (the next step's input); wall clock"}
+    else:
+        H.close()
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    # ---------------- roofline of the dress kernel
+    peak, peak_kind = measured_peak()
+    n_dress = max(stats["n_dress"], 1)
+    dress_s = stats["dress_kernel_ms"] / 1e3
+    achieved = stats["dress_bytes"] / dress_s / 1e9 if dress_s > 0 else 0.0
+    avg_rows = stats["dressed_terms"] / n_dress
+    shares = {"dress": stats["dress_kernel_ms"], "hash_insert_rebuild": stats["hash_ms"],
+              "compression": stats["prune_ms"], "dis_screening": stats["dis_ms"],
+              "energy_abc": stats["energy_kernel_ms"]}
+    tot_ms = sum(shares.values())
+    roofline = {"bound": "hbm", "kernel": "k_dress (classify, partner lookup, rotate/append)",
+                "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
+                "traffic": profile_traffic(avg_rows),
+                "bytes_per_launch": stats["dress_bytes"] / n_dress, "launches": stats["n_dress"],
+                "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
+                "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {}}
+
+    # ---------------- oracle on the host cores (N = 1 only)
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rows = 8000
+        d, t = oracle_dressed(w, n, x, z, c, th, ph, rows)
+        cpu = {"value": d / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one oracle iteration (DIS, {w.n_gen} x (A,B,C + dress + term limit), compression, "
+                         f"energy) on the first {rows} of the {M0} strings; {d} dressed terms in {t:.2f} s"}
+
+    line = {"metric": METRIC, "value": total_dressed / t_max, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(w, {
+                "M0": M0, "M_first_timed": M_start, "M_last": recs[-1]["M"] if recs else M_start,
+                "iterations": f"{args.warmup + 1}..{args.warmup + args.steps}",
+                "s_per_iteration": t_max / args.steps,
+                "l2": ("flushed before each step (256 MiB write)" if flush else
+                       f"inputs larger than L2: H >= {M_start * (16 * ((n + 63) // 64) + 8) / 2**20:.0f} MiB "
+                       "at the first timed step"),
+                "energies": [r["energy"] for r in recs],
+                "wall_s": wall}),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": stats["kernel_launches"], "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -149,7 +149,7 @@ iqcc_status iqcc_dis_gradients(iqcc_ctx* ctx, const double* theta, const double*
 typedef struct {
     int n_gen;                 /* generators per iteration (<= 64) */
     double eps;                /* compression threshold, as iqcc_prune */
-    int64_t max_terms;         /* term cap, as iqcc_prune (<= 0: none) */
+    int64_t max_terms;         /* term limit, as iqcc_prune (<= 0: none); it holds after every dress */
     double min_gradient;       /* candidates need |g| > this; 0 -> 1e-12 */
     int n_forced;              /* > 0: use these generators instead of screening */
     const uint64_t* forced_x;  /* host [n_forced][W] */
@@ -177,8 +177,11 @@ typedef struct {
  * DIS screening (iqcc_dis_gradients with n_cand = 0) and the top n_gen
  * candidates with |g| > min_gradient (or the forced list); for each in order,
  * A, B, C on the current H, tau = atan2(-C, -B) (0 when B = C = 0; or the
- * forced amplitude), and the dress; then iqcc_prune(eps, max_terms) and the
- * energy.  The generators of one iteration come from one screening.
+ * forced amplitude), and the dress, after which a Hamiltonian larger than
+ * max_terms is cut to the max_terms largest |C| at once (the term limit of the
+ * paper's Tables 2-3 holds after every dress, which bounds device memory by
+ * 2 max_terms rows); then iqcc_prune(eps, max_terms) and the energy.  The
+ * generators of one iteration come from one screening.
  */
 iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi,
                          const iqcc_iter_opts* opts, iqcc_iter_result* out);
@@ -210,6 +213,7 @@ typedef struct {
     int64_t hash_rebuilds;
     int64_t rows_allocated;    /* rows currently allocated on the device */
     int64_t hash_slots;        /* active hash slots */
+    int64_t kernel_launches;   /* kernels launched by the library (all contexts) since the reset */
     int words;                 /* device words per x or z vector (1, 2 or 4) */
     int pad;
 } iqcc_stats;

@@ -420,7 +420,9 @@ int64_t orc_prune(void* h, double eps, int64_t max_terms) {
      2. the top n_gen candidates with |g| > 1e-12 (or the n_forced given ones);
      3. for each in turn: A, B, C on the current H and tau = atan2(-C, -B)
         (the minimiser of A + B cos tau + C sin tau; 0 when B = C = 0), or the
-        given tau when tau_forced is not null; dress;
+        given tau when tau_forced is not null; dress; when max_terms > 0 and
+        the dressed H holds more than max_terms terms, keep the max_terms
+        largest at once (the term limit holds after every dress);
      4. compress with (eps, max_terms);
      5. energy.
    Outputs: gens_x/gens_z [n_gen][W], g[n_gen], tau[n_gen], abc[n_gen][3];
@@ -432,6 +434,7 @@ int orc_iterate(void* h, const double* theta, const double* phi, int n_gen, int 
     Oracle* o = (Oracle*)h;
     int W = (o->n + 63) / 64;
     int used = 0;
+    *removed = 0;
     if (n_forced > 0) {
         used = n_forced;
         for (int k = 0; k < used; ++k) {
@@ -454,8 +457,9 @@ int orc_iterate(void* h, const double* theta, const double* phi, int n_gen, int 
         if (tau_forced) tau[k] = tau_forced[k];
         else tau[k] = (B == 0.0 && C == 0.0) ? 0.0 : std::atan2(-C, -B);
         if (orc_dress(h, gens_x + k * W, gens_z + k * W, tau[k])) return -1;
+        if (max_terms > 0 && (int64_t)o->H.size() > max_terms) *removed += orc_prune(h, 0.0, max_terms);
     }
-    *removed = orc_prune(h, eps, max_terms);
+    *removed += orc_prune(h, eps, max_terms);
     *energy = orc_energy(h, theta, phi);
     return used;
 }

@@ -186,20 +186,15 @@ iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
         want = std::min<int64_t>(want, ctx->capacity);
         want = std::max<int64_t>(want, rows_needed);
         const size_t rb = row_bytes(ctx);
-        if (!grow_keep(ctx, ctx->keys[ctx->cur], (size_t)want * rb, (size_t)ctx->M * rb) ||
-            !grow_keep(ctx, ctx->coef[ctx->cur], (size_t)want * 8, (size_t)ctx->M * 8))
-            return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
-        release(ctx, ctx->keys[ctx->cur ^ 1]);
-        release(ctx, ctx->coef[ctx->cur ^ 1]);
-        if (!ensure(ctx, ctx->keys[ctx->cur ^ 1], (size_t)want * rb) ||
-            !ensure(ctx, ctx->coef[ctx->cur ^ 1], (size_t)want * 8))
+        if (!grow_keep(ctx, ctx->keys, (size_t)want * rb, (size_t)ctx->M * rb) ||
+            !grow_keep(ctx, ctx->coef, (size_t)want * 8, (size_t)ctx->M * 8))
             return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
         ctx->rows_alloc = want;
         ctx->stats.rows_allocated = want;
     }
-    // load factor <= 1/2 after the rows are inserted
+    // load factor <= 1/2 once the rows are inserted
     if ((uint64_t)rows_needed * 2 > ctx->hash_slots) {
-        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 4));
+        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 2));
         if (st) return st;
     }
     return IQCC_OK;
@@ -382,14 +377,14 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     Carver cv;
     cv.take<uint8_t>(M);
     cv.take<unsigned long long>(256);
-    cv.take<char>(compact_scratch_bytes(M));
+    cv.take<char>(compact_inplace_scratch_bytes(M));
     cv.take<uint32_t>(M);  // tie list
     cv.off += sort_area_bytes(M);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
     uint8_t* flags = cv.take<uint8_t>(M);
     unsigned long long* hist = cv.take<unsigned long long>(256);
-    char* cscratch = cv.take<char>(compact_scratch_bytes(M));
+    char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
     SortArea sa = carve_sort(cv, M);
 
@@ -442,8 +437,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
         CK_LAUNCH();
     }
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_compact_rows(ctx->Wd, flags, ctx->rows(), ctx->c(), ctx->rows_alt(), ctx->c_alt(), M, cscratch, &c->aux,
-                        ctx->stream);
+    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
@@ -452,11 +446,11 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.prune_ms += ms;
     const int64_t newM = (int64_t)ctx->h_counters->aux;
-    ctx->cur ^= 1;
     ctx->M = newM;
     *removed = M - newM;
+    if (newM == M) return IQCC_OK;  // nothing moved
     // rows moved: rebuild the index (same size)
-    return rebuild_hash(ctx, ctx->hash_slots ? ctx->hash_slots : pow2_at_least((uint64_t)newM * 4));
+    return rebuild_hash(ctx, ctx->hash_slots ? ctx->hash_slots : pow2_at_least((uint64_t)newM * 2));
 }
 
 // DIS candidates and gradients (n_cand == 0 path).  Leaves the ordered
@@ -482,7 +476,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     cv.take<double>(2 * ctx->n);
     cv.take<double>((size_t)n_groups(ctx) * 256);
     cv.take<uint64_t>(16 * 2 * 4);
-    cv.take<double>((size_t)nblk * 16);
+    cv.take<double>(std::max<size_t>((size_t)nblk * 16, 256));
     cv.take<double>(16);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
@@ -496,7 +490,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     double* angles = cv.take<double>(2 * ctx->n);
     double* tables = cv.take<double>((size_t)n_groups(ctx) * 256);
     uint64_t* cand = cv.take<uint64_t>(16 * 2 * 4);
-    double* partials = cv.take<double>((size_t)nblk * 16);
+    double* partials = cv.take<double>(std::max<size_t>((size_t)nblk * 16, 256));
     double* colsum = cv.take<double>(16);
 
     DevCounters* c = dctr(ctx);
@@ -542,18 +536,59 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     }
     *n_out = G;
     if (cap > 0 && G > 0) {
-        launch_dis_sort_keys(Wd, gkeys, gsum, G, skeys, ctx->stream);
-        CK_LAUNCH();
-        launch_iota(sa.a, G, ctx->stream);
-        CK_LAUNCH();
         SortPlan plan{};
         plan.n_words = Wd + 1;
         plan.n_order = Wd + 1;
         for (int w = 0; w <= Wd; ++w) plan.order[w] = w;
+        // Order either all G candidates, or - for a short head - only those whose
+        // coarse |g| reaches the cap-th largest value (radix select, 8 bits at a time).
+        int64_t n_sort = G;
+        bool subset = false;
+        if (cap <= 64 && G > 4 * cap) {
+            int64_t need = cap;
+            uint64_t prefix = 0, pmask = 0;
+            unsigned long long* hist = (unsigned long long*)partials;  // >= 256 words
+            for (int shift = 56; shift >= 0; shift -= 8) {
+                CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), ctx->stream));
+                launch_coarse_digit_hist(gsum, G, shift, prefix, pmask, hist, ctx->stream);
+                CK_LAUNCH();
+                unsigned long long h[256];
+                CK(cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                int64_t cum = 0;
+                int sel = 0;
+                for (int d = 255; d >= 0; --d) {
+                    if (cum + (int64_t)h[d] >= need) { sel = d; break; }
+                    cum += (int64_t)h[d];
+                }
+                need -= cum;
+                prefix |= (uint64_t)sel << shift;
+                pmask |= (uint64_t)255 << shift;
+            }
+            const int64_t limit = std::min<int64_t>(G, 1 << 16);
+            CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+            launch_collect_ge(gsum, G, prefix, sa.a, limit, &c->aux, ctx->stream);
+            CK_LAUNCH();
+            st = read_counters(ctx);
+            if (st) return st;
+            const int64_t got = (int64_t)ctx->h_counters->aux;
+            if (got <= limit) {
+                subset = true;
+                n_sort = got;
+                launch_dis_sort_keys_sub(Wd, gkeys, gsum, sa.a, got, skeys, ctx->stream);
+                CK_LAUNCH();
+            }
+        }
+        if (!subset) {
+            launch_dis_sort_keys(Wd, gkeys, gsum, G, skeys, ctx->stream);
+            CK_LAUNCH();
+            launch_iota(sa.a, G, ctx->stream);
+            CK_LAUNCH();
+        }
         uint32_t* sorted = nullptr;
-        radix_sort_indirect(skeys, Wd + 1, plan, sa.a, sa.b, G, &sorted, sa.tmp, sa.tmp_bytes, ctx->stream);
+        radix_sort_indirect(skeys, Wd + 1, plan, sa.a, sa.b, n_sort, &sorted, sa.tmp, sa.tmp_bytes, ctx->stream);
         CK_LAUNCH();
-        const int64_t k = std::min(cap, G);
+        const int64_t k = std::min(cap, n_sort);
         launch_dis_export(W, Wd, gkeys, gsum, sorted, k, stage_x, stage_x + (size_t)k * W, stage_g, ctx->stream);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(ox, stage_x, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
@@ -659,11 +694,10 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
     }
     const int64_t rows0 = std::min<int64_t>(ctx->capacity, std::max<int64_t>(1024, 2 * n_terms));
     const size_t rb = row_bytes(ctx);
-    for (int b = 0; b < 2; ++b)
-        if (!ensure(ctx, ctx->keys[b], (size_t)rows0 * rb) || !ensure(ctx, ctx->coef[b], (size_t)rows0 * 8)) {
-            fail(ctx, IQCC_ERR_OOM, "row allocation failed");
-            return bail(IQCC_ERR_OOM);
-        }
+    if (!ensure(ctx, ctx->keys, (size_t)rows0 * rb) || !ensure(ctx, ctx->coef, (size_t)rows0 * 8)) {
+        fail(ctx, IQCC_ERR_OOM, "row allocation failed");
+        return bail(IQCC_ERR_OOM);
+    }
     ctx->rows_alloc = rows0;
     ctx->stats.rows_allocated = rows0;
     const int64_t n = n_terms;
@@ -672,8 +706,10 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
         Carver cv;
         cv.take<uint64_t>((size_t)n * W);
         cv.take<uint64_t>((size_t)n * W);
+        cv.take<uint64_t>((size_t)n * 2 * Wd);  // packed rows in input order
+        cv.take<double>(n);                     // coefficients in input order
         cv.take<uint8_t>(n);
-        cv.take<char>(compact_scratch_bytes(n));
+        cv.take<char>(compact_inplace_scratch_bytes(n));
         cv.off += sort_area_bytes(n);
         if (!ensure(ctx, ctx->scratch, cv.off)) {
             fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
@@ -682,12 +718,12 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
         cv = Carver{(char*)ctx->scratch.p, 0};
         uint64_t* dx = cv.take<uint64_t>((size_t)n * W);
         uint64_t* dz = cv.take<uint64_t>((size_t)n * W);
+        uint64_t* staged = cv.take<uint64_t>((size_t)n * 2 * Wd);
+        double* c_staged = cv.take<double>(n);
         uint8_t* flags = cv.take<uint8_t>(n);
-        char* cscratch = cv.take<char>(compact_scratch_bytes(n));
+        char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(n));
         SortArea sa = carve_sort(cv, n);
         cudaStream_t s = ctx->stream;
-        uint64_t* staged = ctx->rows_alt();
-        double* c_staged = ctx->c_alt();
         iqcc_status st = IQCC_OK;
         do {
             if (cudaMemcpyAsync(dx, x, sizeof(uint64_t) * n * W, cudaMemcpyHostToDevice, s) ||
@@ -700,20 +736,20 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
             launch_iota(sa.a, n, s);
             uint32_t* sorted = nullptr;
             radix_sort_indirect(staged, 2 * Wd, canonical_plan(ctx), sa.a, sa.b, n, &sorted, sa.tmp, sa.tmp_bytes, s);
-            // run sums land in the current buffers at sorted positions, then compact back into the alternate
+            // run sums land in the row buffer at sorted positions; then keep the non-zero heads
             launch_sum_runs(Wd, staged, c_staged, sorted, n, flags, ctx->rows(), ctx->c(), s);
             DevCounters* c = dctr(ctx);
-            launch_compact_rows(Wd, flags, ctx->rows(), ctx->c(), staged, c_staged, n, cscratch, &c->aux, s);
+            launch_compact_inplace(Wd, flags, ctx->rows(), ctx->c(), n, cscratch, &c->aux, c, s);
             cudaError_t e = cudaGetLastError();
             if (e != cudaSuccess) { st = fail_cuda(ctx, e, "load kernels", __LINE__); break; }
             st = read_counters(ctx);
             if (st) break;
-            ctx->cur ^= 1;
             ctx->M = (int64_t)ctx->h_counters->aux;
         } while (0);
         if (st) return bail(st);
     }
     iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
+    ctx->launch_base = launches();
     if (st) return bail(st);
     ctx->stats.hash_rebuilds = 0;
     ctx->stats.hash_ms = 0;
@@ -850,11 +886,17 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         for (int i = 0; i < 3; ++i) out->abc[k][i] = abc[i];
         out->n_applied = k + 1;
         out->n_terms_peak = std::max(out->n_terms_peak, ctx->M);
+        if (o->max_terms > 0 && ctx->M > o->max_terms) {
+            int64_t cut = 0;
+            st = iqcc_prune(ctx, 0.0, o->max_terms, &cut);
+            if (st) return st;
+            out->n_removed += cut;
+        }
     }
     int64_t removed = 0;
     iqcc_status st = iqcc_prune(ctx, o->eps, o->max_terms, &removed);
     if (st) return st;
-    out->n_removed = removed;
+    out->n_removed += removed;
     out->n_terms = ctx->M;
     return iqcc_qmf_energy(ctx, theta, phi, &out->energy);
 }
@@ -904,6 +946,7 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
 iqcc_status iqcc_get_stats(const iqcc_ctx* ctx, iqcc_stats* out) {
     if (!ctx || !out) return fail(nullptr, IQCC_ERR_ARG, "null argument");
     *out = ctx->stats;
+    out->kernel_launches = launches() - ctx->launch_base;
     return IQCC_OK;
 }
 
@@ -914,6 +957,7 @@ iqcc_status iqcc_reset_stats(iqcc_ctx* ctx) {
     s.hash_slots = (int64_t)ctx->hash_slots;
     s.words = ctx->Wd;
     ctx->stats = s;
+    ctx->launch_base = launches();
     return IQCC_OK;
 }
 
@@ -925,10 +969,8 @@ const char* iqcc_last_error(const iqcc_ctx* ctx) {
 void iqcc_free(iqcc_ctx* ctx) {
     if (!ctx) return;
     cudaStreamSynchronize(ctx->stream);
-    for (int b = 0; b < 2; ++b) {
-        release(ctx, ctx->keys[b]);
-        release(ctx, ctx->coef[b]);
-    }
+    release(ctx, ctx->keys);
+    release(ctx, ctx->coef);
     release(ctx, ctx->hash);
     release(ctx, ctx->counters);
     release(ctx, ctx->scratch);

@@ -175,24 +175,22 @@ struct iqcc_ctx {
     void* alloc_user = nullptr;
 
     int64_t M = 0;                 // live rows
-    int64_t rows_alloc = 0;        // rows allocated in each key/coef buffer
-    int cur = 0;                   // current buffer (0/1)
-    iqcc::Buf keys[2], coef[2];
+    int64_t rows_alloc = 0;        // rows allocated in the key/coef buffers
+    iqcc::Buf keys, coef;
     iqcc::Buf hash;                // slots
     uint64_t hash_slots = 0;       // active slots (power of two)
     iqcc::Buf counters;            // DevCounters
     iqcc::DevCounters* h_counters = nullptr;  // pinned host mirror
     iqcc::Buf scratch;             // general scratch (grows)
+    long long launch_base = 0;     // library launch count at the last stats reset
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
     bool broken = false;
     std::string err;
     iqcc_stats stats{};
 
-    uint64_t* rows() const { return (uint64_t*)keys[cur].p; }
-    double* c() const { return (double*)coef[cur].p; }
-    uint64_t* rows_alt() const { return (uint64_t*)keys[cur ^ 1].p; }
-    double* c_alt() const { return (double*)coef[cur ^ 1].p; }
+    uint64_t* rows() const { return (uint64_t*)keys.p; }
+    double* c() const { return (double*)coef.p; }
 };
 
 namespace iqcc {
@@ -203,6 +201,8 @@ namespace iqcc {
 
 int device_words(int n);
 int sm_count();
+void note_launch();     // counts kernel launches of the library (all launchers call it)
+long long launches();
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
@@ -252,6 +252,19 @@ size_t compact_scratch_bytes(int64_t n);
 void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, const double* c_in,
                          uint64_t* rows_out, double* c_out, int64_t n, void* scratch,
                          unsigned long long* count, cudaStream_t s);
+
+// single-pass in-place stable compaction of rows/coef by flags; kept count to *count
+size_t compact_inplace_scratch_bytes(int64_t n);
+void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double* coef, int64_t n, void* scratch,
+                            unsigned long long* count, DevCounters* ctr, cudaStream_t s);
+
+// DIS top-k: coarse |g| radix select, collect, sort of the collected subset
+void launch_coarse_digit_hist(const double* g, int64_t G, int shift, uint64_t prefix, uint64_t prefix_mask,
+                              unsigned long long* hist, cudaStream_t s);
+void launch_collect_ge(const double* g, int64_t G, uint64_t t, uint32_t* idx, int64_t cap, unsigned long long* count,
+                       cudaStream_t s);
+void launch_dis_sort_keys_sub(int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* idx, int64_t k,
+                              uint64_t* skeys, cudaStream_t s);
 
 // load: pack host-layout x/z into rows, sum runs after the sort
 void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n,

@@ -15,6 +15,8 @@
 // "insert if unique, else add" merge of App. D, Eq. 18, done as a lookup).
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "iqcc_internal.cuh"
 
 namespace iqcc {
@@ -220,12 +222,16 @@ int sm_count() {
 
 int device_words(int n) { return n <= 64 ? 1 : (n <= 128 ? 2 : 4); }
 
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+long long launches() { return g_launches.load(std::memory_order_relaxed); }
+
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s) {
     int grid = (int)((slots / 2 + kThreads - 1) / kThreads);
     int cap = sm_count() * 8;
     if (grid > cap) grid = cap;
     if (grid < 1) grid = 1;
-    k_hash_clear<<<grid, kThreads, 0, s>>>(h.slots, slots);
+    k_hash_clear<<<grid, kThreads, 0, s>>>(h.slots, slots); note_launch();
 }
 
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
@@ -233,9 +239,9 @@ void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, Ha
     if (hi <= lo) return;
     int grid = grid_for(hi - lo, 8);
     switch (Wd) {
-        case 1: k_hash_insert<1><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); break;
-        case 2: k_hash_insert<2><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); break;
-        default: k_hash_insert<4><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); break;
+        case 1: k_hash_insert<1><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
+        case 2: k_hash_insert<2><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
+        default: k_hash_insert<4><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
     }
 }
 
@@ -245,9 +251,9 @@ void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef,
     if (M <= 0) return;
     int grid = grid_for(M, 8);
     switch (Wd) {
-        case 1: k_dress<1><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<1>(pkey, cos_t, sin_t), h, ctr); break;
-        case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr); break;
-        default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr); break;
+        case 1: k_dress<1><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<1>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
+        case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
+        default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
     }
 }
 
@@ -256,9 +262,9 @@ void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t*
     if (M <= 0) return;
     int grid = grid_for(M, 8);
     switch (Wd) {
-        case 1: k_dress_count<1><<<grid, kThreads, 0, s>>>(rows, M, make_gen<1>(pkey, 1, 0), h, ctr); break;
-        case 2: k_dress_count<2><<<grid, kThreads, 0, s>>>(rows, M, make_gen<2>(pkey, 1, 0), h, ctr); break;
-        default: k_dress_count<4><<<grid, kThreads, 0, s>>>(rows, M, make_gen<4>(pkey, 1, 0), h, ctr); break;
+        case 1: k_dress_count<1><<<grid, kThreads, 0, s>>>(rows, M, make_gen<1>(pkey, 1, 0), h, ctr); note_launch(); break;
+        case 2: k_dress_count<2><<<grid, kThreads, 0, s>>>(rows, M, make_gen<2>(pkey, 1, 0), h, ctr); note_launch(); break;
+        default: k_dress_count<4><<<grid, kThreads, 0, s>>>(rows, M, make_gen<4>(pkey, 1, 0), h, ctr); note_launch(); break;
     }
 }
 

@@ -361,7 +361,7 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
     for (int j = 0; j < W; ++j) { occ.x[j] = occ_words[j]; occ.z[j] = 0; }
     const int grid = expect_blocks();
     if (basis) {
-        k_abc<W, true><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials);
+        k_abc<W, true><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
     } else {
         size_t smem = (size_t)n_groups * 256 * sizeof(double);
         static bool attr = false;
@@ -369,7 +369,7 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
             cudaFuncSetAttribute(k_abc<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
             attr = true;
         }
-        k_abc<W, false><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials);
+        k_abc<W, false><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
     }
 }
 
@@ -382,7 +382,7 @@ void grad_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64
         attr = true;
     }
     size_t smem = (size_t)n_groups * 256 * sizeof(double);
-    k_grad_general<W><<<n_blocks, kThreads, smem, s>>>(rows, coef, M, cand, K, tables, n_groups, partials);
+    k_grad_general<W><<<n_blocks, kThreads, smem, s>>>(rows, coef, M, cand, K, tables, n_groups, partials); note_launch();
 }
 
 }  // namespace
@@ -399,17 +399,17 @@ void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, con
 }
 
 void launch_reduce3(const double* partials, int n, double* out3, cudaStream_t s) {
-    k_reduce3<<<1, kThreads, 0, s>>>(partials, n, out3);
+    k_reduce3<<<1, kThreads, 0, s>>>(partials, n, out3); note_launch();
 }
 
 void launch_reduce_cols(const double* partials, int rows, int cols, double* out, cudaStream_t s) {
-    k_reduce_cols<<<(cols + 127) / 128, 128, 0, s>>>(partials, rows, cols, out);
+    k_reduce_cols<<<(cols + 127) / 128, 128, 0, s>>>(partials, rows, cols, out); note_launch();
 }
 
 void launch_qmf_tables(const double* theta, const double* phi, int n, int n_groups, double* tables,
                        cudaStream_t s) {
     int total = n_groups * 256;
-    k_qmf_tables<<<(total + 255) / 256, 256, 0, s>>>(theta, phi, n, n_groups, tables);
+    k_qmf_tables<<<(total + 255) / 256, 256, 0, s>>>(theta, phi, n, n_groups, tables); note_launch();
 }
 
 void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ_words,
@@ -420,17 +420,17 @@ void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t 
     switch (Wd) {
         case 1: {
             Key<1> o{}; o.x[0] = occ_words[0];
-            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr);
+            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr); note_launch();
             break;
         }
         case 2: {
             Key<2> o{}; for (int j = 0; j < 2; ++j) o.x[j] = occ_words[j];
-            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr);
+            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr); note_launch();
             break;
         }
         default: {
             Key<4> o{}; for (int j = 0; j < 4; ++j) o.x[j] = occ_words[j];
-            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr);
+            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr); note_launch();
             break;
         }
     }

@@ -182,6 +182,142 @@ __global__ void k_compact_scatter(const uint8_t* __restrict__ flags, const uint6
     }
 }
 
+// Single-pass stable in-place compaction (decoupled look-back).  Tiles take
+// ids in launch order from a counter; a tile stages its kept rows in shared
+// memory, publishes its count, sums its predecessors' counts (waiting, with a
+// bound, for any not yet published), publishes its inclusive prefix and only
+// then writes.  Its destination [prefix, prefix + count) lies below its own
+// first row, and every earlier tile has read its rows before publishing, so no
+// row is overwritten before it is read.
+constexpr int kCompactTile = 1024;  // rows per tile (4 per thread)
+constexpr unsigned long long kStAgg = 1ull << 62, kStPrefix = 2ull << 62;
+constexpr unsigned long long kStMask = (1ull << 62) - 1;
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __restrict__ flags, uint64_t* rows,
+                                                              double* coef, int64_t n,
+                                                              unsigned long long* state,
+                                                              unsigned int* tile_counter,
+                                                              unsigned long long* total, DevCounters* ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem_raw);
+    double* s_c = reinterpret_cast<double*>(s_rows + (size_t)kCompactTile * 2 * W);
+    __shared__ uint32_t s_w[kThreads / 32];
+    __shared__ uint32_t s_run;
+    __shared__ unsigned int s_tile;
+    __shared__ unsigned long long s_prefix;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) {
+        s_tile = atomicAdd(tile_counter, 1u);
+        s_run = 0;
+    }
+    __syncthreads();
+    const unsigned int t = s_tile;
+    const int64_t base = (int64_t)t * kCompactTile;
+    for (int r = 0; r < kCompactTile / kThreads; ++r) {
+        const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+        const bool f = i < n && flags[i];
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
+        if (lane == 0) s_w[wid] = __popc(b);
+        __syncthreads();
+        uint32_t pos = s_run + __popc(b & ((1u << lane) - 1u));
+        for (int w = 0; w < wid; ++w) pos += s_w[w];
+        if (f) {
+            const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rows + (size_t)i * 2 * W);
+            ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rows + (size_t)pos * 2 * W);
+#pragma unroll
+            for (int j = 0; j < W; ++j) dst[j] = src[j];
+            s_c[pos] = coef[i];
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            uint32_t tot = 0;
+            for (int w = 0; w < kThreads / 32; ++w) tot += s_w[w];
+            s_run += tot;
+        }
+        __syncthreads();
+    }
+    const uint32_t count = s_run;
+    if (threadIdx.x == 0) {
+        __threadfence();
+        if (t == 0) {
+            atomicExch(state + t, kStPrefix | count);
+            s_prefix = 0;
+        } else {
+            atomicExch(state + t, kStAgg | count);
+            unsigned long long prefix = 0;
+            int64_t p = (int64_t)t - 1;
+            int spins = 0;
+            while (p >= 0) {
+                unsigned long long v = *(volatile unsigned long long*)(state + p);
+                if (v == 0) {
+                    if (++spins > (1 << 24)) {
+                        if (atomicCAS(&ctr->err, 0, (int)IQCC_ERR_TIMEOUT) == 0) ctr->err_where = 20;
+                        break;
+                    }
+                    __nanosleep(32);
+                    continue;
+                }
+                prefix += v & kStMask;
+                if ((v & ~kStMask) == kStPrefix) break;
+                --p;
+            }
+            atomicExch(state + t, kStPrefix | (prefix + count));
+            s_prefix = prefix;
+        }
+        if (base + kCompactTile >= n) *total = s_prefix + count;  // last tile
+    }
+    __syncthreads();
+    const unsigned long long out = s_prefix;
+    for (uint32_t k = threadIdx.x; k < count; k += kThreads) {
+        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(s_rows + (size_t)k * 2 * W);
+        ulonglong2* dst = reinterpret_cast<ulonglong2*>(rows + (size_t)(out + k) * 2 * W);
+#pragma unroll
+        for (int j = 0; j < W; ++j) dst[j] = src[j];
+        coef[out + k] = s_c[k];
+    }
+}
+
+// Coarse |g| (20 low mantissa bits cleared) digit histogram of all groups.
+__global__ void k_coarse_digit_hist(const double* __restrict__ g, int64_t G, int shift, uint64_t prefix,
+                                    uint64_t prefix_mask, unsigned long long* hist) {
+    __shared__ unsigned int h[256];
+    h[threadIdx.x] = 0;
+    __syncthreads();
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += s) {
+        const uint64_t b = ((uint64_t)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull) & ~((1ull << 20) - 1ull);
+        if ((b & prefix_mask) != prefix) continue;
+        atomicAdd(&h[(b >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (h[threadIdx.x]) atomicAdd(hist + threadIdx.x, (unsigned long long)h[threadIdx.x]);
+}
+
+// Indices of groups whose coarse |g| >= t (at most cap of them are written).
+__global__ void k_collect_ge(const double* __restrict__ g, int64_t G, uint64_t t, uint32_t* idx, int64_t cap,
+                             unsigned long long* count) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < G; i += s) {
+        const uint64_t b = ((uint64_t)__double_as_longlong(g[i]) & 0x7FFFFFFFFFFFFFFFull) & ~((1ull << 20) - 1ull);
+        if (b < t) continue;
+        const unsigned long long k = atomicAdd(count, 1ull);
+        if ((int64_t)k < cap) idx[k] = (uint32_t)i;
+    }
+}
+
+// skeys for a listed subset of groups (same layout as k_dis_sort_keys).
+__global__ void k_dis_sort_keys_sub(int Wd, const uint64_t* __restrict__ gkeys, const double* __restrict__ gsum,
+                                    const uint32_t* __restrict__ idx, int64_t k, uint64_t* skeys) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) {
+        const uint32_t g = idx[i];
+        uint64_t a = ((uint64_t)__double_as_longlong(gsum[g]) & 0x7FFFFFFFFFFFFFFFull) & ~((1ull << 20) - 1ull);
+        skeys[(size_t)g * (Wd + 1)] = ~a;
+        for (int w = 0; w < Wd; ++w) skeys[(size_t)g * (Wd + 1) + 1 + w] = gkeys[(size_t)g * Wd + (Wd - 1 - w)];
+    }
+}
+
 // ---------------------------------------------------------------- load / export
 
 __global__ void k_pack_rows(int W, int Wd, const uint64_t* __restrict__ x, const uint64_t* __restrict__ z,
@@ -343,7 +479,10 @@ size_t radix_sort_scratch_bytes(int64_t n) {
 }
 
 void launch_iota(uint32_t* p, int64_t n, cudaStream_t s) {
-    if (n > 0) k_iota<<<grid_stride_blocks(n), kThreads, 0, s>>>(p, n);
+    if (n > 0) {
+        k_iota<<<grid_stride_blocks(n), kThreads, 0, s>>>(p, n);
+        note_launch();
+    }
 }
 
 void radix_sort_indirect(const uint64_t* keys, int stride, const SortPlan& plan, uint32_t* perm,
@@ -361,7 +500,7 @@ void radix_sort_indirect(const uint64_t* keys, int stride, const SortPlan& plan,
     for (int w = 0; w < stride; ++w) { init[w] = 0ull; init[stride + w] = ~0ull; }
     cudaMemcpyAsync(orand, init, sizeof(unsigned long long) * 2 * stride, cudaMemcpyHostToDevice, s);
     k_word_orand<<<grid_stride_blocks(n), kThreads, 2 * stride * sizeof(unsigned long long), s>>>(keys, stride, perm,
-                                                                                                 n, orand);
+                                                                                                 n, orand); note_launch();
     unsigned long long host_orand[18];
     cudaMemcpyAsync(host_orand, orand, sizeof(unsigned long long) * 2 * stride, cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -372,9 +511,9 @@ void radix_sort_indirect(const uint64_t* keys, int stride, const SortPlan& plan,
         const uint64_t varying = host_orand[word] ^ host_orand[stride + word];
         for (int shift = 0; shift < 64; shift += 8) {
             if (((varying >> shift) & 255ull) == 0) continue;
-            k_sort_hist<<<(unsigned)nb, kThreads, 0, s>>>(keys, stride, word, shift, a, n, hist, nb);
-            k_scan_u32<<<1, 1024, 0, s>>>(hist, 256 * nb);
-            k_sort_scatter<<<(unsigned)nb, kThreads, 0, s>>>(keys, stride, word, shift, a, b, n, hist, nb);
+            k_sort_hist<<<(unsigned)nb, kThreads, 0, s>>>(keys, stride, word, shift, a, n, hist, nb); note_launch();
+            k_scan_u32<<<1, 1024, 0, s>>>(hist, 256 * nb); note_launch();
+            k_sort_scatter<<<(unsigned)nb, kThreads, 0, s>>>(keys, stride, word, shift, a, b, n, hist, nb); note_launch();
             uint32_t* t = a; a = b; b = t;
         }
     }
@@ -393,25 +532,92 @@ void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, 
     const int64_t nb = n_tiles(n);
     uint32_t* counts = (uint32_t*)scratch;
     uint32_t* offsets = counts + nb;
-    k_flag_count<<<(unsigned)nb, kThreads, 0, s>>>(flags, n, counts);
+    k_flag_count<<<(unsigned)nb, kThreads, 0, s>>>(flags, n, counts); note_launch();
     cudaMemcpyAsync(offsets, counts, nb * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s);
-    k_scan_u32<<<1, 1024, 0, s>>>(offsets, nb);
-    k_total<<<1, 1, 0, s>>>(offsets, counts + nb - 1, nb, count);
+    k_scan_u32<<<1, 1024, 0, s>>>(offsets, nb); note_launch();
+    k_total<<<1, 1, 0, s>>>(offsets, counts + nb - 1, nb, count); note_launch();
     switch (Wd) {
-        case 1: k_compact_scatter<1><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); break;
-        case 2: k_compact_scatter<2><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); break;
-        default: k_compact_scatter<4><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); break;
+        case 1: k_compact_scatter<1><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); note_launch(); break;
+        case 2: k_compact_scatter<2><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); note_launch(); break;
+        default: k_compact_scatter<4><<<(unsigned)nb, kThreads, 0, s>>>(flags, rows_in, c_in, rows_out, c_out, n, offsets); note_launch(); break;
+    }
+}
+
+size_t compact_inplace_scratch_bytes(int64_t n) {
+    return ((size_t)((n + kCompactTile - 1) / kCompactTile) + 1) * sizeof(unsigned long long) + 256;
+}
+
+void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double* coef, int64_t n, void* scratch,
+                            unsigned long long* count, DevCounters* ctr, cudaStream_t s) {
+    const int64_t nt = (n + kCompactTile - 1) / kCompactTile;
+    if (n <= 0) {
+        cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
+        return;
+    }
+    unsigned long long* state = (unsigned long long*)scratch;
+    unsigned int* tile_counter = (unsigned int*)(state + nt);
+    cudaMemsetAsync(scratch, 0, (size_t)(nt + 1) * sizeof(unsigned long long), s);
+    const size_t smem = (size_t)kCompactTile * (16 * Wd + 8);
+    switch (Wd) {
+        case 1: {
+            static bool a = false;
+            if (!a) { cudaFuncSetAttribute(k_compact_inplace<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
+            k_compact_inplace<1><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr); note_launch();
+            break;
+        }
+        case 2: {
+            static bool a = false;
+            if (!a) { cudaFuncSetAttribute(k_compact_inplace<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
+            k_compact_inplace<2><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr); note_launch();
+            break;
+        }
+        default: {
+            static bool a = false;
+            if (!a) { cudaFuncSetAttribute(k_compact_inplace<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
+            k_compact_inplace<4><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr); note_launch();
+            break;
+        }
+    }
+}
+
+void launch_coarse_digit_hist(const double* g, int64_t G, int shift, uint64_t prefix, uint64_t prefix_mask,
+                              unsigned long long* hist, cudaStream_t s) {
+    if (G > 0) {
+        k_coarse_digit_hist<<<grid_stride_blocks(G), kThreads, 0, s>>>(g, G, shift, prefix, prefix_mask, hist);
+        note_launch();
+    }
+}
+
+void launch_collect_ge(const double* g, int64_t G, uint64_t t, uint32_t* idx, int64_t cap, unsigned long long* count,
+                       cudaStream_t s) {
+    if (G > 0) {
+        k_collect_ge<<<grid_stride_blocks(G), kThreads, 0, s>>>(g, G, t, idx, cap, count);
+        note_launch();
+    }
+}
+
+void launch_dis_sort_keys_sub(int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* idx, int64_t k,
+                              uint64_t* skeys, cudaStream_t s) {
+    if (k > 0) {
+        k_dis_sort_keys_sub<<<grid_stride_blocks(k), kThreads, 0, s>>>(Wd, gkeys, gsum, idx, k, skeys);
+        note_launch();
     }
 }
 
 void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n,
                       cudaStream_t s) {
-    if (n > 0) k_pack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, x, z, rows, n);
+    if (n > 0) {
+        k_pack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, x, z, rows, n);
+        note_launch();
+    }
 }
 
 void launch_unpack_rows(int W, int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
                         uint64_t* x, uint64_t* z, double* c, int64_t n, cudaStream_t s) {
-    if (n > 0) k_unpack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, rows, coef, perm, x, z, c, n);
+    if (n > 0) {
+        k_unpack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, rows, coef, perm, x, z, c, n);
+        note_launch();
+    }
 }
 
 void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,
@@ -419,9 +625,9 @@ void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uin
     if (n <= 0) return;
     int g = grid_stride_blocks(n);
     switch (Wd) {
-        case 1: k_sum_runs<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); break;
-        case 2: k_sum_runs<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); break;
-        default: k_sum_runs<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); break;
+        case 1: k_sum_runs<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); note_launch(); break;
+        case 2: k_sum_runs<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); note_launch(); break;
+        default: k_sum_runs<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); note_launch(); break;
     }
 }
 
@@ -430,40 +636,55 @@ void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const 
     if (n <= 0) return;
     int g = grid_stride_blocks(n);
     switch (Wd) {
-        case 1: k_gather_rows<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); break;
-        case 2: k_gather_rows<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); break;
-        default: k_gather_rows<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); break;
+        case 1: k_gather_rows<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); note_launch(); break;
+        case 2: k_gather_rows<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); note_launch(); break;
+        default: k_gather_rows<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, rows_out, c_out); note_launch(); break;
     }
 }
 
 void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags, unsigned long long* count,
                         cudaStream_t s) {
-    if (n > 0) k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count);
+    if (n > 0) {
+        k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count);
+        note_launch();
+    }
 }
 
 void launch_abs_digit_hist(const double* coef, const uint8_t* flags, int64_t n, int shift, uint64_t prefix,
                            uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s) {
     if (n > 0)
-        k_abs_digit_hist<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift, prefix, prefix_mask, hist);
+        k_abs_digit_hist<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift, prefix, prefix_mask, hist); note_launch();
 }
 
 void launch_budget_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t t_bits, uint32_t* tie_idx,
                          unsigned long long* tie_count, cudaStream_t s) {
-    if (n > 0) k_budget_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, t_bits, tie_idx, tie_count);
+    if (n > 0) {
+        k_budget_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, t_bits, tie_idx, tie_count);
+        note_launch();
+    }
 }
 
 void launch_set_flags(const uint32_t* idx, int64_t k, uint8_t* flags, cudaStream_t s) {
-    if (k > 0) k_set_flags<<<grid_stride_blocks(k), kThreads, 0, s>>>(idx, k, flags);
+    if (k > 0) {
+        k_set_flags<<<grid_stride_blocks(k), kThreads, 0, s>>>(idx, k, flags);
+        note_launch();
+    }
 }
 
 void launch_dis_sort_keys(int Wd, const uint64_t* gkeys, const double* gsum, int64_t G, uint64_t* skeys,
                           cudaStream_t s) {
-    if (G > 0) k_dis_sort_keys<<<grid_stride_blocks(G), kThreads, 0, s>>>(Wd, gkeys, gsum, G, skeys);
+    if (G > 0) {
+        k_dis_sort_keys<<<grid_stride_blocks(G), kThreads, 0, s>>>(Wd, gkeys, gsum, G, skeys);
+        note_launch();
+    }
 }
 
 void launch_dis_export(int W, int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* perm, int64_t k,
                        uint64_t* ox, uint64_t* oz, double* og, cudaStream_t s) {
-    if (k > 0) k_dis_export<<<grid_stride_blocks(k), kThreads, 0, s>>>(W, Wd, gkeys, gsum, perm, k, ox, oz, og);
+    if (k > 0) {
+        k_dis_export<<<grid_stride_blocks(k), kThreads, 0, s>>>(W, Wd, gkeys, gsum, perm, k, ox, oz, og);
+        note_launch();
+    }
 }
 
 }  // namespace iqcc

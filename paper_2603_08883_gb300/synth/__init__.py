@@ -259,8 +259,8 @@ class Workload:
     n_iter: int
     n_gen: int
     eps: float
-    max_terms: int                 # <= 0: no cap
-    capacity: int                  # rows reserved on the device
+    max_terms: int                 # term limit after every dress; <= 0: none
+    capacity: int                  # admission limit in rows (2 x max_terms covers one dress)
     notes: str = field(default="")
 
     @property
@@ -271,9 +271,9 @@ class Workload:
 WORKLOADS = {
     "jw8": Workload("jw8", 8, 4, "plain", "uniform", 3, 2, 0.0, 0, 1 << 14,
                     "8 qubits, 4 orbitals, random QMF angles, no pruning"),
-    "jw24": Workload("jw24", 24, 12, "decay", "basis", 20, 4, 1e-10, 0, 1 << 25,
+    "jw24": Workload("jw24", 24, 12, "decay", "basis", 20, 4, 1e-10, 0, 1 << 30,
                      "24 qubits, 12 orbitals with exp(-d/3) decay, prune 1e-10"),
-    "jw100": Workload("jw100", 100, 50, "dblock", "basis", 10, 8, 1e-8, 800_000_000, 800_000_000,
+    "jw100": Workload("jw100", 100, 50, "dblock", "basis", 10, 8, 1e-8, 800_000_000, 1_600_000_000,
                       "100 qubits, 50 orbitals, strongly coupled 10-orbital block, prune 1e-8, "
                       "term cap 8e8"),
 }

@@ -277,3 +277,23 @@ def test_jw24_iterations_teacher_forced_and_free():
         assert rf["energy"] == pytest.approx(ro["energy"], abs=1e-9)
         rs = iqcc.iqcc_iterate(Hs, th, ph, w.n_gen, w.eps, w.max_terms)
         assert rs["energy"] == pytest.approx(ro["energy"], abs=1e-9)
+
+
+def test_term_limit_inside_the_iteration():
+    """With a small term limit the cut happens after every dress; the GPU,
+    given the oracle's generators and amplitudes, keeps the same strings."""
+    w = synth.WORKLOADS["jw24"]
+    n, x, z, c = synth.workload_hamiltonian(w)
+    th, ph = synth.workload_angles(w)
+    cap = 60_000
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=2 * cap)
+    for it in range(3):
+        ro = o.iterate(th, ph, w.n_gen, w.eps, cap)
+        rg = iqcc.iqcc_iterate(H, th, ph, w.n_gen, w.eps, cap, forced_x=ro["gx"], forced_z=ro["gz"],
+                               forced_tau=ro["tau"])
+        assert rg["M"] <= cap and rg["M_peak"] <= 2 * cap
+        bad = compare(iqcc.iqcc_export(H), o.export(), eps=w.eps)
+        # strings at the cut's threshold may differ by rounding; allow a handful
+        assert len(bad) <= 8, bad[:8]
+        assert rg["energy"] == pytest.approx(ro["energy"], abs=1e-9)

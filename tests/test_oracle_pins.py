@@ -328,3 +328,26 @@ def test_canonical_export_order():
     xs, zs, cs = oracle.Oracle(n, x, z, c).export()
     keys = [tuple(xs[i][::-1]) + tuple(zs[i][::-1]) for i in range(len(cs))]
     assert keys == sorted(keys)
+
+
+def test_iteration_applies_the_term_limit_after_every_dress():
+    """orc_iterate = the pinned primitives in App. A order: each dress followed by
+    a cut to max_terms when exceeded, then (eps, max_terms) compression."""
+    w = synth.WORKLOADS["jw8"]
+    n, x, z, c = synth.workload_hamiltonian(w)
+    th, ph = synth.workload_angles(w)
+    cap = 500
+    a = oracle.Oracle(n, x, z, c)
+    ra = a.iterate(th, ph, 3, 1e-3, cap)
+    b = oracle.Oracle(n, x, z, c)
+    removed = 0
+    for k in range(len(ra["tau"])):
+        _, bb, cc = b.abc(ra["gx"][k], ra["gz"][k], th, ph)
+        assert math.atan2(-cc, -bb) == ra["tau"][k]
+        b.dress(ra["gx"][k], ra["gz"][k], ra["tau"][k])
+        if len(b) > cap:
+            removed += b.prune(0.0, cap)
+    removed += b.prune(1e-3, cap)
+    assert a.as_dict() == b.as_dict()
+    assert ra["removed"] == removed and removed > 0
+    assert ra["energy"] == b.energy(th, ph)
