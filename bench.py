@@ -16,6 +16,7 @@ the path has no cross-rank exchange in this configuration).
 from __future__ import annotations
 
 import argparse
+import faulthandler
 import json
 import os
 import statistics
@@ -205,6 +206,7 @@ def run_gpu(args):
     n, x, z, c = synth.workload_hamiltonian(w)
     th, ph = synth.workload_angles(w)
     M0 = len(c)
+    log(f"generated {w.name}: n={n} M0={M0}")
     stream = torch.cuda.current_stream()
     capacity = w.capacity
 
@@ -215,8 +217,12 @@ def run_gpu(args):
 
     # ---------------- device-resident run
     H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=capacity)
-    for _ in range(args.warmup):
-        iqcc.iqcc_iterate(H, th, ph, w.n_gen, w.eps, w.max_terms)
+    log(f"loaded: M={len(H)}")
+    for it in range(args.warmup):
+        r = iqcc.iqcc_iterate(H, th, ph, w.n_gen, w.eps, w.max_terms)
+        free_b, total_b = torch.cuda.mem_get_info()
+        log(f"warmup {it}: M {r['M_before']} -> peak {r['M_peak']} -> {r['M']}, E={r['energy']:.9f}, "
+            f"device free {free_b / 2**30:.1f} GiB")
     M_start = len(H)
     flush = M_start * (16 * ((n + 63) // 64) + 8) < 2 * L2_BYTES
     scratch = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda") if flush else None
@@ -236,6 +242,7 @@ def run_gpu(args):
         barrier()
         wall = time.perf_counter() - t0
     dev_s = ev0.elapsed_time(ev1) / 1e3
+    log(f"timed: {args.steps} iterations in {dev_s:.3f} s; M {[r['M'] for r in recs]}")
     stats = iqcc.iqcc_get_stats(H)
     dressed = sum(r["dressed_terms"] for r in recs)
     t_max = dev_s
@@ -280,6 +287,7 @@ def run_gpu(args):
             m = len(oc)
             e_dressed += r["dressed_terms"]
             Hk.close()
+            log(f"e2e step {k}: M -> {m}")
         barrier()
         e_wall = time.perf_counter() - t0
         e2e = {"value": e_dressed / e_wall, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
@@ -340,7 +348,14 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def log(msg):
+    if int(os.environ.get("RANK", "0")) == 0:
+        sys.stderr.write(f"[bench {time.strftime('%H:%M:%S')}] {msg}\n")
+        sys.stderr.flush()
+
+
 def main():
+    faulthandler.enable()
     args = parse()
     if args.impl == "reference":
         run_reference(args)

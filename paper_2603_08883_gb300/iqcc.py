@@ -2,8 +2,8 @@
 
 Every function below has the name of the C entry point it calls (see
 ``include/iqcc.h``) and does no arithmetic of the method itself.  PyTorch, when
-present, supplies the CUDA stream and the device allocator (its caching
-allocator) to the library.  There is no CPU fallback: importing this module
+present, supplies the CUDA stream (and, on request, the device allocator) to
+the library.  There is no CPU fallback: importing this module
 raises when the compiled library is missing, and creating a Hamiltonian raises
 when no CUDA device is visible.
 """
@@ -65,7 +65,8 @@ class iqcc_stats(ctypes.Structure):
                 ("n_energy", ctypes.c_int64), ("energy_kernel_ms", ctypes.c_double),
                 ("energy_bytes", ctypes.c_double), ("prune_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
                 ("hash_ms", ctypes.c_double), ("hash_rebuilds", ctypes.c_int64), ("rows_allocated", ctypes.c_int64),
-                ("hash_slots", ctypes.c_int64), ("words", ctypes.c_int), ("pad", ctypes.c_int)]
+                ("hash_slots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("words", ctypes.c_int),
+                ("pad", ctypes.c_int)]
 
 
 def _sig(name, res, args):
@@ -108,8 +109,11 @@ def _f64(a, n=None):
     return a, a.ctypes.data_as(_f64p)
 
 
-def _torch_hooks(device):
-    """(stream handle, alloc callback, free callback) from PyTorch, or Nones."""
+def _torch_hooks(device, torch_alloc):
+    """(stream handle, alloc callback, free callback) from PyTorch, or Nones.
+    The stream is PyTorch's current stream; device memory comes from PyTorch's
+    caching allocator only when ``torch_alloc`` (else the library's cudaMalloc,
+    which returns freed memory to the device at once)."""
     try:
         import torch
     except ImportError:
@@ -118,6 +122,8 @@ def _torch_hooks(device):
         return None, None, None
     dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
     stream = torch.cuda.current_stream(dev)
+    if not torch_alloc:
+        return stream.cuda_stream, None, None
 
     def _alloc(size, _user):
         try:
@@ -126,7 +132,10 @@ def _torch_hooks(device):
             return None
 
     def _free(ptr, _user):
-        torch.cuda.caching_allocator_delete(int(ptr))
+        try:
+            torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
 
     return stream.cuda_stream, ALLOC_FN(_alloc), FREE_FN(_free)
 
@@ -161,15 +170,16 @@ class Hamiltonian:
 
 
 def iqcc_load_hamiltonian(n_qubits: int, x, z, coef, capacity: int = 0, max_probe: int = 0,
-                          use_torch: bool = True, device=None) -> Hamiltonian:
-    """Load H = sum_k coef[k] P(x[k], z[k]) onto the GPU (iqcc_load_hamiltonian)."""
+                          use_torch: bool = True, device=None, torch_alloc: bool = False) -> Hamiltonian:
+    """Load H = sum_k coef[k] P(x[k], z[k]) onto the GPU (iqcc_load_hamiltonian).
+    With ``use_torch`` the library runs on PyTorch's current stream."""
     W = (n_qubits + 63) // 64
     xa, xp = _u64(x, (-1, W))
     za, zp = _u64(z, (-1, W))
     ca, cp = _f64(coef)
     if not (len(xa) == len(za) == len(ca)):
         raise ValueError("x, z and coef lengths differ")
-    stream, alloc, free = _torch_hooks(device) if use_torch else (None, None, None)
+    stream, alloc, free = _torch_hooks(device, torch_alloc) if use_torch else (None, None, None)
     opts = iqcc_opts(n_qubits, capacity, max_probe, stream, alloc or ALLOC_FN(), free or FREE_FN(), None)
     h = _vp()
     st = _load(ctypes.byref(h), ctypes.byref(opts), len(ca), xp, zp, cp)

@@ -67,3 +67,33 @@ def test_argument_errors_before_any_device_work(lib):
         iqcc.iqcc_load_hamiltonian(3, np.array([[8]], np.uint64), np.zeros((1, 1), np.uint64), np.ones(1),
                                    use_torch=False)
     assert e.value.status == 1
+
+
+def test_ctypes_structs_match_the_header(tmp_path):
+    """Size and field offsets of every struct the binding mirrors, as gcc lays
+    them out from include/iqcc.h."""
+    import subprocess
+    from paper_2603_08883_gb300 import iqcc
+    structs = {"iqcc_opts": iqcc.iqcc_opts, "iqcc_iter_opts": iqcc.iqcc_iter_opts,
+               "iqcc_iter_result": iqcc.iqcc_iter_result, "iqcc_stats": iqcc.iqcc_stats}
+    lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/iqcc.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            c_field = "free" if field == "free" else field
+            lines.append(f'printf("{name} {field} %zu\\n", offsetof({name}, {c_field}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call(["gcc", "-std=c99", "-o", str(exe), str(src)])
+    out = subprocess.check_output([str(exe)], text=True).split("\n")
+    got = {}
+    for line in out:
+        if line:
+            name, field, val = line.split()
+            got[(name, field)] = int(val)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)

@@ -135,7 +135,8 @@ def test_dis_basis_matches_oracle(n, seed):
             assert (gx[i].tobytes(), gz[i].tobytes()) == (ox[i].tobytes(), oz[i].tobytes())
     # the capped query returns the head of the same order
     hx, hz, hg = iqcc.iqcc_dis_gradients(H, th, ph, cap=5)
-    assert np.array_equal(hx, gx[:5]) and np.array_equal(hg, gg[:5])
+    assert np.array_equal(hx, gx[:5])
+    assert np.allclose(hg, gg[:5], rtol=1e-12, atol=1e-14)   # FP64 atomics: order of the group sums varies
 
 
 @pytest.mark.parametrize("n,seed", [(5, 1), (12, 2), (70, 3)])
@@ -297,3 +298,20 @@ def test_term_limit_inside_the_iteration():
         # strings at the cut's threshold may differ by rounding; allow a handful
         assert len(bad) <= 8, bad[:8]
         assert rg["energy"] == pytest.approx(ro["energy"], abs=1e-9)
+
+
+def test_torch_caching_allocator_path():
+    """Device memory from PyTorch's caching allocator through the alloc/free hooks."""
+    n = 30
+    _, x, z, c = synth.random_hamiltonian(n, 20_000, 12)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, torch_alloc=True)
+    rng = np.random.Generator(np.random.PCG64(12))
+    for _ in range(3):
+        gx, gz = synth.random_generator(n, rng)
+        iqcc.iqcc_dress(H, gx, gz, [0.4])
+        o.dress(gx, gz, 0.4)
+    iqcc.iqcc_prune(H, 1e-4)
+    o.prune(1e-4)
+    assert not compare(iqcc.iqcc_export(H), o.export(), eps=1e-4)
+    H.close()
