@@ -125,6 +125,9 @@ struct Carver {
     }
 };
 
+// The real carve must end inside the scratch allocation (guards the dry-run sizing).
+bool carve_fits(const iqcc_ctx* ctx, const Carver& cv) { return cv.off <= ctx->scratch.bytes; }
+
 size_t row_bytes(const iqcc_ctx* ctx) { return (size_t)16 * ctx->Wd; }
 
 HashView hash_view(const iqcc_ctx* ctx) {
@@ -263,6 +266,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     double* out3 = cv.take<double>(4);
     double* angles = cv.take<double>(2 * ctx->n);
     double* tables = cv.take<double>((size_t)n_groups(ctx) * 256);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
     if (!basis) {
         iqcc_status st = upload_tables(ctx, theta, phi, angles, tables);
         if (st) return st;
@@ -357,10 +361,6 @@ struct SortArea {
     size_t tmp_bytes;
 };
 
-size_t sort_area_bytes(int64_t n) {
-    return align256((size_t)n * 4 + 1) * 2 + align256(radix_sort_scratch_bytes(n));
-}
-
 SortArea carve_sort(Carver& cv, int64_t n) {
     SortArea s;
     s.a = cv.take<uint32_t>(n);
@@ -368,6 +368,13 @@ SortArea carve_sort(Carver& cv, int64_t n) {
     s.tmp_bytes = radix_sort_scratch_bytes(n);
     s.tmp = cv.take<char>(s.tmp_bytes);
     return s;
+}
+
+// Bytes carve_sort takes (a dry run of the same carve, so the two never differ).
+size_t sort_area_bytes(int64_t n) {
+    Carver dry;
+    carve_sort(dry, n);
+    return dry.off;
 }
 
 iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed) {
@@ -387,6 +394,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
     SortArea sa = carve_sort(cv, M);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
     DevCounters* c = dctr(ctx);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -492,6 +500,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     uint64_t* cand = cv.take<uint64_t>(16 * 2 * 4);
     double* partials = cv.take<double>(std::max<size_t>((size_t)nblk * 16, 256));
     double* colsum = cv.take<double>(16);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
     DevCounters* c = dctr(ctx);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -620,6 +629,7 @@ iqcc_status gradients_given(iqcc_ctx* ctx, const double* theta, const double* ph
     uint64_t* cand = cv.take<uint64_t>(16 * 2 * 4);
     double* partials = cv.take<double>((size_t)nblk * 16);
     double* colsum = cv.take<double>(16);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
     iqcc_status st = upload_tables(ctx, theta, phi, angles, tables);
     if (st) return st;
     for (int64_t k0 = 0; k0 < K; k0 += 16) {
@@ -723,6 +733,10 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
         uint8_t* flags = cv.take<uint8_t>(n);
         char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(n));
         SortArea sa = carve_sort(cv, n);
+        if (!carve_fits(ctx, cv)) {
+            fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+            return bail(IQCC_ERR_STATE);
+        }
         cudaStream_t s = ctx->stream;
         iqcc_status st = IQCC_OK;
         do {
@@ -929,6 +943,7 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
     uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
     double* sc = cv.take<double>(k);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
     launch_iota(sa.a, M, ctx->stream);
     uint32_t* sorted = nullptr;
     radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, M, &sorted, sa.tmp, sa.tmp_bytes,
