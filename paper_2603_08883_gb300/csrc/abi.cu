@@ -650,6 +650,11 @@ iqcc_status gradients_given(iqcc_ctx* ctx, const double* theta, const double* ph
 
 }  // namespace
 
+namespace iqcc {
+// Message for iqcc_last_error(NULL) from entry points that have no context.
+void set_thread_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace iqcc
+
 extern "C" {
 
 iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t n_terms, const uint64_t* x,

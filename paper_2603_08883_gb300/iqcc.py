@@ -93,6 +93,8 @@ _stats = _sig("iqcc_get_stats", _c, [_vp, ctypes.POINTER(iqcc_stats)])
 _reset = _sig("iqcc_reset_stats", _c, [_vp])
 _err = _sig("iqcc_last_error", ctypes.c_char_p, [_vp])
 _free = _sig("iqcc_free", None, [_vp])
+_energy_noalloc = _sig("iqcc_qmf_energy_noalloc", _c, [ctypes.c_int, ctypes.c_int64, _vp, _vp, _f64p, _f64p, _vp,
+                                                       _f64p])
 
 
 def _u64(a, shape=None):
@@ -317,3 +319,31 @@ def iqcc_free(H: Hamiltonian) -> None:
 def exported_symbols():
     """Names of the C entry points this binding resolves."""
     return sorted(n for n in globals() if n.startswith("iqcc_") and callable(globals()[n]))
+
+
+def iqcc_qmf_energy_noalloc(n_qubits: int, d_rows, d_coef, n_terms: int, theta, phi, stream=None) -> float:
+    """QMF energy of rows already on the device, with no device allocation.
+
+    ``d_rows`` / ``d_coef``: device addresses (ints) or CUDA tensors holding
+    [n_terms][2*Wd] uint64 rows (x words then z words, Wd = 1, 2 or 4) and
+    [n_terms] float64 coefficients.  ``stream``: a cudaStream_t handle, a
+    torch stream, or None (then PyTorch's current stream when available)."""
+    def addr(v):
+        return int(v.data_ptr()) if hasattr(v, "data_ptr") else int(v)
+
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            stream = None
+    elif hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    ta, tp = _f64(theta, n_qubits)
+    pa, pp = _f64(phi, n_qubits)
+    e = ctypes.c_double(0.0)
+    st = _energy_noalloc(int(n_qubits), int(n_terms), addr(d_rows), addr(d_coef), tp, pp, stream, ctypes.byref(e))
+    if st != 0:
+        raise IqccError(st, _err(None).decode())
+    return e.value
