@@ -330,13 +330,7 @@ iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
     const int64_t n_anti = (int64_t)ctx->h_counters->n_anti;
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    // index the appended rows
-    cudaEvent_t h0 = ctx->ev0, h1 = ctx->ev1;
-    CK(cudaEventRecord(h0, ctx->stream));
-    launch_hash_insert(ctx->Wd, ctx->rows(), M, M + n_new, hash_view(ctx), c, ctx->stream);
-    CK_LAUNCH();
-    CK(cudaEventRecord(h1, ctx->stream));
-    ctx->M = M + n_new;
+    ctx->M = M + n_new;  // the dress kernel indexed the appended rows itself
     iqcc_stats& s = ctx->stats;
     s.n_dress++;
     s.dressed_terms += M;
@@ -344,11 +338,6 @@ iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
     s.appended += n_new;
     s.dress_kernel_ms += ms;
     s.dress_bytes += 16.0 * ctx->Wd * (double)M + 16.0 * (double)n_anti + (16.0 * ctx->Wd + 8.0) * (double)n_new;
-    st = read_counters(ctx);
-    if (st) return st;
-    float hms = 0;
-    cudaEventElapsedTime(&hms, h0, h1);
-    s.hash_ms += hms;
     return IQCC_OK;
 }
 
@@ -405,44 +394,72 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     if (st) return st;
     const int64_t kept = (int64_t)ctx->h_counters->aux;
     if (max_terms > 0 && kept > max_terms) {
-        // radix select of the max_terms-th largest |C| bit pattern, 8 bits at a time
-        int64_t need = max_terms;
+        // Radix select on the |C| bit pattern, 12 bits at a time from the top,
+        // until the bucket holding the max_terms-th largest value is small; the
+        // bucket's rows are then ordered exactly by (|C| desc, canonical key asc).
+        constexpr int64_t kBucketLimit = 1 << 16;
+        int64_t need = max_terms, bucket = kept;
         uint64_t prefix = 0, pmask = 0;
-        for (int shift = 56; shift >= 0; shift -= 8) {
-            CK(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), ctx->stream));
-            launch_abs_digit_hist(ctx->c(), flags, M, shift, prefix, pmask, hist, ctx->stream);
+        int hi = 63;
+        unsigned long long* hist12 = nullptr;
+        std::vector<unsigned long long> h(4096);
+        while (bucket > kBucketLimit && hi > 0) {
+            const int shift = std::max(0, hi - 12);
+            if (!hist12) {
+                if (!ensure(ctx, ctx->aux, 4096 * sizeof(unsigned long long)))
+                    return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+                hist12 = (unsigned long long*)ctx->aux.p;
+            }
+            CK(cudaMemsetAsync(hist12, 0, 4096 * sizeof(unsigned long long), ctx->stream));
+            launch_abs_digit_hist12(ctx->c(), flags, M, shift, prefix, pmask, hist12, ctx->stream);
             CK_LAUNCH();
-            unsigned long long h[256];
-            CK(cudaMemcpyAsync(h, hist, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                               ctx->stream));
             CK(cudaStreamSynchronize(ctx->stream));
             int64_t cum = 0;
             int sel = 0;
-            for (int d = 255; d >= 0; --d) {
+            for (int d = 4095; d >= 0; --d) {
                 if (cum + (int64_t)h[d] >= need) { sel = d; break; }
                 cum += (int64_t)h[d];
             }
             need -= cum;
+            bucket = (int64_t)h[sel];
             prefix |= (uint64_t)sel << shift;
-            pmask |= (uint64_t)255 << shift;
+            pmask |= (uint64_t)4095 << shift;
+            hi = shift;
         }
-        // strictly larger kept; the `need` smallest keys among the ties kept
+        pmask &= 0x7FFFFFFFFFFFFFFFull;
         CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-        launch_budget_flags(ctx->c(), flags, M, prefix, ties, &c->aux, ctx->stream);
+        launch_bucket_flags(ctx->c(), flags, M, prefix, pmask, ties, &c->aux, ctx->stream);
         CK_LAUNCH();
         st = read_counters(ctx);
         if (st) return st;
-        const int64_t n_ties = (int64_t)ctx->h_counters->aux;
-        if (need >= n_ties) {
-            launch_set_flags(ties, n_ties, flags, ctx->stream);
-        } else {
-            CK(cudaMemcpyAsync(sa.a, ties, (size_t)n_ties * 4, cudaMemcpyDeviceToDevice, ctx->stream));
-            uint32_t* sorted = nullptr;
-            radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, n_ties, &sorted, sa.tmp,
-                                sa.tmp_bytes, ctx->stream);
+        const int64_t n_cand = (int64_t)ctx->h_counters->aux;
+        if (need >= n_cand) {
+            launch_set_flags(ties, n_cand, flags, ctx->stream);
             CK_LAUNCH();
-            launch_set_flags(sorted, need, flags, ctx->stream);
+        } else {
+            const int stride = 2 * ctx->Wd + 1;
+            Carver dry;
+            dry.take<uint64_t>((size_t)n_cand * stride);
+            carve_sort(dry, n_cand);
+            if (!ensure(ctx, ctx->aux, dry.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+            Carver cv2{(char*)ctx->aux.p, 0};
+            uint64_t* skeys = cv2.take<uint64_t>((size_t)n_cand * stride);
+            SortArea ca = carve_sort(cv2, n_cand);
+            if (cv2.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+            launch_candidate_keys(ctx->Wd, ctx->rows(), ctx->c(), ties, n_cand, skeys, ctx->stream);
+            launch_iota(ca.a, n_cand, ctx->stream);
+            SortPlan plan{};
+            plan.n_words = stride;
+            plan.n_order = stride;
+            for (int w = 0; w < stride; ++w) plan.order[w] = w;
+            uint32_t* sorted = nullptr;
+            radix_sort_indirect(skeys, stride, plan, ca.a, ca.b, n_cand, &sorted, ca.tmp, ca.tmp_bytes, ctx->stream);
+            CK_LAUNCH();
+            launch_set_flags_sorted(ties, sorted, need, flags, ctx->stream);
+            CK_LAUNCH();
         }
-        CK_LAUNCH();
     }
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
     launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
@@ -994,6 +1011,7 @@ void iqcc_free(iqcc_ctx* ctx) {
     release(ctx, ctx->hash);
     release(ctx, ctx->counters);
     release(ctx, ctx->scratch);
+    release(ctx, ctx->aux);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -182,6 +182,7 @@ struct iqcc_ctx {
     iqcc::Buf counters;            // DevCounters
     iqcc::DevCounters* h_counters = nullptr;  // pinned host mirror
     iqcc::Buf scratch;             // general scratch (grows)
+    iqcc::Buf aux;                 // second scratch for sizes known only mid-call
     long long launch_base = 0;     // library launch count at the last stats reset
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 
@@ -287,6 +288,14 @@ void launch_abs_digit_hist(const double* coef, const uint8_t* flags, int64_t n, 
 void launch_budget_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t t_bits,
                          uint32_t* tie_idx, unsigned long long* tie_count, cudaStream_t s);
 void launch_set_flags(const uint32_t* idx, int64_t k, uint8_t* flags, cudaStream_t s);
+// term-limit select with 12-bit digits, then an exact sort of the threshold bucket
+void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n, int shift, uint64_t prefix,
+                             uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s);
+void launch_bucket_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
+                         uint32_t* cand, unsigned long long* n_cand, cudaStream_t s);
+void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, const uint32_t* cand, int64_t k,
+                           uint64_t* skeys, cudaStream_t s);
+void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s);
 
 // DIS candidate keys for the sort: [coarse |g| complement, x words...]
 void launch_dis_sort_keys(int Wd, const uint64_t* gkeys, const double* gsum, int64_t G, uint64_t* skeys,

@@ -10,7 +10,7 @@
 // looked up.  Exactly one member of each present pair - the one with a zero at
 // P's lowest set bit - rotates both coefficients; a row whose partner is
 // absent scales itself by cos(tau) and appends (Q, s sin(tau) C_T) behind the
-// M input rows.  q -> q xor P is a bijection, so appended keys are distinct and
+// M input rows, indexing it in the same pass.  q -> q xor P is a bijection, so appended keys are distinct and
 // absent from H: no duplicate merge is needed within one generator (the
 // "insert if unique, else add" merge of App. D, Eq. 18, done as a lookup).
 #include <cuda_runtime.h>
@@ -73,6 +73,22 @@ __device__ __forceinline__ bool insert(const Key<W>& k, uint32_t row, const Hash
     return false;
 }
 
+// Insert `entry` at or after `slot` in its probe sequence (the slot may have
+// been taken since it was seen empty).
+__device__ __forceinline__ bool insert_from(uint64_t entry, uint64_t slot, const HashView& h) {
+    uint64_t b = slot / kBucketSlots;
+    int k0 = (int)(slot % kBucketSlots);
+    for (int p = 0; p < h.max_probe; ++p) {
+        unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
+        for (int k = k0; k < 4; ++k)
+            if (atomicCAS(s + k, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot)
+                return true;
+        k0 = 0;
+        b = (b + 1) & h.bucket_mask;
+    }
+    return false;
+}
+
 template <int W>
 __device__ __forceinline__ bool bit_of(const Key<W>& k, int word, uint64_t mask) {
     uint64_t v = 0;
@@ -91,40 +107,129 @@ __global__ void k_hash_clear(uint64_t* slots, uint64_t n) {
         p[i] = make_ulonglong2(kEmptySlot, kEmptySlot);
 }
 
+// Index rows [lo, hi).  Four rows per thread: their bucket sectors are read
+// together, each row then claims the first empty slot it saw by CAS, and a row
+// that loses that slot continues its probe sequence one slot at a time.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_hash_insert(const uint64_t* __restrict__ rows, int64_t lo,
                                                           int64_t hi, HashView h, DevCounters* ctr) {
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += stride) {
-        Key<W> k = load_key<W>(rows, i);
-        if (!insert<W>(k, (uint32_t)i, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
+    constexpr int R = 4;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i0 = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < hi; i0 += R * stride) {
+        uint64_t entry[R], slot[R];
+        bool live[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int64_t i = i0 + r * stride;
+            live[r] = i < hi;
+            entry[r] = 0;
+            slot[r] = 0;
+            if (live[r]) {
+                const uint64_t hv = hash_key<W>(load_key<W>(rows, i));
+                entry[r] = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)i;
+                slot[r] = (hv & h.bucket_mask) * kBucketSlots;
+            }
+        }
+        ulonglong2 a[R], b[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (live[r]) {
+                const ulonglong2* p = reinterpret_cast<const ulonglong2*>(h.slots + slot[r]);
+                a[r] = __ldcg(p);
+                b[r] = __ldcg(p + 1);
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (!live[r]) continue;
+            int k = a[r].x == kEmptySlot ? 0 : a[r].y == kEmptySlot ? 1 : b[r].x == kEmptySlot ? 2
+                    : b[r].y == kEmptySlot ? 3 : 4;
+            if (k < 4 && atomicCAS(reinterpret_cast<unsigned long long*>(h.slots + slot[r] + k),
+                                   (unsigned long long)kEmptySlot, (unsigned long long)entry[r]) == kEmptySlot)
+                continue;
+            if (!insert_from(entry[r], slot[r] + (k < 4 ? k : 3), h)) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
+        }
     }
 }
 
-// One pass of Eq. 5 over rows [0, M).  rows_app is the same buffer as rows;
-// appended rows land at M + slot and are not visited by this pass.
+// Lookup that also reports the first empty slot met, where q would be inserted.
 template <int W>
-__global__ void __launch_bounds__(kThreads) k_dress(const uint64_t* __restrict__ rows, uint64_t* rows_app,
+__device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, const HashView& h,
+                                               const uint64_t* __restrict__ rows, uint64_t* empty_slot) {
+    const uint32_t fp = (uint32_t)(hv >> 32);
+    uint64_t b = hv & h.bucket_mask;
+    for (int p = 0; p < h.max_probe; ++p) {
+        const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
+        const ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
+        const uint64_t sl[4] = {s01.x, s01.y, s23.x, s23.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sl[k] == kEmptySlot) {
+                *empty_slot = b * kBucketSlots + k;
+                return -1;
+            }
+            if ((uint32_t)(sl[k] >> 32) == fp) {
+                const uint32_t idx = (uint32_t)sl[k];
+                const Key<W> r = load_key<W>(rows, idx);
+                if (key_equal<W>(r, q)) return (int64_t)idx;
+            }
+        }
+        b = (b + 1) & h.bucket_mask;
+    }
+    return -2;
+}
+
+constexpr int kWarpTile = 64;  // rows classified per warp before the probes
+
+// One pass of Eq. 5 over rows [0, M).  Each warp classifies a tile of 64 rows
+// (two per lane) and queues the anticommuting ones in shared memory, so that
+// every lane then works on one queued row: partner lookup, pair rotation or
+// append.  An appended partner is inserted into the index at the empty slot
+// where its lookup stopped.  Concurrent inserts leave every lookup correct:
+// slots only go from empty to full, a key present before the pass has no empty
+// slot ahead of it in its probe sequence, and an appended key is the partner
+// of exactly one row (q -> q xor P is a bijection), so no other lookup seeks
+// it.  rows_app is the same buffer as rows; appended rows land at M + slot and
+// are not visited by this pass.
+template <int W>
+__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64_t* __restrict__ rows, uint64_t* rows_app,
                                                     double* coef, int64_t M, Gen<W> g, HashView h,
                                                     DevCounters* ctr) {
+    __shared__ uint32_t s_queue[kThreads / 32][kWarpTile];
     const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const unsigned lt = (1u << lane) - 1u;
+    uint32_t* queue = s_queue[wid];
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
     unsigned n_anti = 0;
-    for (int64_t base = warp * 32; base < M; base += n_warps * 32) {
-        const int64_t i = base + lane;
-        bool append = false;
-        Key<W> q;
-        double c_new = 0.0;
-        if (i < M) {
-            Key<W> t = load_key<W>(rows, i);
-            if (anticommutes<W>(t, g.p)) {
-                ++n_anti;
+    for (int64_t base = warp * kWarpTile; base < M; base += n_warps * kWarpTile) {
+        int nq = 0;
+#pragma unroll
+        for (int r = 0; r < kWarpTile / 32; ++r) {
+            const int64_t i = base + r * 32 + lane;
+            bool a = false;
+            if (i < M) a = anticommutes<W>(load_key<W>(rows, i), g.p);
+            const unsigned m = __ballot_sync(FULL, a);
+            if (a) queue[nq + __popc(m & lt)] = (uint32_t)(r * 32 + lane);
+            nq += __popc(m);
+        }
+        __syncwarp();
+        n_anti += (lane == 0) ? (unsigned)nq : 0u;
+        for (int e0 = 0; e0 < nq; e0 += 32) {
+            const int e = e0 + lane;
+            bool append = false;
+            Key<W> q;
+            double c_new = 0.0;
+            uint64_t hv = 0, eslot = 0;
+            if (e < nq) {
+                const int64_t i = base + queue[e];
+                const Key<W> t = load_key<W>(rows, i);
                 q = key_xor<W>(t, g.p);
                 const double s = (double)product_sign<W>(t, g.yP, g.p, q);
                 const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
-                const int64_t j = lookup<W>(q, h, rows);
+                hv = hash_key<W>(q);
+                const int64_t j = lookup_slot<W>(q, hv, h, rows, &eslot);
                 if (j == -1) {
                     const double c = coef[i];
                     coef[i] = c * g.cos_t;
@@ -140,22 +245,23 @@ __global__ void __launch_bounds__(kThreads) k_dress(const uint64_t* __restrict__
                     set_error(ctr, IQCC_ERR_HASH_FULL, 2);
                 }
             }
-        }
-        const unsigned need = __ballot_sync(FULL, append);
-        if (need) {
-            const int leader = __ffs(need) - 1;
-            unsigned long long slot0 = 0;
-            if (lane == leader) slot0 = atomicAdd(&ctr->n_new, (unsigned long long)__popc(need));
-            slot0 = __shfl_sync(FULL, slot0, leader);
-            if (append) {
-                const int64_t r = M + (int64_t)slot0 + __popc(need & ((1u << lane) - 1u));
-                store_key<W>(rows_app, r, q);
-                coef[r] = c_new;
+            const unsigned need = __ballot_sync(FULL, append);
+            if (need) {
+                const int leader = __ffs(need) - 1;
+                unsigned long long slot0 = 0;
+                if (lane == leader) slot0 = atomicAdd(&ctr->n_new, (unsigned long long)__popc(need));
+                slot0 = __shfl_sync(FULL, slot0, leader);
+                if (append) {
+                    const int64_t r = M + (int64_t)slot0 + __popc(need & lt);
+                    store_key<W>(rows_app, r, q);
+                    coef[r] = c_new;
+                    const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)r;
+                    if (!insert_from(entry, eslot, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
+                }
             }
         }
+        __syncwarp();
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(FULL, n_anti, o);
     if (lane == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
 }
 

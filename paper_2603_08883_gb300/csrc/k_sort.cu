@@ -434,6 +434,64 @@ __global__ void k_set_flags(const uint32_t* __restrict__ idx, int64_t k, uint8_t
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) flags[idx[i]] = 1;
 }
 
+// 12-bit digit histogram of |C| bit patterns among kept rows whose higher bits
+// equal `prefix` (bits under `prefix_mask`).
+__global__ void k_abs_digit_hist12(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
+                                   int shift, uint64_t prefix, uint64_t prefix_mask, unsigned long long* hist) {
+    __shared__ unsigned int h[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        if (!flags[i]) continue;
+        const uint64_t b = abs_bits(coef[i]);
+        if ((b & prefix_mask) != prefix) continue;
+        atomicAdd(&h[(b >> shift) & 4095u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x)
+        if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
+}
+
+// Kept rows above the threshold bucket stay kept; rows in it become candidates
+// (listed, flag cleared); rows below are dropped.
+__global__ void k_bucket_flags(const double* __restrict__ coef, uint8_t* flags, int64_t n, uint64_t prefix,
+                               uint64_t prefix_mask, uint32_t* cand, unsigned long long* n_cand) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        if (!flags[i]) continue;
+        const uint64_t b = abs_bits(coef[i]) & prefix_mask;
+        if (b > prefix) continue;
+        flags[i] = 0;
+        if (b == prefix) cand[atomicAdd(n_cand, 1ull)] = (uint32_t)i;
+    }
+}
+
+// Sort keys of the candidates: [~|C| bits, x most significant word first, ..., z ...]:
+// ascending order = |C| descending, then canonical key ascending.
+template <int W>
+__global__ void k_candidate_keys(const uint64_t* __restrict__ rows, const double* __restrict__ coef,
+                                 const uint32_t* __restrict__ cand, int64_t k, uint64_t* skeys) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) {
+        const uint32_t r = cand[i];
+        const Key<W> key = load_key<W>(rows, r);
+        uint64_t* o = skeys + (size_t)i * (2 * W + 1);
+        o[0] = ~abs_bits(coef[r]);
+#pragma unroll
+        for (int w = 0; w < W; ++w) {
+            o[1 + w] = key.x[W - 1 - w];
+            o[1 + W + w] = key.z[W - 1 - w];
+        }
+    }
+}
+
+__global__ void k_set_flags_sorted(const uint32_t* __restrict__ cand, const uint32_t* __restrict__ order, int64_t k,
+                                   uint8_t* flags) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) flags[cand[order[i]]] = 1;
+}
+
 // ---------------------------------------------------------------- DIS ordering
 
 // skeys[g] = [~coarse(|g|), x[Wd-1], ..., x[0]]: ascending order of these words
@@ -667,6 +725,40 @@ void launch_budget_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t
 void launch_set_flags(const uint32_t* idx, int64_t k, uint8_t* flags, cudaStream_t s) {
     if (k > 0) {
         k_set_flags<<<grid_stride_blocks(k), kThreads, 0, s>>>(idx, k, flags);
+        note_launch();
+    }
+}
+
+void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n, int shift, uint64_t prefix,
+                             uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s) {
+    if (n > 0) {
+        k_abs_digit_hist12<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift, prefix, prefix_mask, hist);
+        note_launch();
+    }
+}
+
+void launch_bucket_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
+                         uint32_t* cand, unsigned long long* n_cand, cudaStream_t s) {
+    if (n > 0) {
+        k_bucket_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, prefix, prefix_mask, cand, n_cand);
+        note_launch();
+    }
+}
+
+void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, const uint32_t* cand, int64_t k,
+                           uint64_t* skeys, cudaStream_t s) {
+    if (k <= 0) return;
+    const int g = grid_stride_blocks(k);
+    switch (Wd) {
+        case 1: k_candidate_keys<1><<<g, kThreads, 0, s>>>(rows, coef, cand, k, skeys); note_launch(); break;
+        case 2: k_candidate_keys<2><<<g, kThreads, 0, s>>>(rows, coef, cand, k, skeys); note_launch(); break;
+        default: k_candidate_keys<4><<<g, kThreads, 0, s>>>(rows, coef, cand, k, skeys); note_launch(); break;
+    }
+}
+
+void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s) {
+    if (k > 0) {
+        k_set_flags_sorted<<<grid_stride_blocks(k), kThreads, 0, s>>>(cand, order, k, flags);
         note_launch();
     }
 }

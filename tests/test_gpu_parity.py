@@ -315,3 +315,19 @@ def test_torch_caching_allocator_path():
     o.prune(1e-4)
     assert not compare(iqcc.iqcc_export(H), o.export(), eps=1e-4)
     H.close()
+
+
+@pytest.mark.parametrize("cap", [150_001, 299_000, 20_000])
+def test_term_limit_select_on_large_sets(cap):
+    """More rows than the exact-sort bucket (65536): the 12-bit radix select
+    narrows the threshold bucket first; ties at the threshold in key order."""
+    n = 40
+    _, x, z, c = synth.random_hamiltonian(n, 320_000, 77)
+    c = np.round(c, 4)
+    c[c == 0] = 1e-4
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    assert iqcc.iqcc_prune(H, 0.0, cap) == o.prune(0.0, cap)
+    gx, gz, gc = iqcc.iqcc_export(H)
+    ox, oz, oc = o.export()
+    assert np.array_equal(gx, ox) and np.array_equal(gz, oz) and np.array_equal(gc, oc)
