@@ -375,6 +375,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     cv.take<unsigned long long>(256);
     cv.take<char>(compact_inplace_scratch_bytes(M));
     cv.take<uint32_t>(M);  // tie list
+    cv.take<uint32_t>(M);  // old row -> new row
     cv.off += sort_area_bytes(M);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
@@ -382,6 +383,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     unsigned long long* hist = cv.take<unsigned long long>(256);
     char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
+    uint32_t* new_row = cv.take<uint32_t>(M);
     SortArea sa = carve_sort(cv, M);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
@@ -462,7 +464,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
         }
     }
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
+    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream, new_row);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
@@ -474,8 +476,16 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     ctx->M = newM;
     *removed = M - newM;
     if (newM == M) return IQCC_OK;  // nothing moved
-    // rows moved: rebuild the index (same size)
-    return rebuild_hash(ctx, ctx->hash_slots ? ctx->hash_slots : pow2_at_least((uint64_t)newM * 2));
+    // rows moved: remap the index in place (kept keys keep their slots, removed keys become tombstones)
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    launch_hash_remap(hash_view(ctx), ctx->hash_slots, new_row, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float hms = 0;
+    cudaEventElapsedTime(&hms, ctx->ev0, ctx->ev1);
+    ctx->stats.hash_ms += hms;
+    return IQCC_OK;
 }
 
 // DIS candidates and gradients (n_cand == 0 path).  Leaves the ordered

@@ -17,6 +17,8 @@ namespace iqcc {
 // ----------------------------------------------------------------------------
 
 constexpr uint64_t kEmptySlot = ~0ull;        // hash slot never used
+constexpr uint64_t kTombSlot = ~1ull;         // hash slot whose row was removed (row field 0xFFFFFFFE)
+constexpr uint32_t kRowRemoved = 0xFFFFFFFFu; // compaction map entry of a removed row
 constexpr uint32_t kPendingGroup = 0xFFFFFFFEu;  // group slot claimed, key not yet published
 constexpr int kBucketSlots = 4;               // 4 x 8-byte slots = one 32-byte sector
 
@@ -207,6 +209,8 @@ long long launches();
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
+// after an in-place compaction with map new_row (old row -> new row or kRowRemoved)
+void launch_hash_remap(HashView h, uint64_t slots, const uint32_t* new_row, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
                         DevCounters* ctr, cudaStream_t s);
 void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
@@ -256,8 +260,10 @@ void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, 
 
 // single-pass in-place stable compaction of rows/coef by flags; kept count to *count
 size_t compact_inplace_scratch_bytes(int64_t n);
+// new_row (may be NULL): per old row, its new index or kRowRemoved
 void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double* coef, int64_t n, void* scratch,
-                            unsigned long long* count, DevCounters* ctr, cudaStream_t s);
+                            unsigned long long* count, DevCounters* ctr, cudaStream_t s,
+                            uint32_t* new_row = nullptr);
 
 // DIS top-k: coarse |g| radix select, collect, sort of the collected subset
 void launch_coarse_digit_hist(const double* g, int64_t G, int shift, uint64_t prefix, uint64_t prefix_mask,

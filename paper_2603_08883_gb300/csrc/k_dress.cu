@@ -2,17 +2,22 @@
 // library convention, Eq. 6) and the open-addressing index it relies on.
 //
 // Index: 2^k buckets of 4 eight-byte slots (one 32-byte sector); a slot holds
-// (fingerprint32 << 32) | row32, ~0 when empty.  Rows are never deleted from
-// the index; compression rebuilds it.  Lookups stop at the first empty slot.
+// (fingerprint32 << 32) | row32, kEmptySlot when never used and kTombSlot
+// when its row was removed by compression.  Lookups skip tombstones and stop
+// at the first empty slot.  Compression does not rebuild the index: it remaps
+// every slot through the old-row -> new-row map of the compaction (removed
+// rows become tombstones), and inserts reuse the first tombstone on a probe
+// sequence, so tombstones are recycled by later dresses.
 //
 // Dress: one streaming pass over the M rows.  For a row T that anticommutes
 // with P (popcount parity of (xT & zP) ^ (zT & xP)), its partner Q = T xor P is
 // looked up.  Exactly one member of each present pair - the one with a zero at
 // P's lowest set bit - rotates both coefficients; a row whose partner is
 // absent scales itself by cos(tau) and appends (Q, s sin(tau) C_T) behind the
-// M input rows, indexing it in the same pass.  q -> q xor P is a bijection, so appended keys are distinct and
-// absent from H: no duplicate merge is needed within one generator (the
-// "insert if unique, else add" merge of App. D, Eq. 18, done as a lookup).
+// M input rows, indexing it in the same pass.  q -> q xor P is a bijection, so
+// appended keys are distinct and absent from H: no duplicate merge is needed
+// within one generator (the "insert if unique, else add" merge of App. D,
+// Eq. 18, done as a lookup).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -29,24 +34,45 @@ __device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where)
     if (atomicCAS(&ctr->err, 0, code) == 0) ctr->err_where = where;
 }
 
-// Row index of key q in the index, -1 when absent, -2 when the probe bound
-// was reached.  Read-only use of the table (no inserts run concurrently).
+__device__ __forceinline__ bool is_entry(uint64_t v) { return v != kEmptySlot && v != kTombSlot; }
+
+// Row index of key q, -1 when absent, -2 when the probe bound was reached.
+// When absent, *free_slot is the first tombstone met (else the empty slot that
+// ended the probe) and *free_val its content: where q would be inserted.
+// Read-only use of the slots through the non-coherent path: a slot read stale
+// can only be empty or a tombstone that was since filled with a key that no
+// lookup of this pass seeks (see k_dress).
 template <int W>
-__device__ __forceinline__ int64_t lookup(const Key<W>& q, const HashView& h,
-                                          const uint64_t* __restrict__ rows) {
-    uint64_t hv = hash_key<W>(q);
-    uint32_t fp = (uint32_t)(hv >> 32);
+__device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, const HashView& h,
+                                               const uint64_t* __restrict__ rows, uint64_t* free_slot,
+                                               uint64_t* free_val) {
+    const uint32_t fp = (uint32_t)(hv >> 32);
     uint64_t b = hv & h.bucket_mask;
+    bool have_tomb = false;
     for (int p = 0; p < h.max_probe; ++p) {
         const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
-        ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
-        uint64_t sl[4] = {s01.x, s01.y, s23.x, s23.y};
+        const ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
+        const uint64_t sl[4] = {s01.x, s01.y, s23.x, s23.y};
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
-            if (sl[k] == kEmptySlot) return -1;
+            if (sl[k] == kEmptySlot) {
+                if (!have_tomb) {
+                    *free_slot = b * kBucketSlots + k;
+                    *free_val = kEmptySlot;
+                }
+                return -1;
+            }
+            if (sl[k] == kTombSlot) {
+                if (!have_tomb) {
+                    have_tomb = true;
+                    *free_slot = b * kBucketSlots + k;
+                    *free_val = kTombSlot;
+                }
+                continue;
+            }
             if ((uint32_t)(sl[k] >> 32) == fp) {
-                uint32_t idx = (uint32_t)sl[k];
-                Key<W> r = load_key<W>(rows, idx);
+                const uint32_t idx = (uint32_t)sl[k];
+                const Key<W> r = load_key<W>(rows, idx);
                 if (key_equal<W>(r, q)) return (int64_t)idx;
             }
         }
@@ -55,34 +81,23 @@ __device__ __forceinline__ int64_t lookup(const Key<W>& q, const HashView& h,
     return -2;
 }
 
-template <int W>
-__device__ __forceinline__ bool insert(const Key<W>& k, uint32_t row, const HashView& h) {
-    uint64_t hv = hash_key<W>(k);
-    uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)row;
-    uint64_t b = hv & h.bucket_mask;
-    for (int p = 0; p < h.max_probe; ++p) {
-        unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
-#pragma unroll
-        for (int k2 = 0; k2 < 4; ++k2) {
-            if (s[k2] == kEmptySlot &&
-                atomicCAS(s + k2, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot)
-                return true;
-        }
-        b = (b + 1) & h.bucket_mask;
-    }
-    return false;
-}
-
-// Insert `entry` at or after `slot` in its probe sequence (the slot may have
-// been taken since it was seen empty).
-__device__ __forceinline__ bool insert_from(uint64_t entry, uint64_t slot, const HashView& h) {
+// Insert `entry` (a key proven absent) at `slot` if it still holds `expect`,
+// else at the next empty or tombstone slot of its probe sequence.
+__device__ __forceinline__ bool insert_from(uint64_t entry, uint64_t slot, uint64_t expect, const HashView& h) {
+    unsigned long long* base = reinterpret_cast<unsigned long long*>(h.slots);
+    if (atomicCAS(base + slot, (unsigned long long)expect, (unsigned long long)entry) == expect) return true;
     uint64_t b = slot / kBucketSlots;
-    int k0 = (int)(slot % kBucketSlots);
+    int k0 = (int)(slot % kBucketSlots) + 1;
     for (int p = 0; p < h.max_probe; ++p) {
-        unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
-        for (int k = k0; k < 4; ++k)
-            if (atomicCAS(s + k, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot)
-                return true;
+        for (int k = k0; k < 4; ++k) {
+            unsigned long long* s = base + b * kBucketSlots + k;
+            unsigned long long v = __ldcg(s);
+            while (!is_entry(v)) {
+                const unsigned long long prev = atomicCAS(s, v, (unsigned long long)entry);
+                if (prev == v) return true;
+                v = prev;
+            }
+        }
         k0 = 0;
         b = (b + 1) & h.bucket_mask;
     }
@@ -107,76 +122,44 @@ __global__ void k_hash_clear(uint64_t* slots, uint64_t n) {
         p[i] = make_ulonglong2(kEmptySlot, kEmptySlot);
 }
 
-// Index rows [lo, hi).  Four rows per thread: their bucket sectors are read
-// together, each row then claims the first empty slot it saw by CAS, and a row
-// that loses that slot continues its probe sequence one slot at a time.
+// Index rows [lo, hi) into a table without tombstones (a fresh build): one row
+// per thread, occupied slots skipped by a plain read before the CAS.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_hash_insert(const uint64_t* __restrict__ rows, int64_t lo,
                                                           int64_t hi, HashView h, DevCounters* ctr) {
-    constexpr int R = 4;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i0 < hi; i0 += R * stride) {
-        uint64_t entry[R], slot[R];
-        bool live[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int64_t i = i0 + r * stride;
-            live[r] = i < hi;
-            entry[r] = 0;
-            slot[r] = 0;
-            if (live[r]) {
-                const uint64_t hv = hash_key<W>(load_key<W>(rows, i));
-                entry[r] = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)i;
-                slot[r] = (hv & h.bucket_mask) * kBucketSlots;
-            }
+    for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += stride) {
+        const uint64_t hv = hash_key<W>(load_key<W>(rows, i));
+        const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)i;
+        uint64_t b = hv & h.bucket_mask;
+        bool done = false;
+        for (int p = 0; p < h.max_probe && !done; ++p) {
+            unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
+            for (int k = 0; k < 4 && !done; ++k)
+                done = s[k] == kEmptySlot &&
+                       atomicCAS(s + k, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot;
+            b = (b + 1) & h.bucket_mask;
         }
-        ulonglong2 a[R], b[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (live[r]) {
-                const ulonglong2* p = reinterpret_cast<const ulonglong2*>(h.slots + slot[r]);
-                a[r] = __ldcg(p);
-                b[r] = __ldcg(p + 1);
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (!live[r]) continue;
-            int k = a[r].x == kEmptySlot ? 0 : a[r].y == kEmptySlot ? 1 : b[r].x == kEmptySlot ? 2
-                    : b[r].y == kEmptySlot ? 3 : 4;
-            if (k < 4 && atomicCAS(reinterpret_cast<unsigned long long*>(h.slots + slot[r] + k),
-                                   (unsigned long long)kEmptySlot, (unsigned long long)entry[r]) == kEmptySlot)
-                continue;
-            if (!insert_from(entry[r], slot[r] + (k < 4 ? k : 3), h)) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
-        }
+        if (!done) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
     }
 }
 
-// Lookup that also reports the first empty slot met, where q would be inserted.
-template <int W>
-__device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, const HashView& h,
-                                               const uint64_t* __restrict__ rows, uint64_t* empty_slot) {
-    const uint32_t fp = (uint32_t)(hv >> 32);
-    uint64_t b = hv & h.bucket_mask;
-    for (int p = 0; p < h.max_probe; ++p) {
-        const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
-        const ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
-        const uint64_t sl[4] = {s01.x, s01.y, s23.x, s23.y};
+// After an in-place compaction: entries of kept rows get their new row index,
+// entries of removed rows become tombstones (new_row == kRowRemoved).
+__global__ void k_hash_remap(uint64_t* slots, uint64_t n, const uint32_t* __restrict__ new_row) {
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(slots);
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n / 2; i += stride) {
+        const ulonglong2 v = p[i];
+        uint64_t w[2] = {v.x, v.y};
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            if (sl[k] == kEmptySlot) {
-                *empty_slot = b * kBucketSlots + k;
-                return -1;
-            }
-            if ((uint32_t)(sl[k] >> 32) == fp) {
-                const uint32_t idx = (uint32_t)sl[k];
-                const Key<W> r = load_key<W>(rows, idx);
-                if (key_equal<W>(r, q)) return (int64_t)idx;
-            }
+        for (int k = 0; k < 2; ++k) {
+            if (!is_entry(w[k])) continue;
+            const uint32_t nr = __ldg(new_row + (uint32_t)w[k]);
+            w[k] = (nr == kRowRemoved) ? kTombSlot : ((w[k] & 0xFFFFFFFF00000000ull) | (uint64_t)nr);
         }
-        b = (b + 1) & h.bucket_mask;
+        p[i] = make_ulonglong2(w[0], w[1]);
     }
-    return -2;
 }
 
 constexpr int kWarpTile = 64;  // rows classified per warp before the probes
@@ -184,17 +167,18 @@ constexpr int kWarpTile = 64;  // rows classified per warp before the probes
 // One pass of Eq. 5 over rows [0, M).  Each warp classifies a tile of 64 rows
 // (two per lane) and queues the anticommuting ones in shared memory, so that
 // every lane then works on one queued row: partner lookup, pair rotation or
-// append.  An appended partner is inserted into the index at the empty slot
-// where its lookup stopped.  Concurrent inserts leave every lookup correct:
-// slots only go from empty to full, a key present before the pass has no empty
-// slot ahead of it in its probe sequence, and an appended key is the partner
-// of exactly one row (q -> q xor P is a bijection), so no other lookup seeks
-// it.  rows_app is the same buffer as rows; appended rows land at M + slot and
-// are not visited by this pass.
+// append.  An appended partner is inserted into the index at the first free
+// slot (tombstone or empty) its lookup met.  Concurrent inserts leave every
+// lookup correct: a key present before the pass has no empty slot ahead of it
+// in its probe sequence, and a slot filled during the pass only ever held an
+// empty or a tombstone (which a lookup passes over or stops at) and receives a
+// key no lookup seeks (an appended key is the partner of exactly one row,
+// q -> q xor P being a bijection).  rows_app is the same buffer as rows;
+// appended rows land at M + slot and are not visited by this pass.
 template <int W>
-__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64_t* __restrict__ rows, uint64_t* rows_app,
-                                                    double* coef, int64_t M, Gen<W> g, HashView h,
-                                                    DevCounters* ctr) {
+__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64_t* __restrict__ rows,
+                                                                    uint64_t* rows_app, double* coef, int64_t M,
+                                                                    Gen<W> g, HashView h, DevCounters* ctr) {
     __shared__ uint32_t s_queue[kThreads / 32][kWarpTile];
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -221,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64
             bool append = false;
             Key<W> q;
             double c_new = 0.0;
-            uint64_t hv = 0, eslot = 0;
+            uint64_t hv = 0, fslot = 0, fval = kEmptySlot;
             if (e < nq) {
                 const int64_t i = base + queue[e];
                 const Key<W> t = load_key<W>(rows, i);
@@ -229,7 +213,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64
                 const double s = (double)product_sign<W>(t, g.yP, g.p, q);
                 const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
                 hv = hash_key<W>(q);
-                const int64_t j = lookup_slot<W>(q, hv, h, rows, &eslot);
+                const int64_t j = lookup_slot<W>(q, hv, h, rows, &fslot, &fval);
                 if (j == -1) {
                     const double c = coef[i];
                     coef[i] = c * g.cos_t;
@@ -256,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64
                     store_key<W>(rows_app, r, q);
                     coef[r] = c_new;
                     const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)r;
-                    if (!insert_from(entry, eslot, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
+                    if (!insert_from(entry, fslot, fval, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
                 }
             }
         }
@@ -277,7 +261,8 @@ __global__ void __launch_bounds__(kThreads) k_dress_count(const uint64_t* __rest
         Key<W> t = load_key<W>(rows, i);
         if (anticommutes<W>(t, g.p)) {
             Key<W> q = key_xor<W>(t, g.p);
-            int64_t j = lookup<W>(q, h, rows);
+            uint64_t fslot, fval;
+            int64_t j = lookup_slot<W>(q, hash_key<W>(q), h, rows, &fslot, &fval);
             if (j == -1) ++cnt;
             else if (j == -2) set_error(ctr, IQCC_ERR_HASH_FULL, 3);
         }
@@ -313,6 +298,13 @@ int grid_for(int64_t n, int per_sm) {
     return (int)(want < 1 ? 1 : want);
 }
 
+int grid_for_slots(uint64_t slots) {
+    int grid = (int)((slots / 2 + kThreads - 1) / kThreads);
+    int cap = sm_count() * 8;
+    if (grid > cap) grid = cap;
+    return grid < 1 ? 1 : grid;
+}
+
 }  // namespace
 
 int sm_count() {
@@ -333,11 +325,11 @@ void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s) {
-    int grid = (int)((slots / 2 + kThreads - 1) / kThreads);
-    int cap = sm_count() * 8;
-    if (grid > cap) grid = cap;
-    if (grid < 1) grid = 1;
-    k_hash_clear<<<grid, kThreads, 0, s>>>(h.slots, slots); note_launch();
+    k_hash_clear<<<grid_for_slots(slots), kThreads, 0, s>>>(h.slots, slots); note_launch();
+}
+
+void launch_hash_remap(HashView h, uint64_t slots, const uint32_t* new_row, cudaStream_t s) {
+    k_hash_remap<<<grid_for_slots(slots), kThreads, 0, s>>>(h.slots, slots, new_row); note_launch();
 }
 
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,

@@ -198,7 +198,8 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
                                                               double* coef, int64_t n,
                                                               unsigned long long* state,
                                                               unsigned int* tile_counter,
-                                                              unsigned long long* total, DevCounters* ctr) {
+                                                              unsigned long long* total, DevCounters* ctr,
+                                                              uint32_t* new_row) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem_raw);
     double* s_c = reinterpret_cast<double*>(s_rows + (size_t)kCompactTile * 2 * W);
@@ -214,6 +215,9 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
     __syncthreads();
     const unsigned int t = s_tile;
     const int64_t base = (int64_t)t * kCompactTile;
+    uint32_t my_pos[kCompactTile / kThreads];
+    bool my_keep[kCompactTile / kThreads];
+#pragma unroll
     for (int r = 0; r < kCompactTile / kThreads; ++r) {
         const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
         const bool f = i < n && flags[i];
@@ -222,6 +226,8 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
         __syncthreads();
         uint32_t pos = s_run + __popc(b & ((1u << lane) - 1u));
         for (int w = 0; w < wid; ++w) pos += s_w[w];
+        my_pos[r] = pos;
+        my_keep[r] = f;
         if (f) {
             const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rows + (size_t)i * 2 * W);
             ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rows + (size_t)pos * 2 * W);
@@ -269,6 +275,13 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
     }
     __syncthreads();
     const unsigned long long out = s_prefix;
+    if (new_row) {
+#pragma unroll
+        for (int r = 0; r < kCompactTile / kThreads; ++r) {
+            const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
+            if (i < n) new_row[i] = my_keep[r] ? (uint32_t)(out + my_pos[r]) : kRowRemoved;
+        }
+    }
     for (uint32_t k = threadIdx.x; k < count; k += kThreads) {
         const ulonglong2* src = reinterpret_cast<const ulonglong2*>(s_rows + (size_t)k * 2 * W);
         ulonglong2* dst = reinterpret_cast<ulonglong2*>(rows + (size_t)(out + k) * 2 * W);
@@ -606,7 +619,7 @@ size_t compact_inplace_scratch_bytes(int64_t n) {
 }
 
 void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double* coef, int64_t n, void* scratch,
-                            unsigned long long* count, DevCounters* ctr, cudaStream_t s) {
+                            unsigned long long* count, DevCounters* ctr, cudaStream_t s, uint32_t* new_row) {
     const int64_t nt = (n + kCompactTile - 1) / kCompactTile;
     if (n <= 0) {
         cudaMemsetAsync(count, 0, sizeof(unsigned long long), s);
@@ -620,19 +633,19 @@ void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double
         case 1: {
             static bool a = false;
             if (!a) { cudaFuncSetAttribute(k_compact_inplace<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
-            k_compact_inplace<1><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr); note_launch();
+            k_compact_inplace<1><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr, new_row); note_launch();
             break;
         }
         case 2: {
             static bool a = false;
             if (!a) { cudaFuncSetAttribute(k_compact_inplace<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
-            k_compact_inplace<2><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr); note_launch();
+            k_compact_inplace<2><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr, new_row); note_launch();
             break;
         }
         default: {
             static bool a = false;
             if (!a) { cudaFuncSetAttribute(k_compact_inplace<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
-            k_compact_inplace<4><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr); note_launch();
+            k_compact_inplace<4><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr, new_row); note_launch();
             break;
         }
     }

@@ -331,3 +331,25 @@ def test_term_limit_select_on_large_sets(cap):
     gx, gz, gc = iqcc.iqcc_export(H)
     ox, oz, oc = o.export()
     assert np.array_equal(gx, ox) and np.array_equal(gz, oz) and np.array_equal(gc, oc)
+
+
+@pytest.mark.parametrize("n", [20, 100])
+def test_dress_after_compression_reuses_tombstones(n):
+    """Compression remaps the index in place (removed keys become tombstones);
+    later dresses must find every kept key, see removed keys as absent and
+    reuse the tombstones for new partners."""
+    rng = np.random.Generator(np.random.PCG64(n))
+    _, x, z, c = synth.random_hamiltonian(n, 60_000, 300 + n)
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    for rnd in range(4):
+        eps = float(np.quantile(np.abs(iqcc.iqcc_export(H)[2]), 0.4))
+        assert iqcc.iqcc_prune(H, eps, 0) == o.prune(eps, 0)
+        for _ in range(3):
+            gx, gz = synth.random_generator(n, rng, weight=3)
+            t = float(rng.uniform(-2, 2))
+            iqcc.iqcc_dress(H, gx, gz, [t])
+            o.dress(gx, gz, t)
+        bad = compare(iqcc.iqcc_export(H), o.export(), eps=eps)
+        assert not bad, bad[:5]
+        assert len(H) == len(o)
