@@ -162,7 +162,56 @@ __global__ void k_hash_remap(uint64_t* slots, uint64_t n, const uint32_t* __rest
     }
 }
 
+// As lookup_slot, and loads the partner's coefficient together with its key
+// (both depend only on the candidate row), so the caller needs no further
+// dependent load for a found pair.
+template <int W>
+__device__ __forceinline__ int64_t lookup_slot_coef(const Key<W>& q, uint64_t hv, const HashView& h,
+                                                    const uint64_t* __restrict__ rows, const double* coef,
+                                                    uint64_t* free_slot, uint64_t* free_val, double* cq) {
+    const uint32_t fp = (uint32_t)(hv >> 32);
+    uint64_t b = hv & h.bucket_mask;
+    bool have_tomb = false;
+    for (int p = 0; p < h.max_probe; ++p) {
+        const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
+        const ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
+        const uint64_t sl[4] = {s01.x, s01.y, s23.x, s23.y};
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            if (sl[k] == kEmptySlot) {
+                if (!have_tomb) {
+                    *free_slot = b * kBucketSlots + k;
+                    *free_val = kEmptySlot;
+                }
+                return -1;
+            }
+            if (sl[k] == kTombSlot) {
+                if (!have_tomb) {
+                    have_tomb = true;
+                    *free_slot = b * kBucketSlots + k;
+                    *free_val = kTombSlot;
+                }
+                continue;
+            }
+            if ((uint32_t)(sl[k] >> 32) == fp) {
+                const uint32_t idx = (uint32_t)sl[k];
+                const double c = coef[idx];
+                const Key<W> r = load_key<W>(rows, idx);
+                if (key_equal<W>(r, q)) {
+                    *cq = c;
+                    return (int64_t)idx;
+                }
+            }
+        }
+        b = (b + 1) & h.bucket_mask;
+    }
+    return -2;
+}
+
 constexpr int kWarpTile = 64;  // rows classified per warp before the probes
+#ifndef IQCC_DRESS_MIN_BLOCKS
+#define IQCC_DRESS_MIN_BLOCKS 4     // resident 256-thread blocks per SM the register budget targets (5 spills)
+#endif
 
 // One pass of Eq. 5 over rows [0, M).  Each warp classifies a tile of 64 rows
 // (two per lane) and queues the anticommuting ones in shared memory, so that
@@ -176,7 +225,7 @@ constexpr int kWarpTile = 64;  // rows classified per warp before the probes
 // q -> q xor P being a bijection).  rows_app is the same buffer as rows;
 // appended rows land at M + slot and are not visited by this pass.
 template <int W>
-__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64_t* __restrict__ rows,
+__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) k_dress(const uint64_t* __restrict__ rows,
                                                                     uint64_t* rows_app, double* coef, int64_t M,
                                                                     Gen<W> g, HashView h, DevCounters* ctr) {
     __shared__ uint32_t s_queue[kThreads / 32][kWarpTile];
@@ -208,20 +257,20 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : 5) k_dress(const uint64
             uint64_t hv = 0, fslot = 0, fval = kEmptySlot;
             if (e < nq) {
                 const int64_t i = base + queue[e];
+                const double ct = coef[i];  // independent of the lookup: issued first
                 const Key<W> t = load_key<W>(rows, i);
                 q = key_xor<W>(t, g.p);
                 const double s = (double)product_sign<W>(t, g.yP, g.p, q);
                 const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
                 hv = hash_key<W>(q);
-                const int64_t j = lookup_slot<W>(q, hv, h, rows, &fslot, &fval);
+                double cq = 0.0;
+                const int64_t j = lookup_slot_coef<W>(q, hv, h, rows, coef, &fslot, &fval, &cq);
                 if (j == -1) {
-                    const double c = coef[i];
-                    coef[i] = c * g.cos_t;
-                    c_new = s * c * g.sin_t;
+                    coef[i] = ct * g.cos_t;
+                    c_new = s * ct * g.sin_t;
                     append = true;
                 } else if (j >= 0) {
                     if (!upper) {
-                        const double ct = coef[i], cq = coef[j];
                         coef[i] = ct * g.cos_t - s * cq * g.sin_t;
                         coef[j] = cq * g.cos_t + s * ct * g.sin_t;
                     }
