@@ -158,7 +158,8 @@ uint64_t pow2_at_least(uint64_t v) {
     return p;
 }
 
-// (Re)build the index over rows [0, M) with `slots` slots.
+// (Re)build the index over the live rows of [0, M) with `slots` slots (no
+// tombstones afterwards; each live row's slot is recorded in backptr).
 iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     if (slots != ctx->hash_slots || !ctx->hash.p) {
         release(ctx, ctx->hash);
@@ -170,8 +171,9 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     HashView h = hash_view(ctx);
     launch_hash_clear(h, ctx->hash_slots, ctx->stream);
     CK_LAUNCH();
-    launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream);
+    launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream, ctx->state(), ctx->back());
     CK_LAUNCH();
+    ctx->n_tomb = 0;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0;
@@ -182,22 +184,27 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     return read_counters(ctx);
 }
 
-// Rows and index able to hold `rows_needed` rows (current rows kept).
-iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
+// Row buffers able to hold `rows_needed` rows (current rows, states, slots and
+// free list kept), and an index whose entries plus tombstones stay at or below
+// half its slots once `new_entries` more keys are inserted.
+iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed, int64_t new_entries) {
     if (rows_needed > ctx->rows_alloc) {
         int64_t want = std::max<int64_t>(rows_needed, ctx->rows_alloc + ctx->rows_alloc / 2);
         want = std::min<int64_t>(want, ctx->capacity);
         want = std::max<int64_t>(want, rows_needed);
         const size_t rb = row_bytes(ctx);
         if (!grow_keep(ctx, ctx->keys, (size_t)want * rb, (size_t)ctx->M * rb) ||
-            !grow_keep(ctx, ctx->coef, (size_t)want * 8, (size_t)ctx->M * 8))
+            !grow_keep(ctx, ctx->coef, (size_t)want * 8, (size_t)ctx->M * 8) ||
+            !grow_keep(ctx, ctx->epoch, (size_t)want, (size_t)ctx->M) ||
+            !grow_keep(ctx, ctx->backptr, (size_t)want * 4, (size_t)ctx->M * 4) ||
+            !grow_keep(ctx, ctx->freelist, (size_t)want * 4, (size_t)ctx->n_free * 4))
             return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
         ctx->rows_alloc = want;
         ctx->stats.rows_allocated = want;
     }
-    // load factor <= 1/2 once the rows are inserted
-    if ((uint64_t)rows_needed * 2 > ctx->hash_slots) {
-        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 2));
+    const uint64_t occupied = (uint64_t)(ctx->n_live + new_entries + ctx->n_tomb);
+    if (occupied * 2 > ctx->hash_slots) {
+        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)(ctx->n_live + new_entries) * 2));
         if (st) return st;
     }
     return IQCC_OK;
@@ -273,7 +280,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_abc(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pkey, basis, occ, tables, n_groups(ctx), partials,
-               ctx->stream);
+               ctx->stream, ctx->state());
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     launch_reduce3(partials, nb, out3, ctx->stream);
@@ -285,7 +292,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.n_energy++;
     ctx->stats.energy_kernel_ms += ms;
-    ctx->stats.energy_bytes += (double)ctx->M * (16.0 * ctx->Wd + 8.0);
+    ctx->stats.energy_bytes += (double)ctx->n_live * (16.0 * ctx->Wd + 8.0);
     abc[0] = h3[0];
     abc[1] = h3[1];
     abc[2] = h3[2];
@@ -294,50 +301,60 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
 
 // One generator (device-layout key); on IQCC_ERR_CAPACITY / OOM H is unchanged.
 iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
-    if (ctx->M == 0) {
+    if (ctx->n_live == 0) {
         ctx->stats.n_dress++;
         return IQCC_OK;
     }
-    const int64_t M = ctx->M;
-    int64_t upper = 2 * M;
+    const int64_t M = ctx->M, live = ctx->n_live, nf = ctx->n_free;
+    // appends are at most the live anticommuting rows; they fill holes first
+    int64_t new_upper = live;
+    int64_t rows_upper = M + std::max<int64_t>(0, new_upper - nf);
     DevCounters* c = dctr(ctx);
-    if (upper > ctx->capacity) {
+    if (rows_upper > ctx->capacity) {
         // exact admission count (probe only)
         CK(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), ctx->stream));
-        launch_dress_count(ctx->Wd, ctx->rows(), M, pkey, hash_view(ctx), c, ctx->stream);
+        launch_dress_count(ctx->Wd, ctx->rows(), M, pkey, hash_view(ctx), c, ctx->stream, ctx->state());
         CK_LAUNCH();
         iqcc_status st = read_counters(ctx);
         if (st) return st;
-        upper = M + (int64_t)ctx->h_counters->n_new;
-        if (upper > ctx->capacity) {
+        new_upper = (int64_t)ctx->h_counters->n_new;
+        rows_upper = M + std::max<int64_t>(0, new_upper - nf);
+        if (rows_upper > ctx->capacity) {
             char buf[200];
-            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)upper,
+            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)rows_upper,
                      (long long)ctx->capacity);
             return fail(ctx, IQCC_ERR_CAPACITY, buf);
         }
     }
-    iqcc_status st = reserve_rows(ctx, upper);
+    iqcc_status st = reserve_rows(ctx, rows_upper, new_upper);
     if (st) return st;
-    CK(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(c, 0, 5 * sizeof(unsigned long long), ctx->stream));  // n_new .. tomb_reused
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_dress(ctx->Wd, ctx->rows(), ctx->rows(), ctx->c(), M, pkey, std::cos(tau), std::sin(tau),
-                 hash_view(ctx), c, ctx->stream);
+                 hash_view(ctx), c, ctx->stream, ctx->state(), ctx->back(), ctx->holes(), nf);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
     if (st) return st;
     const int64_t n_new = (int64_t)ctx->h_counters->n_new;
     const int64_t n_anti = (int64_t)ctx->h_counters->n_anti;
+    const int64_t reused = (int64_t)ctx->h_counters->tomb_reused;
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    ctx->M = M + n_new;  // the dress kernel indexed the appended rows itself
+    // the dress kernel indexed the appended rows itself; they took holes first
+    ctx->M = M + std::max<int64_t>(0, n_new - nf);
+    ctx->n_free = std::max<int64_t>(0, nf - n_new);
+    ctx->n_live = live + n_new;
+    ctx->n_tomb = std::max<int64_t>(0, ctx->n_tomb - reused);
+    launch_state_settle(ctx->state(), ctx->M, ctx->stream);
+    CK_LAUNCH();
     iqcc_stats& s = ctx->stats;
     s.n_dress++;
-    s.dressed_terms += M;
+    s.dressed_terms += live;
     s.anticommuting += n_anti;
     s.appended += n_new;
     s.dress_kernel_ms += ms;
-    s.dress_bytes += 16.0 * ctx->Wd * (double)M + 16.0 * (double)n_anti + (16.0 * ctx->Wd + 8.0) * (double)n_new;
+    s.dress_bytes += 16.0 * ctx->Wd * (double)live + 16.0 * (double)n_anti + (16.0 * ctx->Wd + 8.0) * (double)n_new;
     return IQCC_OK;
 }
 
@@ -366,16 +383,45 @@ size_t sort_area_bytes(int64_t n) {
     return dry.off;
 }
 
+// Remove the holes: compact the live rows to [0, n_live) in place (stable)
+// and rebuild the index.  flags and cscratch: scratch of at least M entries.
+iqcc_status defragment(iqcc_ctx* ctx, uint8_t* flags, char* cscratch) {
+    const int64_t M = ctx->M;
+    DevCounters* c = dctr(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_prune_flags(ctx->c(), M, 0.0, flags, &c->aux, ctx->stream, ctx->state());  // flags = live
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.prune_ms += ms;
+    const int64_t live = (int64_t)ctx->h_counters->aux;
+    if (live != ctx->n_live) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "internal: %lld live rows found, %lld expected", (long long)live,
+                 (long long)ctx->n_live);
+        return fail(ctx, IQCC_ERR_STATE, buf);
+    }
+    CK(cudaMemsetAsync(ctx->state(), kLive, (size_t)live, ctx->stream));
+    ctx->M = live;
+    ctx->n_free = 0;
+    return rebuild_hash(ctx, ctx->hash_slots);
+}
+
 iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed) {
     const int64_t M = ctx->M;
     *removed = 0;
-    if (M == 0) return IQCC_OK;
+    if (ctx->n_live == 0) return IQCC_OK;
     Carver cv;
     cv.take<uint8_t>(M);
     cv.take<unsigned long long>(256);
     cv.take<char>(compact_inplace_scratch_bytes(M));
     cv.take<uint32_t>(M);  // tie list
-    cv.take<uint32_t>(M);  // old row -> new row
     cv.off += sort_area_bytes(M);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
@@ -383,14 +429,13 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     unsigned long long* hist = cv.take<unsigned long long>(256);
     char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
-    uint32_t* new_row = cv.take<uint32_t>(M);
     SortArea sa = carve_sort(cv, M);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
     DevCounters* c = dctr(ctx);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
-    launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream);
+    launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream, ctx->state());
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
@@ -463,8 +508,9 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
             CK_LAUNCH();
         }
     }
+    // removed rows become holes: state kDead, index slot a tombstone, row on the free list
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream, new_row);
+    launch_kill(ctx->state(), flags, ctx->back(), hash_view(ctx), M, ctx->holes() + ctx->n_free, &c->aux, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
@@ -472,19 +518,12 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.prune_ms += ms;
-    const int64_t newM = (int64_t)ctx->h_counters->aux;
-    ctx->M = newM;
-    *removed = M - newM;
-    if (newM == M) return IQCC_OK;  // nothing moved
-    // rows moved: remap the index in place (kept keys keep their slots, removed keys become tombstones)
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    launch_hash_remap(hash_view(ctx), ctx->hash_slots, new_row, ctx->stream);
-    CK_LAUNCH();
-    CK(cudaEventRecord(ctx->ev1, ctx->stream));
-    CK(cudaEventSynchronize(ctx->ev1));
-    float hms = 0;
-    cudaEventElapsedTime(&hms, ctx->ev0, ctx->ev1);
-    ctx->stats.hash_ms += hms;
+    const int64_t killed = (int64_t)ctx->h_counters->aux;
+    ctx->n_live -= killed;
+    ctx->n_free += killed;
+    ctx->n_tomb += killed;
+    *removed = killed;
+    if (ctx->n_free > ctx->M / 2 && ctx->M > (1 << 16)) return defragment(ctx, flags, cscratch);
     return IQCC_OK;
 }
 
@@ -497,17 +536,16 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     const bool basis = is_basis(ctx, theta);
     uint64_t occ[4];
     occ_words(ctx, theta, occ);
-    const uint64_t gslots = pow2_at_least((uint64_t)std::max<int64_t>(M, 1) * 2);
+    // groups (distinct flip sets) are at most the live rows
+    const int64_t Mg = std::max<int64_t>(ctx->n_live, 1);
+    const uint64_t gslots = pow2_at_least((uint64_t)Mg * 2);
     const int nblk = expect_blocks();
-    const int64_t Mg = std::max<int64_t>(M, 1);
+    constexpr int64_t kHeadLimit = 1 << 16;  // the top-k path orders at most this many candidates
     Carver cv;
     cv.take<uint64_t>(gslots);
     cv.take<uint64_t>((size_t)Mg * Wd);
     cv.take<double>(Mg);
-    cv.take<uint64_t>((size_t)Mg * (Wd + 1));
-    cv.off += sort_area_bytes(Mg);
-    cv.take<uint64_t>((size_t)Mg * W * 2);
-    cv.take<double>(Mg);
+    cv.take<uint32_t>(kHeadLimit);
     cv.take<double>(2 * ctx->n);
     cv.take<double>((size_t)n_groups(ctx) * 256);
     cv.take<uint64_t>(16 * 2 * 4);
@@ -518,10 +556,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     uint64_t* slots = cv.take<uint64_t>(gslots);
     uint64_t* gkeys = cv.take<uint64_t>((size_t)Mg * Wd);
     double* gsum = cv.take<double>(Mg);
-    uint64_t* skeys = cv.take<uint64_t>((size_t)Mg * (Wd + 1));
-    SortArea sa = carve_sort(cv, Mg);
-    uint64_t* stage_x = cv.take<uint64_t>((size_t)Mg * W * 2);
-    double* stage_g = cv.take<double>(Mg);
+    uint32_t* head = cv.take<uint32_t>(kHeadLimit);
     double* angles = cv.take<double>(2 * ctx->n);
     double* tables = cv.take<double>((size_t)n_groups(ctx) * 256);
     uint64_t* cand = cv.take<uint64_t>(16 * 2 * 4);
@@ -536,7 +571,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     CK_LAUNCH();
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
     launch_dis_group(Wd, ctx->rows(), ctx->c(), M, occ, basis, slots, gh.bucket_mask, ctx->max_probe, gkeys, gsum, c,
-                     ctx->stream);
+                     ctx->stream, ctx->state());
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
@@ -562,7 +597,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
             }
             CK(cudaMemcpyAsync(cand, hc, sizeof(uint64_t) * 2 * Wd * K, cudaMemcpyHostToDevice, ctx->stream));
             launch_grad_general(Wd, ctx->rows(), ctx->c(), M, cand, K, tables, n_groups(ctx), partials, nblk,
-                                ctx->stream);
+                                ctx->stream, ctx->state());
             CK_LAUNCH();
             launch_reduce_cols(partials, nblk, 16, colsum, ctx->stream);
             CK_LAUNCH();
@@ -601,9 +636,9 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
                 prefix |= (uint64_t)sel << shift;
                 pmask |= (uint64_t)255 << shift;
             }
-            const int64_t limit = std::min<int64_t>(G, 1 << 16);
+            const int64_t limit = std::min<int64_t>(G, kHeadLimit);
             CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-            launch_collect_ge(gsum, G, prefix, sa.a, limit, &c->aux, ctx->stream);
+            launch_collect_ge(gsum, G, prefix, head, limit, &c->aux, ctx->stream);
             CK_LAUNCH();
             st = read_counters(ctx);
             if (st) return st;
@@ -611,21 +646,32 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
             if (got <= limit) {
                 subset = true;
                 n_sort = got;
-                launch_dis_sort_keys_sub(Wd, gkeys, gsum, sa.a, got, skeys, ctx->stream);
-                CK_LAUNCH();
             }
         }
-        if (!subset) {
-            launch_dis_sort_keys(Wd, gkeys, gsum, G, skeys, ctx->stream);
-            CK_LAUNCH();
-            launch_iota(sa.a, G, ctx->stream);
-            CK_LAUNCH();
-        }
+        const int64_t k = std::min(cap, n_sort);
+        // sort keys, permutations and the output staging, sized for this path
+        Carver dry;
+        dry.take<uint64_t>((size_t)n_sort * (Wd + 1));
+        carve_sort(dry, n_sort);
+        dry.take<uint64_t>((size_t)k * W * 2);
+        dry.take<double>(k);
+        if (!ensure(ctx, ctx->aux, dry.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        Carver cv2{(char*)ctx->aux.p, 0};
+        uint64_t* skeys = cv2.take<uint64_t>((size_t)n_sort * (Wd + 1));
+        SortArea sa = carve_sort(cv2, n_sort);
+        uint64_t* stage_x = cv2.take<uint64_t>((size_t)k * W * 2);
+        double* stage_g = cv2.take<double>(k);
+        if (cv2.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+        if (subset) launch_dis_sort_keys_sub(Wd, gkeys, gsum, head, n_sort, skeys, ctx->stream);
+        else launch_dis_sort_keys(Wd, gkeys, gsum, G, skeys, ctx->stream);
+        CK_LAUNCH();
+        launch_iota(sa.a, n_sort, ctx->stream);
+        CK_LAUNCH();
         uint32_t* sorted = nullptr;
         radix_sort_indirect(skeys, Wd + 1, plan, sa.a, sa.b, n_sort, &sorted, sa.tmp, sa.tmp_bytes, ctx->stream);
         CK_LAUNCH();
-        const int64_t k = std::min(cap, n_sort);
-        launch_dis_export(W, Wd, gkeys, gsum, sorted, k, stage_x, stage_x + (size_t)k * W, stage_g, ctx->stream);
+        launch_dis_export(W, Wd, gkeys, gsum, sorted, subset ? head : nullptr, k, stage_x, stage_x + (size_t)k * W,
+                          stage_g, ctx->stream);
         CK_LAUNCH();
         CK(cudaMemcpyAsync(ox, stage_x, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaMemcpyAsync(oz, stage_x + (size_t)k * W, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
@@ -665,7 +711,7 @@ iqcc_status gradients_given(iqcc_ctx* ctx, const double* theta, const double* ph
         for (int i = 0; i < k; ++i) pad_key(ctx, cx + (k0 + i) * ctx->W, cz + (k0 + i) * ctx->W, hc + i * 2 * Wd);
         CK(cudaMemcpyAsync(cand, hc, sizeof(uint64_t) * 2 * Wd * k, cudaMemcpyHostToDevice, ctx->stream));
         launch_grad_general(Wd, ctx->rows(), ctx->c(), ctx->M, cand, k, tables, n_groups(ctx), partials, nblk,
-                            ctx->stream);
+                            ctx->stream, ctx->state());
         CK_LAUNCH();
         launch_reduce_cols(partials, nblk, 16, colsum, ctx->stream);
         CK_LAUNCH();
@@ -736,7 +782,9 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
     }
     const int64_t rows0 = std::min<int64_t>(ctx->capacity, std::max<int64_t>(1024, 2 * n_terms));
     const size_t rb = row_bytes(ctx);
-    if (!ensure(ctx, ctx->keys, (size_t)rows0 * rb) || !ensure(ctx, ctx->coef, (size_t)rows0 * 8)) {
+    if (!ensure(ctx, ctx->keys, (size_t)rows0 * rb) || !ensure(ctx, ctx->coef, (size_t)rows0 * 8) ||
+        !ensure(ctx, ctx->epoch, (size_t)rows0) || !ensure(ctx, ctx->backptr, (size_t)rows0 * 4) ||
+        !ensure(ctx, ctx->freelist, (size_t)rows0 * 4)) {
         fail(ctx, IQCC_ERR_OOM, "row allocation failed");
         return bail(IQCC_ERR_OOM);
     }
@@ -793,6 +841,12 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
             ctx->M = (int64_t)ctx->h_counters->aux;
         } while (0);
         if (st) return bail(st);
+    }
+    ctx->n_live = ctx->M;
+    ctx->n_free = 0;
+    if (ctx->M > 0 && cudaMemsetAsync(ctx->state(), kLive, (size_t)ctx->M, ctx->stream) != cudaSuccess) {
+        fail_cuda(ctx, cudaGetLastError(), "state init", __LINE__);
+        return bail(IQCC_ERR_CUDA);
     }
     iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
     ctx->launch_base = launches();
@@ -889,8 +943,8 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     if (n_gen < 0 || n_gen > 64) return fail(ctx, IQCC_ERR_ARG, "n_gen must be in 0..64");
     if (o->n_forced > 0 && (!o->forced_x || !o->forced_z)) return fail(ctx, IQCC_ERR_ARG, "null forced generators");
     std::memset(out, 0, sizeof *out);
-    out->n_terms_before = ctx->M;
-    out->n_terms_peak = ctx->M;
+    out->n_terms_before = ctx->n_live;
+    out->n_terms_peak = ctx->n_live;
     const double gmin = o->min_gradient > 0 ? o->min_gradient : 1e-12;
     std::vector<uint64_t> gx((size_t)64 * W), gz((size_t)64 * W);
     std::vector<double> g(64);
@@ -918,7 +972,7 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         double tau;
         if (o->n_forced > 0 && o->forced_tau) tau = o->forced_tau[k];
         else tau = (abc[1] == 0.0 && abc[2] == 0.0) ? 0.0 : std::atan2(-abc[2], -abc[1]);
-        out->dressed_terms += ctx->M;
+        out->dressed_terms += ctx->n_live;
         int applied = 0;
         st = iqcc_dress(ctx, 1, gx.data() + k * W, gz.data() + k * W, &tau, &applied);
         if (st) {
@@ -931,8 +985,8 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         out->tau[k] = tau;
         for (int i = 0; i < 3; ++i) out->abc[k][i] = abc[i];
         out->n_applied = k + 1;
-        out->n_terms_peak = std::max(out->n_terms_peak, ctx->M);
-        if (o->max_terms > 0 && ctx->M > o->max_terms) {
+        out->n_terms_peak = std::max(out->n_terms_peak, ctx->n_live);
+        if (o->max_terms > 0 && ctx->n_live > o->max_terms) {
             int64_t cut = 0;
             st = iqcc_prune(ctx, 0.0, o->max_terms, &cut);
             if (st) return st;
@@ -943,14 +997,14 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     iqcc_status st = iqcc_prune(ctx, o->eps, o->max_terms, &removed);
     if (st) return st;
     out->n_removed += removed;
-    out->n_terms = ctx->M;
+    out->n_terms = ctx->n_live;
     return iqcc_qmf_energy(ctx, theta, phi, &out->energy);
 }
 
 iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms) {
     if (!ctx || !n_terms) return fail(nullptr, IQCC_ERR_ARG, "null argument");
     if (ctx->broken) return IQCC_ERR_STATE;
-    *n_terms = ctx->M;
+    *n_terms = ctx->n_live;
     return IQCC_OK;
 }
 
@@ -958,27 +1012,34 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     GUARD(ctx);
     if (!n) return fail(ctx, IQCC_ERR_ARG, "n is NULL");
     if (cap < 0) return fail(ctx, IQCC_ERR_ARG, "cap < 0");
-    *n = ctx->M;
-    const int64_t k = std::min(cap, ctx->M);
+    *n = ctx->n_live;
+    const int64_t k = std::min(cap, ctx->n_live);
     if (k == 0) return IQCC_OK;
     if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
-    const int64_t M = ctx->M;
+    const int64_t M = ctx->M, live = ctx->n_live;
     const int W = ctx->W;
     Carver cv;
-    cv.off += sort_area_bytes(M);
+    cv.off += sort_area_bytes(live);
     cv.take<uint64_t>((size_t)k * W);
     cv.take<uint64_t>((size_t)k * W);
     cv.take<double>(k);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
-    SortArea sa = carve_sort(cv, M);
+    SortArea sa = carve_sort(cv, live);
     uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
     uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
     double* sc = cv.take<double>(k);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    launch_iota(sa.a, M, ctx->stream);
+    // the live rows (holes skipped), then their canonical order
+    DevCounters* c = dctr(ctx);
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_live_list(ctx->state(), M, sa.a, &c->aux, ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    if ((int64_t)ctx->h_counters->aux != live) return fail(ctx, IQCC_ERR_STATE, "internal: live row count mismatch");
     uint32_t* sorted = nullptr;
-    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, M, &sorted, sa.tmp, sa.tmp_bytes,
+    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, live, &sorted, sa.tmp, sa.tmp_bytes,
                         ctx->stream);
     CK_LAUNCH();
     launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), sorted, sx, sz, sc, k, ctx->stream);
@@ -1018,6 +1079,9 @@ void iqcc_free(iqcc_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     release(ctx, ctx->keys);
     release(ctx, ctx->coef);
+    release(ctx, ctx->epoch);
+    release(ctx, ctx->backptr);
+    release(ctx, ctx->freelist);
     release(ctx, ctx->hash);
     release(ctx, ctx->counters);
     release(ctx, ctx->scratch);

@@ -326,8 +326,8 @@ __global__ void k_dis_sort_keys_sub(int Wd, const uint64_t* __restrict__ gkeys, 
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) {
         const uint32_t g = idx[i];
         uint64_t a = ((uint64_t)__double_as_longlong(gsum[g]) & 0x7FFFFFFFFFFFFFFFull) & ~((1ull << 20) - 1ull);
-        skeys[(size_t)g * (Wd + 1)] = ~a;
-        for (int w = 0; w < Wd; ++w) skeys[(size_t)g * (Wd + 1) + 1 + w] = gkeys[(size_t)g * Wd + (Wd - 1 - w)];
+        skeys[(size_t)i * (Wd + 1)] = ~a;  // compact: entry i is the i-th listed group
+        for (int w = 0; w < Wd; ++w) skeys[(size_t)i * (Wd + 1) + 1 + w] = gkeys[(size_t)g * Wd + (Wd - 1 - w)];
     }
 }
 
@@ -402,16 +402,35 @@ __device__ __forceinline__ uint64_t abs_bits(double c) {
 }
 
 __global__ void k_prune_flags(const double* __restrict__ coef, int64_t n, double eps, uint8_t* flags,
-                              unsigned long long* count) {
+                              unsigned long long* count, const uint8_t* __restrict__ state) {
     unsigned c = 0;
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
-        const bool keep = !(fabs(coef[i]) < eps);
+        const bool keep = (!state || state[i] == kLive) && !(fabs(coef[i]) < eps);
         flags[i] = keep;
         c += keep;
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
+}
+
+// Indices of kLive rows (warp-aggregated; the order is not fixed).
+__global__ void k_live_list(const uint8_t* __restrict__ state, int64_t n, uint32_t* idx, unsigned long long* count) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+        const int64_t i = base + lane;
+        const bool live = i < n && state[i] == kLive;
+        const unsigned m = __ballot_sync(FULL, live);
+        if (m) {
+            const int leader = __ffs(m) - 1;
+            unsigned long long p0 = 0;
+            if (lane == leader) p0 = atomicAdd(count, (unsigned long long)__popc(m));
+            p0 = __shfl_sync(FULL, p0, leader);
+            if (live) idx[p0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+        }
+    }
 }
 
 __global__ void k_abs_digit_hist(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
@@ -520,10 +539,11 @@ __global__ void k_dis_sort_keys(int Wd, const uint64_t* __restrict__ gkeys, cons
 }
 
 __global__ void k_dis_export(int W, int Wd, const uint64_t* __restrict__ gkeys, const double* __restrict__ gsum,
-                             const uint32_t* __restrict__ perm, int64_t k, uint64_t* ox, uint64_t* oz, double* og) {
+                             const uint32_t* __restrict__ perm, const uint32_t* __restrict__ idx, int64_t k,
+                             uint64_t* ox, uint64_t* oz, double* og) {
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) {
-        const uint32_t g = perm[i];
+        const uint32_t g = idx ? idx[perm[i]] : perm[i];
         bool found = false;
         for (int w = 0; w < W; ++w) {
             const uint64_t x = gkeys[(size_t)g * Wd + w];
@@ -714,9 +734,16 @@ void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const 
 }
 
 void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags, unsigned long long* count,
-                        cudaStream_t s) {
+                        cudaStream_t s, const uint8_t* state) {
     if (n > 0) {
-        k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count);
+        k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count, state);
+        note_launch();
+    }
+}
+
+void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, cudaStream_t s) {
+    if (n > 0) {
+        k_live_list<<<grid_stride_blocks(n), kThreads, 0, s>>>(state, n, idx, count);
         note_launch();
     }
 }
@@ -784,10 +811,10 @@ void launch_dis_sort_keys(int Wd, const uint64_t* gkeys, const double* gsum, int
     }
 }
 
-void launch_dis_export(int W, int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* perm, int64_t k,
-                       uint64_t* ox, uint64_t* oz, double* og, cudaStream_t s) {
+void launch_dis_export(int W, int Wd, const uint64_t* gkeys, const double* gsum, const uint32_t* perm,
+                       const uint32_t* idx, int64_t k, uint64_t* ox, uint64_t* oz, double* og, cudaStream_t s) {
     if (k > 0) {
-        k_dis_export<<<grid_stride_blocks(k), kThreads, 0, s>>>(W, Wd, gkeys, gsum, perm, k, ox, oz, og);
+        k_dis_export<<<grid_stride_blocks(k), kThreads, 0, s>>>(W, Wd, gkeys, gsum, perm, idx, k, ox, oz, og);
         note_launch();
     }
 }

@@ -353,3 +353,37 @@ def test_dress_after_compression_reuses_tombstones(n):
         bad = compare(iqcc.iqcc_export(H), o.export(), eps=eps)
         assert not bad, bad[:5]
         assert len(H) == len(o)
+
+
+@pytest.mark.parametrize("frac", [0.3, 0.7])
+def test_holes_energy_dis_and_defragmentation(frac):
+    """Compression leaves holes (removed rows stay in place until an append
+    reuses them); with more than half the rows removed the library compacts
+    and rebuilds its index.  Every reduction must ignore the holes."""
+    n = 40
+    rng = np.random.Generator(np.random.PCG64(int(frac * 100)))
+    _, x, z, c = synth.random_hamiltonian(n, 150_000, 41, density=0.2)
+    x[: len(x) // 4] = 0
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    th, ph = synth.qmf_angles(n, "basis")
+    for rnd in range(3):
+        eps = float(np.quantile(np.abs(iqcc.iqcc_export(H)[2]), frac))
+        assert iqcc.iqcc_prune(H, eps, 0) == o.prune(eps, 0)
+        assert len(H) == len(o)
+        assert iqcc.iqcc_qmf_energy(H, th, ph) == pytest.approx(o.energy(th, ph), abs=1e-9)
+        gx, gz = synth.random_generator(n, rng, weight=2)
+        assert np.allclose(iqcc.iqcc_generator_abc(H, gx, gz, th, ph), o.abc(gx, gz, th, ph), rtol=0, atol=1e-9)
+        ox, oz, og = o.dis(th, ph)
+        hx, hz, hg = iqcc.iqcc_dis_gradients(H, th, ph)
+        assert len(hg) == len(og)
+        ref = {(a.tobytes(), b.tobytes()): v for a, b, v in zip(ox, oz, og)}
+        got = {(a.tobytes(), b.tobytes()): v for a, b, v in zip(hx, hz, hg)}
+        assert ref.keys() == got.keys()
+        for _ in range(2):
+            gx, gz = synth.random_generator(n, rng, weight=3)
+            t = float(rng.uniform(-2, 2))
+            iqcc.iqcc_dress(H, gx, gz, [t])
+            o.dress(gx, gz, t)
+        bad = compare(iqcc.iqcc_export(H), o.export(), eps=eps)
+        assert not bad, bad[:5]
