@@ -239,7 +239,7 @@ void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t*
 void launch_state_settle(uint8_t* state, int64_t n, cudaStream_t s);
 // rows kLive with flags 0 -> kDead: tombstone their slot, push them on the free list (count in *n_free)
 void launch_kill(uint8_t* state, const uint8_t* flags, const uint32_t* backptr, HashView h, int64_t n,
-                 uint32_t* free_rows, unsigned long long* n_free, cudaStream_t s);
+                 uint32_t* free_rows, unsigned long long* n_free, int64_t cap, DevCounters* ctr, cudaStream_t s);
 
 // k_expect.cu
 int expect_blocks();
@@ -253,7 +253,8 @@ void launch_qmf_tables(const double* theta, const double* phi, int n, int n_grou
 // DIS basis path: group by x, sum signed contributions.
 void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ,
                       bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe,
-                      uint64_t* gkeys, double* gsum, DevCounters* ctr, cudaStream_t s, const uint8_t* state);
+                      uint64_t* gkeys, double* gsum, DevCounters* ctr, cudaStream_t s, const uint8_t* state,
+                      int64_t max_groups);
 // General-angle gradients of K candidates: partials[block][K].
 void launch_grad_general(int Wd, const uint64_t* rows, const double* coef, int64_t M,
                          const uint64_t* cand, int K, const double* tables, int n_groups,
@@ -310,7 +311,8 @@ void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const 
 void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags,
                         unsigned long long* count, cudaStream_t s, const uint8_t* state);
 // indices of kLive rows (any order), count to *count
-void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, cudaStream_t s);
+void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, int64_t cap,
+                      cudaStream_t s);
 // histogram of one 8-bit digit of |c| bits among kept rows whose higher digits equal prefix
 void launch_abs_digit_hist(const double* coef, const uint8_t* flags, int64_t n, int shift,
                            uint64_t prefix, uint64_t prefix_mask, unsigned long long* hist,

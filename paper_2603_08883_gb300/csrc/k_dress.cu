@@ -183,7 +183,8 @@ __global__ void k_state_settle(uint8_t* state, int64_t n) {
 // Compression: a live row with flag 0 is removed - state kDead, its index slot
 // a tombstone, its row pushed on the free list (warp-aggregated).
 __global__ void k_kill(uint8_t* state, const uint8_t* __restrict__ flags, const uint32_t* __restrict__ backptr,
-                       uint64_t* slots, int64_t n, uint32_t* free_rows, unsigned long long* n_free) {
+                       uint64_t* slots, int64_t n, uint32_t* free_rows, unsigned long long* n_free, int64_t cap,
+                       DevCounters* ctr) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -201,7 +202,11 @@ __global__ void k_kill(uint8_t* state, const uint8_t* __restrict__ flags, const 
             unsigned long long p0 = 0;
             if (lane == leader) p0 = atomicAdd(n_free, (unsigned long long)__popc(m));
             p0 = __shfl_sync(FULL, p0, leader);
-            if (kill) free_rows[p0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+            const unsigned long long at = p0 + __popc(m & ((1u << lane) - 1u));
+            if (kill) {
+                if ((int64_t)at < cap) free_rows[at] = (uint32_t)i;
+                else set_error(ctr, IQCC_ERR_STATE, 30);
+            }
         }
     }
 }
@@ -476,9 +481,10 @@ void launch_state_settle(uint8_t* state, int64_t n, cudaStream_t s) {
 }
 
 void launch_kill(uint8_t* state, const uint8_t* flags, const uint32_t* backptr, HashView h, int64_t n,
-                 uint32_t* free_rows, unsigned long long* n_free, cudaStream_t s) {
+                 uint32_t* free_rows, unsigned long long* n_free, int64_t cap, DevCounters* ctr, cudaStream_t s) {
     if (n <= 0) return;
-    k_kill<<<grid_for(n, 8), kThreads, 0, s>>>(state, flags, backptr, h.slots, n, free_rows, n_free); note_launch();
+    k_kill<<<grid_for(n, 8), kThreads, 0, s>>>(state, flags, backptr, h.slots, n, free_rows, n_free, cap, ctr);
+    note_launch();
 }
 
 void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,

@@ -221,7 +221,8 @@ __global__ void __launch_bounds__(kThreads) k_dis_group(const uint64_t* __restri
                                                         const double* __restrict__ coef, int64_t M, Key<W> occ,
                                                         bool with_values, uint64_t* gslots, uint64_t bucket_mask,
                                                         int max_probe, uint64_t* gkeys, double* gsum,
-                                                        DevCounters* ctr, const uint8_t* __restrict__ state) {
+                                                        DevCounters* ctr, const uint8_t* __restrict__ state,
+                                                        int64_t max_groups) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         if (state && state[i] != kLive) continue;
@@ -244,6 +245,10 @@ __global__ void __launch_bounds__(kThreads) k_dis_group(const uint64_t* __restri
                     unsigned long long prev = atomicCAS(slot, (unsigned long long)kEmptySlot, claim);
                     if (prev == kEmptySlot) {
                         unsigned long long g = atomicAdd(&ctr->n_groups, 1ull);
+                        if ((int64_t)g >= max_groups) {  // never with a correct live count
+                            set_error(ctr, IQCC_ERR_STATE, 12);
+                            g = 0;
+                        }
 #pragma unroll
                         for (int j = 0; j < W; ++j) gkeys[g * W + j] = t.x[j];
                         if (with_values) gsum[g] = 0.0;
@@ -421,23 +426,23 @@ void launch_qmf_tables(const double* theta, const double* phi, int n, int n_grou
 
 void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ_words,
                       bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe, uint64_t* gkeys,
-                      double* gsum, DevCounters* ctr, cudaStream_t s, const uint8_t* state) {
+                      double* gsum, DevCounters* ctr, cudaStream_t s, const uint8_t* state, int64_t max_groups) {
     if (M <= 0) return;
     int grid = abc_grid(M) * 2;
     switch (Wd) {
         case 1: {
             Key<1> o{}; o.x[0] = occ_words[0];
-            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state); note_launch();
+            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state, max_groups); note_launch();
             break;
         }
         case 2: {
             Key<2> o{}; for (int j = 0; j < 2; ++j) o.x[j] = occ_words[j];
-            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state); note_launch();
+            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state, max_groups); note_launch();
             break;
         }
         default: {
             Key<4> o{}; for (int j = 0; j < 4; ++j) o.x[j] = occ_words[j];
-            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state); note_launch();
+            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state, max_groups); note_launch();
             break;
         }
     }

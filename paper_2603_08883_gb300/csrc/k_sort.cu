@@ -415,7 +415,8 @@ __global__ void k_prune_flags(const double* __restrict__ coef, int64_t n, double
 }
 
 // Indices of kLive rows (warp-aggregated; the order is not fixed).
-__global__ void k_live_list(const uint8_t* __restrict__ state, int64_t n, uint32_t* idx, unsigned long long* count) {
+__global__ void k_live_list(const uint8_t* __restrict__ state, int64_t n, uint32_t* idx, unsigned long long* count,
+                            int64_t cap) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -428,7 +429,8 @@ __global__ void k_live_list(const uint8_t* __restrict__ state, int64_t n, uint32
             unsigned long long p0 = 0;
             if (lane == leader) p0 = atomicAdd(count, (unsigned long long)__popc(m));
             p0 = __shfl_sync(FULL, p0, leader);
-            if (live) idx[p0 + __popc(m & ((1u << lane) - 1u))] = (uint32_t)i;
+            const unsigned long long at = p0 + __popc(m & ((1u << lane) - 1u));
+            if (live && (int64_t)at < cap) idx[at] = (uint32_t)i;
         }
     }
 }
@@ -741,9 +743,10 @@ void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flag
     }
 }
 
-void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, cudaStream_t s) {
+void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, int64_t cap,
+                      cudaStream_t s) {
     if (n > 0) {
-        k_live_list<<<grid_stride_blocks(n), kThreads, 0, s>>>(state, n, idx, count);
+        k_live_list<<<grid_stride_blocks(n), kThreads, 0, s>>>(state, n, idx, count, cap);
         note_launch();
     }
 }
