@@ -510,7 +510,8 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     }
     // removed rows become holes: state kDead, index slot a tombstone, row on the free list
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_kill(ctx->state(), flags, ctx->back(), hash_view(ctx), M, ctx->holes() + ctx->n_free, &c->aux, ctx->stream);
+    launch_kill(ctx->state(), flags, ctx->back(), hash_view(ctx), M, ctx->holes() + ctx->n_free, &c->aux,
+                ctx->rows_alloc - ctx->n_free, c, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
@@ -571,7 +572,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     CK_LAUNCH();
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
     launch_dis_group(Wd, ctx->rows(), ctx->c(), M, occ, basis, slots, gh.bucket_mask, ctx->max_probe, gkeys, gsum, c,
-                     ctx->stream, ctx->state());
+                     ctx->stream, ctx->state(), Mg);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
@@ -1033,7 +1034,7 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     // the live rows (holes skipped), then their canonical order
     DevCounters* c = dctr(ctx);
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_live_list(ctx->state(), M, sa.a, &c->aux, ctx->stream);
+    launch_live_list(ctx->state(), M, sa.a, &c->aux, live, ctx->stream);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
