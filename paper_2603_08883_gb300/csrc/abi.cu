@@ -158,8 +158,7 @@ uint64_t pow2_at_least(uint64_t v) {
     return p;
 }
 
-// (Re)build the index over the live rows of [0, M) with `slots` slots (no
-// tombstones afterwards; each live row's slot is recorded in backptr).
+// (Re)build the index over rows [0, M) with `slots` slots.
 iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     if (slots != ctx->hash_slots || !ctx->hash.p) {
         release(ctx, ctx->hash);
@@ -171,7 +170,7 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     HashView h = hash_view(ctx);
     launch_hash_clear(h, ctx->hash_slots, ctx->stream);
     CK_LAUNCH();
-    launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream, ctx->state(), ctx->back());
+    launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream);
     CK_LAUNCH();
     ctx->n_tomb = 0;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -184,27 +183,26 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     return read_counters(ctx);
 }
 
-// Row buffers able to hold `rows_needed` rows (current rows, states, slots and
-// free list kept), and an index whose entries plus tombstones stay at or below
-// half its slots once `new_entries` more keys are inserted.
-iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed, int64_t new_entries) {
+// Rows and index able to hold `rows_needed` rows (current rows kept).
+iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
     if (rows_needed > ctx->rows_alloc) {
         int64_t want = std::max<int64_t>(rows_needed, ctx->rows_alloc + ctx->rows_alloc / 2);
         want = std::min<int64_t>(want, ctx->capacity);
         want = std::max<int64_t>(want, rows_needed);
         const size_t rb = row_bytes(ctx);
         if (!grow_keep(ctx, ctx->keys, (size_t)want * rb, (size_t)ctx->M * rb) ||
-            !grow_keep(ctx, ctx->coef, (size_t)want * 8, (size_t)ctx->M * 8) ||
-            !grow_keep(ctx, ctx->epoch, (size_t)want, (size_t)ctx->M) ||
-            !grow_keep(ctx, ctx->backptr, (size_t)want * 4, (size_t)ctx->M * 4) ||
-            !grow_keep(ctx, ctx->freelist, (size_t)want * 4, (size_t)ctx->n_free * 4))
+            !grow_keep(ctx, ctx->coef, (size_t)want * 8, (size_t)ctx->M * 8))
             return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
         ctx->rows_alloc = want;
         ctx->stats.rows_allocated = want;
     }
-    const uint64_t occupied = (uint64_t)(ctx->n_live + new_entries + ctx->n_tomb);
-    if (occupied * 2 > ctx->hash_slots) {
-        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)(ctx->n_live + new_entries) * 2));
+    // entries at most 1/2 of the slots once the rows are inserted (else a larger
+    // table), and entries plus tombstones at most 3/4 (else a fresh build)
+    if ((uint64_t)rows_needed * 2 > ctx->hash_slots) {
+        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 2));
+        if (st) return st;
+    } else if ((uint64_t)(rows_needed + ctx->n_tomb) * 4 > ctx->hash_slots * 3) {
+        iqcc_status st = rebuild_hash(ctx, ctx->hash_slots);
         if (st) return st;
     }
     return IQCC_OK;
@@ -280,7 +278,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_abc(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pkey, basis, occ, tables, n_groups(ctx), partials,
-               ctx->stream, ctx->state());
+               ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     launch_reduce3(partials, nb, out3, ctx->stream);
@@ -292,7 +290,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.n_energy++;
     ctx->stats.energy_kernel_ms += ms;
-    ctx->stats.energy_bytes += (double)ctx->n_live * (16.0 * ctx->Wd + 8.0);
+    ctx->stats.energy_bytes += (double)ctx->M * (16.0 * ctx->Wd + 8.0);
     abc[0] = h3[0];
     abc[1] = h3[1];
     abc[2] = h3[2];
@@ -301,60 +299,51 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
 
 // One generator (device-layout key); on IQCC_ERR_CAPACITY / OOM H is unchanged.
 iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
-    if (ctx->n_live == 0) {
+    if (ctx->M == 0) {
         ctx->stats.n_dress++;
         return IQCC_OK;
     }
-    const int64_t M = ctx->M, live = ctx->n_live, nf = ctx->n_free;
-    // appends are at most the live anticommuting rows; they fill holes first
-    int64_t new_upper = live;
-    int64_t rows_upper = M + std::max<int64_t>(0, new_upper - nf);
+    const int64_t M = ctx->M;
+    int64_t upper = 2 * M;
     DevCounters* c = dctr(ctx);
-    if (rows_upper > ctx->capacity) {
+    if (upper > ctx->capacity) {
         // exact admission count (probe only)
         CK(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), ctx->stream));
-        launch_dress_count(ctx->Wd, ctx->rows(), M, pkey, hash_view(ctx), c, ctx->stream, ctx->state());
+        launch_dress_count(ctx->Wd, ctx->rows(), M, pkey, hash_view(ctx), c, ctx->stream);
         CK_LAUNCH();
         iqcc_status st = read_counters(ctx);
         if (st) return st;
-        new_upper = (int64_t)ctx->h_counters->n_new;
-        rows_upper = M + std::max<int64_t>(0, new_upper - nf);
-        if (rows_upper > ctx->capacity) {
+        upper = M + (int64_t)ctx->h_counters->n_new;
+        if (upper > ctx->capacity) {
             char buf[200];
-            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)rows_upper,
+            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)upper,
                      (long long)ctx->capacity);
             return fail(ctx, IQCC_ERR_CAPACITY, buf);
         }
     }
-    iqcc_status st = reserve_rows(ctx, rows_upper, new_upper);
+    iqcc_status st = reserve_rows(ctx, upper);
     if (st) return st;
     CK(cudaMemsetAsync(c, 0, 5 * sizeof(unsigned long long), ctx->stream));  // n_new .. tomb_reused
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_dress(ctx->Wd, ctx->rows(), ctx->rows(), ctx->c(), M, pkey, std::cos(tau), std::sin(tau),
-                 hash_view(ctx), c, ctx->stream, ctx->state(), ctx->back(), ctx->holes(), nf);
+                 hash_view(ctx), c, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
     if (st) return st;
     const int64_t n_new = (int64_t)ctx->h_counters->n_new;
     const int64_t n_anti = (int64_t)ctx->h_counters->n_anti;
-    const int64_t reused = (int64_t)ctx->h_counters->tomb_reused;
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    // the dress kernel indexed the appended rows itself; they took holes first
-    ctx->M = M + std::max<int64_t>(0, n_new - nf);
-    ctx->n_free = std::max<int64_t>(0, nf - n_new);
-    ctx->n_live = live + n_new;
-    ctx->n_tomb = std::max<int64_t>(0, ctx->n_tomb - reused);
-    launch_state_settle(ctx->state(), ctx->M, ctx->stream);
-    CK_LAUNCH();
+    ctx->M = M + n_new;  // the dress kernel indexed the appended rows itself
+    ctx->n_tomb = std::max<int64_t>(0, ctx->n_tomb - (int64_t)ctx->h_counters->tomb_reused);
     iqcc_stats& s = ctx->stats;
     s.n_dress++;
-    s.dressed_terms += live;
+    s.dressed_terms += M;
     s.anticommuting += n_anti;
     s.appended += n_new;
     s.dress_kernel_ms += ms;
-    s.dress_bytes += 16.0 * ctx->Wd * (double)live + 16.0 * (double)n_anti + (16.0 * ctx->Wd + 8.0) * (double)n_new;
+    s.dress_bytes += 16.0 * ctx->Wd * (double)M + 16.0 * (double)n_anti + (16.0 * ctx->Wd + 8.0) * (double)n_new;
     return IQCC_OK;
 }
 
@@ -383,45 +372,16 @@ size_t sort_area_bytes(int64_t n) {
     return dry.off;
 }
 
-// Remove the holes: compact the live rows to [0, n_live) in place (stable)
-// and rebuild the index.  flags and cscratch: scratch of at least M entries.
-iqcc_status defragment(iqcc_ctx* ctx, uint8_t* flags, char* cscratch) {
-    const int64_t M = ctx->M;
-    DevCounters* c = dctr(ctx);
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_prune_flags(ctx->c(), M, 0.0, flags, &c->aux, ctx->stream, ctx->state());  // flags = live
-    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
-    CK_LAUNCH();
-    CK(cudaEventRecord(ctx->ev1, ctx->stream));
-    iqcc_status st = read_counters(ctx);
-    if (st) return st;
-    float ms = 0;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    ctx->stats.prune_ms += ms;
-    const int64_t live = (int64_t)ctx->h_counters->aux;
-    if (live != ctx->n_live) {
-        char buf[160];
-        snprintf(buf, sizeof buf, "internal: %lld live rows found, %lld expected", (long long)live,
-                 (long long)ctx->n_live);
-        return fail(ctx, IQCC_ERR_STATE, buf);
-    }
-    CK(cudaMemsetAsync(ctx->state(), kLive, (size_t)live, ctx->stream));
-    ctx->M = live;
-    ctx->n_free = 0;
-    return rebuild_hash(ctx, ctx->hash_slots);
-}
-
 iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed) {
     const int64_t M = ctx->M;
     *removed = 0;
-    if (ctx->n_live == 0) return IQCC_OK;
+    if (M == 0) return IQCC_OK;
     Carver cv;
     cv.take<uint8_t>(M);
     cv.take<unsigned long long>(256);
     cv.take<char>(compact_inplace_scratch_bytes(M));
     cv.take<uint32_t>(M);  // tie list
+    cv.take<uint32_t>(M);  // old row -> new row
     cv.off += sort_area_bytes(M);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
@@ -429,13 +389,14 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     unsigned long long* hist = cv.take<unsigned long long>(256);
     char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
+    uint32_t* new_row = cv.take<uint32_t>(M);
     SortArea sa = carve_sort(cv, M);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
     DevCounters* c = dctr(ctx);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
-    launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream, ctx->state());
+    launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
@@ -508,10 +469,8 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
             CK_LAUNCH();
         }
     }
-    // removed rows become holes: state kDead, index slot a tombstone, row on the free list
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_kill(ctx->state(), flags, ctx->back(), hash_view(ctx), M, ctx->holes() + ctx->n_free, &c->aux,
-                ctx->rows_alloc - ctx->n_free, c, ctx->stream);
+    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream, new_row);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
@@ -519,12 +478,20 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.prune_ms += ms;
-    const int64_t killed = (int64_t)ctx->h_counters->aux;
-    ctx->n_live -= killed;
-    ctx->n_free += killed;
-    ctx->n_tomb += killed;
-    *removed = killed;
-    if (ctx->n_free > ctx->M / 2 && ctx->M > (1 << 16)) return defragment(ctx, flags, cscratch);
+    const int64_t newM = (int64_t)ctx->h_counters->aux;
+    ctx->M = newM;
+    *removed = M - newM;
+    if (newM == M) return IQCC_OK;  // nothing moved
+    // rows moved: remap the index in place (kept keys keep their slots, removed keys become tombstones)
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    launch_hash_remap(hash_view(ctx), ctx->hash_slots, new_row, ctx->stream);
+    CK_LAUNCH();
+    ctx->n_tomb += M - newM;
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float hms = 0;
+    cudaEventElapsedTime(&hms, ctx->ev0, ctx->ev1);
+    ctx->stats.hash_ms += hms;
     return IQCC_OK;
 }
 
@@ -537,8 +504,8 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     const bool basis = is_basis(ctx, theta);
     uint64_t occ[4];
     occ_words(ctx, theta, occ);
-    // groups (distinct flip sets) are at most the live rows
-    const int64_t Mg = std::max<int64_t>(ctx->n_live, 1);
+    // groups (distinct flip sets) are at most the rows
+    const int64_t Mg = std::max<int64_t>(M, 1);
     const uint64_t gslots = pow2_at_least((uint64_t)Mg * 2);
     const int nblk = expect_blocks();
     constexpr int64_t kHeadLimit = 1 << 16;  // the top-k path orders at most this many candidates
@@ -572,7 +539,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     CK_LAUNCH();
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
     launch_dis_group(Wd, ctx->rows(), ctx->c(), M, occ, basis, slots, gh.bucket_mask, ctx->max_probe, gkeys, gsum, c,
-                     ctx->stream, ctx->state(), Mg);
+                     ctx->stream, Mg);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
@@ -598,7 +565,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
             }
             CK(cudaMemcpyAsync(cand, hc, sizeof(uint64_t) * 2 * Wd * K, cudaMemcpyHostToDevice, ctx->stream));
             launch_grad_general(Wd, ctx->rows(), ctx->c(), M, cand, K, tables, n_groups(ctx), partials, nblk,
-                                ctx->stream, ctx->state());
+                                ctx->stream);
             CK_LAUNCH();
             launch_reduce_cols(partials, nblk, 16, colsum, ctx->stream);
             CK_LAUNCH();
@@ -712,7 +679,7 @@ iqcc_status gradients_given(iqcc_ctx* ctx, const double* theta, const double* ph
         for (int i = 0; i < k; ++i) pad_key(ctx, cx + (k0 + i) * ctx->W, cz + (k0 + i) * ctx->W, hc + i * 2 * Wd);
         CK(cudaMemcpyAsync(cand, hc, sizeof(uint64_t) * 2 * Wd * k, cudaMemcpyHostToDevice, ctx->stream));
         launch_grad_general(Wd, ctx->rows(), ctx->c(), ctx->M, cand, k, tables, n_groups(ctx), partials, nblk,
-                            ctx->stream, ctx->state());
+                            ctx->stream);
         CK_LAUNCH();
         launch_reduce_cols(partials, nblk, 16, colsum, ctx->stream);
         CK_LAUNCH();
@@ -783,9 +750,7 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
     }
     const int64_t rows0 = std::min<int64_t>(ctx->capacity, std::max<int64_t>(1024, 2 * n_terms));
     const size_t rb = row_bytes(ctx);
-    if (!ensure(ctx, ctx->keys, (size_t)rows0 * rb) || !ensure(ctx, ctx->coef, (size_t)rows0 * 8) ||
-        !ensure(ctx, ctx->epoch, (size_t)rows0) || !ensure(ctx, ctx->backptr, (size_t)rows0 * 4) ||
-        !ensure(ctx, ctx->freelist, (size_t)rows0 * 4)) {
+    if (!ensure(ctx, ctx->keys, (size_t)rows0 * rb) || !ensure(ctx, ctx->coef, (size_t)rows0 * 8)) {
         fail(ctx, IQCC_ERR_OOM, "row allocation failed");
         return bail(IQCC_ERR_OOM);
     }
@@ -842,12 +807,6 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
             ctx->M = (int64_t)ctx->h_counters->aux;
         } while (0);
         if (st) return bail(st);
-    }
-    ctx->n_live = ctx->M;
-    ctx->n_free = 0;
-    if (ctx->M > 0 && cudaMemsetAsync(ctx->state(), kLive, (size_t)ctx->M, ctx->stream) != cudaSuccess) {
-        fail_cuda(ctx, cudaGetLastError(), "state init", __LINE__);
-        return bail(IQCC_ERR_CUDA);
     }
     iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
     ctx->launch_base = launches();
@@ -944,8 +903,8 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     if (n_gen < 0 || n_gen > 64) return fail(ctx, IQCC_ERR_ARG, "n_gen must be in 0..64");
     if (o->n_forced > 0 && (!o->forced_x || !o->forced_z)) return fail(ctx, IQCC_ERR_ARG, "null forced generators");
     std::memset(out, 0, sizeof *out);
-    out->n_terms_before = ctx->n_live;
-    out->n_terms_peak = ctx->n_live;
+    out->n_terms_before = ctx->M;
+    out->n_terms_peak = ctx->M;
     const double gmin = o->min_gradient > 0 ? o->min_gradient : 1e-12;
     std::vector<uint64_t> gx((size_t)64 * W), gz((size_t)64 * W);
     std::vector<double> g(64);
@@ -973,7 +932,7 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         double tau;
         if (o->n_forced > 0 && o->forced_tau) tau = o->forced_tau[k];
         else tau = (abc[1] == 0.0 && abc[2] == 0.0) ? 0.0 : std::atan2(-abc[2], -abc[1]);
-        out->dressed_terms += ctx->n_live;
+        out->dressed_terms += ctx->M;
         int applied = 0;
         st = iqcc_dress(ctx, 1, gx.data() + k * W, gz.data() + k * W, &tau, &applied);
         if (st) {
@@ -986,8 +945,8 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         out->tau[k] = tau;
         for (int i = 0; i < 3; ++i) out->abc[k][i] = abc[i];
         out->n_applied = k + 1;
-        out->n_terms_peak = std::max(out->n_terms_peak, ctx->n_live);
-        if (o->max_terms > 0 && ctx->n_live > o->max_terms) {
+        out->n_terms_peak = std::max(out->n_terms_peak, ctx->M);
+        if (o->max_terms > 0 && ctx->M > o->max_terms) {
             int64_t cut = 0;
             st = iqcc_prune(ctx, 0.0, o->max_terms, &cut);
             if (st) return st;
@@ -998,14 +957,14 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     iqcc_status st = iqcc_prune(ctx, o->eps, o->max_terms, &removed);
     if (st) return st;
     out->n_removed += removed;
-    out->n_terms = ctx->n_live;
+    out->n_terms = ctx->M;
     return iqcc_qmf_energy(ctx, theta, phi, &out->energy);
 }
 
 iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms) {
     if (!ctx || !n_terms) return fail(nullptr, IQCC_ERR_ARG, "null argument");
     if (ctx->broken) return IQCC_ERR_STATE;
-    *n_terms = ctx->n_live;
+    *n_terms = ctx->M;
     return IQCC_OK;
 }
 
@@ -1013,34 +972,27 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     GUARD(ctx);
     if (!n) return fail(ctx, IQCC_ERR_ARG, "n is NULL");
     if (cap < 0) return fail(ctx, IQCC_ERR_ARG, "cap < 0");
-    *n = ctx->n_live;
-    const int64_t k = std::min(cap, ctx->n_live);
+    *n = ctx->M;
+    const int64_t k = std::min(cap, ctx->M);
     if (k == 0) return IQCC_OK;
     if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
-    const int64_t M = ctx->M, live = ctx->n_live;
+    const int64_t M = ctx->M;
     const int W = ctx->W;
     Carver cv;
-    cv.off += sort_area_bytes(live);
+    cv.off += sort_area_bytes(M);
     cv.take<uint64_t>((size_t)k * W);
     cv.take<uint64_t>((size_t)k * W);
     cv.take<double>(k);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
-    SortArea sa = carve_sort(cv, live);
+    SortArea sa = carve_sort(cv, M);
     uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
     uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
     double* sc = cv.take<double>(k);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    // the live rows (holes skipped), then their canonical order
-    DevCounters* c = dctr(ctx);
-    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_live_list(ctx->state(), M, sa.a, &c->aux, live, ctx->stream);
-    CK_LAUNCH();
-    iqcc_status st = read_counters(ctx);
-    if (st) return st;
-    if ((int64_t)ctx->h_counters->aux != live) return fail(ctx, IQCC_ERR_STATE, "internal: live row count mismatch");
+    launch_iota(sa.a, M, ctx->stream);
     uint32_t* sorted = nullptr;
-    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, live, &sorted, sa.tmp, sa.tmp_bytes,
+    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, M, &sorted, sa.tmp, sa.tmp_bytes,
                         ctx->stream);
     CK_LAUNCH();
     launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), sorted, sx, sz, sc, k, ctx->stream);
@@ -1080,9 +1032,6 @@ void iqcc_free(iqcc_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     release(ctx, ctx->keys);
     release(ctx, ctx->coef);
-    release(ctx, ctx->epoch);
-    release(ctx, ctx->backptr);
-    release(ctx, ctx->freelist);
     release(ctx, ctx->hash);
     release(ctx, ctx->counters);
     release(ctx, ctx->scratch);

@@ -19,11 +19,6 @@ namespace iqcc {
 constexpr uint64_t kEmptySlot = ~0ull;        // hash slot never used
 constexpr uint64_t kTombSlot = ~1ull;         // hash slot whose row was removed (row field 0xFFFFFFFE)
 constexpr uint32_t kRowRemoved = 0xFFFFFFFFu; // compaction map entry of a removed row
-// Row states (one byte per row).  Removed rows stay in place as holes until an
-// append reuses them; kernels that stream the rows visit only kLive rows.
-constexpr uint8_t kLive = 0;   // a term of H
-constexpr uint8_t kNew = 1;    // appended by the dress pass in progress (not visited by it)
-constexpr uint8_t kDead = 2;   // removed; its index slot is a tombstone and its row is on the free list
 constexpr uint32_t kPendingGroup = 0xFFFFFFFEu;  // group slot claimed, key not yet published
 constexpr int kBucketSlots = 4;               // 4 x 8-byte slots = one 32-byte sector
 
@@ -138,7 +133,7 @@ struct DevCounters {
     unsigned long long n_anti;     // anticommuting rows seen by a dress
     unsigned long long n_groups;   // DIS groups / compaction output
     unsigned long long aux;        // scratch counter
-    unsigned long long tomb_reused;  // inserts that reused a tombstone
+    unsigned long long tomb_reused;  // dress inserts that took a tombstone
     int err;                       // iqcc_status set by a kernel (first error wins)
     int err_where;                 // which kernel
 };
@@ -182,17 +177,12 @@ struct iqcc_ctx {
     void (*dfree)(void*, void*) = nullptr;
     void* alloc_user = nullptr;
 
-    int64_t M = 0;                 // rows in use, holes included (kernels stream [0, M))
-    int64_t n_live = 0;            // terms of H (rows in state kLive)
-    int64_t n_free = 0;            // holes on the free list
-    int64_t n_tomb = 0;            // tombstones in the index (upper bound)
-    int64_t rows_alloc = 0;        // rows allocated in the row buffers
+    int64_t M = 0;                 // live rows
+    int64_t rows_alloc = 0;        // rows allocated in the key/coef buffers
     iqcc::Buf keys, coef;
-    iqcc::Buf epoch;               // uint8 row state
-    iqcc::Buf backptr;             // uint32 index slot of each live row
-    iqcc::Buf freelist;            // uint32 holes (LIFO)
     iqcc::Buf hash;                // slots
     uint64_t hash_slots = 0;       // active slots (power of two)
+    int64_t n_tomb = 0;            // tombstones in the index (counted: removed rows minus reuses)
     iqcc::Buf counters;            // DevCounters
     iqcc::DevCounters* h_counters = nullptr;  // pinned host mirror
     iqcc::Buf scratch;             // general scratch (grows)
@@ -206,9 +196,6 @@ struct iqcc_ctx {
 
     uint64_t* rows() const { return (uint64_t*)keys.p; }
     double* c() const { return (double*)coef.p; }
-    uint8_t* state() const { return (uint8_t*)epoch.p; }
-    uint32_t* back() const { return (uint32_t*)backptr.p; }
-    uint32_t* holes() const { return (uint32_t*)freelist.p; }
 };
 
 namespace iqcc {
@@ -226,39 +213,31 @@ long long launches();
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
 // after an in-place compaction with map new_row (old row -> new row or kRowRemoved)
 void launch_hash_remap(HashView h, uint64_t slots, const uint32_t* new_row, cudaStream_t s);
-// index the kLive rows of [lo, hi) (state may be NULL: all), recording each row's slot in backptr
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
-                        DevCounters* ctr, cudaStream_t s, const uint8_t* state, uint32_t* backptr);
-// rows [0, M) in place; appends pop free[n_free-1], free[n_free-2], ... then take rows M, M+1, ...
+                        DevCounters* ctr, cudaStream_t s);
 void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
                   const uint64_t* pkey, double cos_t, double sin_t, HashView h, DevCounters* ctr,
-                  cudaStream_t s, uint8_t* state, uint32_t* backptr, const uint32_t* free_rows, int64_t n_free);
+                  cudaStream_t s);
 void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,
-                        DevCounters* ctr, cudaStream_t s, const uint8_t* state);
-// kNew -> kLive over [0, n)
-void launch_state_settle(uint8_t* state, int64_t n, cudaStream_t s);
-// rows kLive with flags 0 -> kDead: tombstone their slot, push them on the free list (count in *n_free)
-void launch_kill(uint8_t* state, const uint8_t* flags, const uint32_t* backptr, HashView h, int64_t n,
-                 uint32_t* free_rows, unsigned long long* n_free, int64_t cap, DevCounters* ctr, cudaStream_t s);
+                        DevCounters* ctr, cudaStream_t s);
 
 // k_expect.cu
 int expect_blocks();
 // Fills partials[block][3] with (A, B, C) sums; pkey may be all-zero (energy).
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,
                 bool basis, const uint64_t* occ, const double* tables, int n_groups, double* partials,
-                cudaStream_t s, const uint8_t* state = nullptr);
+                cudaStream_t s);
 void launch_reduce3(const double* partials, int n, double* out3, cudaStream_t s);
 void launch_qmf_tables(const double* theta, const double* phi, int n, int n_groups, double* tables,
                        cudaStream_t s);
 // DIS basis path: group by x, sum signed contributions.
 void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ,
                       bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe,
-                      uint64_t* gkeys, double* gsum, DevCounters* ctr, cudaStream_t s, const uint8_t* state,
-                      int64_t max_groups);
+                      uint64_t* gkeys, double* gsum, DevCounters* ctr, cudaStream_t s, int64_t max_groups);
 // General-angle gradients of K candidates: partials[block][K].
 void launch_grad_general(int Wd, const uint64_t* rows, const double* coef, int64_t M,
                          const uint64_t* cand, int K, const double* tables, int n_groups,
-                         double* partials, int n_blocks, cudaStream_t s, const uint8_t* state);
+                         double* partials, int n_blocks, cudaStream_t s);
 void launch_reduce_cols(const double* partials, int rows, int cols, double* out, cudaStream_t s);
 
 // k_sort.cu
@@ -307,12 +286,8 @@ void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const 
                         int64_t n, uint64_t* rows_out, double* c_out, cudaStream_t s);
 
 // prune
-// flags = state kLive (state may be NULL) and !(|c| < eps); count of set flags to *count
 void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags,
-                        unsigned long long* count, cudaStream_t s, const uint8_t* state);
-// indices of kLive rows (any order), count to *count
-void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, int64_t cap,
-                      cudaStream_t s);
+                        unsigned long long* count, cudaStream_t s);
 // histogram of one 8-bit digit of |c| bits among kept rows whose higher digits equal prefix
 void launch_abs_digit_hist(const double* coef, const uint8_t* flags, int64_t n, int shift,
                            uint64_t prefix, uint64_t prefix_mask, unsigned long long* hist,

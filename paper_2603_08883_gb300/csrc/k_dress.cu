@@ -3,11 +3,11 @@
 //
 // Index: 2^k buckets of 4 eight-byte slots (one 32-byte sector); a slot holds
 // (fingerprint32 << 32) | row32, kEmptySlot when never used and kTombSlot
-// when its row was removed.  Lookups skip tombstones and stop at the first
-// empty slot.  Each live row records its slot (backptr), so removing a row
-// writes one tombstone without a lookup; inserts reuse the first tombstone on
-// their probe sequence.  A removed row stays in place as a hole (state kDead)
-// on a free list that later appends pop, so compression moves no rows.
+// when its row was removed by compression.  Lookups skip tombstones and stop
+// at the first empty slot.  Compression does not rebuild the index: it remaps
+// every slot through the old-row -> new-row map of the compaction (removed
+// rows become tombstones), and inserts reuse the first tombstone on a probe
+// sequence, so tombstones are recycled by later dresses.
 //
 // Dress: one streaming pass over the M rows.  For a row T that anticommutes
 // with P (popcount parity of (xT & zP) ^ (zT & xP)), its partner Q = T xor P is
@@ -82,15 +82,14 @@ __device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, con
 }
 
 // Insert `entry` (a key proven absent) at `slot` if it still holds `expect`,
-// else at the next empty or tombstone slot of its probe sequence.  Returns the
-// slot used (~0 when the probe bound was reached); *tomb tells whether it held
-// a tombstone.
-__device__ __forceinline__ uint64_t insert_from(uint64_t entry, uint64_t slot, uint64_t expect, const HashView& h,
-                                                bool* tomb) {
+// else at the next empty or tombstone slot of its probe sequence.  *tomb tells
+// whether the slot used held a tombstone.
+__device__ __forceinline__ bool insert_from(uint64_t entry, uint64_t slot, uint64_t expect, const HashView& h,
+                                            bool* tomb) {
     unsigned long long* base = reinterpret_cast<unsigned long long*>(h.slots);
     if (atomicCAS(base + slot, (unsigned long long)expect, (unsigned long long)entry) == expect) {
         *tomb = expect == kTombSlot;
-        return slot;
+        return true;
     }
     uint64_t b = slot / kBucketSlots;
     int k0 = (int)(slot % kBucketSlots) + 1;
@@ -102,7 +101,7 @@ __device__ __forceinline__ uint64_t insert_from(uint64_t entry, uint64_t slot, u
                 const unsigned long long prev = atomicCAS(s, v, (unsigned long long)entry);
                 if (prev == v) {
                     *tomb = v == kTombSlot;
-                    return b * kBucketSlots + k;
+                    return true;
                 }
                 v = prev;
             }
@@ -110,7 +109,7 @@ __device__ __forceinline__ uint64_t insert_from(uint64_t entry, uint64_t slot, u
         k0 = 0;
         b = (b + 1) & h.bucket_mask;
     }
-    return ~0ull;
+    return false;
 }
 
 template <int W>
@@ -131,83 +130,25 @@ __global__ void k_hash_clear(uint64_t* slots, uint64_t n) {
         p[i] = make_ulonglong2(kEmptySlot, kEmptySlot);
 }
 
-// Index the live rows of [lo, hi) into a table without tombstones (a fresh
-// build): one row per thread, occupied slots skipped by a plain read before
-// the CAS; each row's slot is recorded in backptr.
+// Index rows [lo, hi) into a table without tombstones (a fresh build): one row
+// per thread, occupied slots skipped by a plain read before the CAS.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_hash_insert(const uint64_t* __restrict__ rows, int64_t lo,
-                                                          int64_t hi, HashView h, DevCounters* ctr,
-                                                          const uint8_t* __restrict__ state, uint32_t* backptr) {
+                                                          int64_t hi, HashView h, DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += stride) {
-        if (state && state[i] != kLive) continue;
         const uint64_t hv = hash_key<W>(load_key<W>(rows, i));
         const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)i;
         uint64_t b = hv & h.bucket_mask;
         bool done = false;
         for (int p = 0; p < h.max_probe && !done; ++p) {
             unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
-            for (int k = 0; k < 4 && !done; ++k) {
+            for (int k = 0; k < 4 && !done; ++k)
                 done = s[k] == kEmptySlot &&
                        atomicCAS(s + k, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot;
-                if (done && backptr) backptr[i] = (uint32_t)(b * kBucketSlots + k);
-            }
             b = (b + 1) & h.bucket_mask;
         }
         if (!done) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
-    }
-}
-
-// kNew -> kLive once a dress has finished.
-__global__ void k_state_settle(uint8_t* state, int64_t n) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x * 16;
-    for (int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * 16; i < n; i += stride) {
-        if (i + 16 <= n) {
-            uint4 v = *reinterpret_cast<uint4*>(state + i);
-            uint32_t w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {  // bytes equal to kNew (1) become kLive (0)
-                const uint32_t x = w[k] ^ 0x01010101u;  // kNew bytes -> 0
-                // exact per-byte zero test: high bit set iff the byte of x is 0
-                const uint32_t zero = ~(((x & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | x | 0x7F7F7F7Fu);
-                w[k] &= ~(zero >> 7);
-            }
-            *reinterpret_cast<uint4*>(state + i) = make_uint4(w[0], w[1], w[2], w[3]);
-        } else {
-            for (int64_t j = i; j < n; ++j)
-                if (state[j] == kNew) state[j] = kLive;
-        }
-    }
-}
-
-// Compression: a live row with flag 0 is removed - state kDead, its index slot
-// a tombstone, its row pushed on the free list (warp-aggregated).
-__global__ void k_kill(uint8_t* state, const uint8_t* __restrict__ flags, const uint32_t* __restrict__ backptr,
-                       uint64_t* slots, int64_t n, uint32_t* free_rows, unsigned long long* n_free, int64_t cap,
-                       DevCounters* ctr) {
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t i = base + lane;
-        bool kill = false;
-        if (i < n && state[i] == kLive && !flags[i]) {
-            kill = true;
-            state[i] = kDead;
-            slots[backptr[i]] = kTombSlot;
-        }
-        const unsigned m = __ballot_sync(FULL, kill);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            unsigned long long p0 = 0;
-            if (lane == leader) p0 = atomicAdd(n_free, (unsigned long long)__popc(m));
-            p0 = __shfl_sync(FULL, p0, leader);
-            const unsigned long long at = p0 + __popc(m & ((1u << lane) - 1u));
-            if (kill) {
-                if ((int64_t)at < cap) free_rows[at] = (uint32_t)i;
-                else set_error(ctr, IQCC_ERR_STATE, 30);
-            }
-        }
     }
 }
 
@@ -294,10 +235,7 @@ constexpr int kWarpTile = 64;  // rows classified per warp before the probes
 template <int W>
 __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) k_dress(const uint64_t* __restrict__ rows,
                                                                     uint64_t* rows_app, double* coef, int64_t M,
-                                                                    Gen<W> g, HashView h, DevCounters* ctr,
-                                                                    uint8_t* state, uint32_t* backptr,
-                                                                    const uint32_t* __restrict__ free_rows,
-                                                                    int64_t n_free) {
+                                                                    Gen<W> g, HashView h, DevCounters* ctr) {
     __shared__ uint32_t s_queue[kThreads / 32][kWarpTile];
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -312,7 +250,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
         for (int r = 0; r < kWarpTile / 32; ++r) {
             const int64_t i = base + r * 32 + lane;
             bool a = false;
-            if (i < M && state[i] == kLive) a = anticommutes<W>(load_key<W>(rows, i), g.p);
+            if (i < M) a = anticommutes<W>(load_key<W>(rows, i), g.p);
             const unsigned m = __ballot_sync(FULL, a);
             if (a) queue[nq + __popc(m & lt)] = (uint32_t)(r * 32 + lane);
             nq += __popc(m);
@@ -355,21 +293,13 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
                 if (lane == leader) slot0 = atomicAdd(&ctr->n_new, (unsigned long long)__popc(need));
                 slot0 = __shfl_sync(FULL, slot0, leader);
                 if (append) {
-                    // a hole from the free list while there are any, else the next row past M
-                    const int64_t pos = (int64_t)slot0 + __popc(need & lt);
-                    const int64_t r = pos < n_free ? (int64_t)free_rows[n_free - 1 - pos] : M + (pos - n_free);
+                    const int64_t r = M + (int64_t)slot0 + __popc(need & lt);
                     store_key<W>(rows_app, r, q);
                     coef[r] = c_new;
-                    state[r] = kNew;
                     const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)r;
                     bool tomb = false;
-                    const uint64_t slot = insert_from(entry, fslot, fval, h, &tomb);
-                    if (slot == ~0ull) {
-                        set_error(ctr, IQCC_ERR_HASH_FULL, 4);
-                    } else {
-                        backptr[r] = (uint32_t)slot;
-                        if (tomb) atomicAdd(&ctr->tomb_reused, 1ull);
-                    }
+                    if (!insert_from(entry, fslot, fval, h, &tomb)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
+                    else if (tomb) atomicAdd(&ctr->tomb_reused, 1ull);
                 }
             }
         }
@@ -381,14 +311,12 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
 // Admission count: how many partners a dress would append (no writes to H).
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_dress_count(const uint64_t* __restrict__ rows, int64_t M,
-                                                          Gen<W> g, HashView h, DevCounters* ctr,
-                                                          const uint8_t* __restrict__ state) {
+                                                          Gen<W> g, HashView h, DevCounters* ctr) {
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31;
     unsigned cnt = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        if (state[i] != kLive) continue;
         Key<W> t = load_key<W>(rows, i);
         if (anticommutes<W>(t, g.p)) {
             Key<W> q = key_xor<W>(t, g.p);
@@ -464,49 +392,36 @@ void launch_hash_remap(HashView h, uint64_t slots, const uint32_t* new_row, cuda
 }
 
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
-                        DevCounters* ctr, cudaStream_t s, const uint8_t* state, uint32_t* backptr) {
+                        DevCounters* ctr, cudaStream_t s) {
     if (hi <= lo) return;
     int grid = grid_for(hi - lo, 8);
     switch (Wd) {
-        case 1: k_hash_insert<1><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr, state, backptr); note_launch(); break;
-        case 2: k_hash_insert<2><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr, state, backptr); note_launch(); break;
-        default: k_hash_insert<4><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr, state, backptr); note_launch(); break;
+        case 1: k_hash_insert<1><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
+        case 2: k_hash_insert<2><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
+        default: k_hash_insert<4><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
     }
-}
-
-void launch_state_settle(uint8_t* state, int64_t n, cudaStream_t s) {
-    if (n <= 0) return;
-    int grid = grid_for((n + 15) / 16, 8);
-    k_state_settle<<<grid, kThreads, 0, s>>>(state, n); note_launch();
-}
-
-void launch_kill(uint8_t* state, const uint8_t* flags, const uint32_t* backptr, HashView h, int64_t n,
-                 uint32_t* free_rows, unsigned long long* n_free, int64_t cap, DevCounters* ctr, cudaStream_t s) {
-    if (n <= 0) return;
-    k_kill<<<grid_for(n, 8), kThreads, 0, s>>>(state, flags, backptr, h.slots, n, free_rows, n_free, cap, ctr);
-    note_launch();
 }
 
 void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
                   const uint64_t* pkey, double cos_t, double sin_t, HashView h, DevCounters* ctr,
-                  cudaStream_t s, uint8_t* state, uint32_t* backptr, const uint32_t* free_rows, int64_t n_free) {
+                  cudaStream_t s) {
     if (M <= 0) return;
     int grid = grid_for(M, 8);
     switch (Wd) {
-        case 1: k_dress<1><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<1>(pkey, cos_t, sin_t), h, ctr, state, backptr, free_rows, n_free); note_launch(); break;
-        case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr, state, backptr, free_rows, n_free); note_launch(); break;
-        default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr, state, backptr, free_rows, n_free); note_launch(); break;
+        case 1: k_dress<1><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<1>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
+        case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
+        default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
     }
 }
 
 void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,
-                        DevCounters* ctr, cudaStream_t s, const uint8_t* state) {
+                        DevCounters* ctr, cudaStream_t s) {
     if (M <= 0) return;
     int grid = grid_for(M, 8);
     switch (Wd) {
-        case 1: k_dress_count<1><<<grid, kThreads, 0, s>>>(rows, M, make_gen<1>(pkey, 1, 0), h, ctr, state); note_launch(); break;
-        case 2: k_dress_count<2><<<grid, kThreads, 0, s>>>(rows, M, make_gen<2>(pkey, 1, 0), h, ctr, state); note_launch(); break;
-        default: k_dress_count<4><<<grid, kThreads, 0, s>>>(rows, M, make_gen<4>(pkey, 1, 0), h, ctr, state); note_launch(); break;
+        case 1: k_dress_count<1><<<grid, kThreads, 0, s>>>(rows, M, make_gen<1>(pkey, 1, 0), h, ctr); note_launch(); break;
+        case 2: k_dress_count<2><<<grid, kThreads, 0, s>>>(rows, M, make_gen<2>(pkey, 1, 0), h, ctr); note_launch(); break;
+        default: k_dress_count<4><<<grid, kThreads, 0, s>>>(rows, M, make_gen<4>(pkey, 1, 0), h, ctr); note_launch(); break;
     }
 }
 

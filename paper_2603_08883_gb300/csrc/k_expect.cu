@@ -99,8 +99,7 @@ template <int W, bool BASIS>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
                                                   int yP, Key<W> occ, const double* __restrict__ tables,
-                                                  int n_groups, double* partials,
-                                                  const uint8_t* __restrict__ state) {
+                                                  int n_groups, double* partials) {
     extern __shared__ double s_tab[];
     if (!BASIS) {
         for (int i = threadIdx.x; i < n_groups * 256; i += blockDim.x) s_tab[i] = tables[i];
@@ -109,7 +108,6 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
     double acc[3] = {0.0, 0.0, 0.0};
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        if (state && state[i] != kLive) continue;
         Key<W> t = load_key<W>(rows, i);
         const int anti = anticommutes<W>(t, p);
         if (BASIS) {
@@ -221,11 +219,9 @@ __global__ void __launch_bounds__(kThreads) k_dis_group(const uint64_t* __restri
                                                         const double* __restrict__ coef, int64_t M, Key<W> occ,
                                                         bool with_values, uint64_t* gslots, uint64_t bucket_mask,
                                                         int max_probe, uint64_t* gkeys, double* gsum,
-                                                        DevCounters* ctr, const uint8_t* __restrict__ state,
-                                                        int64_t max_groups) {
+                                                        DevCounters* ctr, int64_t max_groups) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        if (state && state[i] != kLive) continue;
         Key<W> t = load_key<W>(rows, i);
         if (x_is_zero<W>(t)) continue;
         // group key: the flip set (x words, z = 0)
@@ -245,7 +241,7 @@ __global__ void __launch_bounds__(kThreads) k_dis_group(const uint64_t* __restri
                     unsigned long long prev = atomicCAS(slot, (unsigned long long)kEmptySlot, claim);
                     if (prev == kEmptySlot) {
                         unsigned long long g = atomicAdd(&ctr->n_groups, 1ull);
-                        if ((int64_t)g >= max_groups) {  // never with a correct live count
+                        if ((int64_t)g >= max_groups) {  // cannot happen: groups <= rows
                             set_error(ctr, IQCC_ERR_STATE, 12);
                             g = 0;
                         }
@@ -309,7 +305,7 @@ __global__ void __launch_bounds__(kThreads) k_grad_general(const uint64_t* __res
                                                            const double* __restrict__ coef, int64_t M,
                                                            const uint64_t* __restrict__ cand, int K,
                                                            const double* __restrict__ tables, int n_groups,
-                                                           double* partials, const uint8_t* __restrict__ state) {
+                                                           double* partials) {
     extern __shared__ double s_tab[];
     __shared__ Key<W> s_c[kGradTile];
     __shared__ int s_y[kGradTile];
@@ -331,7 +327,6 @@ __global__ void __launch_bounds__(kThreads) k_grad_general(const uint64_t* __res
     for (int k = 0; k < kGradTile; ++k) acc[k] = 0.0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        if (state && state[i] != kLive) continue;
         Key<W> t = load_key<W>(rows, i);
         const double c = coef[i];
 #pragma unroll
@@ -362,8 +357,7 @@ int abc_grid(int64_t M) {
 
 template <int W>
 void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, bool basis,
-              const uint64_t* occ_words, const double* tables, int n_groups, double* partials, cudaStream_t s,
-              const uint8_t* state) {
+              const uint64_t* occ_words, const double* tables, int n_groups, double* partials, cudaStream_t s) {
     Key<W> p = key_from<W>(pkey);
     int y = 0;
     for (int j = 0; j < W; ++j) y += __builtin_popcountll(p.x[j] & p.z[j]);
@@ -371,7 +365,7 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
     for (int j = 0; j < W; ++j) { occ.x[j] = occ_words[j]; occ.z[j] = 0; }
     const int grid = expect_blocks();
     if (basis) {
-        k_abc<W, true><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, state); note_launch();
+        k_abc<W, true><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
     } else {
         size_t smem = (size_t)n_groups * 256 * sizeof(double);
         static bool attr = false;
@@ -379,21 +373,20 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
             cudaFuncSetAttribute(k_abc<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
             attr = true;
         }
-        k_abc<W, false><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, state); note_launch();
+        k_abc<W, false><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
     }
 }
 
 template <int W>
 void grad_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* cand, int K,
-               const double* tables, int n_groups, double* partials, int n_blocks, cudaStream_t s,
-               const uint8_t* state) {
+               const double* tables, int n_groups, double* partials, int n_blocks, cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_grad_general<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
         attr = true;
     }
     size_t smem = (size_t)n_groups * 256 * sizeof(double);
-    k_grad_general<W><<<n_blocks, kThreads, smem, s>>>(rows, coef, M, cand, K, tables, n_groups, partials, state); note_launch();
+    k_grad_general<W><<<n_blocks, kThreads, smem, s>>>(rows, coef, M, cand, K, tables, n_groups, partials); note_launch();
 }
 
 }  // namespace
@@ -401,12 +394,11 @@ void grad_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64
 int expect_blocks() { return sm_count() * 4; }
 
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, bool basis,
-                const uint64_t* occ, const double* tables, int n_groups, double* partials, cudaStream_t s,
-                const uint8_t* state) {
+                const uint64_t* occ, const double* tables, int n_groups, double* partials, cudaStream_t s) {
     switch (Wd) {
-        case 1: abc_impl<1>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, state); break;
-        case 2: abc_impl<2>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, state); break;
-        default: abc_impl<4>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, state); break;
+        case 1: abc_impl<1>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s); break;
+        case 2: abc_impl<2>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s); break;
+        default: abc_impl<4>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s); break;
     }
 }
 
@@ -426,23 +418,23 @@ void launch_qmf_tables(const double* theta, const double* phi, int n, int n_grou
 
 void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ_words,
                       bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe, uint64_t* gkeys,
-                      double* gsum, DevCounters* ctr, cudaStream_t s, const uint8_t* state, int64_t max_groups) {
+                      double* gsum, DevCounters* ctr, cudaStream_t s, int64_t max_groups) {
     if (M <= 0) return;
     int grid = abc_grid(M) * 2;
     switch (Wd) {
         case 1: {
             Key<1> o{}; o.x[0] = occ_words[0];
-            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state, max_groups); note_launch();
+            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, max_groups); note_launch();
             break;
         }
         case 2: {
             Key<2> o{}; for (int j = 0; j < 2; ++j) o.x[j] = occ_words[j];
-            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state, max_groups); note_launch();
+            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, max_groups); note_launch();
             break;
         }
         default: {
             Key<4> o{}; for (int j = 0; j < 4; ++j) o.x[j] = occ_words[j];
-            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, state, max_groups); note_launch();
+            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, max_groups); note_launch();
             break;
         }
     }
@@ -450,11 +442,11 @@ void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t 
 
 void launch_grad_general(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* cand,
                          int K, const double* tables, int n_groups, double* partials, int n_blocks,
-                         cudaStream_t s, const uint8_t* state) {
+                         cudaStream_t s) {
     switch (Wd) {
-        case 1: grad_impl<1>(rows, coef, M, cand, K, tables, n_groups, partials, n_blocks, s, state); break;
-        case 2: grad_impl<2>(rows, coef, M, cand, K, tables, n_groups, partials, n_blocks, s, state); break;
-        default: grad_impl<4>(rows, coef, M, cand, K, tables, n_groups, partials, n_blocks, s, state); break;
+        case 1: grad_impl<1>(rows, coef, M, cand, K, tables, n_groups, partials, n_blocks, s); break;
+        case 2: grad_impl<2>(rows, coef, M, cand, K, tables, n_groups, partials, n_blocks, s); break;
+        default: grad_impl<4>(rows, coef, M, cand, K, tables, n_groups, partials, n_blocks, s); break;
     }
 }
 

@@ -402,37 +402,16 @@ __device__ __forceinline__ uint64_t abs_bits(double c) {
 }
 
 __global__ void k_prune_flags(const double* __restrict__ coef, int64_t n, double eps, uint8_t* flags,
-                              unsigned long long* count, const uint8_t* __restrict__ state) {
+                              unsigned long long* count) {
     unsigned c = 0;
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
-        const bool keep = (!state || state[i] == kLive) && !(fabs(coef[i]) < eps);
+        const bool keep = !(fabs(coef[i]) < eps);
         flags[i] = keep;
         c += keep;
     }
     for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(0xFFFFFFFFu, c, o);
     if ((threadIdx.x & 31) == 0 && c) atomicAdd(count, (unsigned long long)c);
-}
-
-// Indices of kLive rows (warp-aggregated; the order is not fixed).
-__global__ void k_live_list(const uint8_t* __restrict__ state, int64_t n, uint32_t* idx, unsigned long long* count,
-                            int64_t cap) {
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
-        const int64_t i = base + lane;
-        const bool live = i < n && state[i] == kLive;
-        const unsigned m = __ballot_sync(FULL, live);
-        if (m) {
-            const int leader = __ffs(m) - 1;
-            unsigned long long p0 = 0;
-            if (lane == leader) p0 = atomicAdd(count, (unsigned long long)__popc(m));
-            p0 = __shfl_sync(FULL, p0, leader);
-            const unsigned long long at = p0 + __popc(m & ((1u << lane) - 1u));
-            if (live && (int64_t)at < cap) idx[at] = (uint32_t)i;
-        }
-    }
 }
 
 __global__ void k_abs_digit_hist(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
@@ -736,17 +715,9 @@ void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const 
 }
 
 void launch_prune_flags(const double* coef, int64_t n, double eps, uint8_t* flags, unsigned long long* count,
-                        cudaStream_t s, const uint8_t* state) {
+                        cudaStream_t s) {
     if (n > 0) {
-        k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count, state);
-        note_launch();
-    }
-}
-
-void launch_live_list(const uint8_t* state, int64_t n, uint32_t* idx, unsigned long long* count, int64_t cap,
-                      cudaStream_t s) {
-    if (n > 0) {
-        k_live_list<<<grid_stride_blocks(n), kThreads, 0, s>>>(state, n, idx, count, cap);
+        k_prune_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, n, eps, flags, count);
         note_launch();
     }
 }
