@@ -482,6 +482,13 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     ctx->M = newM;
     *removed = M - newM;
     if (newM == M) return IQCC_OK;  // nothing moved
+#ifndef IQCC_TOMB_FRACTION
+#define IQCC_TOMB_FRACTION 0.5  // tombstones allowed per live row before the index is rebuilt
+#endif
+    // Tombstones lengthen every later probe; once they pass a fraction of the
+    // live rows a fresh build is cheaper than another remap.
+    if ((double)(ctx->n_tomb + (M - newM)) > IQCC_TOMB_FRACTION * (double)newM)
+        return rebuild_hash(ctx, ctx->hash_slots);
     // rows moved: remap the index in place (kept keys keep their slots, removed keys become tombstones)
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_hash_remap(hash_view(ctx), ctx->hash_slots, new_row, ctx->stream);
