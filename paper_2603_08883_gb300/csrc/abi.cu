@@ -168,10 +168,20 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     HashView h = hash_view(ctx);
-    launch_hash_clear(h, ctx->hash_slots, ctx->stream);
-    CK_LAUNCH();
-    launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream);
-    CK_LAUNCH();
+#ifndef IQCC_INDEX_BUILD_CAS
+    // partitioned build (k_build.cu) in the auxiliary buffer; CAS inserts into a
+    // cleared table where that buffer cannot grow
+    if (ensure(ctx, ctx->aux, index_build_scratch_bytes(ctx->M, ctx->hash_slots))) {
+        launch_index_build(ctx->Wd, ctx->rows(), ctx->M, h, ctx->hash_slots, ctx->aux.p, dctr(ctx), ctx->stream);
+        CK_LAUNCH();
+    } else
+#endif
+    {
+        launch_hash_clear(h, ctx->hash_slots, ctx->stream);
+        CK_LAUNCH();
+        launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream);
+        CK_LAUNCH();
+    }
     ctx->n_tomb = 0;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));

@@ -138,6 +138,11 @@ struct DevCounters {
     int err_where;                 // which kernel
 };
 
+// First error wins; `where` names the raising site.
+__device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where) {
+    if (atomicCAS(&ctr->err, 0, code) == 0) ctr->err_where = where;
+}
+
 // Hash table view.
 struct HashView {
     uint64_t* slots;
@@ -207,7 +212,14 @@ namespace iqcc {
 int device_words(int n);
 int sm_count();
 void note_launch();     // counts kernel launches of the library (all launchers call it)
+void note_launch(int k);  // k launches
 long long launches();
+
+// k_build.cu: index build without global atomics on the table (partitioned in
+// shared memory); writes every slot, so no clear is needed first.
+size_t index_build_scratch_bytes(int64_t n, uint64_t n_slots);
+void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView h, uint64_t n_slots, void* scratch,
+                        DevCounters* ctr, cudaStream_t s);
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);

@@ -30,10 +30,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where) {
-    if (atomicCAS(&ctr->err, 0, code) == 0) ctr->err_where = where;
-}
-
 __device__ __forceinline__ bool is_entry(uint64_t v) { return v != kEmptySlot && v != kTombSlot; }
 
 // Row index of key q, -1 when absent, -2 when the probe bound was reached.
@@ -381,6 +377,7 @@ int device_words(int n) { return n <= 64 ? 1 : (n <= 128 ? 2 : 4); }
 
 static std::atomic<long long> g_launches{0};
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s) {

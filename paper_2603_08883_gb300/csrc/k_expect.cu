@@ -27,10 +27,6 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where) {
-    if (atomicCAS(&ctr->err, 0, code) == 0) ctr->err_where = where;
-}
-
 template <int W>
 __device__ __forceinline__ bool x_is_zero(const Key<W>& k) {
     uint64_t v = 0;
