@@ -63,7 +63,7 @@ typedef enum {
 typedef struct {
     int n_qubits;          /* 1..256 */
     int64_t capacity;      /* maximum number of terms held; 0 -> 1<<30; at most 4294967294 */
-    int max_probe;         /* hash buckets probed per lookup before IQCC_ERR_HASH_FULL; 0 -> 64 */
+    int max_probe;         /* hash buckets probed per lookup before IQCC_ERR_HASH_FULL; 0 -> 64, at most 256 */
     void* stream;          /* cudaStream_t to run on; NULL -> the legacy default stream */
     void* (*alloc)(size_t bytes, void* user); /* device allocator or NULL (cudaMalloc) */
     void (*free)(void* ptr, void* user);      /* matching free or NULL (cudaFree) */

@@ -182,7 +182,6 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
         launch_hash_insert(ctx->Wd, ctx->rows(), 0, ctx->M, h, dctr(ctx), ctx->stream);
         CK_LAUNCH();
     }
-    ctx->n_tomb = 0;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0;
@@ -206,13 +205,9 @@ iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
         ctx->rows_alloc = want;
         ctx->stats.rows_allocated = want;
     }
-    // entries at most 1/2 of the slots once the rows are inserted (else a larger
-    // table), and entries plus tombstones at most 3/4 (else a fresh build)
+    // entries at most 1/2 of the slots once the rows are inserted (else a larger table)
     if ((uint64_t)rows_needed * 2 > ctx->hash_slots) {
         iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 2));
-        if (st) return st;
-    } else if ((uint64_t)(rows_needed + ctx->n_tomb) * 4 > ctx->hash_slots * 3) {
-        iqcc_status st = rebuild_hash(ctx, ctx->hash_slots);
         if (st) return st;
     }
     return IQCC_OK;
@@ -333,7 +328,7 @@ iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
     }
     iqcc_status st = reserve_rows(ctx, upper);
     if (st) return st;
-    CK(cudaMemsetAsync(c, 0, 5 * sizeof(unsigned long long), ctx->stream));  // n_new .. tomb_reused
+    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));  // n_new .. aux
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_dress(ctx->Wd, ctx->rows(), ctx->rows(), ctx->c(), M, pkey, std::cos(tau), std::sin(tau),
                  hash_view(ctx), c, ctx->stream);
@@ -346,7 +341,6 @@ iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->M = M + n_new;  // the dress kernel indexed the appended rows itself
-    ctx->n_tomb = std::max<int64_t>(0, ctx->n_tomb - (int64_t)ctx->h_counters->tomb_reused);
     iqcc_stats& s = ctx->stats;
     s.n_dress++;
     s.dressed_terms += M;
@@ -492,20 +486,16 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     ctx->M = newM;
     *removed = M - newM;
     if (newM == M) return IQCC_OK;  // nothing moved
-#ifndef IQCC_TOMB_FRACTION
-#define IQCC_TOMB_FRACTION 0.5  // tombstones allowed per live row before the index is rebuilt
-#endif
-    // Tombstones lengthen every later probe; once they pass a fraction of the
-    // live rows a fresh build is cheaper than another remap.
-    if ((double)(ctx->n_tomb + (M - newM)) > IQCC_TOMB_FRACTION * (double)newM)
-        return rebuild_hash(ctx, ctx->hash_slots);
-    // rows moved: remap the index in place (kept keys keep their slots, removed keys become tombstones)
+    // rows moved: every partition of the index rebuilt from its own entries
+    // through the compaction map (removed rows dropped); a full build where the
+    // auxiliary buffer cannot hold the list of cross-partition probes
+    if (!ensure(ctx, ctx->aux, index_reindex_scratch_bytes(M))) return rebuild_hash(ctx, ctx->hash_slots);
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    launch_hash_remap(hash_view(ctx), ctx->hash_slots, new_row, ctx->stream);
+    launch_index_reindex(hash_view(ctx), ctx->hash_slots, new_row, M, ctx->aux.p, c, ctx->stream);
     CK_LAUNCH();
-    ctx->n_tomb += M - newM;
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
-    CK(cudaEventSynchronize(ctx->ev1));
+    st = read_counters(ctx);
+    if (st) return st;
     float hms = 0;
     cudaEventElapsedTime(&hms, ctx->ev0, ctx->ev1);
     ctx->stats.hash_ms += hms;
@@ -724,6 +714,7 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
     if (n_terms < 0) return fail(nullptr, IQCC_ERR_ARG, "n_terms < 0");
     if (n_terms > 0 && (!x || !z || !coef)) return fail(nullptr, IQCC_ERR_ARG, "null input array");
     if (opts->capacity < 0 || opts->capacity > 0xFFFFFFFEll) return fail(nullptr, IQCC_ERR_ARG, "capacity out of range");
+    if (opts->max_probe > kMaxProbeLimit) return fail(nullptr, IQCC_ERR_ARG, "max_probe above 256");
     if ((opts->alloc == nullptr) != (opts->free == nullptr))
         return fail(nullptr, IQCC_ERR_ARG, "alloc and free must be given together");
     iqcc_ctx* ctx = new iqcc_ctx();

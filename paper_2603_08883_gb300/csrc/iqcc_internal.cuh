@@ -17,7 +17,6 @@ namespace iqcc {
 // ----------------------------------------------------------------------------
 
 constexpr uint64_t kEmptySlot = ~0ull;        // hash slot never used
-constexpr uint64_t kTombSlot = ~1ull;         // hash slot whose row was removed (row field 0xFFFFFFFE)
 constexpr uint32_t kRowRemoved = 0xFFFFFFFFu; // compaction map entry of a removed row
 constexpr uint32_t kPendingGroup = 0xFFFFFFFEu;  // group slot claimed, key not yet published
 constexpr int kBucketSlots = 4;               // 4 x 8-byte slots = one 32-byte sector
@@ -133,7 +132,6 @@ struct DevCounters {
     unsigned long long n_anti;     // anticommuting rows seen by a dress
     unsigned long long n_groups;   // DIS groups / compaction output
     unsigned long long aux;        // scratch counter
-    unsigned long long tomb_reused;  // dress inserts that took a tombstone
     int err;                       // iqcc_status set by a kernel (first error wins)
     int err_where;                 // which kernel
 };
@@ -142,6 +140,22 @@ struct DevCounters {
 __device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where) {
     if (atomicCAS(&ctr->err, 0, code) == 0) ctr->err_where = where;
 }
+
+// Index entries (one 8-byte slot each): bits 63..40 are the top 24 bits of the
+// key's hash (a fingerprint checked before the key itself is read), bits 39..32
+// the entry's distance in buckets from its home bucket (so an entry's home is
+// known without its key), bits 31..0 the row.  Rows stay below 0xFFFFFFFE, so
+// no entry equals kEmptySlot.
+constexpr uint64_t kFpMask = 0xFFFFFF0000000000ull;
+constexpr int kMaxProbeLimit = 256;  // displacements fit 8 bits
+
+__host__ __device__ __forceinline__ uint64_t make_entry(uint64_t hv, uint32_t row, uint64_t disp) {
+    return (hv & kFpMask) | (disp << 32) | (uint64_t)row;
+}
+__host__ __device__ __forceinline__ bool fp_match(uint64_t entry, uint64_t hv) {
+    return ((entry ^ hv) & kFpMask) == 0;
+}
+__host__ __device__ __forceinline__ uint32_t entry_disp(uint64_t entry) { return (uint32_t)(entry >> 32) & 0xFFu; }
 
 // Hash table view.
 struct HashView {
@@ -187,7 +201,6 @@ struct iqcc_ctx {
     iqcc::Buf keys, coef;
     iqcc::Buf hash;                // slots
     uint64_t hash_slots = 0;       // active slots (power of two)
-    int64_t n_tomb = 0;            // tombstones in the index (counted: removed rows minus reuses)
     iqcc::Buf counters;            // DevCounters
     iqcc::DevCounters* h_counters = nullptr;  // pinned host mirror
     iqcc::Buf scratch;             // general scratch (grows)
@@ -220,11 +233,15 @@ long long launches();
 size_t index_build_scratch_bytes(int64_t n, uint64_t n_slots);
 void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView h, uint64_t n_slots, void* scratch,
                         DevCounters* ctr, cudaStream_t s);
+// After an in-place compaction with map new_row (old row -> new row or
+// kRowRemoved): the index rebuilt partition by partition from its own entries
+// (no key is read), removed rows dropped.  n_entries: rows indexed before.
+size_t index_reindex_scratch_bytes(int64_t n_entries);
+void launch_index_reindex(HashView h, uint64_t n_slots, const uint32_t* new_row, int64_t n_entries, void* scratch,
+                          DevCounters* ctr, cudaStream_t s);
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
-// after an in-place compaction with map new_row (old row -> new row or kRowRemoved)
-void launch_hash_remap(HashView h, uint64_t slots, const uint32_t* new_row, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
                         DevCounters* ctr, cudaStream_t s);
 void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,

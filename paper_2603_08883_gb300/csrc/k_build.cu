@@ -161,9 +161,38 @@ __global__ void k_part_starts(const uint64_t* __restrict__ h, int64_t n, uint64_
     }
 }
 
-// One block per partition: linear probing in a shared-memory copy of the
-// partition, then a coalesced write of all its slots.  A record whose probe
-// runs past the partition end is listed with its entry and home slot.
+// Linear probing in a shared-memory copy of one partition, from the slot
+// `home` (partition-relative, bucket-aligned) to the partition end and within
+// max_slots of home.  Returns 1 when placed, 0 when the probe ran past the
+// partition end, -1 when it reached the probe bound inside the partition.
+__device__ __forceinline__ int place_local(unsigned long long* tab, uint32_t part_slots, uint32_t home,
+                                           uint64_t hv_fp, uint32_t row, int max_slots) {
+    for (uint32_t j = home; j < part_slots; ++j) {
+        if ((int)(j - home) >= max_slots) return -1;
+        if (tab[j] == kEmptySlot) {
+            const unsigned long long e = make_entry(hv_fp, row, (uint64_t)((j - home) / kBucketSlots));
+            if (atomicCAS(tab + j, (unsigned long long)kEmptySlot, e) == kEmptySlot) return 1;
+        }
+    }
+    return 0;
+}
+
+__device__ __forceinline__ void list_overflow(uint64_t hv_fp, uint32_t row, uint64_t home_slot, uint64_t* ovf_entry,
+                                              uint64_t* ovf_home, unsigned long long* n_ovf, int64_t ovf_cap,
+                                              DevCounters* ctr, int where) {
+    const unsigned long long at = atomicAdd(n_ovf, 1ull);
+    if ((int64_t)at < ovf_cap) {
+        ovf_entry[at] = make_entry(hv_fp, row, 0);
+        ovf_home[at] = home_slot;
+    } else {
+        set_error(ctr, IQCC_ERR_HASH_FULL, where);
+    }
+}
+
+// One block per partition: the partition's records are placed by linear
+// probing in a shared-memory copy, which is then written out whole (empty
+// slots included) in one coalesced sweep.  A record whose probe runs past the
+// partition end is listed with its home slot.
 __global__ void __launch_bounds__(kThreads) k_part_build(const uint64_t* __restrict__ h, const uint32_t* __restrict__ r,
                                                          const uint32_t* __restrict__ start, uint64_t bmask,
                                                          int pshift, int max_slots, uint64_t* slots,
@@ -173,36 +202,16 @@ __global__ void __launch_bounds__(kThreads) k_part_build(const uint64_t* __restr
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned long long* tab = reinterpret_cast<unsigned long long*>(smem_raw);
     const uint32_t part_slots = 1u << pshift;
-    const uint32_t p = blockIdx.x;
     for (uint32_t k = threadIdx.x; k < part_slots; k += blockDim.x) tab[k] = kEmptySlot;
     __syncthreads();
-    const uint64_t first = (uint64_t)p << pshift;
-    const uint32_t k0 = start[p], k1 = start[p + 1];
+    const uint64_t first = (uint64_t)blockIdx.x << pshift;
+    const uint32_t k0 = start[blockIdx.x], k1 = start[blockIdx.x + 1];
     for (uint32_t k = k0 + threadIdx.x; k < k1; k += blockDim.x) {
         const uint64_t hv = h[k];
-        const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)r[k];
         const uint32_t home = (uint32_t)((hv & bmask) * kBucketSlots - first);
-        uint32_t j = home;
-        bool done = false;
-        for (; j < part_slots && (int)(j - home) < max_slots; ++j) {
-            if (tab[j] == kEmptySlot &&
-                atomicCAS(tab + j, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot) {
-                done = true;
-                break;
-            }
-        }
-        if (done) continue;
-        if (j < part_slots) {  // probe bound reached inside the partition
-            set_error(ctr, IQCC_ERR_HASH_FULL, 40);
-            continue;
-        }
-        const unsigned long long at = atomicAdd(n_ovf, 1ull);
-        if ((int64_t)at < ovf_cap) {
-            ovf_entry[at] = entry;
-            ovf_home[at] = first + home;
-        } else {
-            set_error(ctr, IQCC_ERR_HASH_FULL, 41);
-        }
+        const int res = place_local(tab, part_slots, home, hv, r[k], max_slots);
+        if (res < 0) set_error(ctr, IQCC_ERR_HASH_FULL, 40);
+        else if (res == 0) list_overflow(hv, r[k], first + home, ovf_entry, ovf_home, n_ovf, ovf_cap, ctr, 41);
     }
     __syncthreads();
     ulonglong2* out = reinterpret_cast<ulonglong2*>(slots + first);
@@ -210,22 +219,81 @@ __global__ void __launch_bounds__(kThreads) k_part_build(const uint64_t* __restr
     for (uint32_t k = threadIdx.x; k < part_slots / 2; k += blockDim.x) out[k] = src[k];
 }
 
-// The listed records, inserted into the written table by global CAS from the
-// first slot after their home partition (linear probing, wrapping at the
-// table end), within the same probe bound as every other insertion.
+// After an in-place compaction: one block per partition reads its slots, drops
+// the entries of removed rows, gives the others their new row, and places
+// those whose home bucket lies in the partition into a fresh shared-memory
+// copy (the home is the slot's bucket minus the stored distance).  Entries
+// whose home lies in another partition (probes that ran in from an earlier
+// one) or whose new probe runs past the end are listed with their home slot.
+// Blocks read and write only their own partition.  Each thread first issues
+// all its slot loads and then all its row-map gathers, so that the random
+// gathers of a block are in flight together.
+constexpr int kReindexThreads = 1024;
+constexpr int kReindexPairs = (1 << kPartLog2) / 2 / kReindexThreads;  // slot pairs per thread (full partitions)
+
+__global__ void __launch_bounds__(kReindexThreads, 2) k_part_reindex(uint64_t* slots, uint64_t bmask, int pshift,
+                                                                  int max_slots, const uint32_t* __restrict__ new_row,
+                                                                  uint64_t* ovf_entry, uint64_t* ovf_home,
+                                                                  unsigned long long* n_ovf, int64_t ovf_cap,
+                                                                  DevCounters* ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned long long* tab = reinterpret_cast<unsigned long long*>(smem_raw);
+    const uint32_t part_slots = 1u << pshift;
+    const uint32_t pairs = part_slots / 2;
+    for (uint32_t k = threadIdx.x; k < part_slots; k += blockDim.x) tab[k] = kEmptySlot;
+    const uint64_t first = (uint64_t)blockIdx.x << pshift;
+    const ulonglong2* in = reinterpret_cast<const ulonglong2*>(slots + first);
+    uint64_t e[2 * kReindexPairs];
+#pragma unroll
+    for (int t = 0; t < kReindexPairs; ++t) {
+        const uint32_t k2 = threadIdx.x + (uint32_t)t * kReindexThreads;
+        ulonglong2 v = make_ulonglong2(kEmptySlot, kEmptySlot);
+        if (k2 < pairs) v = __ldcs(in + k2);
+        e[2 * t] = v.x;
+        e[2 * t + 1] = v.y;
+    }
+#pragma unroll
+    for (int t = 0; t < 2 * kReindexPairs; ++t) {  // the new row replaces the old (empty when removed)
+        if (e[t] == kEmptySlot) continue;
+        const uint32_t nr = __ldg(new_row + (uint32_t)e[t]);
+        e[t] = (nr == kRowRemoved) ? kEmptySlot : ((e[t] & 0xFFFFFFFF00000000ull) | nr);
+    }
+    __syncthreads();  // table cleared
+#pragma unroll
+    for (int t = 0; t < 2 * kReindexPairs; ++t) {
+        if (e[t] == kEmptySlot) continue;
+        const uint64_t slot = first + 2 * (threadIdx.x + (uint64_t)(t / 2) * kReindexThreads) + (t & 1);
+        const uint64_t home_slot = ((slot / kBucketSlots - entry_disp(e[t])) & bmask) * kBucketSlots;
+        int res = 0;
+        if ((home_slot >> pshift) == blockIdx.x)
+            res = place_local(tab, part_slots, (uint32_t)(home_slot - first), e[t], (uint32_t)e[t], max_slots);
+        if (res < 0) set_error(ctr, IQCC_ERR_HASH_FULL, 43);
+        else if (res == 0)
+            list_overflow(e[t], (uint32_t)e[t], home_slot, ovf_entry, ovf_home, n_ovf, ovf_cap, ctr, 44);
+    }
+    __syncthreads();
+    ulonglong2* out = reinterpret_cast<ulonglong2*>(slots + first);
+    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(tab);
+    for (uint32_t k = threadIdx.x; k < pairs; k += blockDim.x) out[k] = src[k];
+}
+
+// The listed entries, inserted into the written table by global CAS: linear
+// probing from the home slot (wrapping at the table end), within the probe
+// bound, the stored distance set to the slot found.
 __global__ void k_part_overflow(const uint64_t* __restrict__ ovf_entry, const uint64_t* __restrict__ ovf_home,
-                                const unsigned long long* n_ovf, int64_t ovf_cap, int pshift, uint64_t* slots,
+                                const unsigned long long* n_ovf, int64_t ovf_cap, uint64_t* slots,
                                 uint64_t n_slots, int max_slots, DevCounters* ctr) {
     const int64_t n = min((int64_t)*n_ovf, ovf_cap);
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
         const uint64_t home = ovf_home[i];
-        const uint64_t next = ((home >> pshift) + 1) << pshift;
+        const uint64_t e0 = ovf_entry[i];
         bool done = false;
-        for (uint64_t d = next - home; d < (uint64_t)max_slots && !done; ++d) {
+        for (int d = 0; d < max_slots && !done; ++d) {
             unsigned long long* sl = reinterpret_cast<unsigned long long*>(slots + ((home + d) & (n_slots - 1)));
-            done = *sl == kEmptySlot &&
-                   atomicCAS(sl, (unsigned long long)kEmptySlot, (unsigned long long)ovf_entry[i]) == kEmptySlot;
+            if (*sl != kEmptySlot) continue;
+            const unsigned long long e = make_entry(e0, (uint32_t)e0, (uint64_t)(d / kBucketSlots));
+            done = atomicCAS(sl, (unsigned long long)kEmptySlot, e) == kEmptySlot;
         }
         if (!done) set_error(ctr, IQCC_ERR_HASH_FULL, 42);
     }
@@ -363,6 +431,8 @@ void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView hv, ui
     const size_t scatter_smem = (size_t)kTile * 12;
     cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)scatter_smem);
     cudaFuncSetAttribute(k_part_build, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << kPartLog2);
+    cudaFuncSetAttribute(k_part_scatter, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    cudaFuncSetAttribute(k_part_build, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     if (n > 0) {
         const int g = grid_stride_blocks(n);
         switch (Wd) {
@@ -401,9 +471,33 @@ void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView hv, ui
     k_part_build<<<b.parts, kThreads, (size_t)8 << b.pshift, s>>>(hin, rin, start, hv.bucket_mask, b.pshift,
                                                                   hv.max_probe * kBucketSlots, hv.slots, ovf_e, ovf_h,
                                                                   n_ovf, b.ovf_cap, ctr);
-    k_part_overflow<<<64, kThreads, 0, s>>>(ovf_e, ovf_h, n_ovf, b.ovf_cap, b.pshift, hv.slots, n_slots,
+    k_part_overflow<<<64, kThreads, 0, s>>>(ovf_e, ovf_h, n_ovf, b.ovf_cap, hv.slots, n_slots,
                                             hv.max_probe * kBucketSlots, ctr);
     note_launch(3);
+}
+
+size_t index_reindex_scratch_bytes(int64_t n_entries) {
+    const int64_t cap = n_entries / 16 + 4096;
+    return align_up((size_t)cap * 8) * 2 + 256;
+}
+
+void launch_index_reindex(HashView hv, uint64_t n_slots, const uint32_t* new_row, int64_t n_entries, void* scratch,
+                          DevCounters* ctr, cudaStream_t s) {
+    const BuildPlan b = plan_for(0, n_slots);
+    const int64_t cap = n_entries / 16 + 4096;
+    char* p = (char*)scratch;
+    uint64_t* ovf_e = (uint64_t*)p; p += align_up((size_t)cap * 8);
+    uint64_t* ovf_h = (uint64_t*)p; p += align_up((size_t)cap * 8);
+    unsigned long long* n_ovf = (unsigned long long*)p;
+    cudaMemsetAsync(n_ovf, 0, sizeof(unsigned long long), s);
+    cudaFuncSetAttribute(k_part_reindex, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << kPartLog2);
+    cudaFuncSetAttribute(k_part_reindex, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    k_part_reindex<<<b.parts, kReindexThreads, (size_t)8 << b.pshift, s>>>(hv.slots, hv.bucket_mask, b.pshift,
+                                                                    hv.max_probe * kBucketSlots, new_row, ovf_e,
+                                                                    ovf_h, n_ovf, cap, ctr);
+    k_part_overflow<<<64, kThreads, 0, s>>>(ovf_e, ovf_h, n_ovf, cap, hv.slots, n_slots, hv.max_probe * kBucketSlots,
+                                            ctr);
+    note_launch(2);
 }
 
 }  // namespace iqcc

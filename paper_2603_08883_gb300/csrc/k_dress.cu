@@ -1,13 +1,13 @@
 // Dressing of the resident Hamiltonian by one generator (Eq. 5 in the
 // library convention, Eq. 6) and the open-addressing index it relies on.
 //
-// Index: 2^k buckets of 4 eight-byte slots (one 32-byte sector); a slot holds
-// (fingerprint32 << 32) | row32, kEmptySlot when never used and kTombSlot
-// when its row was removed by compression.  Lookups skip tombstones and stop
-// at the first empty slot.  Compression does not rebuild the index: it remaps
-// every slot through the old-row -> new-row map of the compaction (removed
-// rows become tombstones), and inserts reuse the first tombstone on a probe
-// sequence, so tombstones are recycled by later dresses.
+// Index: 2^k buckets of 4 eight-byte slots (one 32-byte sector), linear
+// probing bucket by bucket; a slot holds an entry (fingerprint, distance from
+// the home bucket, row; see make_entry) or kEmptySlot.  Lookups stop at the
+// first empty slot.  Compression does not touch the keys of the index: it
+// rebuilds each partition of slots from the entries themselves (k_build.cu),
+// which the stored distances make possible, so the table never holds
+// tombstones.
 //
 // Dress: one streaming pass over the M rows.  For a row T that anticommutes
 // with P (popcount parity of (xT & zP) ^ (zT & xP)), its partner Q = T xor P is
@@ -30,21 +30,15 @@ namespace {
 
 constexpr int kThreads = 256;
 
-__device__ __forceinline__ bool is_entry(uint64_t v) { return v != kEmptySlot && v != kTombSlot; }
-
 // Row index of key q, -1 when absent, -2 when the probe bound was reached.
-// When absent, *free_slot is the first tombstone met (else the empty slot that
-// ended the probe) and *free_val its content: where q would be inserted.
-// Read-only use of the slots through the non-coherent path: a slot read stale
-// can only be empty or a tombstone that was since filled with a key that no
-// lookup of this pass seeks (see k_dress).
+// When absent, *free_slot is the empty slot that ended the probe: where q
+// would be inserted.  Read-only use of the slots through the non-coherent
+// path: a slot read stale can only be an empty slot since filled with a key
+// that no lookup of this pass seeks (see k_dress).
 template <int W>
 __device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, const HashView& h,
-                                               const uint64_t* __restrict__ rows, uint64_t* free_slot,
-                                               uint64_t* free_val) {
-    const uint32_t fp = (uint32_t)(hv >> 32);
+                                               const uint64_t* __restrict__ rows, uint64_t* free_slot) {
     uint64_t b = hv & h.bucket_mask;
-    bool have_tomb = false;
     for (int p = 0; p < h.max_probe; ++p) {
         const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
         const ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
@@ -52,21 +46,10 @@ __device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, con
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (sl[k] == kEmptySlot) {
-                if (!have_tomb) {
-                    *free_slot = b * kBucketSlots + k;
-                    *free_val = kEmptySlot;
-                }
+                *free_slot = b * kBucketSlots + k;
                 return -1;
             }
-            if (sl[k] == kTombSlot) {
-                if (!have_tomb) {
-                    have_tomb = true;
-                    *free_slot = b * kBucketSlots + k;
-                    *free_val = kTombSlot;
-                }
-                continue;
-            }
-            if ((uint32_t)(sl[k] >> 32) == fp) {
+            if (fp_match(sl[k], hv)) {
                 const uint32_t idx = (uint32_t)sl[k];
                 const Key<W> r = load_key<W>(rows, idx);
                 if (key_equal<W>(r, q)) return (int64_t)idx;
@@ -77,30 +60,20 @@ __device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, con
     return -2;
 }
 
-// Insert `entry` (a key proven absent) at `slot` if it still holds `expect`,
-// else at the next empty or tombstone slot of its probe sequence.  *tomb tells
-// whether the slot used held a tombstone.
-__device__ __forceinline__ bool insert_from(uint64_t entry, uint64_t slot, uint64_t expect, const HashView& h,
-                                            bool* tomb) {
+// Insert the key with hash hv (proven absent) for `row` at `slot`, the empty
+// slot its lookup ended on, or, if another insertion took that slot since, at
+// the next empty slot of its probe sequence, within max_probe buckets of its
+// home bucket.  The entry records its distance from home.
+__device__ __forceinline__ bool insert_from(uint64_t hv, uint32_t row, uint64_t slot, const HashView& h) {
     unsigned long long* base = reinterpret_cast<unsigned long long*>(h.slots);
-    if (atomicCAS(base + slot, (unsigned long long)expect, (unsigned long long)entry) == expect) {
-        *tomb = expect == kTombSlot;
-        return true;
-    }
+    const uint64_t b0 = hv & h.bucket_mask;
     uint64_t b = slot / kBucketSlots;
-    int k0 = (int)(slot % kBucketSlots) + 1;
-    for (int p = 0; p < h.max_probe; ++p) {
+    int k0 = (int)(slot % kBucketSlots);
+    for (int p = (int)((b - b0) & h.bucket_mask); p < h.max_probe; ++p) {
+        const unsigned long long e = make_entry(hv, row, (uint64_t)p);
         for (int k = k0; k < 4; ++k) {
             unsigned long long* s = base + b * kBucketSlots + k;
-            unsigned long long v = __ldcg(s);
-            while (!is_entry(v)) {
-                const unsigned long long prev = atomicCAS(s, v, (unsigned long long)entry);
-                if (prev == v) {
-                    *tomb = v == kTombSlot;
-                    return true;
-                }
-                v = prev;
-            }
+            if (__ldcg(s) == kEmptySlot && atomicCAS(s, (unsigned long long)kEmptySlot, e) == kEmptySlot) return true;
         }
         k0 = 0;
         b = (b + 1) & h.bucket_mask;
@@ -126,43 +99,24 @@ __global__ void k_hash_clear(uint64_t* slots, uint64_t n) {
         p[i] = make_ulonglong2(kEmptySlot, kEmptySlot);
 }
 
-// Index rows [lo, hi) into a table without tombstones (a fresh build): one row
-// per thread, occupied slots skipped by a plain read before the CAS.
+// Index rows [lo, hi) into a cleared table: one row per thread, occupied slots
+// skipped by a plain read before the CAS.
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_hash_insert(const uint64_t* __restrict__ rows, int64_t lo,
                                                           int64_t hi, HashView h, DevCounters* ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = lo + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < hi; i += stride) {
         const uint64_t hv = hash_key<W>(load_key<W>(rows, i));
-        const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)i;
         uint64_t b = hv & h.bucket_mask;
         bool done = false;
         for (int p = 0; p < h.max_probe && !done; ++p) {
+            const unsigned long long entry = make_entry(hv, (uint32_t)i, (uint64_t)p);
             unsigned long long* s = reinterpret_cast<unsigned long long*>(h.slots + b * kBucketSlots);
             for (int k = 0; k < 4 && !done; ++k)
-                done = s[k] == kEmptySlot &&
-                       atomicCAS(s + k, (unsigned long long)kEmptySlot, (unsigned long long)entry) == kEmptySlot;
+                done = s[k] == kEmptySlot && atomicCAS(s + k, (unsigned long long)kEmptySlot, entry) == kEmptySlot;
             b = (b + 1) & h.bucket_mask;
         }
         if (!done) set_error(ctr, IQCC_ERR_HASH_FULL, 1);
-    }
-}
-
-// After an in-place compaction: entries of kept rows get their new row index,
-// entries of removed rows become tombstones (new_row == kRowRemoved).
-__global__ void k_hash_remap(uint64_t* slots, uint64_t n, const uint32_t* __restrict__ new_row) {
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    ulonglong2* p = reinterpret_cast<ulonglong2*>(slots);
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n / 2; i += stride) {
-        const ulonglong2 v = p[i];
-        uint64_t w[2] = {v.x, v.y};
-#pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            if (!is_entry(w[k])) continue;
-            const uint32_t nr = __ldg(new_row + (uint32_t)w[k]);
-            w[k] = (nr == kRowRemoved) ? kTombSlot : ((w[k] & 0xFFFFFFFF00000000ull) | (uint64_t)nr);
-        }
-        p[i] = make_ulonglong2(w[0], w[1]);
     }
 }
 
@@ -172,10 +126,8 @@ __global__ void k_hash_remap(uint64_t* slots, uint64_t n, const uint32_t* __rest
 template <int W>
 __device__ __forceinline__ int64_t lookup_slot_coef(const Key<W>& q, uint64_t hv, const HashView& h,
                                                     const uint64_t* __restrict__ rows, const double* coef,
-                                                    uint64_t* free_slot, uint64_t* free_val, double* cq) {
-    const uint32_t fp = (uint32_t)(hv >> 32);
+                                                    uint64_t* free_slot, double* cq) {
     uint64_t b = hv & h.bucket_mask;
-    bool have_tomb = false;
     for (int p = 0; p < h.max_probe; ++p) {
         const ulonglong2* s = reinterpret_cast<const ulonglong2*>(h.slots + b * kBucketSlots);
         const ulonglong2 s01 = __ldg(s), s23 = __ldg(s + 1);
@@ -183,21 +135,10 @@ __device__ __forceinline__ int64_t lookup_slot_coef(const Key<W>& q, uint64_t hv
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
             if (sl[k] == kEmptySlot) {
-                if (!have_tomb) {
-                    *free_slot = b * kBucketSlots + k;
-                    *free_val = kEmptySlot;
-                }
+                *free_slot = b * kBucketSlots + k;
                 return -1;
             }
-            if (sl[k] == kTombSlot) {
-                if (!have_tomb) {
-                    have_tomb = true;
-                    *free_slot = b * kBucketSlots + k;
-                    *free_val = kTombSlot;
-                }
-                continue;
-            }
-            if ((uint32_t)(sl[k] >> 32) == fp) {
+            if (fp_match(sl[k], hv)) {
                 const uint32_t idx = (uint32_t)sl[k];
                 const double c = coef[idx];
                 const Key<W> r = load_key<W>(rows, idx);
@@ -220,13 +161,13 @@ constexpr int kWarpTile = 64;  // rows classified per warp before the probes
 // One pass of Eq. 5 over rows [0, M).  Each warp classifies a tile of 64 rows
 // (two per lane) and queues the anticommuting ones in shared memory, so that
 // every lane then works on one queued row: partner lookup, pair rotation or
-// append.  An appended partner is inserted into the index at the first free
-// slot (tombstone or empty) its lookup met.  Concurrent inserts leave every
+// append.  An appended partner is inserted into the index at the empty slot
+// its lookup ended on (or the next one).  Concurrent inserts leave every
 // lookup correct: a key present before the pass has no empty slot ahead of it
-// in its probe sequence, and a slot filled during the pass only ever held an
-// empty or a tombstone (which a lookup passes over or stops at) and receives a
-// key no lookup seeks (an appended key is the partner of exactly one row,
-// q -> q xor P being a bijection).  rows_app is the same buffer as rows;
+// in its probe sequence, and a slot filled during the pass was empty (a lookup
+// that read it so stops there) and receives a key no lookup seeks (an
+// appended key is the partner of exactly one row, q -> q xor P being a
+// bijection).  rows_app is the same buffer as rows;
 // appended rows land at M + slot and are not visited by this pass.
 template <int W>
 __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) k_dress(const uint64_t* __restrict__ rows,
@@ -258,7 +199,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
             bool append = false;
             Key<W> q;
             double c_new = 0.0;
-            uint64_t hv = 0, fslot = 0, fval = kEmptySlot;
+            uint64_t hv = 0, fslot = 0;
             if (e < nq) {
                 const int64_t i = base + queue[e];
                 const double ct = coef[i];  // independent of the lookup: issued first
@@ -268,7 +209,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
                 const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
                 hv = hash_key<W>(q);
                 double cq = 0.0;
-                const int64_t j = lookup_slot_coef<W>(q, hv, h, rows, coef, &fslot, &fval, &cq);
+                const int64_t j = lookup_slot_coef<W>(q, hv, h, rows, coef, &fslot, &cq);
                 if (j == -1) {
                     coef[i] = ct * g.cos_t;
                     c_new = s * ct * g.sin_t;
@@ -292,10 +233,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
                     const int64_t r = M + (int64_t)slot0 + __popc(need & lt);
                     store_key<W>(rows_app, r, q);
                     coef[r] = c_new;
-                    const uint64_t entry = (hv & 0xFFFFFFFF00000000ull) | (uint64_t)r;
-                    bool tomb = false;
-                    if (!insert_from(entry, fslot, fval, h, &tomb)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
-                    else if (tomb) atomicAdd(&ctr->tomb_reused, 1ull);
+                    if (!insert_from(hv, (uint32_t)r, fslot, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
                 }
             }
         }
@@ -316,8 +254,8 @@ __global__ void __launch_bounds__(kThreads) k_dress_count(const uint64_t* __rest
         Key<W> t = load_key<W>(rows, i);
         if (anticommutes<W>(t, g.p)) {
             Key<W> q = key_xor<W>(t, g.p);
-            uint64_t fslot, fval;
-            int64_t j = lookup_slot<W>(q, hash_key<W>(q), h, rows, &fslot, &fval);
+            uint64_t fslot;
+            int64_t j = lookup_slot<W>(q, hash_key<W>(q), h, rows, &fslot);
             if (j == -1) ++cnt;
             else if (j == -2) set_error(ctr, IQCC_ERR_HASH_FULL, 3);
         }
@@ -382,10 +320,6 @@ long long launches() { return g_launches.load(std::memory_order_relaxed); }
 
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s) {
     k_hash_clear<<<grid_for_slots(slots), kThreads, 0, s>>>(h.slots, slots); note_launch();
-}
-
-void launch_hash_remap(HashView h, uint64_t slots, const uint32_t* new_row, cudaStream_t s) {
-    k_hash_remap<<<grid_for_slots(slots), kThreads, 0, s>>>(h.slots, slots, new_row); note_launch();
 }
 
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,

@@ -67,6 +67,10 @@ def test_argument_errors_before_any_device_work(lib):
         iqcc.iqcc_load_hamiltonian(3, np.array([[8]], np.uint64), np.zeros((1, 1), np.uint64), np.ones(1),
                                    use_torch=False)
     assert e.value.status == 1
+    with pytest.raises(iqcc.IqccError) as e:   # index distances are stored in 8 bits
+        iqcc.iqcc_load_hamiltonian(3, np.zeros((1, 1), np.uint64), np.zeros((1, 1), np.uint64), np.ones(1),
+                                   max_probe=257, use_torch=False)
+    assert e.value.status == 1
 
 
 def test_ctypes_structs_match_the_header(tmp_path):

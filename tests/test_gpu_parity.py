@@ -334,10 +334,10 @@ def test_term_limit_select_on_large_sets(cap):
 
 
 @pytest.mark.parametrize("n", [20, 100])
-def test_dress_after_compression_reuses_tombstones(n):
-    """Compression remaps the index in place (removed keys become tombstones);
-    later dresses must find every kept key, see removed keys as absent and
-    reuse the tombstones for new partners."""
+def test_dress_after_compression_finds_kept_keys(n):
+    """Compression rebuilds each partition of the index from its own entries
+    (new rows through the compaction map, removed rows dropped); later dresses
+    must find every kept key and see removed keys as absent."""
     rng = np.random.Generator(np.random.PCG64(n))
     _, x, z, c = synth.random_hamiltonian(n, 60_000, 300 + n)
     o = oracle.Oracle(n, x, z, c)
