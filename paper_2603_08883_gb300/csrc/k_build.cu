@@ -225,11 +225,16 @@ __global__ void __launch_bounds__(kThreads) k_part_build(const uint64_t* __restr
 // copy (the home is the slot's bucket minus the stored distance).  Entries
 // whose home lies in another partition (probes that ran in from an earlier
 // one) or whose new probe runs past the end are listed with their home slot.
-// Blocks read and write only their own partition.  Each thread first issues
-// all its slot loads and then all its row-map gathers, so that the random
-// gathers of a block are in flight together.
+// Blocks read and write only their own partition.  In each round a thread
+// first issues its slot loads and then its row-map gathers, so that the
+// random gathers of a block are in flight together.
+// Shape chosen by measurement on the 100-qubit workload (2^32 slots): 8
+// entries per thread in one round and 2 blocks per SM (47.7 ms) beat 4 per
+// thread in two rounds (53 ms), 1 block per SM (61 ms) and 512-thread blocks
+// (58-65 ms): gathers in flight matter more than the few spilled registers.
 constexpr int kReindexThreads = 1024;
-constexpr int kReindexPairs = (1 << kPartLog2) / 2 / kReindexThreads;  // slot pairs per thread (full partitions)
+constexpr int kReindexPairs = 4;  // slot pairs per thread and round
+constexpr int kReindexRounds = (1 << kPartLog2) / 2 / kReindexThreads / kReindexPairs;
 
 __global__ void __launch_bounds__(kReindexThreads, 2) k_part_reindex(uint64_t* slots, uint64_t bmask, int pshift,
                                                                   int max_slots, const uint32_t* __restrict__ new_row,
@@ -241,35 +246,39 @@ __global__ void __launch_bounds__(kReindexThreads, 2) k_part_reindex(uint64_t* s
     const uint32_t part_slots = 1u << pshift;
     const uint32_t pairs = part_slots / 2;
     for (uint32_t k = threadIdx.x; k < part_slots; k += blockDim.x) tab[k] = kEmptySlot;
+    __syncthreads();
     const uint64_t first = (uint64_t)blockIdx.x << pshift;
     const ulonglong2* in = reinterpret_cast<const ulonglong2*>(slots + first);
-    uint64_t e[2 * kReindexPairs];
+#pragma unroll 1
+    for (int round = 0; round < kReindexRounds; ++round) {
+        uint64_t e[2 * kReindexPairs];
 #pragma unroll
-    for (int t = 0; t < kReindexPairs; ++t) {
-        const uint32_t k2 = threadIdx.x + (uint32_t)t * kReindexThreads;
-        ulonglong2 v = make_ulonglong2(kEmptySlot, kEmptySlot);
-        if (k2 < pairs) v = __ldcs(in + k2);
-        e[2 * t] = v.x;
-        e[2 * t + 1] = v.y;
-    }
+        for (int t = 0; t < kReindexPairs; ++t) {
+            const uint32_t k2 = threadIdx.x + (uint32_t)(round * kReindexPairs + t) * kReindexThreads;
+            ulonglong2 v = make_ulonglong2(kEmptySlot, kEmptySlot);
+            if (k2 < pairs) v = __ldcs(in + k2);
+            e[2 * t] = v.x;
+            e[2 * t + 1] = v.y;
+        }
 #pragma unroll
-    for (int t = 0; t < 2 * kReindexPairs; ++t) {  // the new row replaces the old (empty when removed)
-        if (e[t] == kEmptySlot) continue;
-        const uint32_t nr = __ldg(new_row + (uint32_t)e[t]);
-        e[t] = (nr == kRowRemoved) ? kEmptySlot : ((e[t] & 0xFFFFFFFF00000000ull) | nr);
-    }
-    __syncthreads();  // table cleared
+        for (int t = 0; t < 2 * kReindexPairs; ++t) {  // the new row replaces the old (empty when removed)
+            if (e[t] == kEmptySlot) continue;
+            const uint32_t nr = __ldg(new_row + (uint32_t)e[t]);
+            e[t] = (nr == kRowRemoved) ? kEmptySlot : ((e[t] & 0xFFFFFFFF00000000ull) | nr);
+        }
 #pragma unroll
-    for (int t = 0; t < 2 * kReindexPairs; ++t) {
-        if (e[t] == kEmptySlot) continue;
-        const uint64_t slot = first + 2 * (threadIdx.x + (uint64_t)(t / 2) * kReindexThreads) + (t & 1);
-        const uint64_t home_slot = ((slot / kBucketSlots - entry_disp(e[t])) & bmask) * kBucketSlots;
-        int res = 0;
-        if ((home_slot >> pshift) == blockIdx.x)
-            res = place_local(tab, part_slots, (uint32_t)(home_slot - first), e[t], (uint32_t)e[t], max_slots);
-        if (res < 0) set_error(ctr, IQCC_ERR_HASH_FULL, 43);
-        else if (res == 0)
-            list_overflow(e[t], (uint32_t)e[t], home_slot, ovf_entry, ovf_home, n_ovf, ovf_cap, ctr, 44);
+        for (int t = 0; t < 2 * kReindexPairs; ++t) {
+            if (e[t] == kEmptySlot) continue;
+            const uint32_t k2 = threadIdx.x + (uint32_t)(round * kReindexPairs + t / 2) * kReindexThreads;
+            const uint64_t slot = first + 2 * (uint64_t)k2 + (t & 1);
+            const uint64_t home_slot = ((slot / kBucketSlots - entry_disp(e[t])) & bmask) * kBucketSlots;
+            int res = 0;
+            if ((home_slot >> pshift) == blockIdx.x)
+                res = place_local(tab, part_slots, (uint32_t)(home_slot - first), e[t], (uint32_t)e[t], max_slots);
+            if (res < 0) set_error(ctr, IQCC_ERR_HASH_FULL, 43);
+            else if (res == 0)
+                list_overflow(e[t], (uint32_t)e[t], home_slot, ovf_entry, ovf_home, n_ovf, ovf_cap, ctr, 44);
+        }
     }
     __syncthreads();
     ulonglong2* out = reinterpret_cast<ulonglong2*>(slots + first);
