@@ -53,7 +53,7 @@ __global__ void k_part_hist(const uint64_t* __restrict__ h, int64_t n, uint64_t 
     hist[(int64_t)threadIdx.x * nblocks + blockIdx.x] = sh[threadIdx.x];
 }
 
-// Exclusive scan of 256 values held one per thread (kThreads == kBins).
+// Exclusive scan over the block of one value per thread (warp_tot: one entry per warp).
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* warp_tot) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint32_t x = v;
@@ -70,34 +70,36 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* w
     return before + x - v;
 }
 
-// One stable pass.  Each warp ranks its own contiguous 512 records (16 rounds
+// One stable pass.  Each warp ranks its own contiguous 256 records (8 rounds
 // of 32; lanes with the same digit find each other with match_any and the
 // lowest of them advances the warp's counter for that digit), so no block-wide
 // barrier is needed until the counts of all warps are combined.  Records are
 // then staged in shared memory in digit order and written out in runs.
-constexpr int kWarps = kThreads / 32;
+constexpr int kSThreads = 512;                // scatter block: 16 warps of 8 x 32 records
+constexpr int kSItems = kTile / kSThreads;
+constexpr int kSWarps = kSThreads / 32;
 
-__global__ void __launch_bounds__(kThreads) k_part_scatter(const uint64_t* __restrict__ h_in,
-                                                           const uint32_t* __restrict__ r_in, int64_t n,
-                                                           uint64_t bmask, int pshift, int dshift,
-                                                           const uint32_t* __restrict__ offsets, int64_t nblocks,
-                                                           uint64_t* h_out, uint32_t* r_out) {
+__global__ void __launch_bounds__(kSThreads, 2) k_part_scatter(const uint64_t* __restrict__ h_in,
+                                                               const uint32_t* __restrict__ r_in, int64_t n,
+                                                               uint64_t bmask, int pshift, int dshift,
+                                                               const uint32_t* __restrict__ offsets, int64_t nblocks,
+                                                               uint64_t* h_out, uint32_t* r_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     uint64_t* st_h = reinterpret_cast<uint64_t*>(smem_raw);
     uint32_t* st_r = reinterpret_cast<uint32_t*>(st_h + kTile);
-    __shared__ uint32_t s_wh[kWarps][kBins];  // per-warp digit counts, then per-warp offsets
-    __shared__ uint32_t s_tile_off[kBins], s_glob[kBins], s_warp[kWarps];
+    __shared__ uint32_t s_wh[kSWarps][kBins];  // per-warp digit counts, then per-warp offsets
+    __shared__ uint32_t s_tile_off[kBins], s_glob[kBins], s_warp[kSWarps];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
     const int64_t base = (int64_t)blockIdx.x * kTile;
-    const int64_t wbase = base + (int64_t)wid * (kItems * 32);
+    const int64_t wbase = base + (int64_t)wid * (kSItems * 32);
     for (int d = lane; d < kBins; d += 32) s_wh[wid][d] = 0;
     __syncwarp();
-    uint64_t hv[kItems];
-    uint32_t rv[kItems];
-    uint32_t pk[kItems];  // digit << 16 | position among the warp's records of that digit
+    uint64_t hv[kSItems];
+    uint32_t rv[kSItems];
+    uint32_t pk[kSItems];  // digit << 16 | position among the warp's records of that digit
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < kSItems; ++r) {
         const int64_t i = wbase + (int64_t)r * 32 + lane;
         uint32_t d = kBins;  // sentinel for the ragged tail
         hv[r] = 0;
@@ -119,18 +121,23 @@ __global__ void __launch_bounds__(kThreads) k_part_scatter(const uint64_t* __res
         pk[r] = (d << 16) | (before + __popc(peers & lt));
     }
     __syncthreads();
-    // thread t owns digit t: offsets of each warp within the digit, then of the digit within the tile
+    // thread t < 256 owns digit t: offsets of each warp within the digit, then of the digit within the tile
     uint32_t tot = 0;
-    for (int w = 0; w < kWarps; ++w) {
-        const uint32_t c = s_wh[w][threadIdx.x];
-        s_wh[w][threadIdx.x] = tot;
-        tot += c;
+    if (threadIdx.x < kBins) {
+        for (int w = 0; w < kSWarps; ++w) {
+            const uint32_t c = s_wh[w][threadIdx.x];
+            s_wh[w][threadIdx.x] = tot;
+            tot += c;
+        }
     }
-    s_tile_off[threadIdx.x] = block_exclusive_scan(tot, s_warp);
-    s_glob[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    const uint32_t excl = block_exclusive_scan(tot, s_warp);
+    if (threadIdx.x < kBins) {
+        s_tile_off[threadIdx.x] = excl;
+        s_glob[threadIdx.x] = offsets[(int64_t)threadIdx.x * nblocks + blockIdx.x];
+    }
     __syncthreads();
 #pragma unroll
-    for (int r = 0; r < kItems; ++r) {
+    for (int r = 0; r < kSItems; ++r) {
         const uint32_t d = pk[r] >> 16;
         if (d < kBins) {
             const uint32_t pos = s_tile_off[d] + s_wh[wid][d] + (pk[r] & 0xFFFFu);
@@ -140,7 +147,7 @@ __global__ void __launch_bounds__(kThreads) k_part_scatter(const uint64_t* __res
     }
     __syncthreads();
     const int64_t cnt = min((int64_t)kTile, n - base);
-    for (int k = threadIdx.x; k < cnt; k += kThreads) {
+    for (int k = threadIdx.x; k < cnt; k += kSThreads) {
         const uint64_t hk = st_h[k];
         const uint32_t d = (part_of(hk, bmask, pshift) >> dshift) & (kBins - 1);
         const int64_t out = (int64_t)s_glob[d] + (k - (int64_t)s_tile_off[d]);
@@ -462,7 +469,7 @@ void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView hv, ui
         k_chunk_sums<<<b.scan_chunks, kThreads, 0, s>>>(hist, b.scan_n, b.scan_chunk, csum);
         k_scan_small<<<1, 1024, 0, s>>>(csum, b.scan_chunks);
         k_chunk_scan<<<b.scan_chunks, kThreads, 0, s>>>(hist, b.scan_n, b.scan_chunk, csum);
-        k_part_scatter<<<(unsigned)b.nblocks, kThreads, scatter_smem, s>>>(hin, rin, n, hv.bucket_mask, b.pshift,
+        k_part_scatter<<<(unsigned)b.nblocks, kSThreads, scatter_smem, s>>>(hin, rin, n, hv.bucket_mask, b.pshift,
                                                                            dshift, hist, b.nblocks, hout, rout);
         note_launch(5);
         uint64_t* hnext = (hin == h0) ? h0 : h1;  // the buffer just read becomes the next output

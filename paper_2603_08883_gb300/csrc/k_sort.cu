@@ -183,12 +183,15 @@ __global__ void k_compact_scatter(const uint8_t* __restrict__ flags, const uint6
 }
 
 // Single-pass stable in-place compaction (decoupled look-back).  Tiles take
-// ids in launch order from a counter; a tile stages its kept rows in shared
-// memory, publishes its count, sums its predecessors' counts (waiting, with a
+// ids in launch order from a counter.  Each warp of a tile reads its own 128
+// consecutive rows (the keys and coefficients of kept rows only) into
+// registers and ranks them with ballots; the tile publishes its count, sums
+// its predecessors' counts 32 at a time with its first warp (waiting, with a
 // bound, for any not yet published), publishes its inclusive prefix and only
-// then writes.  Its destination [prefix, prefix + count) lies below its own
-// first row, and every earlier tile has read its rows before publishing, so no
-// row is overwritten before it is read.
+// then writes, straight from registers.  Its destination [prefix, prefix + count) lies below the
+// end of its own rows, its own rows were all read before the barrier that
+// precedes the writes, and every earlier tile read its rows before
+// publishing, so no row is overwritten before it is read.
 constexpr int kCompactTile = 1024;  // rows per tile (4 per thread)
 constexpr unsigned long long kStAgg = 1ull << 62, kStPrefix = 2ull << 62;
 constexpr unsigned long long kStMask = (1ull << 62) - 1;
@@ -200,94 +203,95 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
                                                               unsigned int* tile_counter,
                                                               unsigned long long* total, DevCounters* ctr,
                                                               uint32_t* new_row) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    uint64_t* s_rows = reinterpret_cast<uint64_t*>(smem_raw);
-    double* s_c = reinterpret_cast<double*>(s_rows + (size_t)kCompactTile * 2 * W);
-    __shared__ uint32_t s_w[kThreads / 32];
-    __shared__ uint32_t s_run;
+    constexpr int kPer = kCompactTile / kThreads;
+    __shared__ uint32_t s_w[kThreads / 32];  // warp counts, then warp offsets within the tile
     __shared__ unsigned int s_tile;
     __shared__ unsigned long long s_prefix;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) {
-        s_tile = atomicAdd(tile_counter, 1u);
-        s_run = 0;
-    }
+    const unsigned lt = (1u << lane) - 1u;
+    if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
     __syncthreads();
     const unsigned int t = s_tile;
     const int64_t base = (int64_t)t * kCompactTile;
-    uint32_t my_pos[kCompactTile / kThreads];
-    bool my_keep[kCompactTile / kThreads];
+    const int64_t wbase = base + (int64_t)wid * (kPer * 32);
+    Key<W> key[kPer];
+    double c[kPer];
+    uint32_t rank[kPer];
+    bool keep[kPer];
+    uint32_t wcount = 0;
 #pragma unroll
-    for (int r = 0; r < kCompactTile / kThreads; ++r) {
-        const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
-        const bool f = i < n && flags[i];
-        const unsigned b = __ballot_sync(0xFFFFFFFFu, f);
-        if (lane == 0) s_w[wid] = __popc(b);
-        __syncthreads();
-        uint32_t pos = s_run + __popc(b & ((1u << lane) - 1u));
-        for (int w = 0; w < wid; ++w) pos += s_w[w];
-        my_pos[r] = pos;
-        my_keep[r] = f;
-        if (f) {
-            const ulonglong2* src = reinterpret_cast<const ulonglong2*>(rows + (size_t)i * 2 * W);
-            ulonglong2* dst = reinterpret_cast<ulonglong2*>(s_rows + (size_t)pos * 2 * W);
-#pragma unroll
-            for (int j = 0; j < W; ++j) dst[j] = src[j];
-            s_c[pos] = coef[i];
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = wbase + (int64_t)r * 32 + lane;
+        keep[r] = i < n && flags[i];
+        if (keep[r]) {
+            key[r] = load_key<W>(rows, i);
+            c[r] = coef[i];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t tot = 0;
-            for (int w = 0; w < kThreads / 32; ++w) tot += s_w[w];
-            s_run += tot;
-        }
-        __syncthreads();
+        const unsigned b = __ballot_sync(0xFFFFFFFFu, keep[r]);
+        rank[r] = wcount + __popc(b & lt);
+        wcount += __popc(b);
     }
-    const uint32_t count = s_run;
-    if (threadIdx.x == 0) {
-        __threadfence();
-        if (t == 0) {
-            atomicExch(state + t, kStPrefix | count);
-            s_prefix = 0;
-        } else {
-            atomicExch(state + t, kStAgg | count);
-            unsigned long long prefix = 0;
-            int64_t p = (int64_t)t - 1;
-            int spins = 0;
-            while (p >= 0) {
-                unsigned long long v = *(volatile unsigned long long*)(state + p);
-                if (v == 0) {
-                    if (++spins > (1 << 24)) {
-                        if (atomicCAS(&ctr->err, 0, (int)IQCC_ERR_TIMEOUT) == 0) ctr->err_where = 20;
-                        break;
-                    }
-                    __nanosleep(32);
-                    continue;
-                }
-                prefix += v & kStMask;
-                if ((v & ~kStMask) == kStPrefix) break;
-                --p;
-            }
-            atomicExch(state + t, kStPrefix | (prefix + count));
-            s_prefix = prefix;
+    if (lane == 0) s_w[wid] = wcount;
+    __syncthreads();
+    if (wid == 0) {
+        // warp offsets within the tile and the tile's count
+        const uint32_t v = lane < kThreads / 32 ? s_w[lane] : 0u;
+        uint32_t incl = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += y;
         }
-        if (base + kCompactTile >= n) *total = s_prefix + count;  // last tile
+        const uint32_t count = __shfl_sync(0xFFFFFFFFu, incl, 31);
+        if (lane < kThreads / 32) s_w[lane] = incl - v;
+        if (lane == 0) {
+            __threadfence();
+            atomicExch(state + t, (t == 0 ? kStPrefix : kStAgg) | count);
+        }
+        // look back 32 predecessors at a time: sum their aggregates up to the
+        // closest one that has published its inclusive prefix
+        unsigned long long prefix = 0;
+        int64_t p = (int64_t)t - 1;
+        int spins = 0;
+        while (p >= 0) {
+            const int64_t q = p - lane;
+            unsigned long long v2 = kStPrefix | 0ull;  // before tile 0: a prefix of 0
+            if (q >= 0) v2 = *(volatile unsigned long long*)(state + q);
+            const unsigned pref = __ballot_sync(0xFFFFFFFFu, (v2 & ~kStMask) == kStPrefix);
+            const unsigned zero = __ballot_sync(0xFFFFFFFFu, v2 == 0);
+            const int stop = pref ? __ffs(pref) - 1 : 31;  // last lane that counts
+            const unsigned upto = stop == 31 ? 0xFFFFFFFFu : ((2u << stop) - 1u);
+            if (zero & upto) {  // a predecessor within the window has not published yet
+                if (++spins > (1 << 24)) {
+                    if (lane == 0 && atomicCAS(&ctr->err, 0, (int)IQCC_ERR_TIMEOUT) == 0) ctr->err_where = 20;
+                    break;
+                }
+                __nanosleep(32);
+                continue;
+            }
+            unsigned long long part = lane <= stop ? (v2 & kStMask) : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, o);
+            prefix += __shfl_sync(0xFFFFFFFFu, part, 0);
+            if (pref) break;
+            p -= 32;
+        }
+        if (lane == 0) {
+            if (t != 0) atomicExch(state + t, kStPrefix | (prefix + count));
+            s_prefix = prefix;
+            if (base + kCompactTile >= n) *total = prefix + count;  // last tile
+        }
     }
     __syncthreads();
-    const unsigned long long out = s_prefix;
-    if (new_row) {
+    const unsigned long long out = s_prefix + s_w[wid];
 #pragma unroll
-        for (int r = 0; r < kCompactTile / kThreads; ++r) {
-            const int64_t i = base + (int64_t)r * kThreads + threadIdx.x;
-            if (i < n) new_row[i] = my_keep[r] ? (uint32_t)(out + my_pos[r]) : kRowRemoved;
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = wbase + (int64_t)r * 32 + lane;
+        if (keep[r]) {
+            store_key<W>(rows, (int64_t)(out + rank[r]), key[r]);
+            coef[out + rank[r]] = c[r];
         }
-    }
-    for (uint32_t k = threadIdx.x; k < count; k += kThreads) {
-        const ulonglong2* src = reinterpret_cast<const ulonglong2*>(s_rows + (size_t)k * 2 * W);
-        ulonglong2* dst = reinterpret_cast<ulonglong2*>(rows + (size_t)(out + k) * 2 * W);
-#pragma unroll
-        for (int j = 0; j < W; ++j) dst[j] = src[j];
-        coef[out + k] = s_c[k];
+        if (new_row && i < n) new_row[i] = keep[r] ? (uint32_t)(out + rank[r]) : kRowRemoved;
     }
 }
 
@@ -629,27 +633,21 @@ void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double
     unsigned long long* state = (unsigned long long*)scratch;
     unsigned int* tile_counter = (unsigned int*)(state + nt);
     cudaMemsetAsync(scratch, 0, (size_t)(nt + 1) * sizeof(unsigned long long), s);
-    const size_t smem = (size_t)kCompactTile * (16 * Wd + 8);
     switch (Wd) {
-        case 1: {
-            static bool a = false;
-            if (!a) { cudaFuncSetAttribute(k_compact_inplace<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
-            k_compact_inplace<1><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr, new_row); note_launch();
+        case 1:
+            k_compact_inplace<1><<<(unsigned)nt, kThreads, 0, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr,
+                                                                  new_row);
             break;
-        }
-        case 2: {
-            static bool a = false;
-            if (!a) { cudaFuncSetAttribute(k_compact_inplace<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
-            k_compact_inplace<2><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr, new_row); note_launch();
+        case 2:
+            k_compact_inplace<2><<<(unsigned)nt, kThreads, 0, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr,
+                                                                  new_row);
             break;
-        }
-        default: {
-            static bool a = false;
-            if (!a) { cudaFuncSetAttribute(k_compact_inplace<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); a = true; }
-            k_compact_inplace<4><<<(unsigned)nt, kThreads, smem, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr, new_row); note_launch();
+        default:
+            k_compact_inplace<4><<<(unsigned)nt, kThreads, 0, s>>>(flags, rows, coef, n, state, tile_counter, count, ctr,
+                                                                  new_row);
             break;
-        }
     }
+    note_launch();
 }
 
 void launch_coarse_digit_hist(const double* g, int64_t G, int shift, uint64_t prefix, uint64_t prefix_mask,
