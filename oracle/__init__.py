@@ -62,6 +62,8 @@ def _load():
         lib.orc_dis.argtypes = [vp, _f64p, _f64p, ctypes.c_int64, _u64p, _u64p, _f64p]
         lib.orc_prune.restype = ctypes.c_int64
         lib.orc_prune.argtypes = [vp, ctypes.c_double, ctypes.c_int64]
+        lib.orc_energy_gradients.argtypes = [vp, vp, vp, ctypes.c_double, _f64p, _f64p, _f64p, _f64p, _f64p]
+        lib.orc_energy_gradients.restype = ctypes.c_double
         lib.orc_iterate.restype = ctypes.c_int
         lib.orc_iterate.argtypes = [vp, _f64p, _f64p, ctypes.c_int, ctypes.c_int, _u64p, _u64p, _f64p,
                                     ctypes.c_double, ctypes.c_int64, _u64p, _u64p, _f64p, _f64p, _f64p,
@@ -154,6 +156,23 @@ class Oracle:
         (gxa, gxp), (gza, gzp) = self._gen(gx, gz)
         (ta, tp), (pa, pp) = self._angles(theta, phi)
         return float(self._lib.orc_gradient(self._h, gxp, gzp, tp, pp))
+
+    def energy_gradients(self, theta, phi, gx=None, gz=None, tau: float = 0.0):
+        """E(tau) after the generator (gx, gz) at amplitude tau (none: E of H),
+        dE/dtheta, dE/dphi (n each) and dE/dtau."""
+        (ta, tp), (pa, pp) = self._angles(theta, phi)
+        dt = np.zeros(self.n)
+        dp = np.zeros(self.n)
+        dtau = np.zeros(1)
+        if gx is None:
+            gxp = gzp = None
+        else:
+            (gxa, gxp), (gza, gzp) = self._gen(gx, gz)
+        e = self._lib.orc_energy_gradients(self._h, gxp, gzp, float(tau), tp, pp, dt.ctypes.data_as(_f64p),
+                                           dp.ctypes.data_as(_f64p), dtau.ctypes.data_as(_f64p))
+        if np.isnan(e):
+            raise RuntimeError("oracle dress produced an imaginary coefficient")
+        return float(e), dt, dp, float(dtau[0])
 
     def dis(self, theta, phi):
         """All DIS candidates, ordered: (cx, cz, g)."""

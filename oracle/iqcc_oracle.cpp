@@ -28,6 +28,9 @@
  *   orc_prune     App. A procedure step 5 (compress small terms) and the
  *                 "Maximum Terms" limit of Tables 2-3
  *   orc_iterate   App. A procedure steps 1-5, one iteration
+ *   orc_energy_gradients
+ *                 derivatives of Eq. 12 (after Eq. 5 for one generator) with
+ *                 respect to the Eq. 3 angles theta_j, phi_j and to tau
  */
 #include <algorithm>
 #include <cmath>
@@ -370,6 +373,83 @@ double orc_gradient(void* h, const uint64_t* gx, const uint64_t* gz, const doubl
         g.add(kv.second * I_POW[a].imag() * expectation(tp, b));
     }
     return -g.value();
+}
+
+/* d<psi|sigma|psi>/d theta and d/d phi for sigma in {I,X,Y,Z}, as
+   2 Re <d psi|sigma|psi> from explicit 2x2 products, with
+   d psi/d theta = (-sin(theta/2)/2, e^{i phi} cos(theta/2)/2) and
+   d psi/d phi = (0, i e^{i phi} sin(theta/2)). */
+void qmf_derivatives(int n, const double* theta, const double* phi, std::vector<Bloch>& dth,
+                     std::vector<Bloch>& dph) {
+    const cplx SIG[4][2][2] = {
+        {{1, 0}, {0, 1}},
+        {{0, 1}, {1, 0}},
+        {{0, cplx(0, -1)}, {cplx(0, 1), 0}},
+        {{1, 0}, {0, -1}},
+    };
+    dth.assign(n, Bloch{});
+    dph.assign(n, Bloch{});
+    for (int j = 0; j < n; ++j) {
+        const cplx e = std::polar(1.0, phi[j]);
+        const cplx psi[2] = {cplx(std::cos(theta[j] / 2), 0), e * std::sin(theta[j] / 2)};
+        const cplx d_t[2] = {cplx(-std::sin(theta[j] / 2) / 2, 0), e * std::cos(theta[j] / 2) / 2.0};
+        const cplx d_p[2] = {cplx(0, 0), cplx(0, 1) * e * std::sin(theta[j] / 2)};
+        for (int s = 0; s < 4; ++s) {
+            cplx at = 0, ap = 0;
+            for (int r = 0; r < 2; ++r)
+                for (int c = 0; c < 2; ++c) {
+                    at += std::conj(d_t[r]) * SIG[s][r][c] * psi[c];
+                    ap += std::conj(d_p[r]) * SIG[s][r][c] * psi[c];
+                }
+            dth[j].e[s] = 2.0 * at.real();
+            dph[j].e[s] = 2.0 * ap.real();
+        }
+    }
+}
+
+/* E(tau) = <Omega| e^{-i tau P/2} H e^{+i tau P/2} |Omega> (Eq. 5 inserted into
+   Eq. 12) and its derivatives with respect to the angles of Eq. 3 and to tau.
+   Route: dress a copy of H by (P, tau) with orc_dress, then differentiate each
+   string of the copy qubit by qubit (product rule: the derivative of qubit k's
+   factor times the product of the other qubits' factors, by an explicit loop).
+   dE/dtau = -B sin tau + C cos tau with A, B, C from orc_abc on H.  gx = gz =
+   NULL: no generator (the energy of H and its angle gradient; d_tau = 0).
+   Returns E(tau); d_theta, d_phi: n values each. */
+double orc_energy_gradients(void* h, const uint64_t* gx, const uint64_t* gz, double tau, const double* theta,
+                            const double* phi, double* d_theta, double* d_phi, double* d_tau) {
+    Oracle* o = (Oracle*)h;
+    Oracle work = *o;
+    *d_tau = 0.0;
+    if (gx && gz) {
+        if (orc_dress(&work, gx, gz, tau) != 0) return std::nan("");
+        double abc[3];
+        orc_abc(h, gx, gz, theta, phi, abc);
+        *d_tau = -abc[1] * std::sin(tau) + abc[2] * std::cos(tau);
+    }
+    const int n = o->n;
+    std::vector<Bloch> b = qmf_expectations(n, theta, phi);
+    std::vector<Bloch> dth, dph;
+    qmf_derivatives(n, theta, phi, dth, dph);
+    std::vector<Neumaier> gt(n), gp(n);
+    Neumaier e;
+    for (const auto& kv : work.H) {
+        const std::string& s = kv.first;
+        e.add(kv.second * expectation(s, b));
+        for (int k = 0; k < n; ++k) {
+            const int lk = letter_index(s[k]);
+            if (lk == 0) continue;
+            double others = 1.0;
+            for (int j = 0; j < n; ++j)
+                if (j != k) others *= b[j].e[letter_index(s[j])];
+            gt[k].add(kv.second * dth[k].e[lk] * others);
+            gp[k].add(kv.second * dph[k].e[lk] * others);
+        }
+    }
+    for (int k = 0; k < n; ++k) {
+        d_theta[k] = gt[k].value();
+        d_phi[k] = gp[k].value();
+    }
+    return e.value();
 }
 
 /* DIS candidates: one representative per distinct non-empty flip set

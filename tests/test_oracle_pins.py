@@ -351,3 +351,93 @@ def test_iteration_applies_the_term_limit_after_every_dress():
     assert a.as_dict() == b.as_dict()
     assert ra["removed"] == removed and removed > 0
     assert ra["energy"] == b.energy(th, ph)
+
+
+# ---------------------------------------------------------------------------
+# Angle and amplitude derivatives of the dressed QMF energy (Eq. 3, Eq. 5, Eq. 12)
+
+
+def _dense_dressed_energy(n, x, z, c, word, tau, theta, phi):
+    Hm = dense.dense(n, x, z, c)
+    if word is not None:
+        Hm = dense.conjugate(Hm, word, tau)
+    return float(dense.expval(Hm, dense.qmf_state(theta, phi)).real)
+
+
+@pytest.mark.parametrize("n,with_gen", [(3, False), (3, True), (4, True), (5, False)])
+def test_energy_gradients_match_dense_finite_differences(n, with_gen):
+    """Every derivative against a central difference of the dense energy
+    <Omega| U H U^dagger |Omega> (np.kron statevectors, dense conjugation)."""
+    rng = np.random.Generator(np.random.PCG64(40 + n + 7 * with_gen))
+    _, x, z, c = synth.random_hamiltonian(n, 12, 90 + n)
+    theta = rng.uniform(0, np.pi, n)
+    phi = rng.uniform(0, 2 * np.pi, n)
+    o = oracle.Oracle(n, x, z, c)
+    word, gx, gz, tau = None, None, None, 0.0
+    if with_gen:
+        gx, gz = synth.random_generator(n, rng, weight=2)
+        word = dense.letters(n, np.asarray(gx).reshape(-1), np.asarray(gz).reshape(-1))
+        tau = float(rng.uniform(-1.5, 1.5))
+    e, dt, dp, dtau = o.energy_gradients(theta, phi, gx, gz, tau)
+    assert e == pytest.approx(_dense_dressed_energy(n, x, z, c, word, tau, theta, phi), abs=1e-12)
+    h = 1e-6
+    for k in range(n):
+        for arr, got in ((theta, dt[k]), (phi, dp[k])):
+            up, dn = arr.copy(), arr.copy()
+            up[k] += h
+            dn[k] -= h
+            args_up = (theta, up) if arr is phi else (up, phi)
+            args_dn = (theta, dn) if arr is phi else (dn, phi)
+            fd = (_dense_dressed_energy(n, x, z, c, word, tau, args_up[0], args_up[1])
+                  - _dense_dressed_energy(n, x, z, c, word, tau, args_dn[0], args_dn[1])) / (2 * h)
+            assert got == pytest.approx(fd, abs=2e-8), (k, got, fd)
+    if with_gen:
+        fd = (_dense_dressed_energy(n, x, z, c, word, tau + h, theta, phi)
+              - _dense_dressed_energy(n, x, z, c, word, tau - h, theta, phi)) / (2 * h)
+        assert dtau == pytest.approx(fd, abs=2e-8)
+    else:
+        assert dtau == 0.0
+
+
+@pytest.mark.parametrize("word,theta,phi", [("X", [0.7], [0.3]), ("Y", [1.9], [2.2]), ("Z", [0.4], [1.0]),
+                                            ("XZ", [0.8, 2.1], [0.5, 1.3])])
+def test_energy_gradients_closed_forms(word, theta, phi):
+    """<X> = sin t cos p, <Y> = sin t sin p, <Z> = cos t per qubit, differentiated by hand."""
+    n = len(word)
+    x, z, c = _from_words(n, {word: 1.5})
+    e, dt, dp, _ = oracle.Oracle(n, x, z, c).energy_gradients(theta, phi)
+    t, p = np.array(theta), np.array(phi)
+    f = {"X": (np.sin(t) * np.cos(p), np.cos(t) * np.cos(p), -np.sin(t) * np.sin(p)),
+         "Y": (np.sin(t) * np.sin(p), np.cos(t) * np.sin(p), np.sin(t) * np.cos(p)),
+         "Z": (np.cos(t), -np.sin(t), np.zeros_like(t))}
+    val = np.array([f[l][0][j] for j, l in enumerate(word)])
+    for k, l in enumerate(word):
+        others = np.prod(np.delete(val, k))
+        assert dt[k] == pytest.approx(1.5 * f[l][1][k] * others, abs=1e-14)
+        assert dp[k] == pytest.approx(1.5 * f[l][2][k] * others, abs=1e-14)
+    assert e == pytest.approx(1.5 * np.prod(val), abs=1e-14)
+
+
+@pytest.mark.parametrize("n", [6, 9])
+def test_energy_gradient_in_tau_at_zero_is_eq7(n):
+    """dE/dtau at tau = 0 equals the Eq. 7 gradient (orc_gradient, pinned on its own)."""
+    rng = np.random.Generator(np.random.PCG64(300 + n))
+    _, x, z, c = synth.random_hamiltonian(n, 60, 500 + n)
+    theta = rng.uniform(0, np.pi, n)
+    phi = rng.uniform(0, 2 * np.pi, n)
+    o = oracle.Oracle(n, x, z, c)
+    for _ in range(3):
+        gx, gz = synth.random_generator(n, rng, weight=3)
+        _, _, _, dtau = o.energy_gradients(theta, phi, gx, gz, 0.0)
+        assert dtau == pytest.approx(o.gradient(gx, gz, theta, phi), abs=1e-12)
+
+
+def test_phi_gradients_vanish_at_basis_states():
+    """On a z-eigenstate every single-qubit state is |0> or |1>, where phi is a
+    global phase of the qubit: dE/dphi = 0 (sin(pi) ~ 1e-16 aside)."""
+    n = 7
+    _, x, z, c = synth.random_hamiltonian(n, 80, 77)
+    theta = np.where(np.arange(n) < 3, np.pi, 0.0)
+    phi = np.linspace(0.1, 2.0, n)
+    _, dt, dp, _ = oracle.Oracle(n, x, z, c).energy_gradients(theta, phi)
+    assert np.max(np.abs(dp)) < 1e-14 * max(1.0, np.abs(c).sum())
