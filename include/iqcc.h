@@ -124,6 +124,25 @@ iqcc_status iqcc_generator_abc(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t
                                const double* theta, const double* phi, double abc[3]);
 
 /*
+ * Derivatives of the dressed QMF energy (the adjoint of Eq. 3 / Eq. 12 after
+ * Eq. 5), for joint optimisation of the product-state angles and one
+ * generator's amplitude.  With a generator (gx, gz: host [W] words each, both
+ * non-NULL): *energy = E(tau) = <Omega|e^{-i tau P/2} H e^{i tau P/2}|Omega>
+ * = A + B cos(tau) + C sin(tau) as in iqcc_generator_abc, d_theta[j] =
+ * dE(tau)/d theta_j and d_phi[j] = dE(tau)/d phi_j (host [n_qubits] each),
+ * and *d_tau = -B sin(tau) + C cos(tau).  With gx = gz = NULL: the energy of H
+ * and its angle gradient, *d_tau = 0.  H is not modified; the dressed
+ * Hamiltonian is never formed.  theta/phi: host [n_qubits]; a qubit whose
+ * theta is exactly 0 or pi takes sin(theta) = 0, as in iqcc_qmf_energy.
+ * Sums are FP64 with atomic adds, so the last bits can vary between calls.
+ * Errors: IQCC_ERR_ARG (NULL output or angle pointer, only one of gx/gz,
+ * generator bits above n_qubits), IQCC_ERR_OOM, IQCC_ERR_CUDA.
+ */
+iqcc_status iqcc_energy_gradients(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, double tau,
+                                  const double* theta, const double* phi, double* energy, double* d_theta,
+                                  double* d_phi, double* d_tau);
+
+/*
  * Energy gradients of candidate generators at tau = 0 (Eq. 7 / Eq. 13, sign as
  * above: g = dE/dtau = C of iqcc_generator_abc).
  * n_cand > 0: gradients of the given candidates cx, cz [n_cand][W]; grad[k]

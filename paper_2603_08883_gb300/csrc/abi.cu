@@ -880,6 +880,58 @@ iqcc_status iqcc_generator_abc(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t
     return abc_impl(ctx, pk, theta, phi, abc);
 }
 
+iqcc_status iqcc_energy_gradients(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, double tau,
+                                  const double* theta, const double* phi, double* energy, double* d_theta,
+                                  double* d_phi, double* d_tau) {
+    GUARD(ctx);
+    if (!theta || !phi || !energy || !d_theta || !d_phi || !d_tau) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    if ((gx == nullptr) != (gz == nullptr)) return fail(ctx, IQCC_ERR_ARG, "gx and gz must be given together");
+    const bool has_gen = gx != nullptr;
+    uint64_t pk[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (has_gen) {
+        if (bits_above_n(ctx, gx) || bits_above_n(ctx, gz))
+            return fail(ctx, IQCC_ERR_ARG, "generator bits above n_qubits");
+        pad_key(ctx, gx, gz, pk);
+    }
+    const int n = ctx->n;
+    const int cols = 2 * n + 3;
+    const int nb = energy_grad_blocks();
+    Carver cv;
+    cv.take<double>(2 * (size_t)n);
+    cv.take<double>(12 * (size_t)n);
+    cv.take<double>((size_t)nb * cols);
+    cv.take<double>(cols);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    double* angles = cv.take<double>(2 * (size_t)n);
+    double* tab = cv.take<double>(12 * (size_t)n);
+    double* partials = cv.take<double>((size_t)nb * cols);
+    double* out = cv.take<double>(cols);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+    std::vector<double> h(cols, 0.0);
+    if (ctx->M > 0) {
+        CK(cudaMemcpyAsync(angles, theta, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(angles + n, phi, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+        launch_grad_tables(angles, angles + n, n, tab, ctx->stream);
+        CK_LAUNCH();
+        launch_energy_grad(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pk, has_gen, std::cos(tau), std::sin(tau), tab, n,
+                           partials, nb, ctx->stream);
+        CK_LAUNCH();
+        launch_reduce_cols(partials, nb, cols, out, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(h.data(), out, sizeof(double) * cols, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    const double A = h[2 * n], B = h[2 * n + 1], C = h[2 * n + 2];
+    *energy = has_gen ? A + B * std::cos(tau) + C * std::sin(tau) : A;
+    *d_tau = has_gen ? -B * std::sin(tau) + C * std::cos(tau) : 0.0;
+    for (int k = 0; k < n; ++k) {
+        d_theta[k] = h[k];
+        d_phi[k] = h[n + k];
+    }
+    return IQCC_OK;
+}
+
 iqcc_status iqcc_dis_gradients(iqcc_ctx* ctx, const double* theta, const double* phi, int64_t n_cand,
                                const uint64_t* cx, const uint64_t* cz, int64_t cap, int64_t* n_out, uint64_t* ox,
                                uint64_t* oz, double* grad) {

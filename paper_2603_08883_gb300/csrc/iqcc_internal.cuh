@@ -240,6 +240,14 @@ size_t index_reindex_scratch_bytes(int64_t n_entries);
 void launch_index_reindex(HashView h, uint64_t n_slots, const uint32_t* new_row, int64_t n_entries, void* scratch,
                           DevCounters* ctr, cudaStream_t s);
 
+// k_grad.cu: adjoint of the dressed QMF energy.  tab: [n][12] per-qubit
+// <sigma>, d/dtheta, d/dphi; partials: [blocks][2n + 3] (dE/dtheta, dE/dphi, A, B, C).
+int energy_grad_blocks();
+void launch_grad_tables(const double* theta, const double* phi, int n, double* tab, cudaStream_t s);
+void launch_energy_grad(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,
+                        bool has_gen, double cos_t, double sin_t, const double* tab, int n, double* partials,
+                        int blocks, cudaStream_t s);
+
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,

@@ -83,6 +83,8 @@ _dress = _sig("iqcc_dress", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.
 _prune = _sig("iqcc_prune", _c, [_vp, ctypes.c_double, ctypes.c_int64, _i64p])
 _energy = _sig("iqcc_qmf_energy", _c, [_vp, _f64p, _f64p, _f64p])
 _abc = _sig("iqcc_generator_abc", _c, [_vp, _u64p, _u64p, _f64p, _f64p, _f64p])
+_egrad = _sig("iqcc_energy_gradients", _c, [_vp, _u64p, _u64p, ctypes.c_double, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                            _f64p])
 _dis = _sig("iqcc_dis_gradients", _c, [_vp, _f64p, _f64p, ctypes.c_int64, _u64p, _u64p, ctypes.c_int64, _i64p,
                                        _u64p, _u64p, _f64p])
 _iterate = _sig("iqcc_iterate", _c, [_vp, _f64p, _f64p, ctypes.POINTER(iqcc_iter_opts),
@@ -221,6 +223,26 @@ def iqcc_generator_abc(H: Hamiltonian, gx, gz, theta, phi):
     out = np.zeros(3)
     H._check(_abc(H._h, gxp, gzp, tp, pp, out.ctypes.data_as(_f64p)))
     return out
+
+
+def iqcc_energy_gradients(H: Hamiltonian, theta, phi, gx=None, gz=None, tau: float = 0.0):
+    """(E(tau), dE/dtheta, dE/dphi, dE/dtau) after the generator (gx, gz) at
+    amplitude tau; without a generator, the energy of H and its angle gradient."""
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    if (gx is None) != (gz is None):
+        raise ValueError("gx and gz must be given together")
+    gxp = gzp = None
+    if gx is not None:
+        gxa, gxp = _u64(gx, (H.W,))
+        gza, gzp = _u64(gz, (H.W,))
+    e = np.zeros(1)
+    dt = np.zeros(H.n)
+    dp = np.zeros(H.n)
+    dtau = np.zeros(1)
+    H._check(_egrad(H._h, gxp, gzp, float(tau), tp, pp, e.ctypes.data_as(_f64p), dt.ctypes.data_as(_f64p),
+                    dp.ctypes.data_as(_f64p), dtau.ctypes.data_as(_f64p)))
+    return float(e[0]), dt, dp, float(dtau[0])
 
 
 def iqcc_dis_gradients(H: Hamiltonian, theta, phi, cx=None, cz=None, cap: int | None = None):
