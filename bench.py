@@ -140,6 +140,32 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def measure_adjoint(iqcc, H, n, th, ph, stream):
+    """iqcc_energy_gradients on H as it stands (CUDA events around the call),
+    at the workload's angles and at random general angles, with the top DIS
+    candidate as generator.  Algorithmic bytes: (16W + 8) per term."""
+    import torch
+    M = len(H)
+    W = (n + 63) // 64
+    cx, cz, _ = iqcc.iqcc_dis_gradients(H, th, ph, cap=1)
+    rng = np.random.Generator(np.random.PCG64(11))
+    general = (rng.uniform(0, np.pi, n), rng.uniform(0, 2 * np.pi, n))
+    out = {"M": M, "bytes_per_term": 16 * W + 8, "generator": "top DIS candidate, tau = 0.1"}
+    peak, _ = measured_peak()
+    for name, (t, p) in (("workload_angles", (th, ph)), ("general_angles", general)):
+        iqcc.iqcc_energy_gradients(H, t, p, cx[0], cz[0], 0.1)  # warm-up
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        iqcc.iqcc_energy_gradients(H, t, p, cx[0], cz[0], 0.1)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        gbs = M * (16 * W + 8) / (ms / 1e3) / 1e9
+        out[name] = {"ms": round(ms, 2), "achieved_GBs": round(gbs, 1), "frac_hbm": round(gbs / peak, 4)}
+    return out
+
+
 def profile_traffic(avg_rows):
     """DRAM bytes per dressed term of the dress kernel from the committed ncu
     summary (profiles/dress_kernel_jw100.md, line 'dram_bytes_per_dressed_term:'),
@@ -255,6 +281,11 @@ def run_gpu(args):
         dist.all_reduce(dd, op=dist.ReduceOp.SUM)
         total_dressed = float(dd.item())
 
+    # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
+    adjoint = None
+    if rank == 0:
+        adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
+
     # ---------------- end to end through host buffers (pinned), N = 1 path of a user
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
@@ -318,7 +349,8 @@ def run_gpu(args):
                 "traffic": profile_traffic(avg_rows),
                 "bytes_per_launch": stats["dress_bytes"] / n_dress, "launches": stats["n_dress"],
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
-                "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {}}
+                "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
+                "adjoint_pass": adjoint}
 
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None

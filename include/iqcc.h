@@ -96,6 +96,25 @@ iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint6
                        const double* tau, int* n_applied);
 
 /*
+ * The dress of iqcc_dress by sorting instead of hashing (the alternative merge
+ * of App. D: expansion, sort, segmented reduction).  Generators are taken in
+ * groups of `fuse` (1..8, the last group may be shorter); each group expands
+ * every term along every path through its generators (at generator j a path
+ * keeps the current string, with factor cos(tau_j) when it anticommutes with
+ * P_j, or, only then, moves to its partner with factor s sin(tau_j)), sorts
+ * the expanded terms in canonical key order, sums runs of equal keys in FP64
+ * (exact zeros kept) and compacts them.  The result equals iqcc_dress up to
+ * rounding (summation order); with fuse > 1 the intermediate merges are
+ * skipped.  Terms end in canonical order; the index is rebuilt at the end.
+ * gx, gz: host [n_gen][W]; tau: host [n_gen].  Errors: IQCC_ERR_ARG (bad
+ * fuse, bits above n_qubits, non-finite tau), IQCC_ERR_CAPACITY when a
+ * group's expansion exceeds the capacity (H as after the previous group),
+ * IQCC_ERR_OOM, IQCC_ERR_CUDA.  *n_applied (may be NULL): generators applied.
+ */
+iqcc_status iqcc_dress_sorted(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
+                              const double* tau, int fuse, int* n_applied);
+
+/*
  * Compress H (App. A procedure step 5; the "Maximum Terms" limit of the
  * paper's Tables 2-3): remove every term with |C| < eps (eps <= 0 removes
  * nothing); then, when max_terms > 0 and more terms remain, keep the max_terms
@@ -233,6 +252,8 @@ typedef struct {
     int64_t rows_allocated;    /* rows currently allocated on the device */
     int64_t hash_slots;        /* active hash slots */
     int64_t kernel_launches;   /* kernels launched by the library (all contexts) since the reset */
+    int64_t n_sorted_groups;   /* generator groups applied by iqcc_dress_sorted */
+    double sorted_dress_ms;    /* device time of those groups (expansion, sort, merge; index rebuild excluded) */
     int words;                 /* device words per x or z vector (1, 2 or 4) */
     int pad;
 } iqcc_stats;

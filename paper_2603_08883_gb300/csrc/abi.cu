@@ -847,6 +847,100 @@ iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint6
     return IQCC_OK;
 }
 
+// One group of k generators through the sort-based path: expand every row
+// along every valid path (k_sortdress.cu), sort the leaves canonically, sum
+// runs of equal keys (exact zeros kept, as the hash path keeps them), compact
+// into the row buffer.  The index is not touched (rebuilt by the caller).  On
+// IQCC_ERR_CAPACITY / IQCC_ERR_OOM the Hamiltonian is unchanged.
+iqcc_status sorted_group(iqcc_ctx* ctx, const uint64_t* pkeys, const double* tau, int k) {
+    const int64_t M = ctx->M;
+    if (M == 0) return IQCC_OK;
+    const int Wd = ctx->Wd;
+    DevCounters* c = dctr(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    launch_expand_count(Wd, ctx->rows(), M, pkeys, tau, k, &c->aux, ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    const int64_t total = (int64_t)ctx->h_counters->aux;
+    if (total > ctx->capacity) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "sorted dress would expand to %lld rows, capacity is %lld", (long long)total,
+                 (long long)ctx->capacity);
+        return fail(ctx, IQCC_ERR_CAPACITY, buf);
+    }
+    Carver cv;
+    cv.take<uint64_t>((size_t)total * 2 * Wd);
+    cv.take<double>(total);
+    cv.take<uint8_t>(total);
+    cv.take<char>(compact_inplace_scratch_bytes(total));
+    cv.off += sort_area_bytes(total);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint64_t* staged = cv.take<uint64_t>((size_t)total * 2 * Wd);
+    double* c_staged = cv.take<double>(total);
+    uint8_t* flags = cv.take<uint8_t>(total);
+    char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(total));
+    SortArea sa = carve_sort(cv, total);
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_expand_emit(Wd, ctx->rows(), ctx->c(), M, pkeys, tau, k, staged, c_staged, &c->aux, total, c, ctx->stream);
+    CK_LAUNCH();
+    st = read_counters(ctx);
+    if (st) return st;
+    if (total > ctx->rows_alloc) {  // the old rows are no longer needed: grow without keeping them
+        const size_t rb = row_bytes(ctx);
+        if (!ensure(ctx, ctx->keys, (size_t)total * rb) || !ensure(ctx, ctx->coef, (size_t)total * 8))
+            return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
+        ctx->rows_alloc = total;
+        ctx->stats.rows_allocated = total;
+    }
+    launch_iota(sa.a, total, ctx->stream);
+    uint32_t* sorted = nullptr;
+    radix_sort_indirect(staged, 2 * Wd, canonical_plan(ctx), sa.a, sa.b, total, &sorted, sa.tmp, sa.tmp_bytes,
+                        ctx->stream);
+    launch_sum_runs(Wd, staged, c_staged, sorted, total, flags, ctx->rows(), ctx->c(), ctx->stream, true);
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_compact_inplace(Wd, flags, ctx->rows(), ctx->c(), total, cscratch, &c->aux, c, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    st = read_counters(ctx);
+    if (st) return st;
+    ctx->M = (int64_t)ctx->h_counters->aux;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.sorted_dress_ms += ms;
+    ctx->stats.n_sorted_groups++;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_dress_sorted(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* tau,
+                              int fuse, int* n_applied) {
+    if (n_applied) *n_applied = 0;
+    GUARD(ctx);
+    if (n_gen < 0) return fail(ctx, IQCC_ERR_ARG, "n_gen < 0");
+    if (n_gen > 0 && (!gx || !gz || !tau)) return fail(ctx, IQCC_ERR_ARG, "null generator array");
+    if (fuse < 1 || fuse > max_fuse()) return fail(ctx, IQCC_ERR_ARG, "fuse must be in 1..8");
+    for (int k = 0; k < n_gen; ++k) {
+        if (bits_above_n(ctx, gx + k * ctx->W) || bits_above_n(ctx, gz + k * ctx->W))
+            return fail(ctx, IQCC_ERR_ARG, "generator bits set above n_qubits");
+        if (!std::isfinite(tau[k])) return fail(ctx, IQCC_ERR_ARG, "non-finite amplitude");
+    }
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    for (int g0 = 0; g0 < n_gen; g0 += fuse) {
+        const int k = std::min(fuse, n_gen - g0);
+        std::vector<uint64_t> pk((size_t)k * 2 * ctx->Wd);
+        for (int j = 0; j < k; ++j)
+            pad_key(ctx, gx + (size_t)(g0 + j) * ctx->W, gz + (size_t)(g0 + j) * ctx->W, pk.data() + (size_t)j * 2 * ctx->Wd);
+        iqcc_status st = sorted_group(ctx, pk.data(), tau + g0, k);
+        if (st) return st;
+        if (n_applied) *n_applied = g0 + k;
+    }
+    if (n_gen > 0) return rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
+    return IQCC_OK;
+}
+
 iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_removed) {
     if (n_removed) *n_removed = 0;
     GUARD(ctx);
@@ -894,32 +988,38 @@ iqcc_status iqcc_energy_gradients(iqcc_ctx* ctx, const uint64_t* gx, const uint6
         pad_key(ctx, gx, gz, pk);
     }
     const int n = ctx->n;
-    const int cols = 2 * n + 3;
+    const int cols = energy_grad_cols(n);
     const int nb = energy_grad_blocks();
     Carver cv;
     cv.take<double>(2 * (size_t)n);
-    cv.take<double>(12 * (size_t)n);
+    cv.take<double>(energy_grad_table_doubles(n));
     cv.take<double>((size_t)nb * cols);
     cv.take<double>(cols);
+    cv.take<double>(2 * (size_t)n + 3);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
     double* angles = cv.take<double>(2 * (size_t)n);
-    double* tab = cv.take<double>(12 * (size_t)n);
+    double* tab = cv.take<double>(energy_grad_table_doubles(n));
     double* partials = cv.take<double>((size_t)nb * cols);
-    double* out = cv.take<double>(cols);
+    double* sums = cv.take<double>(cols);
+    double* out = cv.take<double>(2 * (size_t)n + 3);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    std::vector<double> h(cols, 0.0);
+    std::vector<double> h(2 * (size_t)n + 3, 0.0);
     if (ctx->M > 0) {
+        uint64_t occ[4];
+        occ_words(ctx, theta, occ);
         CK(cudaMemcpyAsync(angles, theta, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(angles + n, phi, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
         launch_grad_tables(angles, angles + n, n, tab, ctx->stream);
         CK_LAUNCH();
         launch_energy_grad(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pk, has_gen, std::cos(tau), std::sin(tau), tab, n,
-                           partials, nb, ctx->stream);
+                           occ, is_basis(ctx, theta), partials, nb, ctx->stream);
         CK_LAUNCH();
-        launch_reduce_cols(partials, nb, cols, out, ctx->stream);
+        launch_reduce_cols(partials, nb, cols, sums, ctx->stream);
         CK_LAUNCH();
-        CK(cudaMemcpyAsync(h.data(), out, sizeof(double) * cols, cudaMemcpyDeviceToHost, ctx->stream));
+        launch_grad_combine(sums, tab, n, out, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(h.data(), out, sizeof(double) * (2 * n + 3), cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
     }
     const double A = h[2 * n], B = h[2 * n + 1], C = h[2 * n + 2];

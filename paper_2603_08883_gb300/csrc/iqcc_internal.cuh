@@ -240,13 +240,26 @@ size_t index_reindex_scratch_bytes(int64_t n_entries);
 void launch_index_reindex(HashView h, uint64_t n_slots, const uint32_t* new_row, int64_t n_entries, void* scratch,
                           DevCounters* ctr, cudaStream_t s);
 
-// k_grad.cu: adjoint of the dressed QMF energy.  tab: [n][12] per-qubit
-// <sigma>, d/dtheta, d/dphi; partials: [blocks][2n + 3] (dE/dtheta, dE/dphi, A, B, C).
+// k_grad.cu: adjoint of the dressed QMF energy.  tab: energy_grad_table_doubles(n)
+// per-qubit values; partials: [blocks][energy_grad_cols(n)]; the column sums go
+// through launch_grad_combine to out[2n + 3] = (dE/dtheta, dE/dphi, A, B, C).
 int energy_grad_blocks();
+int energy_grad_table_doubles(int n);
+int energy_grad_cols(int n);
 void launch_grad_tables(const double* theta, const double* phi, int n, double* tab, cudaStream_t s);
 void launch_energy_grad(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,
-                        bool has_gen, double cos_t, double sin_t, const double* tab, int n, double* partials,
-                        int blocks, cudaStream_t s);
+                        bool has_gen, double cos_t, double sin_t, const double* tab, int n, const uint64_t* occ_words,
+                        bool basis, double* partials, int blocks, cudaStream_t s);
+void launch_grad_combine(const double* sums, const double* tab, int n, double* out, cudaStream_t s);
+
+// k_sortdress.cu: expansion of rows through a group of up to max_fuse()
+// generators (pkeys: k device-layout keys of 2*Wd words, host memory; tau: host).
+int max_fuse();
+void launch_expand_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkeys, const double* tau, int k,
+                         unsigned long long* total, cudaStream_t s);
+void launch_expand_emit(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkeys,
+                        const double* tau, int k, uint64_t* out_rows, double* out_coef, unsigned long long* next,
+                        int64_t cap, DevCounters* ctr, cudaStream_t s);
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
@@ -318,7 +331,8 @@ void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint6
 void launch_unpack_rows(int W, int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
                         uint64_t* x, uint64_t* z, double* c, int64_t n, cudaStream_t s);
 void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,
-                     uint8_t* flags, uint64_t* rows_out_gather, double* c_out_gather, cudaStream_t s);
+                     uint8_t* flags, uint64_t* rows_out_gather, double* c_out_gather, cudaStream_t s,
+                     bool keep_zeros = false);
 void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
                         int64_t n, uint64_t* rows_out, double* c_out, cudaStream_t s);
 

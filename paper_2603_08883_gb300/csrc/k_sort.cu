@@ -373,7 +373,7 @@ __device__ __forceinline__ bool same_key_rows(const uint64_t* rows, uint32_t a, 
 template <int W>
 __global__ void k_sum_runs(const uint64_t* __restrict__ rows, const double* __restrict__ coef,
                            const uint32_t* __restrict__ perm, int64_t n, uint8_t* flags, uint64_t* rows_out,
-                           double* c_out) {
+                           double* c_out, bool keep_zeros) {
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
         const uint32_t r = perm[i];
@@ -384,7 +384,7 @@ __global__ void k_sum_runs(const uint64_t* __restrict__ rows, const double* __re
         Key<W> k = load_key<W>(rows, r);
         store_key<W>(rows_out, i, k);
         c_out[i] = sum;
-        flags[i] = (sum != 0.0);
+        flags[i] = keep_zeros || sum != 0.0;
     }
 }
 
@@ -691,13 +691,13 @@ void launch_unpack_rows(int W, int Wd, const uint64_t* rows, const double* coef,
 }
 
 void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,
-                     uint8_t* flags, uint64_t* rows_out, double* c_out, cudaStream_t s) {
+                     uint8_t* flags, uint64_t* rows_out, double* c_out, cudaStream_t s, bool keep_zeros) {
     if (n <= 0) return;
     int g = grid_stride_blocks(n);
     switch (Wd) {
-        case 1: k_sum_runs<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); note_launch(); break;
-        case 2: k_sum_runs<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); note_launch(); break;
-        default: k_sum_runs<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out); note_launch(); break;
+        case 1: k_sum_runs<1><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out, keep_zeros); note_launch(); break;
+        case 2: k_sum_runs<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out, keep_zeros); note_launch(); break;
+        default: k_sum_runs<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out, keep_zeros); note_launch(); break;
     }
 }
 

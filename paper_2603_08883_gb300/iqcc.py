@@ -65,7 +65,8 @@ class iqcc_stats(ctypes.Structure):
                 ("n_energy", ctypes.c_int64), ("energy_kernel_ms", ctypes.c_double),
                 ("energy_bytes", ctypes.c_double), ("prune_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
                 ("hash_ms", ctypes.c_double), ("hash_rebuilds", ctypes.c_int64), ("rows_allocated", ctypes.c_int64),
-                ("hash_slots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64), ("words", ctypes.c_int),
+                ("hash_slots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
+                ("n_sorted_groups", ctypes.c_int64), ("sorted_dress_ms", ctypes.c_double), ("words", ctypes.c_int),
                 ("pad", ctypes.c_int)]
 
 
@@ -80,6 +81,8 @@ _c = ctypes.c_int
 _load = _sig("iqcc_load_hamiltonian", _c, [ctypes.POINTER(_vp), ctypes.POINTER(iqcc_opts), ctypes.c_int64, _u64p,
                                            _u64p, _f64p])
 _dress = _sig("iqcc_dress", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.POINTER(ctypes.c_int)])
+_dress_sorted = _sig("iqcc_dress_sorted", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_int)])
 _prune = _sig("iqcc_prune", _c, [_vp, ctypes.c_double, ctypes.c_int64, _i64p])
 _energy = _sig("iqcc_qmf_energy", _c, [_vp, _f64p, _f64p, _f64p])
 _abc = _sig("iqcc_generator_abc", _c, [_vp, _u64p, _u64p, _f64p, _f64p, _f64p])
@@ -198,6 +201,15 @@ def iqcc_dress(H: Hamiltonian, gx, gz, tau) -> int:
     ta, tp = _f64(np.atleast_1d(tau), len(gxa))
     applied = ctypes.c_int(0)
     H._check(_dress(H._h, len(gxa), gxp, gzp, tp, ctypes.byref(applied)))
+    return applied.value
+
+
+def iqcc_dress_sorted(H: Hamiltonian, gx, gz, tau, fuse: int = 1) -> int:
+    gxa, gxp = _u64(gx, (-1, H.W))
+    gza, gzp = _u64(gz, (-1, H.W))
+    ta, tp = _f64(np.atleast_1d(tau), len(gxa))
+    applied = ctypes.c_int(0)
+    H._check(_dress_sorted(H._h, len(gxa), gxp, gzp, tp, int(fuse), ctypes.byref(applied)))
     return applied.value
 
 
