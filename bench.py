@@ -166,6 +166,32 @@ def measure_adjoint(iqcc, H, n, th, ph, stream):
     return out
 
 
+def measure_sort_variant(iqcc, n, x, z, c, th, ph, stream, n_gen=8, tau=0.1):
+    """The hash dress against the sort-based dress (one sort per generator, and
+    all generators fused into one expansion and one sort) on the loaded
+    Hamiltonian, with its top DIS candidates as generators; CUDA events around
+    each API call (index upkeep included on both sides)."""
+    import torch
+    H0 = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    gx, gz, _ = iqcc.iqcc_dis_gradients(H0, th, ph, cap=n_gen)
+    H0.close()
+    taus = np.full(len(gx), tau)
+    out = {"M0": len(c), "generators": f"top {len(gx)} DIS candidates of the loaded Hamiltonian, tau = {tau}"}
+    for name, call in (("hash", lambda H: iqcc.iqcc_dress(H, gx, gz, taus)),
+                       ("sorted_fuse1", lambda H: iqcc.iqcc_dress_sorted(H, gx, gz, taus, fuse=1)),
+                       (f"sorted_fuse{len(gx)}", lambda H: iqcc.iqcc_dress_sorted(H, gx, gz, taus, fuse=len(gx)))):
+        H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 31)
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        call(H)
+        ev1.record(stream)
+        ev1.synchronize()
+        out[name] = {"ms": round(ev0.elapsed_time(ev1), 2), "M_after": len(H)}
+        H.close()
+    return out
+
+
 def profile_traffic(avg_rows):
     """DRAM bytes per dressed term of the dress kernel from the committed ncu
     summary (profiles/dress_kernel_jw100.md, line 'dram_bytes_per_dressed_term:'),
@@ -282,7 +308,7 @@ def run_gpu(args):
         total_dressed = float(dd.item())
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
-    adjoint = None
+    adjoint = sort_variant = None
     if rank == 0:
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
 
@@ -327,6 +353,8 @@ def run_gpu(args):
                        "pinned host arrays (the next step's input); wall clock"}
     else:
         H.close()
+    if rank == 0:  # after the capped Hamiltonian is released
+        sort_variant = measure_sort_variant(iqcc, n, x, z, c, th, ph, stream)
 
     if rank != 0:
         if dist is not None:
@@ -350,7 +378,7 @@ def run_gpu(args):
                 "bytes_per_launch": stats["dress_bytes"] / n_dress, "launches": stats["n_dress"],
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
-                "adjoint_pass": adjoint}
+                "adjoint_pass": adjoint, "sort_variant": sort_variant}
 
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None
