@@ -294,6 +294,86 @@ const char* iqcc_last_error(const iqcc_ctx* ctx);
 /* Release the context and all its device memory (NULL is allowed). */
 void iqcc_free(iqcc_ctx* ctx);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent Hamiltonians (many small problems screened and
+ * dressed together; the paper runs one Hamiltonian at a time, so this has no
+ * counterpart there beyond the single-problem steps it repeats).  Each problem
+ * has its own qubit count (1..48, one 64-bit word per x and z) and terms; all
+ * live in one device context where problem b's strings carry b in z bits
+ * 48..63 (Z letters on virtual qubits with theta = 0, which cancel in every
+ * product inside a problem and keep problems apart).  References must be
+ * z-eigenstates (every theta_j 0 or pi): screening uses the restricted sums of
+ * Eq. 14-15.
+ * ------------------------------------------------------------------------ */
+typedef struct iqcc_batch iqcc_batch;
+
+/* Per-problem results of a screening; every pointer is a host array of B
+ * entries (abc: 3 B), all required. */
+typedef struct {
+    double* energy;     /* E of the problem at the given angles (Eq. 12 at tau = 0) */
+    uint64_t* gx;       /* x word of its best DIS candidate (largest |g| as in iqcc_dis_gradients); 0: none */
+    uint64_t* gz;       /* z word of that candidate (Y on its lowest flipped qubit) */
+    double* grad;       /* the candidate's gradient dE/dtau at 0 (Eq. 7, library sign) */
+    double* abc;        /* [B][3] A, B, C of the candidate (iqcc_generator_abc) */
+    double* tau;        /* tau* = atan2(-C, -B); 0 without a candidate or when B = C = 0 */
+    int64_t* n_terms;   /* terms held by the problem */
+} iqcc_batch_screen_out;
+
+/*
+ * Load B problems (1..2048): n_qubits[B]; offsets[B + 1] (offsets[0] = 0,
+ * non-decreasing) delimit problem b's terms in the host arrays x, z (one word
+ * each per term) and coef.  Each problem is canonicalised as by
+ * iqcc_load_hamiltonian (repeated strings summed, exact zeros dropped).
+ * opts->n_qubits is ignored; capacity, max_probe, stream and the allocator
+ * hooks apply to the whole batch.  Errors: IQCC_ERR_ARG (counts, offsets, a
+ * qubit count above 48, bits above a problem's qubit count), IQCC_ERR_OOM,
+ * IQCC_ERR_CAPACITY, IQCC_ERR_CUDA (message: iqcc_last_error(NULL)).
+ */
+iqcc_status iqcc_batch_load(iqcc_batch** out, const iqcc_opts* opts, int n_problems, const int* n_qubits,
+                            const int64_t* offsets, const uint64_t* x, const uint64_t* z, const double* coef);
+
+/*
+ * Screen every problem at its reference (theta/phi: host arrays of the
+ * problems' qubit counts concatenated in problem order; theta_j must be 0 or
+ * pi): energy, best DIS candidate, its gradient, A, B, C and tau*.  The
+ * sequence of kernels runs without host synchronisation; on the first call
+ * for a given state of the batch its launch shapes are tuned by timing and it
+ * is captured into a CUDA graph, which later calls replay (with the new
+ * angles) until a step changes the Hamiltonians.  Errors: IQCC_ERR_ARG (NULL
+ * pointer, angles not 0 or pi), IQCC_ERR_HASH_FULL, IQCC_ERR_OOM, IQCC_ERR_CUDA.
+ */
+iqcc_status iqcc_batch_screen(iqcc_batch* batch, const double* theta, const double* phi,
+                              iqcc_batch_screen_out* out);
+
+/*
+ * One iteration of every problem with one generator: screen (out as above),
+ * dress each problem with its best candidate at its tau* (problems without a
+ * candidate are left as they are), remove terms with |C| < eps (eps <= 0:
+ * none), then energy_after[B] and n_terms_after[B] (host arrays, may be NULL)
+ * at the same angles.  Errors: as iqcc_batch_screen and iqcc_dress.
+ */
+iqcc_status iqcc_batch_step(iqcc_batch* batch, const double* theta, const double* phi, double eps,
+                            iqcc_batch_screen_out* out, double* energy_after, int64_t* n_terms_after);
+
+/* Problem b's terms in canonical order (x, z: host [cap] words, coef [cap]);
+ * *n receives the problem's term count.  As iqcc_export. */
+iqcc_status iqcc_batch_export(iqcc_batch* batch, int problem, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z,
+                              double* coef);
+
+typedef struct {
+    int64_t n_terms;        /* terms of all problems */
+    int64_t screens;        /* screenings run */
+    int64_t graph_replays;  /* of which replays of a captured graph */
+    int blocks_energy;      /* tuned grid sizes of the screening kernels */
+    int blocks_group;
+    int blocks_abc;
+    int pad;
+} iqcc_batch_info;
+
+iqcc_status iqcc_batch_get_info(const iqcc_batch* batch, iqcc_batch_info* out);
+const char* iqcc_batch_last_error(const iqcc_batch* batch);
+void iqcc_batch_free(iqcc_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

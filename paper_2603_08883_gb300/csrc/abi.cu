@@ -1204,3 +1204,403 @@ void iqcc_free(iqcc_ctx* ctx) {
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Batches of independent Hamiltonians
+// ============================================================================
+
+struct iqcc_batch {
+    iqcc_ctx* ctx = nullptr;
+    int B = 0;
+    std::vector<int> n;          // qubits per problem
+    std::vector<int64_t> aoff;   // offsets into the concatenated angle arrays
+    Buf dev;                     // per-problem device arrays (carved)
+    Buf groups;                  // DIS group slots and sums
+    uint64_t group_slots = 0;
+    cudaStream_t gs = nullptr;   // stream the screening graph runs on
+    cudaGraphExec_t graph = nullptr;
+    int64_t graph_M = -1;
+    uint64_t* h_occ = nullptr;   // pinned [B]
+    char* h_out = nullptr;       // pinned results
+    int blocks[3] = {0, 0, 0};   // tuned grids: energy, group, abc
+    int64_t screens = 0, replays = 0;
+};
+
+namespace {
+
+constexpr uint64_t kBatchXMask = (1ull << kBatchTagShift) - 1;
+
+// Device arrays of a batch, carved from b->dev.
+struct BatchDev {
+    uint64_t* occ;
+    unsigned long long* best_coarse;
+    unsigned long long* best_key;
+    double* best_g;
+    double* energy;
+    double* abc;
+    double* tau;
+    unsigned long long* counts;
+    Gen<1>* gens;
+    double* part_e;
+    double* part_abc;
+};
+
+int batch_max_blocks() { return sm_count() * 16; }
+
+BatchDev carve_batch(Carver& cv, int B) {
+    BatchDev d;
+    d.occ = cv.take<uint64_t>(B);
+    d.best_coarse = cv.take<unsigned long long>(B);
+    d.best_key = cv.take<unsigned long long>(B);
+    d.best_g = cv.take<double>(B);
+    d.energy = cv.take<double>(B);
+    d.abc = cv.take<double>(3 * (size_t)B);
+    d.tau = cv.take<double>(B);
+    d.counts = cv.take<unsigned long long>(B);
+    d.gens = cv.take<Gen<1>>(B);
+    d.part_e = cv.take<double>((size_t)batch_max_blocks() * B);
+    d.part_abc = cv.take<double>((size_t)batch_max_blocks() * 3 * B);
+    return d;
+}
+
+// Pinned result block: energy, best_key, best_g, abc, tau, counts.
+size_t batch_out_bytes(int B) { return (size_t)B * (8 + 8 + 8 + 24 + 8 + 8); }
+
+// The screening sequence on b->gs (no host synchronisation inside).
+void enqueue_screen(iqcc_batch* b, const BatchDev& d, const int* blocks) {
+    iqcc_ctx* ctx = b->ctx;
+    const int B = b->B;
+    cudaStream_t s = b->gs;
+    cudaMemcpyAsync(d.occ, b->h_occ, sizeof(uint64_t) * B, cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(d.counts, 0, sizeof(unsigned long long) * B, s);
+    cudaMemsetAsync(d.best_coarse, 0, sizeof(unsigned long long) * B, s);
+    cudaMemsetAsync(d.best_key, 0xFF, sizeof(unsigned long long) * B, s);
+    cudaMemsetAsync(d.best_g, 0, sizeof(double) * B, s);
+    uint64_t* slots = (uint64_t*)b->groups.p;
+    double* gsum = (double*)(slots + b->group_slots);
+    cudaMemsetAsync(slots, 0xFF, sizeof(uint64_t) * b->group_slots, s);
+    cudaMemsetAsync(gsum, 0, sizeof(double) * b->group_slots, s);
+    launch_seg_energy(ctx->rows(), ctx->c(), ctx->M, d.occ, B, d.part_e, d.counts, blocks[0], s);
+    launch_reduce_cols(d.part_e, blocks[0], B, d.energy, s);
+    launch_seg_dis_group(ctx->rows(), ctx->c(), ctx->M, d.occ, B, slots, gsum, b->group_slots / kBucketSlots - 1,
+                         ctx->max_probe, dctr(ctx), blocks[1], s);
+    launch_seg_best(slots, gsum, b->group_slots, B, d.best_coarse, d.best_key, d.best_g, blocks[1], s);
+    launch_seg_abc(ctx->rows(), ctx->c(), ctx->M, d.occ, B, d.best_key, d.part_abc, blocks[2], s);
+    launch_reduce_cols(d.part_abc, blocks[2], 3 * B, d.abc, s);
+    launch_seg_tau(d.abc, d.best_key, B, d.tau, d.gens, s);
+    char* o = b->h_out;
+    cudaMemcpyAsync(o, d.energy, sizeof(double) * B, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(o + 8 * B, d.best_key, sizeof(uint64_t) * B, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(o + 16 * B, d.best_g, sizeof(double) * B, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(o + 24 * B, d.abc, sizeof(double) * 3 * B, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(o + 48 * B, d.tau, sizeof(double) * B, cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(o + 56 * B, d.counts, sizeof(uint64_t) * B, cudaMemcpyDeviceToHost, s);
+}
+
+// Launch shapes by measurement: each screening kernel at 2, 4, 8 and 16 blocks
+// per SM, the fastest kept (one untimed run first fills the candidate arrays).
+iqcc_status tune_batch(iqcc_batch* b, const BatchDev& d) {
+    iqcc_ctx* ctx = b->ctx;
+    const int B = b->B;
+    const int sm = sm_count();
+    int blocks[3] = {4 * sm, 4 * sm, 4 * sm};
+    enqueue_screen(b, d, blocks);
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    uint64_t* slots = (uint64_t*)b->groups.p;
+    double* gsum = (double*)(slots + b->group_slots);
+    float best[3] = {1e30f, 1e30f, 1e30f};
+    for (int mult : {2, 4, 8, 16}) {
+        const int g = mult * sm;
+        float ms[3] = {0, 0, 0};
+        for (int k = 0; k < 3; ++k) {
+            if (k == 1) {
+                cudaMemsetAsync(slots, 0xFF, sizeof(uint64_t) * b->group_slots, b->gs);
+                cudaMemsetAsync(gsum, 0, sizeof(double) * b->group_slots, b->gs);
+            }
+            cudaEventRecord(e0, b->gs);
+            if (k == 0) launch_seg_energy(ctx->rows(), ctx->c(), ctx->M, d.occ, B, d.part_e, d.counts, g, b->gs);
+            if (k == 1)
+                launch_seg_dis_group(ctx->rows(), ctx->c(), ctx->M, d.occ, B, slots, gsum,
+                                     b->group_slots / kBucketSlots - 1, ctx->max_probe, dctr(ctx), g, b->gs);
+            if (k == 2) launch_seg_abc(ctx->rows(), ctx->c(), ctx->M, d.occ, B, d.best_key, d.part_abc, g, b->gs);
+            cudaEventRecord(e1, b->gs);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms[k], e0, e1);
+            if (ms[k] < best[k]) {
+                best[k] = ms[k];
+                b->blocks[k] = g;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaStreamSynchronize(b->gs));
+    return IQCC_OK;
+}
+
+// capture: on a state without a valid graph, capture one (else run the sequence directly).
+iqcc_status batch_screen(iqcc_batch* b, const double* theta, const double* phi, iqcc_batch_screen_out* out,
+                         bool capture) {
+    iqcc_ctx* ctx = b->ctx;
+    const int B = b->B;
+    if (!theta || !phi || !out || !out->energy || !out->gx || !out->gz || !out->grad || !out->abc || !out->tau ||
+        !out->n_terms)
+        return fail(ctx, IQCC_ERR_ARG, "null argument");
+    for (int p = 0; p < B; ++p) {
+        uint64_t occ = 0;
+        for (int j = 0; j < b->n[p]; ++j) {
+            const double t = theta[b->aoff[p] + j];
+            if (!(t == 0.0 || t == kPi)) return fail(ctx, IQCC_ERR_ARG, "batched screening needs theta 0 or pi");
+            if (t == kPi) occ |= 1ull << j;
+        }
+        b->h_occ[p] = occ;
+    }
+    // group table for at most one group per term, load <= 1/2
+    const uint64_t want = pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 2);
+    if (want != b->group_slots) {
+        if (!ensure(ctx, b->groups, (size_t)want * 16)) return fail(ctx, IQCC_ERR_OOM, "group table allocation failed");
+        b->group_slots = want;
+        b->graph_M = -1;
+    }
+    Carver cv{(char*)b->dev.p, 0};
+    const BatchDev d = carve_batch(cv, B);
+    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), b->gs));
+    if (b->graph && b->graph_M == ctx->M) {
+        CK(cudaGraphLaunch(b->graph, b->gs));
+        b->replays++;
+    } else {
+        if (!b->blocks[0]) {
+            iqcc_status st = tune_batch(b, d);
+            if (st) return st;
+        }
+        if (!capture) {
+            enqueue_screen(b, d, b->blocks);
+            CK_LAUNCH();
+        } else {
+        if (b->graph) {
+            cudaGraphExecDestroy(b->graph);
+            b->graph = nullptr;
+        }
+        cudaGraph_t g = nullptr;
+        CK(cudaStreamBeginCapture(b->gs, cudaStreamCaptureModeThreadLocal));
+        enqueue_screen(b, d, b->blocks);
+        CK(cudaStreamEndCapture(b->gs, &g));
+        const cudaError_t e = cudaGraphInstantiate(&b->graph, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        b->graph_M = ctx->M;
+        CK(cudaGraphLaunch(b->graph, b->gs));
+        }
+    }
+    CK(cudaStreamSynchronize(b->gs));
+    b->screens++;
+    CK(cudaMemcpy(ctx->h_counters, ctx->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost));
+    if (ctx->h_counters->err) {
+        char buf[160];
+        snprintf(buf, sizeof buf, "device error %d raised by kernel site %d", ctx->h_counters->err,
+                 ctx->h_counters->err_where);
+        return fail(ctx, (iqcc_status)ctx->h_counters->err, buf);
+    }
+    const char* o = b->h_out;
+    for (int p = 0; p < B; ++p) {
+        const uint64_t key = ((const uint64_t*)(o + 8 * B))[p];
+        const bool none = key == kEmptySlot;
+        out->energy[p] = ((const double*)o)[p];
+        out->gx[p] = none ? 0 : (key & kBatchXMask);
+        out->gz[p] = out->gx[p] & (~out->gx[p] + 1);
+        out->grad[p] = ((const double*)(o + 16 * B))[p];
+        for (int k = 0; k < 3; ++k) out->abc[3 * p + k] = ((const double*)(o + 24 * B))[3 * p + k];
+        out->tau[p] = ((const double*)(o + 48 * B))[p];
+        out->n_terms[p] = (int64_t)((const uint64_t*)(o + 56 * B))[p];
+    }
+    return IQCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+iqcc_status iqcc_batch_load(iqcc_batch** out, const iqcc_opts* opts, int n_problems, const int* n_qubits,
+                            const int64_t* offsets, const uint64_t* x, const uint64_t* z, const double* coef) {
+    if (!out) return fail(nullptr, IQCC_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (!opts || !n_qubits || !offsets) return fail(nullptr, IQCC_ERR_ARG, "null argument");
+    if (n_problems < 1 || n_problems > kMaxBatch) return fail(nullptr, IQCC_ERR_ARG, "n_problems must be in 1..2048");
+    if (offsets[0] != 0) return fail(nullptr, IQCC_ERR_ARG, "offsets[0] must be 0");
+    const int B = n_problems;
+    for (int b = 0; b < B; ++b) {
+        if (n_qubits[b] < 1 || n_qubits[b] > kBatchTagShift)
+            return fail(nullptr, IQCC_ERR_ARG, "problem qubit counts must be in 1..48");
+        if (offsets[b + 1] < offsets[b]) return fail(nullptr, IQCC_ERR_ARG, "offsets must not decrease");
+    }
+    const int64_t M = offsets[B];
+    if (M > 0 && (!x || !z || !coef)) return fail(nullptr, IQCC_ERR_ARG, "null input array");
+    std::vector<uint64_t> zt((size_t)M);
+    for (int b = 0; b < B; ++b) {
+        const uint64_t hi = n_qubits[b] >= 64 ? 0ull : ~((1ull << n_qubits[b]) - 1);
+        for (int64_t i = offsets[b]; i < offsets[b + 1]; ++i) {
+            if ((x[i] | z[i]) & hi) return fail(nullptr, IQCC_ERR_ARG, "key bits set above a problem's qubit count");
+            zt[i] = z[i] | ((uint64_t)b << kBatchTagShift);
+        }
+    }
+    iqcc_opts o = *opts;
+    o.n_qubits = 64;
+    iqcc_ctx* ctx = nullptr;
+    iqcc_status st = iqcc_load_hamiltonian(&ctx, &o, M, x, zt.data(), coef);
+    if (st) return st;
+    iqcc_batch* b = new iqcc_batch();
+    b->ctx = ctx;
+    b->B = B;
+    b->n.assign(n_qubits, n_qubits + B);
+    b->aoff.resize(B + 1, 0);
+    for (int p = 0; p < B; ++p) b->aoff[p + 1] = b->aoff[p] + n_qubits[p];
+    Carver dry;
+    carve_batch(dry, B);
+    bool ok = cudaStreamCreateWithFlags(&b->gs, cudaStreamNonBlocking) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_occ, sizeof(uint64_t) * B) == cudaSuccess &&
+              cudaMallocHost((void**)&b->h_out, batch_out_bytes(B)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        set_thread_error("batch stream / pinned allocation failed");
+        iqcc_batch_free(b);
+        return IQCC_ERR_CUDA;
+    }
+    if (!ensure(ctx, b->dev, dry.off)) {
+        set_thread_error("batch allocation failed");
+        iqcc_batch_free(b);
+        return IQCC_ERR_OOM;
+    }
+    *out = b;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_batch_screen(iqcc_batch* b, const double* theta, const double* phi, iqcc_batch_screen_out* out) {
+    if (!b) return fail(nullptr, IQCC_ERR_ARG, "null batch");
+    GUARD(b->ctx);
+    return batch_screen(b, theta, phi, out, true);
+}
+
+iqcc_status iqcc_batch_step(iqcc_batch* b, const double* theta, const double* phi, double eps,
+                            iqcc_batch_screen_out* out, double* energy_after, int64_t* n_terms_after) {
+    if (!b) return fail(nullptr, IQCC_ERR_ARG, "null batch");
+    iqcc_ctx* ctx = b->ctx;
+    GUARD(ctx);
+    if (std::isnan(eps)) return fail(ctx, IQCC_ERR_ARG, "eps is NaN");
+    if (2 * ctx->M > ctx->capacity)
+        return fail(ctx, IQCC_ERR_CAPACITY, "a batch step needs capacity for twice the current terms");
+    iqcc_status st = batch_screen(b, theta, phi, out, false);
+    if (st) return st;
+    Carver cv{(char*)b->dev.p, 0};
+    const BatchDev d = carve_batch(cv, b->B);
+    const int64_t M = ctx->M;
+    if (M > 0) {
+        // every anticommuting term appends at most one partner
+        st = reserve_rows(ctx, 2 * M);
+        if (st) return st;
+        DevCounters* c = dctr(ctx);
+        CK(cudaMemsetAsync(c, 0, sizeof(DevCounters), ctx->stream));
+        CK(cudaEventRecord(ctx->ev0, ctx->stream));
+        launch_dress_seg(ctx->rows(), ctx->rows(), ctx->c(), M, d.gens, b->B, hash_view(ctx), c, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaEventRecord(ctx->ev1, ctx->stream));
+        st = read_counters(ctx);
+        if (st) return st;
+        const int64_t n_new = (int64_t)ctx->h_counters->n_new;
+        if (M + n_new > ctx->rows_alloc) return fail(ctx, IQCC_ERR_STATE, "internal: batch dress overran its rows");
+        ctx->M = M + n_new;
+        float ms = 0;
+        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        ctx->stats.n_dress++;
+        ctx->stats.dressed_terms += M;
+        ctx->stats.anticommuting += (int64_t)ctx->h_counters->n_anti;
+        ctx->stats.appended += n_new;
+        ctx->stats.dress_kernel_ms += ms;
+    }
+    if (eps > 0) {
+        CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+        int64_t removed = 0;
+        st = compress(ctx, eps, 0, &removed);
+        if (st) return st;
+    }
+    b->graph_M = -1;  // the Hamiltonians changed: capture again on the next screening
+    if (energy_after || n_terms_after) {
+        const int B = b->B;
+        std::vector<double> e(B);
+        std::vector<uint64_t> k(B), cnt(B);
+        std::vector<double> g(B), abc(3 * (size_t)B), tau(B);
+        std::vector<int64_t> nt(B);
+        iqcc_batch_screen_out o2{e.data(), k.data(), cnt.data(), g.data(), abc.data(), tau.data(), nt.data()};
+        st = batch_screen(b, theta, phi, &o2, false);
+        if (st) return st;
+        for (int p = 0; p < B; ++p) {
+            if (energy_after) energy_after[p] = e[p];
+            if (n_terms_after) n_terms_after[p] = nt[p];
+        }
+    }
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_batch_export(iqcc_batch* b, int problem, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z,
+                              double* coef) {
+    if (!b) return fail(nullptr, IQCC_ERR_ARG, "null batch");
+    iqcc_ctx* ctx = b->ctx;
+    GUARD(ctx);
+    if (!n || cap < 0 || problem < 0 || problem >= b->B) return fail(ctx, IQCC_ERR_ARG, "bad argument");
+    const int64_t M = ctx->M;
+    std::vector<uint64_t> ax((size_t)M), az((size_t)M);
+    std::vector<double> ac((size_t)M);
+    int64_t got = 0;
+    iqcc_status st = iqcc_export(ctx, M, &got, ax.data(), az.data(), ac.data());
+    if (st) return st;
+    int64_t k = 0;
+    for (int64_t i = 0; i < got; ++i) {
+        if ((int)(az[i] >> kBatchTagShift) != problem) continue;
+        if (k < cap) {
+            if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
+            x[k] = ax[i];
+            z[k] = az[i] & kBatchXMask;
+            coef[k] = ac[i];
+        }
+        ++k;
+    }
+    *n = k;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_batch_get_info(const iqcc_batch* b, iqcc_batch_info* out) {
+    if (!b || !out) return fail(nullptr, IQCC_ERR_ARG, "null argument");
+    out->n_terms = b->ctx->M;
+    out->screens = b->screens;
+    out->graph_replays = b->replays;
+    out->blocks_energy = b->blocks[0];
+    out->blocks_group = b->blocks[1];
+    out->blocks_abc = b->blocks[2];
+    out->pad = 0;
+    return IQCC_OK;
+}
+
+const char* iqcc_batch_last_error(const iqcc_batch* b) {
+    if (!b) return g_last_error.c_str();
+    return iqcc_last_error(b->ctx);
+}
+
+void iqcc_batch_free(iqcc_batch* b) {
+    if (!b) return;
+    if (b->gs) cudaStreamSynchronize(b->gs);
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    if (b->ctx) {
+        release(b->ctx, b->dev);
+        release(b->ctx, b->groups);
+        iqcc_free(b->ctx);
+    }
+    if (b->gs) cudaStreamDestroy(b->gs);
+    if (b->h_occ) cudaFreeHost(b->h_occ);
+    if (b->h_out) cudaFreeHost(b->h_out);
+    cudaGetLastError();
+    delete b;
+}
+
+}  // extern "C"

@@ -174,6 +174,11 @@ struct Gen {
     double cos_t, sin_t;
 };
 
+// Batches of independent Hamiltonians (one word per x and z): problem b's
+// strings carry b in z bits kBatchTagShift.. (Z letters on virtual qubits).
+constexpr int kBatchTagShift = 48;
+constexpr int kMaxBatch = 2048;
+
 // ----------------------------------------------------------------------------
 // Context
 // ----------------------------------------------------------------------------
@@ -260,6 +265,23 @@ void launch_expand_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t
 void launch_expand_emit(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkeys,
                         const double* tau, int k, uint64_t* out_rows, double* out_coef, unsigned long long* next,
                         int64_t cap, DevCounters* ctr, cudaStream_t s);
+
+// k_batch.cu: per-problem reductions of a batch (z-eigenstate references).
+// partials: [blocks][B] (energy), [blocks][3B] (A, B, C); counts[B] accumulate.
+void launch_seg_energy(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ, int B,
+                       double* partials, unsigned long long* counts, int blocks, cudaStream_t s);
+void launch_seg_dis_group(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ, int B,
+                          uint64_t* slots, double* gsum, uint64_t bucket_mask, int max_probe, DevCounters* ctr,
+                          int blocks, cudaStream_t s);
+void launch_seg_best(const uint64_t* slots, const double* gsum, uint64_t n_slots, int B,
+                     unsigned long long* best_coarse, unsigned long long* best_key, double* best_g, int blocks,
+                     cudaStream_t s);
+void launch_seg_abc(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ, int B,
+                    const unsigned long long* best_key, double* partials, int blocks, cudaStream_t s);
+void launch_seg_tau(const double* abc, const unsigned long long* best_key, int B, double* tau, Gen<1>* gens,
+                    cudaStream_t s);
+void launch_dress_seg(const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M, const Gen<1>* gens, int B,
+                      HashView h, DevCounters* ctr, cudaStream_t s);
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);

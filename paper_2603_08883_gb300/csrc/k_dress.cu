@@ -169,10 +169,9 @@ constexpr int kWarpTile = 64;  // rows classified per warp before the probes
 // appended key is the partner of exactly one row, q -> q xor P being a
 // bijection).  rows_app is the same buffer as rows;
 // appended rows land at M + slot and are not visited by this pass.
-template <int W>
-__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) k_dress(const uint64_t* __restrict__ rows,
-                                                                    uint64_t* rows_app, double* coef, int64_t M,
-                                                                    Gen<W> g, HashView h, DevCounters* ctr) {
+template <int W, class GenOf>
+__device__ __forceinline__ void dress_body(const uint64_t* __restrict__ rows, uint64_t* rows_app, double* coef,
+                                           int64_t M, const GenOf& gen_of, HashView h, DevCounters* ctr) {
     __shared__ uint32_t s_queue[kThreads / 32][kWarpTile];
     const unsigned FULL = 0xFFFFFFFFu;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -187,7 +186,10 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
         for (int r = 0; r < kWarpTile / 32; ++r) {
             const int64_t i = base + r * 32 + lane;
             bool a = false;
-            if (i < M) a = anticommutes<W>(load_key<W>(rows, i), g.p);
+            if (i < M) {
+                const Key<W> t = load_key<W>(rows, i);
+                a = anticommutes<W>(t, gen_of(t).p);
+            }
             const unsigned m = __ballot_sync(FULL, a);
             if (a) queue[nq + __popc(m & lt)] = (uint32_t)(r * 32 + lane);
             nq += __popc(m);
@@ -204,6 +206,7 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
                 const int64_t i = base + queue[e];
                 const double ct = coef[i];  // independent of the lookup: issued first
                 const Key<W> t = load_key<W>(rows, i);
+                const Gen<W>& g = gen_of(t);
                 q = key_xor<W>(t, g.p);
                 const double s = (double)product_sign<W>(t, g.yP, g.p, q);
                 const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
@@ -240,6 +243,46 @@ __global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) 
         __syncwarp();
     }
     if (lane == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
+}
+
+
+template <int W>
+struct FixedGen {
+    Gen<W> g;
+    __device__ __forceinline__ const Gen<W>& operator()(const Key<W>&) const { return g; }
+};
+
+template <int W>
+__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) k_dress(const uint64_t* __restrict__ rows,
+                                                                    uint64_t* rows_app, double* coef, int64_t M,
+                                                                    Gen<W> g, HashView h, DevCounters* ctr) {
+    dress_body<W>(rows, rows_app, coef, M, FixedGen<W>{g}, h, ctr);
+}
+
+// Generator of a row of a batch: its problem's (tag in z bits 48..63), from a
+// shared-memory table; the identity (nothing anticommutes) past the table.
+struct TagGen {
+    const Gen<1>* table;
+    int B;
+    Gen<1> none;
+    __device__ __forceinline__ const Gen<1>& operator()(const Key<1>& t) const {
+        const int b = (int)(t.z[0] >> kBatchTagShift);
+        return b < B ? table[b] : none;
+    }
+};
+
+// Per-problem dress of a batch (one 64-bit word per x and z): as k_dress, each
+// row with the generator of its problem.
+__global__ void __launch_bounds__(kThreads, IQCC_DRESS_MIN_BLOCKS) k_dress_seg(const uint64_t* __restrict__ rows,
+                                                                             uint64_t* rows_app, double* coef,
+                                                                             int64_t M, const Gen<1>* gens, int B,
+                                                                             HashView h, DevCounters* ctr) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Gen<1>* table = reinterpret_cast<Gen<1>*>(smem_raw);
+    for (int b = threadIdx.x; b < B; b += blockDim.x) table[b] = gens[b];
+    __syncthreads();
+    TagGen tg{table, B, Gen<1>{}};
+    dress_body<1>(rows, rows_app, coef, M, tg, h, ctr);
 }
 
 // Admission count: how many partners a dress would append (no writes to H).
@@ -343,6 +386,15 @@ void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef,
         case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
         default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
     }
+}
+
+void launch_dress_seg(const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M, const Gen<1>* gens, int B,
+                      HashView h, DevCounters* ctr, cudaStream_t s) {
+    if (M <= 0) return;
+    const size_t smem = (size_t)B * sizeof(Gen<1>);
+    cudaFuncSetAttribute(k_dress_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_dress_seg<<<grid_for(M, 8), kThreads, smem, s>>>(rows_in, rows, coef, M, gens, B, h, ctr);
+    note_launch();
 }
 
 void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,

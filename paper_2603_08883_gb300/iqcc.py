@@ -381,3 +381,134 @@ def iqcc_qmf_energy_noalloc(n_qubits: int, d_rows, d_coef, n_terms: int, theta, 
     if st != 0:
         raise IqccError(st, _err(None).decode())
     return e.value
+
+
+# ---------------------------------------------------------------- batches of Hamiltonians
+
+class iqcc_batch_screen_out(ctypes.Structure):
+    _fields_ = [("energy", _f64p), ("gx", _u64p), ("gz", _u64p), ("grad", _f64p), ("abc", _f64p), ("tau", _f64p),
+                ("n_terms", _i64p)]
+
+
+class iqcc_batch_info(ctypes.Structure):
+    _fields_ = [("n_terms", ctypes.c_int64), ("screens", ctypes.c_int64), ("graph_replays", ctypes.c_int64),
+                ("blocks_energy", ctypes.c_int), ("blocks_group", ctypes.c_int), ("blocks_abc", ctypes.c_int),
+                ("pad", ctypes.c_int)]
+
+
+_bload = _sig("iqcc_batch_load", _c, [ctypes.POINTER(_vp), ctypes.POINTER(iqcc_opts), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int), _i64p, _u64p, _u64p, _f64p])
+_bscreen = _sig("iqcc_batch_screen", _c, [_vp, _f64p, _f64p, ctypes.POINTER(iqcc_batch_screen_out)])
+_bstep = _sig("iqcc_batch_step", _c, [_vp, _f64p, _f64p, ctypes.c_double, ctypes.POINTER(iqcc_batch_screen_out),
+                                       _f64p, _i64p])
+_bexport = _sig("iqcc_batch_export", _c, [_vp, ctypes.c_int, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
+_binfo = _sig("iqcc_batch_get_info", _c, [_vp, ctypes.POINTER(iqcc_batch_info)])
+_berr = _sig("iqcc_batch_last_error", ctypes.c_char_p, [_vp])
+_bfree = _sig("iqcc_batch_free", None, [_vp])
+
+
+class Batch:
+    """Independent Hamiltonians of up to 48 qubits each, resident together (an ``iqcc_batch``)."""
+
+    def __init__(self, handle, n_qubits, keepalive):
+        self._h = handle
+        self.n = list(n_qubits)
+        self.B = len(self.n)
+        self._keepalive = keepalive
+
+    def _check(self, st):
+        if st != 0:
+            raise IqccError(st, _berr(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _bfree(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _angles(self, theta, phi):
+        t = np.concatenate([np.asarray(a, np.float64).reshape(-1) for a in theta])
+        p = np.concatenate([np.asarray(a, np.float64).reshape(-1) for a in phi])
+        if len(t) != sum(self.n) or len(p) != sum(self.n):
+            raise ValueError("one angle per qubit of every problem")
+        return _f64(t), _f64(p)
+
+
+def _screen_out(B):
+    arrs = {"energy": np.zeros(B), "gx": np.zeros(B, np.uint64), "gz": np.zeros(B, np.uint64),
+            "grad": np.zeros(B), "abc": np.zeros((B, 3)), "tau": np.zeros(B), "n_terms": np.zeros(B, np.int64)}
+    s = iqcc_batch_screen_out(arrs["energy"].ctypes.data_as(_f64p), arrs["gx"].ctypes.data_as(_u64p),
+                              arrs["gz"].ctypes.data_as(_u64p), arrs["grad"].ctypes.data_as(_f64p),
+                              arrs["abc"].ctypes.data_as(_f64p), arrs["tau"].ctypes.data_as(_f64p),
+                              arrs["n_terms"].ctypes.data_as(_i64p))
+    return arrs, s
+
+
+def iqcc_batch_load(problems, capacity: int = 0, max_probe: int = 0, use_torch: bool = True,
+                    device=None) -> Batch:
+    """``problems``: a list of (n_qubits, x, z, coef) with one word per string."""
+    n = [int(p[0]) for p in problems]
+    xs = [np.asarray(p[1], np.uint64).reshape(-1) for p in problems]
+    zs = [np.asarray(p[2], np.uint64).reshape(-1) for p in problems]
+    cs = [np.asarray(p[3], np.float64).reshape(-1) for p in problems]
+    offsets = np.zeros(len(problems) + 1, np.int64)
+    offsets[1:] = np.cumsum([len(c) for c in cs])
+    xa, xp = _u64(np.concatenate(xs) if xs else np.zeros(0, np.uint64))
+    za, zp = _u64(np.concatenate(zs) if zs else np.zeros(0, np.uint64))
+    ca, cp = _f64(np.concatenate(cs) if cs else np.zeros(0))
+    na = (ctypes.c_int * len(n))(*n)
+    stream, alloc, free = _torch_hooks(device, False) if use_torch else (None, None, None)
+    opts = iqcc_opts(64, capacity, max_probe, stream, alloc or ALLOC_FN(), free or FREE_FN(), None)
+    h = _vp()
+    st = _bload(ctypes.byref(h), ctypes.byref(opts), len(n), na, offsets.ctypes.data_as(_i64p), xp, zp, cp)
+    if st != 0:
+        raise IqccError(st, _err(None).decode())
+    return Batch(h, n, (alloc, free))
+
+
+def iqcc_batch_screen(batch: Batch, theta, phi) -> dict:
+    """Per problem: energy, best DIS candidate (gx, gz), its gradient, A, B, C, tau*, term count."""
+    (ta, tp), (pa, pp) = batch._angles(theta, phi)
+    arrs, s = _screen_out(batch.B)
+    batch._check(_bscreen(batch._h, tp, pp, ctypes.byref(s)))
+    return arrs
+
+
+def iqcc_batch_step(batch: Batch, theta, phi, eps: float = 0.0):
+    """Screen, dress every problem with its best candidate at tau*, prune eps:
+    (screening dict, energies after, term counts after)."""
+    (ta, tp), (pa, pp) = batch._angles(theta, phi)
+    arrs, s = _screen_out(batch.B)
+    ea = np.zeros(batch.B)
+    na = np.zeros(batch.B, np.int64)
+    batch._check(_bstep(batch._h, tp, pp, float(eps), ctypes.byref(s), ea.ctypes.data_as(_f64p),
+                        na.ctypes.data_as(_i64p)))
+    return arrs, ea, na
+
+
+def iqcc_batch_export(batch: Batch, problem: int):
+    n = ctypes.c_int64(0)
+    batch._check(_bexport(batch._h, int(problem), 0, ctypes.byref(n), None, None, None))
+    k = n.value
+    x = np.zeros(k, np.uint64)
+    z = np.zeros(k, np.uint64)
+    c = np.zeros(k)
+    batch._check(_bexport(batch._h, int(problem), k, ctypes.byref(n), x.ctypes.data_as(_u64p),
+                          z.ctypes.data_as(_u64p), c.ctypes.data_as(_f64p)))
+    return x.reshape(-1, 1), z.reshape(-1, 1), c
+
+
+def iqcc_batch_get_info(batch: Batch) -> dict:
+    s = iqcc_batch_info()
+    batch._check(_binfo(batch._h, ctypes.byref(s)))
+    return {name: getattr(s, name) for name, _ in iqcc_batch_info._fields_ if name != "pad"}
+
+
+def iqcc_batch_last_error(batch: Batch | None = None) -> str:
+    return _berr(batch._h if batch is not None else None).decode()
+
+
+def iqcc_batch_free(batch: Batch) -> None:
+    batch.close()

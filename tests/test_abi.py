@@ -79,7 +79,8 @@ def test_ctypes_structs_match_the_header(tmp_path):
     import subprocess
     from paper_2603_08883_gb300 import iqcc
     structs = {"iqcc_opts": iqcc.iqcc_opts, "iqcc_iter_opts": iqcc.iqcc_iter_opts,
-               "iqcc_iter_result": iqcc.iqcc_iter_result, "iqcc_stats": iqcc.iqcc_stats}
+               "iqcc_iter_result": iqcc.iqcc_iter_result, "iqcc_stats": iqcc.iqcc_stats,
+               "iqcc_batch_screen_out": iqcc.iqcc_batch_screen_out, "iqcc_batch_info": iqcc.iqcc_batch_info}
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{ROOT}/include/iqcc.h"', "int main(void) {"]
     for name, cls in structs.items():
         lines.append(f'printf("{name} size %zu\\n", sizeof({name}));')
