@@ -192,6 +192,50 @@ def measure_sort_variant(iqcc, n, x, z, c, th, ph, stream, n_gen=8, tau=0.1):
     return out
 
 
+def measure_batch(iqcc, synth, n_problems=64, seed=1000, eps=1e-10, screens=20):
+    """Many small Jordan-Wigner Hamiltonians (12..40 qubits, even, decay
+    integrals, basis reference): one batched step against one single-problem
+    iteration per problem, and repeated screening by graph replay."""
+    import torch
+    rng = np.random.Generator(np.random.PCG64(seed))
+    probs, angles = [], []
+    for b in range(n_problems):
+        norb = int(rng.integers(6, 21))
+        h, eri = synth.integrals("decay", norb, seed + b)
+        n, x, z, c = synth.jordan_wigner(h, eri)
+        probs.append((n, x.reshape(-1), z.reshape(-1), c))
+        angles.append(synth.qmf_angles(n, "basis"))
+    th = [a[0] for a in angles]
+    ph = [a[1] for a in angles]
+    out = {"problems": n_problems, "qubits": [int(p[0]) for p in probs], "terms": int(sum(len(p[3]) for p in probs)),
+           "workload": "Jordan-Wigner of seeded decay integrals, 6-20 orbitals each, Hartree-Fock basis reference, "
+                       "one generator per problem, eps 1e-10"}
+    torch.cuda.synchronize()
+    batch = iqcc.iqcc_batch_load(probs)
+    iqcc.iqcc_batch_screen(batch, th, ph)  # tuning and capture
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(screens):
+        iqcc.iqcc_batch_screen(batch, th, ph)
+    out["screen_replay_ms"] = round((time.perf_counter() - t0) / screens * 1e3, 3)
+    t0 = time.perf_counter()
+    iqcc.iqcc_batch_step(batch, th, ph, eps)
+    out["batched_step_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+    info = iqcc.iqcc_batch_get_info(batch)
+    out["tuned_blocks"] = [info["blocks_energy"], info["blocks_group"], info["blocks_abc"]]
+    batch.close()
+    ctxs = [iqcc.iqcc_load_hamiltonian(p[0], p[1].reshape(-1, 1), p[2].reshape(-1, 1), p[3]) for p in probs]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for H, t, p in zip(ctxs, th, ph):
+        iqcc.iqcc_iterate(H, t, p, 1, eps, 0)
+    torch.cuda.synchronize()
+    out["one_context_per_problem_ms"] = round((time.perf_counter() - t0) * 1e3, 2)
+    for H in ctxs:
+        H.close()
+    return out
+
+
 def profile_traffic(avg_rows):
     """DRAM bytes per dressed term of the dress kernel from the committed ncu
     summary (profiles/dress_kernel_jw100.md, line 'dram_bytes_per_dressed_term:'),
@@ -353,8 +397,10 @@ def run_gpu(args):
                        "pinned host arrays (the next step's input); wall clock"}
     else:
         H.close()
+    batch_variant = None
     if rank == 0:  # after the capped Hamiltonian is released
         sort_variant = measure_sort_variant(iqcc, n, x, z, c, th, ph, stream)
+        batch_variant = measure_batch(iqcc, synth)
 
     if rank != 0:
         if dist is not None:
@@ -378,7 +424,7 @@ def run_gpu(args):
                 "bytes_per_launch": stats["dress_bytes"] / n_dress, "launches": stats["n_dress"],
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
-                "adjoint_pass": adjoint, "sort_variant": sort_variant}
+                "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant}
 
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None
