@@ -140,6 +140,26 @@ def measured_peak():
         return 6800.0, "fallback"
 
 
+def workload_for_rank(w, rank: int):
+    """Replicas: rank r runs the workload with seed + 1000 r (an independent
+    Hamiltonian of the same recipe and size)."""
+    import dataclasses
+    return dataclasses.replace(w, seed=w.seed + 1000 * rank) if rank else w
+
+
+def reduce_over_ranks(dist, seconds: float, units: float, device):
+    """(max over ranks of the timed seconds, sum over ranks of the units):
+    whole-job throughput = units / seconds."""
+    if dist is None:
+        return seconds, units
+    import torch
+    tt = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    uu = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(uu, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(uu.item())
+
+
 def measure_adjoint(iqcc, H, n, th, ph, stream):
     """iqcc_energy_gradients on H as it stands (CUDA events around the call),
     at the workload's angles and at random general angles, with the top DIS
@@ -294,11 +314,10 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_2603_08883_gb300 import iqcc, synth
-    import dataclasses
 
     w = synth.WORKLOADS[args.workload]
     if world > 1:
-        w = dataclasses.replace(w, seed=w.seed + 1000 * rank)
+        w = workload_for_rank(w, rank)
     n, x, z, c = synth.workload_hamiltonian(w)
     th, ph = synth.workload_angles(w)
     M0 = len(c)
@@ -341,15 +360,7 @@ def run_gpu(args):
     log(f"timed: {args.steps} iterations in {dev_s:.3f} s; M {[r['M'] for r in recs]}")
     stats = iqcc.iqcc_get_stats(H)
     dressed = sum(r["dressed_terms"] for r in recs)
-    t_max = dev_s
-    total_dressed = dressed
-    if dist is not None:
-        tt = torch.tensor([dev_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max = float(tt.item())
-        dd = torch.tensor([dressed], dtype=torch.float64, device="cuda")
-        dist.all_reduce(dd, op=dist.ReduceOp.SUM)
-        total_dressed = float(dd.item())
+    t_max, total_dressed = reduce_over_ranks(dist, dev_s, dressed, "cuda")
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
     adjoint = sort_variant = None
