@@ -186,6 +186,36 @@ def measure_adjoint(iqcc, H, n, th, ph, stream):
     return out
 
 
+def measure_screening(iqcc, H, th, ph):
+    """The learned-screening perceptron (tensor cores, mma.sync BF16 / FP32)
+    scoring every term of H as it stands: 2 (8 x 256 + 256 x 256 + 256) =
+    135,680 algorithmic FLOP per term; device time from the library's events."""
+    from paper_2603_08883_gb300.screening import load_model
+    M = len(H)
+    iqcc.iqcc_set_screening_model(H, *load_model())
+    gx, gz, _ = iqcc.iqcc_dis_gradients(H, th, ph, cap=4)
+    iqcc.iqcc_prune_learned(H, 0.0, M, th, ph, gx, gz)      # warm-up; a limit of M removes nothing
+    before = iqcc.iqcc_get_stats(H)
+    iqcc.iqcc_prune_learned(H, 0.0, M, th, ph, gx, gz)
+    after = iqcc.iqcc_get_stats(H)
+    ms = after["screen_ms"] - before["screen_ms"]
+    terms = after["screen_terms"] - before["screen_terms"]
+    flop = 135680.0 * terms
+    peak = measured_peak_tensor()
+    tf = flop / (ms / 1e3) / 1e12
+    return {"kernel": "k_mlp_score (features + 8-256-256-1 perceptron, mma.sync m16n8k16 bf16)", "terms": terms,
+            "ms": round(ms, 2), "achieved_tflops": round(tf, 1), "peak_tflops": peak[0], "peak_kind": peak[1],
+            "frac": round(tf / peak[0], 4) if peak[0] else None}
+
+
+def measured_peak_tensor():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured burst bf16 (MEASURED_PEAKS.json bf16_tflops)"
+    except (OSError, KeyError, ValueError):
+        return 1900.0, "fallback 1.9 PFLOP/s bf16"
+
+
 def measure_sort_variant(iqcc, n, x, z, c, th, ph, stream, n_gen=8, tau=0.1):
     """The hash dress against the sort-based dress (one sort per generator, and
     all generators fused into one expansion and one sort) on the loaded
@@ -363,9 +393,10 @@ def run_gpu(args):
     t_max, total_dressed = reduce_over_ranks(dist, dev_s, dressed, "cuda")
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
-    adjoint = sort_variant = None
+    adjoint = sort_variant = screening = None
     if rank == 0:
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
+        screening = measure_screening(iqcc, H, th, ph)
 
     # ---------------- end to end through host buffers (pinned), N = 1 path of a user
     e2e = None
@@ -435,7 +466,8 @@ def run_gpu(args):
                 "bytes_per_launch": stats["dress_bytes"] / n_dress, "launches": stats["n_dress"],
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
-                "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant}
+                "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant,
+                "learned_screening": screening}
 
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None

@@ -193,6 +193,8 @@ typedef struct {
     const uint64_t* forced_x;  /* host [n_forced][W] */
     const uint64_t* forced_z;  /* host [n_forced][W] */
     const double* forced_tau;  /* host [n_forced] or NULL: amplitudes to use */
+    int screening;             /* term limit: 0 keeps the largest |C|, 1 the best learned scores
+                                  (iqcc_prune_learned with the iteration's generators) */
 } iqcc_iter_opts;
 
 typedef struct {
@@ -254,6 +256,8 @@ typedef struct {
     int64_t kernel_launches;   /* kernels launched by the library (all contexts) since the reset */
     int64_t n_sorted_groups;   /* generator groups applied by iqcc_dress_sorted */
     double sorted_dress_ms;    /* device time of those groups (expansion, sort, merge; index rebuild excluded) */
+    int64_t screen_terms;      /* terms scored by the learned screening perceptron */
+    double screen_ms;          /* device time of that scoring (CUDA events) */
     int words;                 /* device words per x or z vector (1, 2 or 4) */
     int pad;
 } iqcc_stats;
@@ -293,6 +297,49 @@ const char* iqcc_last_error(const iqcc_ctx* ctx);
 
 /* Release the context and all its device memory (NULL is allowed). */
 void iqcc_free(iqcc_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Learned term screening (no counterpart in the paper, which limits terms by
+ * magnitude).  A perceptron (8 features -> 256 -> 256 -> 1, ReLU, BF16
+ * weights and activations with FP32 accumulation on the tensor cores) scores
+ * every term from its key and coefficient; the term limit can keep the best
+ * scores instead of the largest |C|.  Features of a term T (G = union of the
+ * supports of the given generators, <T> at the Eq. 3 reference): log10|C|/8,
+ * flipped qubits/16, Y letters/16, Z letters/32, |supp T & G|/8,
+ * |flips of T & G|/8, <T>, and 1 when every flip of T lies in G.  The training
+ * target is log10 |C_T E_fut(T)| (iqcc_future_energies): by linearity of the
+ * dress, removing T changes the energy after the following generators by
+ * exactly -C_T E_fut(T).
+ * ------------------------------------------------------------------------ */
+
+/* Weights (host float, row-major): w1 [256][8], b1 [256], w2 [256][256] (row =
+ * output unit), b2 [256], w3 [256], b3.  Copied (as BF16 for w1, w2) into the
+ * context.  Errors: IQCC_ERR_ARG, IQCC_ERR_OOM, IQCC_ERR_CUDA. */
+iqcc_status iqcc_set_screening_model(iqcc_ctx* ctx, const float* w1, const float* b1, const float* w2,
+                                     const float* b2, const float* w3, float b3);
+
+/* Features of every term, in the order of iqcc_export: out host float
+ * [n_terms][8].  gx, gz: host [n_gen][W] (n_gen <= 64; they define G);
+ * theta/phi: host [n_qubits]. */
+iqcc_status iqcc_term_features(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
+                               const double* theta, const double* phi, float* out);
+
+/* E_fut(T) = <Omega| D_k ... D_1 (T) |Omega> of every term T (in the order of
+ * iqcc_export): the energy of the single string after the n_gen (<= 8)
+ * generators at amplitudes tau (host), expanded along every path as in
+ * iqcc_dress_sorted.  out: host double [n_terms]. */
+iqcc_status iqcc_future_energies(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
+                                 const double* tau, const double* theta, const double* phi, double* out);
+
+/* The model's score of every term (in the order of iqcc_export): out host
+ * float [n_terms].  Errors: IQCC_ERR_ARG without a model. */
+iqcc_status iqcc_term_scores(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
+                             const double* theta, const double* phi, float* out);
+
+/* iqcc_prune with the term limit on the model's scores (ties of equal scores
+ * in ascending canonical key order); eps still applies to |C|. */
+iqcc_status iqcc_prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_gen, const uint64_t* gx,
+                               const uint64_t* gz, const double* theta, const double* phi, int64_t* n_removed);
 
 /* ------------------------------------------------------------------------
  * Batches of independent Hamiltonians (many small problems screened and

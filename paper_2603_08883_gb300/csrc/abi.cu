@@ -376,7 +376,9 @@ size_t sort_area_bytes(int64_t n) {
     return dry.off;
 }
 
-iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed) {
+// rank (device [M], may be NULL): the term limit keeps the largest |rank|
+// instead of the largest |C| (the magnitude threshold eps always uses |C|).
+iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed, const double* rank = nullptr) {
     const int64_t M = ctx->M;
     *removed = 0;
     if (M == 0) return IQCC_OK;
@@ -423,7 +425,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
                 hist12 = (unsigned long long*)ctx->aux.p;
             }
             CK(cudaMemsetAsync(hist12, 0, 4096 * sizeof(unsigned long long), ctx->stream));
-            launch_abs_digit_hist12(ctx->c(), flags, M, shift, prefix, pmask, hist12, ctx->stream);
+            launch_abs_digit_hist12(rank ? rank : ctx->c(), flags, M, shift, prefix, pmask, hist12, ctx->stream);
             CK_LAUNCH();
             CK(cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
                                ctx->stream));
@@ -442,7 +444,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
         }
         pmask &= 0x7FFFFFFFFFFFFFFFull;
         CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-        launch_bucket_flags(ctx->c(), flags, M, prefix, pmask, ties, &c->aux, ctx->stream);
+        launch_bucket_flags(rank ? rank : ctx->c(), flags, M, prefix, pmask, ties, &c->aux, ctx->stream);
         CK_LAUNCH();
         st = read_counters(ctx);
         if (st) return st;
@@ -460,7 +462,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
             uint64_t* skeys = cv2.take<uint64_t>((size_t)n_cand * stride);
             SortArea ca = carve_sort(cv2, n_cand);
             if (cv2.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-            launch_candidate_keys(ctx->Wd, ctx->rows(), ctx->c(), ties, n_cand, skeys, ctx->stream);
+            launch_candidate_keys(ctx->Wd, ctx->rows(), rank ? rank : ctx->c(), ties, n_cand, skeys, ctx->stream);
             launch_iota(ca.a, n_cand, ctx->stream);
             SortPlan plan{};
             plan.n_words = stride;
@@ -694,6 +696,58 @@ iqcc_status gradients_given(iqcc_ctx* ctx, const double* theta, const double* ph
         CK(cudaStreamSynchronize(ctx->stream));
     }
     return IQCC_OK;
+}
+
+// Union of the supports of n_gen generators (host words, W each) in device layout.
+void generator_support(const iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, uint64_t* sup) {
+    for (int w = 0; w < 4; ++w) sup[w] = 0;
+    for (int k = 0; k < n_gen; ++k)
+        for (int w = 0; w < ctx->W; ++w) sup[w] |= gx[(size_t)k * ctx->W + w] | gz[(size_t)k * ctx->W + w];
+}
+
+// Per-qubit <sigma> (the energy-gradient table) for host angles, into scratch
+// region `angles` (2n) and `tab`; returns the table's stride.
+int upload_ev(iqcc_ctx* ctx, const double* theta, const double* phi, double* angles, double* tab) {
+    cudaMemcpyAsync(angles, theta, sizeof(double) * ctx->n, cudaMemcpyHostToDevice, ctx->stream);
+    cudaMemcpyAsync(angles + ctx->n, phi, sizeof(double) * ctx->n, cudaMemcpyHostToDevice, ctx->stream);
+    launch_grad_tables(angles, angles + ctx->n, ctx->n, tab, ctx->stream);
+    return energy_grad_table_doubles(1);
+}
+
+// Learned-screening scores of every row into `rank` (device [M]); score: optional float [M].
+iqcc_status screen_scores(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* theta,
+                          const double* phi, double* rank, float* score, double* angles, double* tab) {
+    if (!ctx->model.p) return fail(ctx, IQCC_ERR_ARG, "no screening model set");
+    uint64_t sup[4];
+    generator_support(ctx, n_gen, gx, gz, sup);
+    const int ts = upload_ev(ctx, theta, phi, angles, tab);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    launch_mlp_score(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, sup, tab, ts, ctx->n, ctx->model.p, score, rank,
+                     ctx->stream);
+    CK_LAUNCH();
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.screen_ms += ms;
+    ctx->stats.screen_terms += ctx->M;
+    return IQCC_OK;
+}
+
+iqcc_status prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_gen, const uint64_t* gx,
+                          const uint64_t* gz, const double* theta, const double* phi, int64_t* removed) {
+    *removed = 0;
+    if (ctx->M == 0) return IQCC_OK;
+    Buf& r = ctx->screen_rank;
+    if (!ensure(ctx, r, (size_t)ctx->M * 8 + 2 * ctx->n * 8 + (size_t)energy_grad_table_doubles(ctx->n) * 8 + 1024))
+        return fail(ctx, IQCC_ERR_OOM, "rank allocation failed");
+    double* rank = (double*)r.p;
+    double* angles = rank + ctx->M + 16;
+    double* tab = angles + 2 * ctx->n + 16;
+    iqcc_status st = screen_scores(ctx, n_gen, gx, gz, theta, phi, rank, nullptr, angles, tab);
+    if (st) return st;
+    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    return compress(ctx, eps, max_terms, removed, rank);
 }
 
 }  // namespace
@@ -1062,6 +1116,8 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     const int n_gen = o->n_forced > 0 ? o->n_forced : o->n_gen;
     if (n_gen < 0 || n_gen > 64) return fail(ctx, IQCC_ERR_ARG, "n_gen must be in 0..64");
     if (o->n_forced > 0 && (!o->forced_x || !o->forced_z)) return fail(ctx, IQCC_ERR_ARG, "null forced generators");
+    if (o->screening != 0 && o->screening != 1) return fail(ctx, IQCC_ERR_ARG, "screening must be 0 or 1");
+    if (o->screening == 1 && !ctx->model.p) return fail(ctx, IQCC_ERR_ARG, "no screening model set");
     std::memset(out, 0, sizeof *out);
     out->n_terms_before = ctx->M;
     out->n_terms_peak = ctx->M;
@@ -1108,13 +1164,16 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         out->n_terms_peak = std::max(out->n_terms_peak, ctx->M);
         if (o->max_terms > 0 && ctx->M > o->max_terms) {
             int64_t cut = 0;
-            st = iqcc_prune(ctx, 0.0, o->max_terms, &cut);
+            st = o->screening == 1 ? prune_learned(ctx, 0.0, o->max_terms, used, gx.data(), gz.data(), theta, phi, &cut)
+                                   : iqcc_prune(ctx, 0.0, o->max_terms, &cut);
             if (st) return st;
             out->n_removed += cut;
         }
     }
     int64_t removed = 0;
-    iqcc_status st = iqcc_prune(ctx, o->eps, o->max_terms, &removed);
+    iqcc_status st = o->screening == 1
+                         ? prune_learned(ctx, o->eps, o->max_terms, used, gx.data(), gz.data(), theta, phi, &removed)
+                         : iqcc_prune(ctx, o->eps, o->max_terms, &removed);
     if (st) return st;
     out->n_removed += removed;
     out->n_terms = ctx->M;
@@ -1164,6 +1223,137 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     return IQCC_OK;
 }
 
+iqcc_status iqcc_set_screening_model(iqcc_ctx* ctx, const float* w1, const float* b1, const float* w2,
+                                     const float* b2, const float* w3, float b3) {
+    GUARD(ctx);
+    if (!w1 || !b1 || !w2 || !b2 || !w3) return fail(ctx, IQCC_ERR_ARG, "null weight array");
+    std::vector<unsigned char> h(screen_model_bytes());
+    pack_screen_model(w1, b1, w2, b2, w3, b3, h.data());
+    if (!ensure(ctx, ctx->model, h.size())) return fail(ctx, IQCC_ERR_OOM, "model allocation failed");
+    CK(cudaMemcpyAsync(ctx->model.p, h.data(), h.size(), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// Canonical (export) order of the rows into perm (device [M]) through the sort area.
+iqcc_status canonical_order(iqcc_ctx* ctx, const SortArea& sa, uint32_t** perm) {
+    launch_iota(sa.a, ctx->M, ctx->stream);
+    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, ctx->M, perm, sa.tmp,
+                        sa.tmp_bytes, ctx->stream);
+    CK_LAUNCH();
+    return IQCC_OK;
+}
+
+// One per-row quantity of the screening family, in export order, to the host:
+// kind 0 features (float [M][8]), 1 future energies (double [M]), 2 scores (float [M]).
+iqcc_status per_row_export(iqcc_ctx* ctx, int kind, int n_gen, const uint64_t* gx, const uint64_t* gz,
+                           const double* tau, const double* theta, const double* phi, void* out) {
+    const int64_t M = ctx->M;
+    if (M == 0) return IQCC_OK;
+    const int n = ctx->n;
+    const size_t width = kind == 0 ? (size_t)screen_features() * 4 : (kind == 1 ? 8 : 4);
+    Carver cv;
+    cv.off += sort_area_bytes(M);
+    cv.take<char>((size_t)M * width);
+    cv.take<char>((size_t)M * width);
+    cv.take<double>(M);
+    cv.take<double>(2 * (size_t)n);
+    cv.take<double>(energy_grad_table_doubles(n));
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    SortArea sa = carve_sort(cv, M);
+    char* vals = cv.take<char>((size_t)M * width);
+    char* sorted_vals = cv.take<char>((size_t)M * width);
+    double* rank = cv.take<double>(M);
+    double* angles = cv.take<double>(2 * (size_t)n);
+    double* tab = cv.take<double>(energy_grad_table_doubles(n));
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+    uint64_t sup[4];
+    generator_support(ctx, n_gen, gx, gz, sup);
+    if (kind == 0) {
+        const int ts = upload_ev(ctx, theta, phi, angles, tab);
+        launch_term_features(ctx->Wd, ctx->rows(), ctx->c(), M, sup, tab, ts, n, (float*)vals, ctx->stream);
+    } else if (kind == 1) {
+        const int ts = upload_ev(ctx, theta, phi, angles, tab);
+        std::vector<uint64_t> pk((size_t)std::max(n_gen, 1) * 2 * ctx->Wd);
+        for (int j = 0; j < n_gen; ++j)
+            pad_key(ctx, gx + (size_t)j * ctx->W, gz + (size_t)j * ctx->W, pk.data() + (size_t)j * 2 * ctx->Wd);
+        launch_future_energy(ctx->Wd, ctx->rows(), M, pk.data(), tau, n_gen, tab, ts, n, (double*)vals, ctx->stream);
+    } else {
+        iqcc_status st = screen_scores(ctx, n_gen, gx, gz, theta, phi, rank, (float*)vals, angles, tab);
+        if (st) return st;
+    }
+    CK_LAUNCH();
+    uint32_t* perm = nullptr;
+    iqcc_status st = canonical_order(ctx, sa, &perm);
+    if (st) return st;
+    launch_gather_bytes(vals, perm, M, (int)width, sorted_vals, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(out, sorted_vals, (size_t)M * width, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
+iqcc_status check_gens(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, int max_gen) {
+    if (n_gen < 0 || n_gen > max_gen) return fail(ctx, IQCC_ERR_ARG, "generator count out of range");
+    if (n_gen > 0 && (!gx || !gz)) return fail(ctx, IQCC_ERR_ARG, "null generator array");
+    for (int k = 0; k < n_gen; ++k)
+        if (bits_above_n(ctx, gx + (size_t)k * ctx->W) || bits_above_n(ctx, gz + (size_t)k * ctx->W))
+            return fail(ctx, IQCC_ERR_ARG, "generator bits set above n_qubits");
+    return IQCC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+iqcc_status iqcc_term_features(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* theta,
+                               const double* phi, float* out) {
+    GUARD(ctx);
+    if (!theta || !phi || (ctx->M > 0 && !out)) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    iqcc_status st = check_gens(ctx, n_gen, gx, gz, 64);
+    if (st) return st;
+    return per_row_export(ctx, 0, n_gen, gx, gz, nullptr, theta, phi, out);
+}
+
+iqcc_status iqcc_future_energies(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* tau,
+                                 const double* theta, const double* phi, double* out) {
+    GUARD(ctx);
+    if (!theta || !phi || (n_gen > 0 && !tau) || (ctx->M > 0 && !out)) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    iqcc_status st = check_gens(ctx, n_gen, gx, gz, max_fuse());
+    if (st) return st;
+    for (int k = 0; k < n_gen; ++k)
+        if (!std::isfinite(tau[k])) return fail(ctx, IQCC_ERR_ARG, "non-finite amplitude");
+    return per_row_export(ctx, 1, n_gen, gx, gz, tau, theta, phi, out);
+}
+
+iqcc_status iqcc_term_scores(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* theta,
+                             const double* phi, float* out) {
+    GUARD(ctx);
+    if (!theta || !phi || (ctx->M > 0 && !out)) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    iqcc_status st = check_gens(ctx, n_gen, gx, gz, 64);
+    if (st) return st;
+    return per_row_export(ctx, 2, n_gen, gx, gz, nullptr, theta, phi, out);
+}
+
+iqcc_status iqcc_prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_gen, const uint64_t* gx,
+                               const uint64_t* gz, const double* theta, const double* phi, int64_t* n_removed) {
+    if (n_removed) *n_removed = 0;
+    GUARD(ctx);
+    if (std::isnan(eps) || !theta || !phi) return fail(ctx, IQCC_ERR_ARG, "bad argument");
+    iqcc_status st = check_gens(ctx, n_gen, gx, gz, 64);
+    if (st) return st;
+    int64_t removed = 0;
+    st = prune_learned(ctx, eps, max_terms, n_gen, gx, gz, theta, phi, &removed);
+    if (st) return st;
+    if (n_removed) *n_removed = removed;
+    return IQCC_OK;
+}
+
 iqcc_status iqcc_get_stats(const iqcc_ctx* ctx, iqcc_stats* out) {
     if (!ctx || !out) return fail(nullptr, IQCC_ERR_ARG, "null argument");
     *out = ctx->stats;
@@ -1196,6 +1386,8 @@ void iqcc_free(iqcc_ctx* ctx) {
     release(ctx, ctx->counters);
     release(ctx, ctx->scratch);
     release(ctx, ctx->aux);
+    release(ctx, ctx->model);
+    release(ctx, ctx->screen_rank);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -216,6 +216,8 @@ struct iqcc_ctx {
     bool broken = false;
     std::string err;
     iqcc_stats stats{};
+    iqcc::Buf model;               // learned screening weights (device layout), when set
+    iqcc::Buf screen_rank;         // learned screening: per-row keys and the <sigma> table
 
     uint64_t* rows() const { return (uint64_t*)keys.p; }
     double* c() const { return (double*)coef.p; }
@@ -282,6 +284,24 @@ void launch_seg_tau(const double* abc, const unsigned long long* best_key, int B
                     cudaStream_t s);
 void launch_dress_seg(const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M, const Gen<1>* gens, int B,
                       HashView h, DevCounters* ctr, cudaStream_t s);
+
+// k_screen.cu: learned term screening (features, perceptron scores).  gsup:
+// union of the generators' supports (Wd words); ev: per-qubit <sigma> at
+// stride ts (the energy-gradient table).  model: screen_model_bytes() on the device.
+int screen_features();
+// out[i] = in[perm[i]] for rows of `width` bytes (a multiple of 4)
+void launch_gather_bytes(const void* in, const uint32_t* perm, int64_t n, int width, void* out, cudaStream_t s);
+size_t screen_model_bytes();
+void pack_screen_model(const float* w1, const float* b1, const float* w2, const float* b2, const float* w3, float b3,
+                       unsigned char* out);
+void launch_term_features(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* gsup,
+                          const double* ev, int ts, int n, float* out, cudaStream_t s);
+void launch_mlp_score(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* gsup,
+                      const double* ev, int ts, int n, const void* model, float* score, double* rank,
+                      cudaStream_t s);
+// k_sortdress.cu: energy of every row after k <= max_fuse() generators (tab: <sigma> at stride ts)
+void launch_future_energy(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkeys, const double* tau, int k,
+                          const double* tab, int ts, int n, double* out, cudaStream_t s);
 
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);

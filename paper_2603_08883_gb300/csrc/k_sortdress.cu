@@ -112,6 +112,43 @@ __global__ void __launch_bounds__(kThreads) k_expand_emit(const uint64_t* __rest
     }
 }
 
+// E_fut(T) = <Omega| D_k ... D_1 (T) |Omega>: the energy of the single string T
+// after the group's generators (Eq. 5, Eq. 12), summed over T's paths (each
+// leaf's factor times its expectation, a product of per-qubit <sigma> from
+// tab[ts k + letter], letter 1..3 = X, Y, Z).  By linearity of the dress, deleting T from H now changes
+// the energy after those generators by exactly -C_T E_fut(T).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_future_energy(const uint64_t* __restrict__ rows, int64_t M, GenGroup<W> g,
+                                                            const double* __restrict__ tab_g, int ts, int n,
+                                                            double* out) {
+    extern __shared__ double tab[];
+    for (int i = threadIdx.x; i < ts * n; i += blockDim.x) tab[i] = tab_g[i];
+    __syncthreads();
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += s) {
+        const Key<W> t = load_key<W>(rows, i);
+        double e = 0.0;
+        for (unsigned mask = 0; mask < (1u << g.k); ++mask) {
+            Key<W> leaf;
+            double f;
+            if (!follow<W>(g, t, mask, &leaf, &f)) continue;
+            double v = f;
+#pragma unroll
+            for (int wd = 0; wd < W && v != 0.0; ++wd) {
+                uint64_t m = leaf.x[wd] | leaf.z[wd];
+                while (m && v != 0.0) {
+                    const int j = __ffsll((long long)m) - 1;
+                    m &= m - 1;
+                    const int xb = (int)((leaf.x[wd] >> j) & 1ull), zb = (int)((leaf.z[wd] >> j) & 1ull);
+                    v *= tab[ts * (64 * wd + j) + (xb ? (zb ? 2 : 1) : 3)];
+                }
+            }
+            e += v;
+        }
+        out[i] = e;
+    }
+}
+
 template <int W>
 GenGroup<W> make_group(const uint64_t* pkeys, const double* tau, int k) {
     GenGroup<W> g{};
@@ -140,6 +177,19 @@ int expand_grid(int64_t M) {
 }  // namespace
 
 int max_fuse() { return kMaxFuse; }
+
+void launch_future_energy(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkeys, const double* tau, int k,
+                          const double* tab, int ts, int n, double* out, cudaStream_t s) {
+    if (M <= 0) return;
+    const int g = expand_grid(M);
+    const size_t smem = (size_t)ts * n * sizeof(double);
+    switch (Wd) {
+        case 1: k_future_energy<1><<<g, kThreads, smem, s>>>(rows, M, make_group<1>(pkeys, tau, k), tab, ts, n, out); break;
+        case 2: k_future_energy<2><<<g, kThreads, smem, s>>>(rows, M, make_group<2>(pkeys, tau, k), tab, ts, n, out); break;
+        default: k_future_energy<4><<<g, kThreads, smem, s>>>(rows, M, make_group<4>(pkeys, tau, k), tab, ts, n, out); break;
+    }
+    note_launch();
+}
 
 void launch_expand_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkeys, const double* tau, int k,
                          unsigned long long* total, cudaStream_t s) {

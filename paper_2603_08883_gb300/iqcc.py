@@ -25,6 +25,7 @@ _lib = ctypes.CDLL(LIB_PATH)
 
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 _f64p = ctypes.POINTER(ctypes.c_double)
+_f32p = ctypes.POINTER(ctypes.c_float)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _vp = ctypes.c_void_p
 
@@ -49,7 +50,7 @@ class iqcc_opts(ctypes.Structure):
 class iqcc_iter_opts(ctypes.Structure):
     _fields_ = [("n_gen", ctypes.c_int), ("eps", ctypes.c_double), ("max_terms", ctypes.c_int64),
                 ("min_gradient", ctypes.c_double), ("n_forced", ctypes.c_int), ("forced_x", _u64p),
-                ("forced_z", _u64p), ("forced_tau", _f64p)]
+                ("forced_z", _u64p), ("forced_tau", _f64p), ("screening", ctypes.c_int)]
 
 
 class iqcc_iter_result(ctypes.Structure):
@@ -66,7 +67,8 @@ class iqcc_stats(ctypes.Structure):
                 ("energy_bytes", ctypes.c_double), ("prune_ms", ctypes.c_double), ("dis_ms", ctypes.c_double),
                 ("hash_ms", ctypes.c_double), ("hash_rebuilds", ctypes.c_int64), ("rows_allocated", ctypes.c_int64),
                 ("hash_slots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
-                ("n_sorted_groups", ctypes.c_int64), ("sorted_dress_ms", ctypes.c_double), ("words", ctypes.c_int),
+                ("n_sorted_groups", ctypes.c_int64), ("sorted_dress_ms", ctypes.c_double),
+                ("screen_terms", ctypes.c_int64), ("screen_ms", ctypes.c_double), ("words", ctypes.c_int),
                 ("pad", ctypes.c_int)]
 
 
@@ -81,6 +83,12 @@ _c = ctypes.c_int
 _load = _sig("iqcc_load_hamiltonian", _c, [ctypes.POINTER(_vp), ctypes.POINTER(iqcc_opts), ctypes.c_int64, _u64p,
                                            _u64p, _f64p])
 _dress = _sig("iqcc_dress", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.POINTER(ctypes.c_int)])
+_set_model = _sig("iqcc_set_screening_model", _c, [_vp, _f32p, _f32p, _f32p, _f32p, _f32p, ctypes.c_float])
+_features = _sig("iqcc_term_features", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f32p])
+_future = _sig("iqcc_future_energies", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f64p, _f64p])
+_scores = _sig("iqcc_term_scores", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f32p])
+_prune_learned = _sig("iqcc_prune_learned", _c, [_vp, ctypes.c_double, ctypes.c_int64, ctypes.c_int, _u64p, _u64p,
+                                                 _f64p, _f64p, _i64p])
 _dress_sorted = _sig("iqcc_dress_sorted", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)])
 _prune = _sig("iqcc_prune", _c, [_vp, ctypes.c_double, ctypes.c_int64, _i64p])
@@ -213,6 +221,62 @@ def iqcc_dress_sorted(H: Hamiltonian, gx, gz, tau, fuse: int = 1) -> int:
     return applied.value
 
 
+def _gens(H, gx, gz):
+    if gx is None:
+        return 0, None, None, []
+    gxa, gxp = _u64(gx, (-1, H.W))
+    gza, gzp = _u64(gz, (-1, H.W))
+    return len(gxa), gxp, gzp, [gxa, gza]
+
+
+def iqcc_set_screening_model(H: Hamiltonian, w1, b1, w2, b2, w3, b3: float) -> None:
+    """Perceptron weights: w1 [256, 8], b1 [256], w2 [256, 256] (out, in), b2 [256], w3 [256], b3."""
+    arrs = [np.ascontiguousarray(a, np.float32).reshape(-1) for a in (w1, b1, w2, b2, w3)]
+    if [a.size for a in arrs] != [256 * 8, 256, 256 * 256, 256, 256]:
+        raise ValueError("weight shapes: w1 [256, 8], b1 [256], w2 [256, 256], b2 [256], w3 [256]")
+    H._check(_set_model(H._h, *[a.ctypes.data_as(_f32p) for a in arrs], float(b3)))
+
+
+def iqcc_term_features(H: Hamiltonian, theta, phi, gx=None, gz=None) -> np.ndarray:
+    """Screening features of every term (rows in iqcc_export order): float32 [M, 8]."""
+    k, gxp, gzp, keep = _gens(H, gx, gz)
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    out = np.zeros((len(H), 8), np.float32)
+    H._check(_features(H._h, k, gxp, gzp, tp, pp, out.ctypes.data_as(_f32p)))
+    return out
+
+
+def iqcc_future_energies(H: Hamiltonian, theta, phi, gx, gz, tau) -> np.ndarray:
+    """E_fut of every term after the generators (<= 8) at amplitudes tau (iqcc_export order)."""
+    k, gxp, gzp, keep = _gens(H, gx, gz)
+    ta, tp = _f64(np.atleast_1d(tau), k)
+    tha, thp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    out = np.zeros(len(H))
+    H._check(_future(H._h, k, gxp, gzp, tp, thp, pp, out.ctypes.data_as(_f64p)))
+    return out
+
+
+def iqcc_term_scores(H: Hamiltonian, theta, phi, gx=None, gz=None) -> np.ndarray:
+    """The screening model's score of every term (iqcc_export order): float32 [M]."""
+    k, gxp, gzp, keep = _gens(H, gx, gz)
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    out = np.zeros(len(H), np.float32)
+    H._check(_scores(H._h, k, gxp, gzp, tp, pp, out.ctypes.data_as(_f32p)))
+    return out
+
+
+def iqcc_prune_learned(H: Hamiltonian, eps: float, max_terms: int, theta, phi, gx=None, gz=None) -> int:
+    k, gxp, gzp, keep = _gens(H, gx, gz)
+    ta, tp = _f64(theta, H.n)
+    pa, pp = _f64(phi, H.n)
+    removed = ctypes.c_int64(0)
+    H._check(_prune_learned(H._h, float(eps), int(max_terms), k, gxp, gzp, tp, pp, ctypes.byref(removed)))
+    return removed.value
+
+
 def iqcc_prune(H: Hamiltonian, eps: float, max_terms: int = 0) -> int:
     removed = ctypes.c_int64(0)
     H._check(_prune(H._h, float(eps), int(max_terms), ctypes.byref(removed)))
@@ -284,11 +348,12 @@ def iqcc_dis_gradients(H: Hamiltonian, theta, phi, cx=None, cz=None, cap: int | 
 
 
 def iqcc_iterate(H: Hamiltonian, theta, phi, n_gen: int, eps: float = 0.0, max_terms: int = 0,
-                 min_gradient: float = 0.0, forced_x=None, forced_z=None, forced_tau=None) -> dict:
+                 min_gradient: float = 0.0, forced_x=None, forced_z=None, forced_tau=None,
+                 screening: int = 0) -> dict:
     ta, tp = _f64(theta, H.n)
     pa, pp = _f64(phi, H.n)
     keep = []
-    o = iqcc_iter_opts(n_gen, eps, max_terms, min_gradient, 0, None, None, None)
+    o = iqcc_iter_opts(n_gen, eps, max_terms, min_gradient, 0, None, None, None, int(screening))
     if forced_x is not None:
         fxa, fxp = _u64(forced_x, (-1, H.W))
         fza, fzp = _u64(forced_z, (-1, H.W))
