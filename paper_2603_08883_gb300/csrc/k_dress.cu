@@ -212,7 +212,9 @@ __device__ __forceinline__ void dress_body(const uint64_t* __restrict__ rows, ui
                 const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
                 hv = hash_key<W>(q);
                 double cq = 0.0;
-                const int64_t j = lookup_slot_coef<W>(q, hv, h, rows, coef, &fslot, &cq);
+                // only the member that rotates a present pair needs its partner's coefficient
+                const int64_t j = upper ? lookup_slot<W>(q, hv, h, rows, &fslot)
+                                        : lookup_slot_coef<W>(q, hv, h, rows, coef, &fslot, &cq);
                 if (j == -1) {
                     coef[i] = ct * g.cos_t;
                     c_new = s * ct * g.sin_t;
