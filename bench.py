@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the measurements of the adjoint pass, learned screening, sort-based dress and batches")
     return ap.parse_args()
 
 
@@ -394,7 +396,7 @@ def run_gpu(args):
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
     adjoint = sort_variant = screening = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
         screening = measure_screening(iqcc, H, th, ph)
 
@@ -440,7 +442,7 @@ def run_gpu(args):
     else:
         H.close()
     batch_variant = None
-    if rank == 0:  # after the capped Hamiltonian is released
+    if rank == 0 and not args.no_extras:  # after the capped Hamiltonian is released
         sort_variant = measure_sort_variant(iqcc, n, x, z, c, th, ph, stream)
         batch_variant = measure_batch(iqcc, synth)
 
