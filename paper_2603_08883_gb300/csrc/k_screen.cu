@@ -1,7 +1,7 @@
 // Learned term screening: a perceptron scores every term of H, and the term
 // limit keeps the highest scores instead of the largest |C|.
 //
-// Features of a term T with coefficient C (kFeat of them, from its key alone;
+// Features of a term T with coefficient C (kFeat of them, in FP32, from its key;
 // G = union of the supports of the iteration's generators, <T> at the
 // reference product state of Eq. 3):
 //   0  log10|C| / 8           1  flipped qubits / 16      2  Y letters / 16
@@ -31,6 +31,9 @@ constexpr int kW1Stride = 24;   // bf16 per layer-1 row in shared memory (16 use
 constexpr int kW2Stride = 264;  // bf16 per layer-2 row in shared memory (256 used)
 constexpr int kMlpThreads = 384;
 constexpr int kMlpWarps = kMlpThreads / 32;
+// Layer-2 output tiles of 8 computed together (8e8 terms: 1 tile 304 ms, 2 tiles
+// 268 ms, 4 tiles 263 ms).
+constexpr int kL2Tiles = 4;
 
 // Device model layout (bytes): w1 [256][16] bf16 (inputs 8..15 zero), w2
 // [256][256] bf16 (row = output unit), then float b1[256], b2[256], w3[256], b3.
@@ -47,11 +50,21 @@ struct GenSupport {
     uint64_t g[W];  // union of the generators' supports
 };
 
+// log10|c| in FP32 from the double's exponent and a float log of its mantissa
+// (no FP64 transcendental: GB300's FP64 rate is low); -300 for c = 0.
+__device__ __forceinline__ float log10_abs(double c) {
+    if (c == 0.0) return -300.0f;
+    int e;
+    const double m = frexp(fabs(c), &e);  // |c| = m 2^e, m in [0.5, 1)
+    return (log2f((float)m) + (float)e) * 0.30102999566f;
+}
+
+// ev: per-qubit <I>, <X>, <Y>, <Z> as floats (4 per qubit).
 template <int W>
-__device__ __forceinline__ void term_features(const Key<W>& t, double c, const GenSupport<W>& gs, const double* ev,
-                                              int ts, float* f) {
+__device__ __forceinline__ void term_features(const Key<W>& t, double c, const GenSupport<W>& gs, const float* ev,
+                                              float* f) {
     int flips = 0, ys = 0, zs = 0, ov = 0, fov = 0;
-    double e = 1.0;
+    float e = 1.0f;
 #pragma unroll
     for (int wd = 0; wd < W; ++wd) {
         const uint64_t x = t.x[wd], z = t.z[wd];
@@ -61,33 +74,38 @@ __device__ __forceinline__ void term_features(const Key<W>& t, double c, const G
         ov += __popcll((x | z) & gs.g[wd]);
         fov += __popcll(x & gs.g[wd]);
         uint64_t m = x | z;
-        while (m && e != 0.0) {
+        while (m && e != 0.0f) {
             const int j = __ffsll((long long)m) - 1;
             m &= m - 1;
             const int xb = (int)((x >> j) & 1ull), zb = (int)((z >> j) & 1ull);
-            e *= ev[ts * (64 * wd + j) + (xb ? (zb ? 2 : 1) : 3)];
+            e *= ev[4 * (64 * wd + j) + (xb ? (zb ? 2 : 1) : 3)];
         }
     }
-    f[0] = (float)(log10(fabs(c) + 1e-300) / 8.0);
+    f[0] = log10_abs(c) / 8.0f;
     f[1] = flips / 16.0f;
     f[2] = ys / 16.0f;
     f[3] = zs / 32.0f;
     f[4] = ov / 8.0f;
     f[5] = fov / 8.0f;
-    f[6] = (float)e;
+    f[6] = e;
     f[7] = (flips > 0 && fov == flips) ? 1.0f : 0.0f;
+}
+
+// The per-qubit <sigma> of the double table (stride ts, letters at 0..3) as floats.
+__device__ __forceinline__ void load_ev(const double* ev_g, int ts, int n, float* ev) {
+    for (int i = threadIdx.x; i < 4 * n; i += blockDim.x) ev[i] = (float)ev_g[ts * (i / 4) + (i % 4)];
 }
 
 template <int W>
 __global__ void k_term_features(const uint64_t* __restrict__ rows, const double* __restrict__ coef, int64_t M,
                                 GenSupport<W> gs, const double* __restrict__ ev_g, int ts, int n, float* out) {
-    extern __shared__ double ev[];
-    for (int i = threadIdx.x; i < ts * n; i += blockDim.x) ev[i] = ev_g[i];
+    extern __shared__ float evf[];
+    load_ev(ev_g, ts, n, evf);
     __syncthreads();
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += s) {
         float f[kFeat];
-        term_features<W>(load_key<W>(rows, i), coef[i], gs, ev, ts, f);
+        term_features<W>(load_key<W>(rows, i), coef[i], gs, evf, f);
 #pragma unroll
         for (int k = 0; k < kFeat; ++k) out[(size_t)i * kFeat + k] = f[k];
     }
@@ -106,7 +124,11 @@ __device__ __forceinline__ void mma_bf16(float* c, const uint32_t* a, uint32_t b
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// score[i] (may be NULL) and rank[i] = 10^score (the term limit's key).
+// The term limit's key: a positive double increasing with the score (exact:
+// a float plus 1024 is representable), scores below -1000 all at 24.
+__device__ __forceinline__ double rank_of(float score) { return (double)fmaxf(score, -1000.0f) + 1024.0; }
+
+// score[i] (may be NULL) and rank[i] = rank_of(score) (the term limit's key).
 template <int W>
 __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_score(const uint64_t* __restrict__ rows,
                                                               const double* __restrict__ coef, int64_t M,
@@ -120,7 +142,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_score(const uint64_t* __
     float* b2 = b1 + kHid;
     float* w3 = b2 + kHid;
     float* stage = w3 + kHid;                                                  // [warps][16][16]
-    double* ev = reinterpret_cast<double*>(stage + kMlpWarps * 256);           // [ts n]
+    float* ev = stage + kMlpWarps * 256;                                       // [4 n]
     const __nv_bfloat16* mw1 = reinterpret_cast<const __nv_bfloat16*>(model + kOffW1);
     const __nv_bfloat16* mw2 = reinterpret_cast<const __nv_bfloat16*>(model + kOffW2);
     for (int i = threadIdx.x; i < kHid * 16; i += blockDim.x) w1[(i / 16) * kW1Stride + (i % 16)] = mw1[i];
@@ -133,7 +155,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_score(const uint64_t* __
         b2[i] = reinterpret_cast<const float*>(model + kOffB2)[i];
         w3[i] = reinterpret_cast<const float*>(model + kOffW3)[i];
     }
-    for (int i = threadIdx.x; i < ts * n; i += blockDim.x) ev[i] = ev_g[i];
+    load_ev(ev_g, ts, n, ev);
     const float b3 = *reinterpret_cast<const float*>(model + kOffB3);
     __syncthreads();
 
@@ -148,7 +170,7 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_score(const uint64_t* __
             const int64_t i = tile * 16 + lane;
             float f[kFeat];
             if (i < M) {
-                term_features<W>(load_key<W>(rows, i), coef[i], gs, ev, ts, f);
+                term_features<W>(load_key<W>(rows, i), coef[i], gs, ev, f);
             } else {
 #pragma unroll
                 for (int k = 0; k < kFeat; ++k) f[k] = 0.0f;
@@ -176,19 +198,29 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_score(const uint64_t* __
             h[jn >> 1][(jn & 1) * 2] = pack_bf16(v0, v1);
             h[jn >> 1][(jn & 1) * 2 + 1] = pack_bf16(v2, v3);
         }
-        // layer 2, with layer 3 in the epilogue
+        // layer 2, with layer 3 in the epilogue; kL2Tiles independent accumulators
+        // per step so that consecutive MMAs do not wait on each other
         float s_lo = 0.f, s_hi = 0.f;
-#pragma unroll 2
-        for (int jn = 0; jn < kHid / 8; ++jn) {
-            float c[4] = {0.f, 0.f, 0.f, 0.f};
-            const __nv_bfloat16* wr = w2 + (8 * jn + g) * kW2Stride;
+#pragma unroll 1
+        for (int jn0 = 0; jn0 < kHid / 8; jn0 += kL2Tiles) {
+            float c[kL2Tiles][4];
 #pragma unroll
-            for (int kk = 0; kk < kHid / 16; ++kk)
-                mma_bf16(c, h[kk], *reinterpret_cast<const uint32_t*>(wr + 16 * kk + 2 * t),
-                         *reinterpret_cast<const uint32_t*>(wr + 16 * kk + 2 * t + 8));
-            const int n0 = 8 * jn + 2 * t;
-            s_lo += fmaxf(c[0] + b2[n0], 0.f) * w3[n0] + fmaxf(c[1] + b2[n0 + 1], 0.f) * w3[n0 + 1];
-            s_hi += fmaxf(c[2] + b2[n0], 0.f) * w3[n0] + fmaxf(c[3] + b2[n0 + 1], 0.f) * w3[n0 + 1];
+            for (int u = 0; u < kL2Tiles; ++u) c[u][0] = c[u][1] = c[u][2] = c[u][3] = 0.f;
+#pragma unroll
+            for (int kk = 0; kk < kHid / 16; ++kk) {
+#pragma unroll
+                for (int u = 0; u < kL2Tiles; ++u) {
+                    const __nv_bfloat16* wr = w2 + (8 * (jn0 + u) + g) * kW2Stride + 16 * kk + 2 * t;
+                    mma_bf16(c[u], h[kk], *reinterpret_cast<const uint32_t*>(wr),
+                             *reinterpret_cast<const uint32_t*>(wr + 8));
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kL2Tiles; ++u) {
+                const int n0 = 8 * (jn0 + u) + 2 * t;
+                s_lo += fmaxf(c[u][0] + b2[n0], 0.f) * w3[n0] + fmaxf(c[u][1] + b2[n0 + 1], 0.f) * w3[n0 + 1];
+                s_hi += fmaxf(c[u][2] + b2[n0], 0.f) * w3[n0] + fmaxf(c[u][3] + b2[n0 + 1], 0.f) * w3[n0 + 1];
+            }
         }
         s_lo += __shfl_xor_sync(0xFFFFFFFFu, s_lo, 1);
         s_lo += __shfl_xor_sync(0xFFFFFFFFu, s_lo, 2);
@@ -198,11 +230,11 @@ __global__ void __launch_bounds__(kMlpThreads, 1) k_mlp_score(const uint64_t* __
             const int64_t i0 = tile * 16 + g, i1 = i0 + 8;
             if (i0 < M) {
                 if (score) score[i0] = s_lo + b3;
-                rank[i0] = exp10((double)(s_lo + b3));
+                rank[i0] = rank_of(s_lo + b3);
             }
             if (i1 < M) {
                 if (score) score[i1] = s_hi + b3;
-                rank[i1] = exp10((double)(s_hi + b3));
+                rank[i1] = rank_of(s_hi + b3);
             }
         }
         __syncwarp();
@@ -218,7 +250,7 @@ GenSupport<W> support_of(const uint64_t* gsup) {
 
 size_t mlp_smem(int ts, int n) {
     return (size_t)kHid * kW1Stride * 2 + (size_t)kHid * kW2Stride * 2 + 3 * kHid * 4 + kMlpWarps * 256 * 4 +
-           (size_t)ts * n * 8;
+           (size_t)4 * n * 4;
 }
 
 __global__ void k_gather_words(const uint32_t* __restrict__ in, const uint32_t* __restrict__ perm, int64_t n, int words,
@@ -245,7 +277,7 @@ void launch_term_features(int Wd, const uint64_t* rows, const double* coef, int6
                           const double* ev, int ts, int n, float* out, cudaStream_t s) {
     if (M <= 0) return;
     const int grid = sm_count() * 4;
-    const size_t smem = (size_t)ts * n * 8;
+    const size_t smem = (size_t)4 * n * 4;
     switch (Wd) {
         case 1: k_term_features<1><<<grid, 256, smem, s>>>(rows, coef, M, support_of<1>(gsup), ev, ts, n, out); break;
         case 2: k_term_features<2><<<grid, 256, smem, s>>>(rows, coef, M, support_of<2>(gsup), ev, ts, n, out); break;

@@ -59,7 +59,7 @@ def test_features_match_their_definition(n):
         want = [math.log10(abs(ec[i])) / 8, flips / 16, _popc_rows(xi & zi)[0] / 16, _popc_rows(zi & ~xi)[0] / 32,
                 _popc_rows((xi | zi) & G)[0] / 8, fov / 8, _single_energy(n, xi, zi, th, ph),
                 1.0 if (flips > 0 and fov == flips) else 0.0]
-        assert np.allclose(f[i], want, rtol=1e-6, atol=1e-6), (i, f[i], want)
+        assert np.allclose(f[i], want, rtol=1e-5, atol=1e-6), (i, f[i], want)  # FP32 features
 
 
 def _random_model(seed):
@@ -115,7 +115,7 @@ def test_learned_term_limit_keeps_the_best_scores():
     s = iqcc.iqcc_term_scores(H, th, ph, gx, gz)
     ex, ez, ec = iqcc.iqcc_export(H)
     keep = 7000
-    rank = 10.0 ** s.astype(np.float64)
+    rank = np.maximum(s, -1000).astype(np.float64) + 1024.0   # the library's key: exact and increasing
     order = sorted(range(len(s)), key=lambda i: (-rank[i], i))  # export order is canonical: index = key order
     expect = {(ex[i].tobytes(), ez[i].tobytes()) for i in order[:keep]}
     removed = iqcc.iqcc_prune_learned(H, 0.0, keep, th, ph, gx, gz)
