@@ -106,8 +106,8 @@ __device__ __forceinline__ int product_sign(const Key<W>& t, int yP, const Key<W
 }
 
 // Key hash: a multiply-xorshift chain over the 2W words, finished with the
-// 64-bit fmix of MurmurHash3.  Low bits pick the bucket, high 32 bits are the
-// fingerprint kept in the slot.
+// 64-bit fmix of MurmurHash3.  Low bits pick the bucket; the top 24 bits are
+// the fingerprint kept in index entries (the DIS group table keeps the top 32).
 template <int W>
 __device__ __forceinline__ uint64_t hash_key(const Key<W>& k) {
     uint64_t h = 0x9E3779B97F4A7C15ull;
