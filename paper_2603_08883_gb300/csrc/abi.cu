@@ -787,11 +787,14 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
         iqcc_free(ctx);
         return st;
     };
-    for (int64_t k = 0; k < n_terms; ++k)
-        if (bits_above_n(ctx, x + k * ctx->W) || bits_above_n(ctx, z + k * ctx->W)) {
-            fail(ctx, IQCC_ERR_ARG, "key bits set above n_qubits");
-            return bail(IQCC_ERR_ARG);
-        }
+    // small inputs are checked on the host (argument errors before any device
+    // work); every input is checked again on the device while it is packed
+    if (n_terms <= (1 << 16))
+        for (int64_t k = 0; k < n_terms; ++k)
+            if (bits_above_n(ctx, x + k * ctx->W) || bits_above_n(ctx, z + k * ctx->W)) {
+                fail(ctx, IQCC_ERR_ARG, "key bits set above n_qubits");
+                return bail(IQCC_ERR_ARG);
+            }
     if (n_terms > ctx->capacity) {
         fail(ctx, IQCC_ERR_CAPACITY, "more input terms than capacity");
         return bail(IQCC_ERR_CAPACITY);
@@ -854,10 +857,28 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
                 st = fail_cuda(ctx, cudaGetLastError(), "input copy", __LINE__);
                 break;
             }
-            launch_pack_rows(W, Wd, dx, dz, staged, n, s);
+            // keys are checked on the device (bits above n_qubits), while packing
+            const int r = ctx->n - 64 * (W - 1);
+            const uint64_t hi_mask = r >= 64 ? 0ull : ~((1ull << r) - 1);
+            DevCounters* cc = dctr(ctx);
+            if (cudaMemsetAsync(cc, 0, 4 * sizeof(unsigned long long), s) != cudaSuccess) {
+                st = fail_cuda(ctx, cudaGetLastError(), "memset", __LINE__);
+                break;
+            }
+            launch_pack_rows(W, Wd, dx, dz, staged, n, s, hi_mask, &cc->n_new);
             launch_iota(sa.a, n, s);
-            uint32_t* sorted = nullptr;
-            radix_sort_indirect(staged, 2 * Wd, canonical_plan(ctx), sa.a, sa.b, n, &sorted, sa.tmp, sa.tmp_bytes, s);
+            // input already in canonical order with distinct keys (an export, for one) needs no sort
+            launch_order_violations(Wd, staged, n, &cc->aux, s);
+            st = read_counters(ctx);
+            if (st) break;
+            if (ctx->h_counters->n_new != 0) {
+                st = fail(ctx, IQCC_ERR_ARG, "key bits set above n_qubits");
+                break;
+            }
+            uint32_t* sorted = sa.a;
+            if (ctx->h_counters->aux != 0)
+                radix_sort_indirect(staged, 2 * Wd, canonical_plan(ctx), sa.a, sa.b, n, &sorted, sa.tmp, sa.tmp_bytes,
+                                    s);
             // run sums land in the row buffer at sorted positions; then keep the non-zero heads
             launch_sum_runs(Wd, staged, c_staged, sorted, n, flags, ctx->rows(), ctx->c(), s);
             DevCounters* c = dctr(ctx);
@@ -1197,24 +1218,13 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
     const int64_t M = ctx->M;
     const int W = ctx->W;
-    Carver cv;
-    cv.off += sort_area_bytes(M);
-    cv.take<uint64_t>((size_t)k * W);
-    cv.take<uint64_t>((size_t)k * W);
-    cv.take<double>(k);
-    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-    cv = Carver{(char*)ctx->scratch.p, 0};
-    SortArea sa = carve_sort(cv, M);
-    uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
-    uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
-    double* sc = cv.take<double>(k);
-    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    launch_iota(sa.a, M, ctx->stream);
-    uint32_t* sorted = nullptr;
-    radix_sort_indirect(ctx->rows(), 2 * ctx->Wd, canonical_plan(ctx), sa.a, sa.b, M, &sorted, sa.tmp, sa.tmp_bytes,
-                        ctx->stream);
-    CK_LAUNCH();
-    launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), sorted, sx, sz, sc, k, ctx->stream);
+    // direct radix sort of (keys, coefficient) columns, written in the export layout
+    if (!ensure(ctx, ctx->scratch, export_sort_scratch_bytes(ctx->Wd, M)))
+        return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    uint64_t* sx = nullptr;
+    uint64_t* sz = nullptr;
+    double* sc = nullptr;
+    launch_export_sort(W, ctx->Wd, ctx->rows(), ctx->c(), M, k, ctx->scratch.p, &sx, &sz, &sc, ctx->stream);
     CK_LAUNCH();
     CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));

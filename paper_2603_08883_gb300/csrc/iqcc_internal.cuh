@@ -238,6 +238,8 @@ long long launches();
 // k_build.cu: index build without global atomics on the table (partitioned in
 // shared memory); writes every slot, so no clear is needed first.
 size_t index_build_scratch_bytes(int64_t n, uint64_t n_slots);
+// exclusive scan of a long u32 array in place (tmp: 1024 words of device scratch)
+void launch_scan_u32_long(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s);
 void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView h, uint64_t n_slots, void* scratch,
                         DevCounters* ctr, cudaStream_t s);
 // After an in-place compaction with map new_row (old row -> new row or
@@ -348,6 +350,13 @@ void launch_iota(uint32_t* p, int64_t n, cudaStream_t s);
 
 // compaction: out[rank] = in[i] for flags[i] != 0 (stable); count to *ctr_count (device).
 size_t compact_scratch_bytes(int64_t n);
+// k_keysort.cu: rows [0, n) and coefficients sorted in canonical order, the
+// first k written as x [k][W], z [k][W], coef [k] inside scratch (pointers out).
+size_t export_sort_scratch_bytes(int Wd, int64_t n);
+void launch_export_sort(int W, int Wd, const uint64_t* rows, const double* coef, int64_t n, int64_t k, void* scratch,
+                        uint64_t** out_x, uint64_t** out_z, double** out_c, cudaStream_t s);
+// adds to *count the consecutive pairs not strictly increasing in canonical order
+void launch_order_violations(int Wd, const uint64_t* rows, int64_t n, unsigned long long* count, cudaStream_t s);
 void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, const double* c_in,
                          uint64_t* rows_out, double* c_out, int64_t n, void* scratch,
                          unsigned long long* count, cudaStream_t s);
@@ -368,8 +377,9 @@ void launch_dis_sort_keys_sub(int Wd, const uint64_t* gkeys, const double* gsum,
                               uint64_t* skeys, cudaStream_t s);
 
 // load: pack host-layout x/z into rows, sum runs after the sort
+// host layout to device rows; keys with bits in hi_mask of their last word counted in *bad (may be NULL)
 void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n,
-                      cudaStream_t s);
+                      cudaStream_t s, uint64_t hi_mask = 0, unsigned long long* bad = nullptr);
 void launch_unpack_rows(int W, int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm,
                         uint64_t* x, uint64_t* z, double* c, int64_t n, cudaStream_t s);
 void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,

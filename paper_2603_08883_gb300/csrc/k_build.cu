@@ -414,6 +414,18 @@ BuildPlan plan_for(int64_t n, uint64_t n_slots) {
 
 }  // namespace
 
+// Exclusive scan of data[0, n) in place; tmp: 1024 words of device scratch.
+void launch_scan_u32_long(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s) {
+    if (n <= 0) return;
+    const int64_t per = (n + 1023) / 1024;
+    const int64_t chunk = (per + kScanChunkAlign - 1) / kScanChunkAlign * kScanChunkAlign;
+    const int chunks = (int)((n + chunk - 1) / chunk);
+    k_chunk_sums<<<chunks, kThreads, 0, s>>>(data, n, chunk, tmp);
+    k_scan_small<<<1, 1024, 0, s>>>(tmp, chunks);
+    k_chunk_scan<<<chunks, kThreads, 0, s>>>(data, n, chunk, tmp);
+    note_launch(3);
+}
+
 size_t index_build_scratch_bytes(int64_t n, uint64_t n_slots) {
     const BuildPlan b = plan_for(n, n_slots);
     size_t t = 0;

@@ -337,15 +337,22 @@ __global__ void k_dis_sort_keys_sub(int Wd, const uint64_t* __restrict__ gkeys, 
 
 // ---------------------------------------------------------------- load / export
 
+// Host layout (x [n][W], z [n][W]) to device rows; keys with bits set in
+// hi_mask of their last word (above n_qubits) are counted in *bad.
 __global__ void k_pack_rows(int W, int Wd, const uint64_t* __restrict__ x, const uint64_t* __restrict__ z,
-                            uint64_t* rows, int64_t n) {
+                            uint64_t* rows, int64_t n, uint64_t hi_mask, unsigned long long* bad) {
+    unsigned long long nbad = 0;
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
         for (int w = 0; w < Wd; ++w) {
             rows[(size_t)i * 2 * Wd + w] = w < W ? x[(size_t)i * W + w] : 0ull;
             rows[(size_t)i * 2 * Wd + Wd + w] = w < W ? z[(size_t)i * W + w] : 0ull;
         }
+        nbad += ((x[(size_t)i * W + W - 1] | z[(size_t)i * W + W - 1]) & hi_mask) ? 1 : 0;
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) nbad += __shfl_down_sync(0xFFFFFFFFu, nbad, o);
+    if (bad && (threadIdx.x & 31) == 0 && nbad) atomicAdd(bad, nbad);
 }
 
 __global__ void k_unpack_rows(int W, int Wd, const uint64_t* __restrict__ rows, const double* __restrict__ coef,
@@ -386,6 +393,29 @@ __global__ void k_sum_runs(const uint64_t* __restrict__ rows, const double* __re
         c_out[i] = sum;
         flags[i] = keep_zeros || sum != 0.0;
     }
+}
+
+// Pairs of consecutive rows not in strictly increasing canonical order (x as
+// an integer, last word most significant, then z): zero means the rows are
+// sorted and their keys distinct.
+template <int W>
+__global__ void k_order_violations(const uint64_t* __restrict__ rows, int64_t n, unsigned long long* count) {
+    unsigned long long bad = 0;
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = 1 + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const Key<W> a = load_key<W>(rows, i - 1), b = load_key<W>(rows, i);
+        int cmp = 0;
+#pragma unroll
+        for (int w = W - 1; w >= 0; --w)
+            if (!cmp && a.x[w] != b.x[w]) cmp = a.x[w] < b.x[w] ? -1 : 1;
+#pragma unroll
+        for (int w = W - 1; w >= 0; --w)
+            if (!cmp && a.z[w] != b.z[w]) cmp = a.z[w] < b.z[w] ? -1 : 1;
+        bad += cmp < 0 ? 0 : 1;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bad += __shfl_down_sync(0xFFFFFFFFu, bad, o);
+    if ((threadIdx.x & 31) == 0 && bad) atomicAdd(count, bad);
 }
 
 template <int W>
@@ -674,10 +704,10 @@ void launch_dis_sort_keys_sub(int Wd, const uint64_t* gkeys, const double* gsum,
     }
 }
 
-void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n,
-                      cudaStream_t s) {
+void launch_pack_rows(int W, int Wd, const uint64_t* x, const uint64_t* z, uint64_t* rows, int64_t n, cudaStream_t s,
+                      uint64_t hi_mask, unsigned long long* bad) {
     if (n > 0) {
-        k_pack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, x, z, rows, n);
+        k_pack_rows<<<grid_stride_blocks(n), kThreads, 0, s>>>(W, Wd, x, z, rows, n, hi_mask, bad);
         note_launch();
     }
 }
@@ -699,6 +729,17 @@ void launch_sum_runs(int Wd, const uint64_t* rows, const double* coef, const uin
         case 2: k_sum_runs<2><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out, keep_zeros); note_launch(); break;
         default: k_sum_runs<4><<<g, kThreads, 0, s>>>(rows, coef, perm, n, flags, rows_out, c_out, keep_zeros); note_launch(); break;
     }
+}
+
+void launch_order_violations(int Wd, const uint64_t* rows, int64_t n, unsigned long long* count, cudaStream_t s) {
+    if (n <= 1) return;
+    const int g = grid_stride_blocks(n);
+    switch (Wd) {
+        case 1: k_order_violations<1><<<g, kThreads, 0, s>>>(rows, n, count); break;
+        case 2: k_order_violations<2><<<g, kThreads, 0, s>>>(rows, n, count); break;
+        default: k_order_violations<4><<<g, kThreads, 0, s>>>(rows, n, count); break;
+    }
+    note_launch();
 }
 
 void launch_gather_rows(int Wd, const uint64_t* rows, const double* coef, const uint32_t* perm, int64_t n,

@@ -387,3 +387,40 @@ def test_holes_energy_dis_and_defragmentation(frac):
             o.dress(gx, gz, t)
         bad = compare(iqcc.iqcc_export(H), o.export(), eps=eps)
         assert not bad, bad[:5]
+
+
+@pytest.mark.parametrize("n", [10, 100, 200])
+def test_load_of_canonical_input_and_of_sorted_input_with_repeats(n):
+    """Input already in canonical order with distinct keys (an export) is loaded
+    without sorting; zeros are still dropped.  Sorted input with repeated keys
+    still has its repeats summed."""
+    _, x, z, c = synth.random_hamiltonian(n, 20_000, 500 + n)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    ex, ez, ec = iqcc.iqcc_export(H)
+    ec = ec.copy()
+    ec[::7] = 0.0
+    H2 = iqcc.iqcc_load_hamiltonian(n, ex, ez, ec)
+    o = oracle.Oracle(n, ex, ez, ec)
+    gx, gz, gc = iqcc.iqcc_export(H2)
+    ox, oz, oc = o.export()
+    assert np.array_equal(gx, ox) and np.array_equal(gz, oz) and np.array_equal(gc, oc)
+    assert len(H2) == int(np.count_nonzero(ec))
+    rx = np.repeat(ex, 2, axis=0)
+    rz = np.repeat(ez, 2, axis=0)
+    rc = np.repeat(ec, 2) * 0.5
+    H3 = iqcc.iqcc_load_hamiltonian(n, rx, rz, rc)
+    o3 = oracle.Oracle(n, rx, rz, rc)
+    gx, gz, gc = iqcc.iqcc_export(H3)
+    ox, oz, oc = o3.export()
+    assert np.array_equal(gx, ox) and np.array_equal(gz, oz) and np.array_equal(gc, oc)
+
+
+def test_load_rejects_bits_above_n_qubits_in_a_large_input():
+    """Inputs beyond the host-checked size are checked on the device while packed."""
+    n = 40
+    _, x, z, c = synth.random_hamiltonian(n, 200_000, 17)
+    z = z.copy()
+    z[123_456, 0] |= np.uint64(1) << np.uint64(45)
+    with pytest.raises(iqcc.IqccError) as err:
+        iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    assert err.value.status == 1
