@@ -231,7 +231,12 @@ iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms);
 
 /*
  * Copy H to the host in canonical order: *n = M; min(cap, M) rows written to
- * x, z [cap][W] and coef [cap].  cap = 0 is a size query.
+ * x, z [cap][W] and coef [cap].  cap = 0 is a size query.  Rows keep their
+ * order through dressing and pruning, so the longest sorted prefix of the
+ * table is only merged with the sorted rest.  When x, z and coef are all
+ * page-locked host memory registered with CUDA (cudaHostAlloc, a pinned torch
+ * tensor) the device writes them directly; other host memory is filled from
+ * device scratch with a copy.  Device scratch: about 2 (2 Wd + 1) 8 M bytes.
  */
 iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z,
                         double* coef);

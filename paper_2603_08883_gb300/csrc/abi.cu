@@ -1208,6 +1208,25 @@ iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms) {
     return IQCC_OK;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The device address of page-locked host memory registered with CUDA (it is
+// mapped under unified addressing), or null for any other pointer.
+void* pinned_device_view(const void* p) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
+}  // namespace
+
+extern "C" {
+
 iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z, double* coef) {
     GUARD(ctx);
     if (!n) return fail(ctx, IQCC_ERR_ARG, "n is NULL");
@@ -1218,17 +1237,26 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
     if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
     const int64_t M = ctx->M;
     const int W = ctx->W;
-    // direct radix sort of (keys, coefficient) columns, written in the export layout
+    // direct radix sort of (keys, coefficient) columns, written in the export
+    // layout: straight into the output arrays when they are pinned host memory
+    // the device can address, else into scratch and copied
     if (!ensure(ctx, ctx->scratch, export_sort_scratch_bytes(ctx->Wd, M)))
         return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    uint64_t* dx = (uint64_t*)pinned_device_view(x);
+    uint64_t* dz = (uint64_t*)pinned_device_view(z);
+    double* dc = (double*)pinned_device_view(coef);
+    const bool direct = dx && dz && dc;
     uint64_t* sx = nullptr;
     uint64_t* sz = nullptr;
     double* sc = nullptr;
-    launch_export_sort(W, ctx->Wd, ctx->rows(), ctx->c(), M, k, ctx->scratch.p, &sx, &sz, &sc, ctx->stream);
+    launch_export_sort(W, ctx->Wd, ctx->rows(), ctx->c(), M, k, ctx->scratch.p, direct ? dx : nullptr,
+                       direct ? dz : nullptr, direct ? dc : nullptr, &sx, &sz, &sc, ctx->stream);
     CK_LAUNCH();
-    CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    if (!direct) {
+        CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     return IQCC_OK;
 }

@@ -351,10 +351,12 @@ void launch_iota(uint32_t* p, int64_t n, cudaStream_t s);
 // compaction: out[rank] = in[i] for flags[i] != 0 (stable); count to *ctr_count (device).
 size_t compact_scratch_bytes(int64_t n);
 // k_keysort.cu: rows [0, n) and coefficients sorted in canonical order, the
-// first k written as x [k][W], z [k][W], coef [k] inside scratch (pointers out).
+// first k written as x [k][W], z [k][W], coef [k] into dst_* when all three
+// are device-writable addresses, else inside scratch (pointers out).
 size_t export_sort_scratch_bytes(int Wd, int64_t n);
 void launch_export_sort(int W, int Wd, const uint64_t* rows, const double* coef, int64_t n, int64_t k, void* scratch,
-                        uint64_t** out_x, uint64_t** out_z, double** out_c, cudaStream_t s);
+                        uint64_t* dst_x, uint64_t* dst_z, double* dst_c, uint64_t** out_x, uint64_t** out_z,
+                        double** out_c, cudaStream_t s);
 // adds to *count the consecutive pairs not strictly increasing in canonical order
 void launch_order_violations(int Wd, const uint64_t* rows, int64_t n, unsigned long long* count, cudaStream_t s);
 void launch_compact_rows(int Wd, const uint8_t* flags, const uint64_t* rows_in, const double* c_in,

@@ -424,3 +424,60 @@ def test_load_rejects_bits_above_n_qubits_in_a_large_input():
     with pytest.raises(iqcc.IqccError) as err:
         iqcc.iqcc_load_hamiltonian(n, x, z, c)
     assert err.value.status == 1
+
+
+def _host(shape, dtype, pinned):
+    """Zeroed host array; page-locked (torch's pinned allocator) when `pinned`."""
+    if not pinned:
+        return None, np.zeros(shape, dtype)
+    import torch
+    nbytes = int(np.prod(shape)) * np.dtype(dtype).itemsize
+    t = torch.zeros(max(nbytes, 8), dtype=torch.uint8, pin_memory=True)
+    return t, t.numpy()[:nbytes].view(dtype).reshape(shape)
+
+
+def _export_capped(H, cap, pinned=False):
+    """iqcc_export with a row limit (the first `cap` rows of the canonical
+    order), into pageable or page-locked host arrays."""
+    import ctypes
+    n = ctypes.c_int64(0)
+    keep = []
+    arrays = []
+    for shape, dtype in (((max(cap, 1), H.W), np.uint64), ((max(cap, 1), H.W), np.uint64), ((max(cap, 1),), np.float64)):
+        t, a = _host(shape, dtype, pinned)
+        keep.append(t)
+        arrays.append(a)
+    x, z, c = arrays
+    H._check(iqcc._export(H._h, cap, ctypes.byref(n), x.ctypes.data_as(iqcc._u64p), z.ctypes.data_as(iqcc._u64p),
+                          c.ctypes.data_as(iqcc._f64p)))
+    return n.value, x[:cap].copy(), z[:cap].copy(), c[:cap].copy()
+
+
+@pytest.mark.parametrize("n", [7, 64, 100, 130, 200])
+@pytest.mark.parametrize("n_gen", [0, 1, 4])
+def test_export_after_dressing_sorted_prefix_and_appended_rows(n, n_gen):
+    """Export of a loaded (sorted) table after 0, 1 or 4 dressings: no appended
+    rows, appended rows below half of the table (sorted prefix merged with the
+    sorted rest) and above half (full sort); full and row-limited exports, into
+    pageable arrays (through device scratch) and page-locked ones (written by
+    the device directly)."""
+    rng = np.random.Generator(np.random.PCG64(700 + n + n_gen))
+    _, x, z, c = synth.random_hamiltonian(n, 30_011, 800 + n, density=min(0.5, 12 / n))
+    o = oracle.Oracle(n, x, z, c)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    if n_gen:
+        gens = [synth.random_generator(n, rng, weight=3) for _ in range(n_gen)]
+        taus = rng.uniform(-1.2, 1.2, n_gen)
+        for (gx, gz), t in zip(gens, taus):
+            o.dress(gx, gz, t)
+        iqcc.iqcc_dress(H, np.array([g[0] for g in gens]), np.array([g[1] for g in gens]), taus)
+    full = iqcc.iqcc_export(H)
+    bad = compare(full, o.export())
+    assert not bad, bad[:5]
+    M = len(full[2])
+    for pinned in (False, True):
+        for cap in (1, M // 3 + 5, M - 1, M):
+            m, cx, cz, cc = _export_capped(H, cap, pinned)
+            assert m == M
+            assert np.array_equal(cx, full[0][:cap]) and np.array_equal(cz, full[1][:cap])
+            assert np.array_equal(cc, full[2][:cap])
