@@ -244,7 +244,55 @@ def measure_sort_variant(iqcc, n, x, z, c, th, ph, stream, n_gen=8, tau=0.1):
     return out
 
 
-def measure_batch(iqcc, synth, n_problems=64, seed=1000, eps=1e-10, screens=20):
+def measure_plain_form(iqcc, n, x, z, c, th, ph, n_gen=8, tau=0.1, max_rows=120_000_000, budget_s=40.0):
+    """The library's dress against the plain PyTorch-tensor form of the same
+    step (baseline/plain_gpu.py: bitwise ops, torch.unique over key rows,
+    index_add_) on the same GPU: the loaded Hamiltonian dressed by its top DIS
+    candidates at tau, generator by generator while the table holds at most
+    max_rows strings and the plain form stays within budget_s; wall time with a
+    device synchronize on both sides of every call."""
+    import torch
+    from baseline.plain_gpu import PlainHamiltonian
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 31)
+    gx, gz, _ = iqcc.iqcc_dis_gradients(H, th, ph, cap=n_gen)
+    H.close()
+    warm = PlainHamiltonian(n, x[:4096], z[:4096], c[:4096], device="cuda")  # first-call costs of the tensor ops
+    warm.dress(gx[0], gz[0], tau)
+    del warm
+    P = PlainHamiltonian(n, x, z, c, device="cuda")
+    m_in, t_plain = [], []
+    for k in range(len(gx)):
+        if len(P) > max_rows or sum(t_plain) > budget_s:
+            break
+        m_in.append(len(P))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        P.dress(gx[k], gz[k], tau)
+        torch.cuda.synchronize()
+        t_plain.append(time.perf_counter() - t0)
+    m_plain = len(P)
+    del P
+    torch.cuda.empty_cache()
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 31)
+    t_lib = []
+    for k in range(len(m_in)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        iqcc.iqcc_dress(H, gx[k:k + 1], gz[k:k + 1], np.array([tau]))
+        torch.cuda.synchronize()
+        t_lib.append(time.perf_counter() - t0)
+    m_lib = len(H)
+    H.close()
+    terms = sum(m_in)
+    return {"form": "plain PyTorch tensor ops on the same GPU (baseline/plain_gpu.py)",
+            "generators": f"top {len(m_in)} DIS candidates of the loaded Hamiltonian, tau = {tau}",
+            "M_in": m_in, "M_after": {"library": m_lib, "plain": m_plain},
+            "ms_plain": [round(t * 1e3, 2) for t in t_plain], "ms_library": [round(t * 1e3, 2) for t in t_lib],
+            "terms_per_s_plain": terms / sum(t_plain), "terms_per_s_library": terms / sum(t_lib),
+            "speedup": round(sum(t_plain) / sum(t_lib), 2)}
+
+
+def measure_batch(iqcc, synth, n_problems=256, seed=1000, eps=1e-10, screens=20):
     """Many small Jordan-Wigner Hamiltonians (12..40 qubits, even, decay
     integrals, basis reference): one batched step against one single-problem
     iteration per problem, and repeated screening by graph replay."""
@@ -395,7 +443,7 @@ def run_gpu(args):
     t_max, total_dressed = reduce_over_ranks(dist, dev_s, dressed, "cuda")
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
-    adjoint = sort_variant = screening = None
+    adjoint = sort_variant = screening = plain_form = None
     if rank == 0 and not args.no_extras:
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
         screening = measure_screening(iqcc, H, th, ph)
@@ -444,6 +492,7 @@ def run_gpu(args):
     batch_variant = None
     if rank == 0 and not args.no_extras:  # after the capped Hamiltonian is released
         sort_variant = measure_sort_variant(iqcc, n, x, z, c, th, ph, stream)
+        plain_form = measure_plain_form(iqcc, n, x, z, c, th, ph)
         batch_variant = measure_batch(iqcc, synth)
 
     if rank != 0:
@@ -469,7 +518,7 @@ def run_gpu(args):
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
                 "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant,
-                "learned_screening": screening}
+                "learned_screening": screening, "plain_gpu_form": plain_form}
 
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None
