@@ -310,8 +310,9 @@ void iqcc_free(iqcc_ctx* ctx);
  * every term from its key and coefficient; the term limit can keep the best
  * scores instead of the largest |C|.  Features of a term T (G = union of the
  * supports of the given generators, <T> at the Eq. 3 reference): log10|C|/8,
- * flipped qubits/16, Y letters/16, Z letters/32, |supp T & G|/8,
- * |flips of T & G|/8, <T>, and 1 when every flip of T lies in G.  The training
+ * min(flipped qubits, 16)/16, min(Y letters, 16)/16, Z letters on G/8,
+ * |supp T & G|/8, |flips of T & G|/8, <T>, and 1 when every flip of T lies
+ * in G (none grows with the number of qubits).  The training
  * target is log10 |C_T E_fut(T)| (iqcc_future_energies): by linearity of the
  * dress, removing T changes the energy after the following generators by
  * exactly -C_T E_fut(T).
@@ -341,8 +342,16 @@ iqcc_status iqcc_future_energies(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, c
 iqcc_status iqcc_term_scores(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
                              const double* theta, const double* phi, float* out);
 
+/* The magnitude floor of the learned term limit: frac (in [0, 1], default
+ * 0.5) of the limit goes to the largest |C| first, the rest to the best
+ * scores among the other terms, so a model that scores badly (outside the
+ * sizes it was trained on, say) can never drop the largest terms.  0 ranks
+ * every term by its score alone.  Errors: IQCC_ERR_ARG. */
+iqcc_status iqcc_set_screening_floor(iqcc_ctx* ctx, double frac);
+
 /* iqcc_prune with the term limit on the model's scores (ties of equal scores
- * in ascending canonical key order); eps still applies to |C|. */
+ * in ascending canonical key order) above the magnitude floor; eps still
+ * applies to |C|. */
 iqcc_status iqcc_prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_gen, const uint64_t* gx,
                                const uint64_t* gz, const double* theta, const double* phi, int64_t* n_removed);
 

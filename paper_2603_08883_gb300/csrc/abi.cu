@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -378,6 +379,51 @@ size_t sort_area_bytes(int64_t n) {
 
 // rank (device [M], may be NULL): the term limit keeps the largest |rank|
 // instead of the largest |C| (the magnitude threshold eps always uses |C|).
+// Radix select on the bit patterns of the non-negative doubles `key` among
+// the rows whose flag is set (`kept` of them), 12 bits at a time from the top,
+// until the bucket that holds the *need-th largest value has at most 65,536
+// rows.  Out: the bucket's bits (*prefix under *pmask) and, in *need, how many
+// of its rows are still needed.
+iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags, int64_t M, int64_t kept,
+                          int64_t* need, uint64_t* prefix_out, uint64_t* pmask_out) {
+    constexpr int64_t kBucketLimit = 1 << 16;
+    int64_t bucket = kept;
+    uint64_t prefix = 0, pmask = 0;
+    int hi = 63;
+    unsigned long long* hist12 = nullptr;
+    std::vector<unsigned long long> h(4096);
+    while (bucket > kBucketLimit && hi > 0) {
+        const int shift = std::max(0, hi - 12);
+        if (!hist12) {
+            if (!ensure(ctx, ctx->aux, 4096 * sizeof(unsigned long long)))
+                return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+            hist12 = (unsigned long long*)ctx->aux.p;
+        }
+        CK(cudaMemsetAsync(hist12, 0, 4096 * sizeof(unsigned long long), ctx->stream));
+        launch_abs_digit_hist12(key, flags, M, shift, prefix, pmask, hist12, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        int64_t cum = 0;
+        int sel = 0;
+        for (int d = 4095; d >= 0; --d) {
+            if (cum + (int64_t)h[d] >= *need) {
+                sel = d;
+                break;
+            }
+            cum += (int64_t)h[d];
+        }
+        *need -= cum;
+        bucket = (int64_t)h[sel];
+        prefix |= (uint64_t)sel << shift;
+        pmask |= (uint64_t)4095 << shift;
+        hi = shift;
+    }
+    *prefix_out = prefix;
+    *pmask_out = pmask & 0x7FFFFFFFFFFFFFFFull;
+    return IQCC_OK;
+}
+
 iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed, const double* rank = nullptr) {
     const int64_t M = ctx->M;
     *removed = 0;
@@ -408,41 +454,13 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     if (st) return st;
     const int64_t kept = (int64_t)ctx->h_counters->aux;
     if (max_terms > 0 && kept > max_terms) {
-        // Radix select on the |C| bit pattern, 12 bits at a time from the top,
-        // until the bucket holding the max_terms-th largest value is small; the
-        // bucket's rows are then ordered exactly by (|C| desc, canonical key asc).
-        constexpr int64_t kBucketLimit = 1 << 16;
-        int64_t need = max_terms, bucket = kept;
+        // Radix select on the |C| bit pattern (or the rank key) down to a small
+        // bucket; the bucket's rows are then ordered exactly by (|C| desc,
+        // canonical key asc).
+        int64_t need = max_terms;
         uint64_t prefix = 0, pmask = 0;
-        int hi = 63;
-        unsigned long long* hist12 = nullptr;
-        std::vector<unsigned long long> h(4096);
-        while (bucket > kBucketLimit && hi > 0) {
-            const int shift = std::max(0, hi - 12);
-            if (!hist12) {
-                if (!ensure(ctx, ctx->aux, 4096 * sizeof(unsigned long long)))
-                    return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-                hist12 = (unsigned long long*)ctx->aux.p;
-            }
-            CK(cudaMemsetAsync(hist12, 0, 4096 * sizeof(unsigned long long), ctx->stream));
-            launch_abs_digit_hist12(rank ? rank : ctx->c(), flags, M, shift, prefix, pmask, hist12, ctx->stream);
-            CK_LAUNCH();
-            CK(cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
-                               ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            int64_t cum = 0;
-            int sel = 0;
-            for (int d = 4095; d >= 0; --d) {
-                if (cum + (int64_t)h[d] >= need) { sel = d; break; }
-                cum += (int64_t)h[d];
-            }
-            need -= cum;
-            bucket = (int64_t)h[sel];
-            prefix |= (uint64_t)sel << shift;
-            pmask |= (uint64_t)4095 << shift;
-            hi = shift;
-        }
-        pmask &= 0x7FFFFFFFFFFFFFFFull;
+        st = select_bucket(ctx, rank ? rank : ctx->c(), flags, M, kept, &need, &prefix, &pmask);
+        if (st) return st;
         CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
         launch_bucket_flags(rank ? rank : ctx->c(), flags, M, prefix, pmask, ties, &c->aux, ctx->stream);
         CK_LAUNCH();
@@ -746,6 +764,44 @@ iqcc_status prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_ge
     double* tab = angles + 2 * ctx->n + 16;
     iqcc_status st = screen_scores(ctx, n_gen, gx, gz, theta, phi, rank, nullptr, angles, tab);
     if (st) return st;
+    // the magnitude floor: the floor x max_terms largest |C| (among |C| >= eps)
+    // outrank every score, so the learned limit never drops them
+    const int64_t M = ctx->M;
+    const int64_t keep_mag = (int64_t)(ctx->screen_floor * (double)max_terms);
+    if (max_terms > 0 && M > max_terms && keep_mag > 0) {
+        if (!ensure(ctx, ctx->scratch, (size_t)M + (size_t)8 * (1 << 16) + 1024))
+            return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        uint8_t* flags = (uint8_t*)ctx->scratch.p;
+        double* vals = (double*)((char*)ctx->scratch.p + ((M + 255) & ~(int64_t)255));
+        DevCounters* c = dctr(ctx);
+        CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream);
+        CK_LAUNCH();
+        st = read_counters(ctx);
+        if (st) return st;
+        const int64_t kept = (int64_t)ctx->h_counters->aux;
+        uint64_t t_bits = 0;  // every kept row when they are no more than keep_mag
+        if (kept > keep_mag) {
+            int64_t need = keep_mag;
+            uint64_t prefix = 0, pmask = 0;
+            st = select_bucket(ctx, ctx->c(), flags, M, kept, &need, &prefix, &pmask);
+            if (st) return st;
+            CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+            launch_bucket_values(ctx->c(), flags, M, prefix, pmask, vals, &c->aux, ctx->stream);
+            CK_LAUNCH();
+            st = read_counters(ctx);
+            if (st) return st;
+            const int64_t nb = (int64_t)ctx->h_counters->aux;
+            if (nb < need || nb > (1 << 16)) return fail(ctx, IQCC_ERR_STATE, "internal: floor bucket");
+            std::vector<uint64_t> hb((size_t)nb);
+            CK(cudaMemcpyAsync(hb.data(), vals, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+            CK(cudaStreamSynchronize(ctx->stream));
+            std::nth_element(hb.begin(), hb.begin() + (need - 1), hb.end(), std::greater<uint64_t>());
+            t_bits = hb[(size_t)(need - 1)];
+        }
+        launch_boost_rank(ctx->c(), flags, M, t_bits, 1e300, rank, ctx->stream);
+        CK_LAUNCH();
+    }
     CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
     return compress(ctx, eps, max_terms, removed, rank);
 }
@@ -1258,6 +1314,13 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
         CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_set_screening_floor(iqcc_ctx* ctx, double frac) {
+    GUARD(ctx);
+    if (!(frac >= 0.0 && frac <= 1.0)) return fail(ctx, IQCC_ERR_ARG, "floor must be in [0, 1]");
+    ctx->screen_floor = frac;
     return IQCC_OK;
 }
 

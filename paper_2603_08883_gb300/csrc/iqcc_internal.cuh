@@ -218,6 +218,7 @@ struct iqcc_ctx {
     iqcc_stats stats{};
     iqcc::Buf model;               // learned screening weights (device layout), when set
     iqcc::Buf screen_rank;         // learned screening: per-row keys and the <sigma> table
+    double screen_floor = 0.5;     // learned term limit: share kept by largest |C| first
 
     uint64_t* rows() const { return (uint64_t*)keys.p; }
     double* c() const { return (double*)coef.p; }
@@ -406,6 +407,12 @@ void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n
                              uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s);
 void launch_bucket_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
                          uint32_t* cand, unsigned long long* n_cand, cudaStream_t s);
+// |c| bit patterns (as doubles) of the kept rows in a select bucket, appended to vals
+void launch_bucket_values(const double* coef, const uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
+                          double* vals, unsigned long long* n_vals, cudaStream_t s);
+// rank[i] = boost where flags[i] and the |c| bits reach t_bits
+void launch_boost_rank(const double* coef, const uint8_t* flags, int64_t n, uint64_t t_bits, double boost, double* rank,
+                       cudaStream_t s);
 void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, const uint32_t* cand, int64_t k,
                            uint64_t* skeys, cudaStream_t s);
 void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s);

@@ -4,9 +4,13 @@
 // Features of a term T with coefficient C (kFeat of them, in FP32, from its key;
 // G = union of the supports of the iteration's generators, <T> at the
 // reference product state of Eq. 3):
-//   0  log10|C| / 8           1  flipped qubits / 16      2  Y letters / 16
-//   3  Z letters / 32          4  |supp T & G| / 8        5  |flips & G| / 8
-//   6  <T>                     7  1 when every flip of T lies in G (and T has one)
+//   0  log10|C| / 8           1  min(flipped qubits, 16) / 16
+//   2  min(Y letters, 16) / 16                           3  Z letters on G / 8
+//   4  |supp T & G| / 8        5  |flips & G| / 8        6  <T>
+//   7  1 when every flip of T lies in G (and T has one)
+// None grows with the number of qubits: the counts that could (flips, Y
+// letters) saturate, and Z letters count only on G (a Z off G neither changes
+// whether T commutes with a generator nor |<T>| at a basis reference).
 // Model: 8 -> 256 -> 256 -> 1 with ReLU, BF16 weights and activations, FP32
 // accumulation, on the tensor cores (mma.sync m16n8k16).  One warp scores 16
 // terms at a time: layer 1 is one MMA per 8 hidden units; its accumulator
@@ -63,14 +67,14 @@ __device__ __forceinline__ float log10_abs(double c) {
 template <int W>
 __device__ __forceinline__ void term_features(const Key<W>& t, double c, const GenSupport<W>& gs, const float* ev,
                                               float* f) {
-    int flips = 0, ys = 0, zs = 0, ov = 0, fov = 0;
+    int flips = 0, ys = 0, zg = 0, ov = 0, fov = 0;
     float e = 1.0f;
 #pragma unroll
     for (int wd = 0; wd < W; ++wd) {
         const uint64_t x = t.x[wd], z = t.z[wd];
         flips += __popcll(x);
         ys += __popcll(x & z);
-        zs += __popcll(z & ~x);
+        zg += __popcll(z & ~x & gs.g[wd]);
         ov += __popcll((x | z) & gs.g[wd]);
         fov += __popcll(x & gs.g[wd]);
         uint64_t m = x | z;
@@ -82,9 +86,9 @@ __device__ __forceinline__ void term_features(const Key<W>& t, double c, const G
         }
     }
     f[0] = log10_abs(c) / 8.0f;
-    f[1] = flips / 16.0f;
-    f[2] = ys / 16.0f;
-    f[3] = zs / 32.0f;
+    f[1] = min(flips, 16) / 16.0f;
+    f[2] = min(ys, 16) / 16.0f;
+    f[3] = zg / 8.0f;
     f[4] = ov / 8.0f;
     f[5] = fov / 8.0f;
     f[6] = e;

@@ -500,6 +500,25 @@ __global__ void k_abs_digit_hist12(const double* __restrict__ coef, const uint8_
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
+// |C| of the kept rows inside the bucket (bits under prefix_mask equal prefix), appended to vals.
+__global__ void k_bucket_values(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
+                                uint64_t prefix, uint64_t prefix_mask, double* vals, unsigned long long* n_vals) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        if (!flags[i]) continue;
+        const uint64_t b = abs_bits(coef[i]);
+        if ((b & prefix_mask) == prefix) vals[atomicAdd(n_vals, 1ull)] = __longlong_as_double((long long)b);
+    }
+}
+
+// rank[i] = boost for kept rows with |C| >= t (t given by its bit pattern).
+__global__ void k_boost_rank(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
+                             uint64_t t_bits, double boost, double* rank) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s)
+        if (flags[i] && abs_bits(coef[i]) >= t_bits) rank[i] = boost;
+}
+
 // Kept rows above the threshold bucket stay kept; rows in it become candidates
 // (listed, flag cleared); rows below are dropped.
 __global__ void k_bucket_flags(const double* __restrict__ coef, uint8_t* flags, int64_t n, uint64_t prefix,
@@ -786,6 +805,22 @@ void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n
                              uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s) {
     if (n > 0) {
         k_abs_digit_hist12<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift, prefix, prefix_mask, hist);
+        note_launch();
+    }
+}
+
+void launch_bucket_values(const double* coef, const uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
+                          double* vals, unsigned long long* n_vals, cudaStream_t s) {
+    if (n > 0) {
+        k_bucket_values<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, prefix, prefix_mask, vals, n_vals);
+        note_launch();
+    }
+}
+
+void launch_boost_rank(const double* coef, const uint8_t* flags, int64_t n, uint64_t t_bits, double boost, double* rank,
+                       cudaStream_t s) {
+    if (n > 0) {
+        k_boost_rank<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, t_bits, boost, rank);
         note_launch();
     }
 }

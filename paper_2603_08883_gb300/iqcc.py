@@ -84,6 +84,7 @@ _load = _sig("iqcc_load_hamiltonian", _c, [ctypes.POINTER(_vp), ctypes.POINTER(i
                                            _u64p, _f64p])
 _dress = _sig("iqcc_dress", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.POINTER(ctypes.c_int)])
 _set_model = _sig("iqcc_set_screening_model", _c, [_vp, _f32p, _f32p, _f32p, _f32p, _f32p, ctypes.c_float])
+_set_floor = _sig("iqcc_set_screening_floor", _c, [_vp, ctypes.c_double])
 _features = _sig("iqcc_term_features", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f32p])
 _future = _sig("iqcc_future_energies", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f64p, _f64p])
 _scores = _sig("iqcc_term_scores", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f32p])
@@ -235,6 +236,11 @@ def iqcc_set_screening_model(H: Hamiltonian, w1, b1, w2, b2, w3, b3: float) -> N
     if [a.size for a in arrs] != [256 * 8, 256, 256 * 256, 256, 256]:
         raise ValueError("weight shapes: w1 [256, 8], b1 [256], w2 [256, 256], b2 [256], w3 [256]")
     H._check(_set_model(H._h, *[a.ctypes.data_as(_f32p) for a in arrs], float(b3)))
+
+
+def iqcc_set_screening_floor(H: Hamiltonian, frac: float) -> None:
+    """Share of the learned term limit kept by largest |C| first (0..1; 0.5 by default)."""
+    H._check(_set_floor(H._h, float(frac)))
 
 
 def iqcc_term_features(H: Hamiltonian, theta, phi, gx=None, gz=None) -> np.ndarray:

@@ -40,10 +40,11 @@ def test_future_energies_match_dressed_single_strings(n, angles):
         assert fut[i] == pytest.approx(ref, abs=1e-12), i
 
 
-@pytest.mark.parametrize("n", [12, 100])
-def test_features_match_their_definition(n):
+@pytest.mark.parametrize("n,density", [(12, 0.2), (100, 0.2), (200, 0.5)])
+def test_features_match_their_definition(n, density):
+    """Including strings past the saturation of the flip and Y counts (200 qubits, half of them set)."""
     rng = np.random.Generator(np.random.PCG64(5 + n))
-    _, x, z, c = synth.random_hamiltonian(n, 300, 80 + n, density=0.2)
+    _, x, z, c = synth.random_hamiltonian(n, 300, 80 + n, density=density)
     th, ph = synth.qmf_angles(n, "uniform", seed=2)
     gens = [synth.random_generator(n, rng, weight=3) for _ in range(2)]
     gx = np.array([g[0] for g in gens])
@@ -56,9 +57,9 @@ def test_features_match_their_definition(n):
         xi, zi = ex[i], ez[i]
         flips = _popc_rows(xi)[0]
         fov = _popc_rows(xi & G)[0]
-        want = [math.log10(abs(ec[i])) / 8, flips / 16, _popc_rows(xi & zi)[0] / 16, _popc_rows(zi & ~xi)[0] / 32,
-                _popc_rows((xi | zi) & G)[0] / 8, fov / 8, _single_energy(n, xi, zi, th, ph),
-                1.0 if (flips > 0 and fov == flips) else 0.0]
+        want = [math.log10(abs(ec[i])) / 8, min(flips, 16) / 16, min(_popc_rows(xi & zi)[0], 16) / 16,
+                _popc_rows(zi & ~xi & G)[0] / 8, _popc_rows((xi | zi) & G)[0] / 8, fov / 8,
+                _single_energy(n, xi, zi, th, ph), 1.0 if (flips > 0 and fov == flips) else 0.0]
         assert np.allclose(f[i], want, rtol=1e-5, atol=1e-6), (i, f[i], want)  # FP32 features
 
 
@@ -112,6 +113,7 @@ def test_learned_term_limit_keeps_the_best_scores():
     gx, gz = synth.random_generator(n, rng, weight=3)
     H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
     iqcc.iqcc_set_screening_model(H, *_random_model(7))
+    iqcc.iqcc_set_screening_floor(H, 0.0)
     s = iqcc.iqcc_term_scores(H, th, ph, gx, gz)
     ex, ez, ec = iqcc.iqcc_export(H)
     keep = 7000
@@ -122,6 +124,45 @@ def test_learned_term_limit_keeps_the_best_scores():
     assert removed == len(s) - keep and len(H) == keep
     kx, kz, kc = iqcc.iqcc_export(H)
     assert {(a.tobytes(), b.tobytes()) for a, b in zip(kx, kz)} == expect
+
+
+@pytest.mark.parametrize("m,floor", [(20_000, 0.4), (20_000, 1.0), (150_000, 0.5)])
+def test_learned_term_limit_keeps_its_magnitude_floor(m, floor):
+    """The floor x limit largest |C| are kept first, then the best scores among
+    the other terms (150,000 terms: the floor's threshold comes out of the
+    12-bit radix select, then an exact pick inside its bucket)."""
+    n = 30
+    rng = np.random.Generator(np.random.PCG64(4))
+    _, x, z, c = synth.random_hamiltonian(n, m, 35, density=0.3)
+    th, ph = synth.qmf_angles(n, "basis")
+    gx, gz = synth.random_generator(n, rng, weight=3)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    iqcc.iqcc_set_screening_model(H, *_random_model(8))
+    iqcc.iqcc_set_screening_floor(H, floor)
+    s = iqcc.iqcc_term_scores(H, th, ph, gx, gz)
+    ex, ez, ec = iqcc.iqcc_export(H)
+    keep = int(0.35 * len(ec))
+    n_mag = int(floor * keep)
+    by_mag = sorted(range(len(ec)), key=lambda i: (-abs(ec[i]), i))
+    top = set(by_mag[:n_mag])
+    rank = np.maximum(s, -1000).astype(np.float64) + 1024.0
+    rest = sorted((i for i in range(len(ec)) if i not in top), key=lambda i: (-rank[i], i))
+    chosen = list(top) + rest[:keep - len(top)]
+    expect = {(ex[i].tobytes(), ez[i].tobytes()) for i in chosen}
+    removed = iqcc.iqcc_prune_learned(H, 0.0, keep, th, ph, gx, gz)
+    assert removed == len(ec) - keep and len(H) == keep
+    kx, kz, kc = iqcc.iqcc_export(H)
+    assert {(a.tobytes(), b.tobytes()) for a, b in zip(kx, kz)} == expect
+
+
+def test_screening_floor_rejects_values_outside_the_unit_interval():
+    _, x, z, c = synth.random_hamiltonian(10, 100, 3)
+    H = iqcc.iqcc_load_hamiltonian(10, x, z, c)
+    for bad in (-0.1, 1.5, float("nan")):
+        with pytest.raises(iqcc.IqccError):
+            iqcc.iqcc_set_screening_floor(H, bad)
+    iqcc.iqcc_set_screening_floor(H, 0.0)
+    iqcc.iqcc_set_screening_floor(H, 1.0)
 
 
 def test_iteration_with_learned_screening_runs_and_respects_the_cap():
