@@ -27,6 +27,8 @@
 // factors times the derivative at k0 directly; two or more zero factors: none.
 // Block sums live in shared memory (FP64 atomic adds) and are reduced column by
 // column.
+#include <cooperative_groups.h>
+#include <cooperative_groups/reduce.h>
 #include <cuda_runtime.h>
 
 #include "iqcc_internal.cuh"
@@ -166,7 +168,15 @@ __device__ __forceinline__ double string_basis(const Key<W>& s, double wc, const
     if (flips == 0) return sign;
     if (wc != 0.0) {
         const double dt = tab[kTab * k0 + 4 + l0];
-        if (dt != 0.0) atomicAdd(acc + 3 * n + k0, wc * sign * dt);
+        if (dt != 0.0) {
+            // single-flip strings pile onto few qubits: lanes with the same
+            // qubit sum their terms first, one shared-memory atomic per qubit
+            namespace cg = cooperative_groups;
+            const cg::coalesced_group g = cg::coalesced_threads();
+            const cg::coalesced_group same = cg::labeled_partition(g, k0);
+            const double sum = cg::reduce(same, wc * sign * dt, cg::plus<double>());
+            if (same.thread_rank() == 0) atomicAdd(acc + 3 * n + k0, sum);
+        }
     }
     return 0.0;
 }
