@@ -188,6 +188,48 @@ def measure_adjoint(iqcc, H, n, th, ph, stream):
     return out
 
 
+def measure_joint_optimisation(iqcc, H, th, ph, max_iter=8):
+    """Joint optimisation of the QMF angles and one amplitude on H as it
+    stands: L-BFGS (strong Wolfe) on E(theta, phi, tau) with the top DIS
+    candidate as generator and tau = 0 to start; every evaluation is one
+    adjoint pass (energy and all gradients).  Two starts: the workload's
+    basis angles (every string flips an even number of qubits, so the angle
+    gradients vanish there and only tau moves), and those angles with seeded
+    N(0, 0.05) noise (general angles: all 2n + 1 variables move)."""
+    import torch
+    from paper_2603_08883_gb300.autograd import dressed_energy
+    cx, cz, _ = iqcc.iqcc_dis_gradients(H, th, ph, cap=1)
+    rng = np.random.Generator(np.random.PCG64(21))
+    n = len(th)
+    out = {"M": len(H), "generator": "top DIS candidate", "optimiser": f"L-BFGS, strong Wolfe, max_iter {max_iter}"}
+    for name, (t0_, p0_) in (("basis_start", (th, ph)),
+                             ("perturbed_start", (th + rng.normal(0, 0.05, n), ph + rng.normal(0, 0.05, n)))):
+        theta = torch.tensor(t0_, dtype=torch.float64, requires_grad=True)
+        phi = torch.tensor(p0_, dtype=torch.float64, requires_grad=True)
+        tau = torch.tensor(0.0, dtype=torch.float64, requires_grad=True)
+        f = lambda: dressed_energy(H, theta, phi, tau, cx[0], cz[0])
+        e0 = float(f().detach())
+        opt = torch.optim.LBFGS([theta, phi, tau], max_iter=max_iter, line_search_fn="strong_wolfe")
+        evals = [0]
+
+        def closure():
+            opt.zero_grad()
+            e = f()
+            e.backward()
+            evals[0] += 1
+            return e
+        t0 = time.perf_counter()
+        opt.step(closure)
+        dt = time.perf_counter() - t0
+        e1 = float(f().detach())
+        out[name] = {"energy_start": e0, "energy_end": e1, "tau_end": float(tau.detach()),
+                     "max_angle_change": float(max((theta.detach() - torch.tensor(t0_)).abs().max(),
+                                                   (phi.detach() - torch.tensor(p0_)).abs().max())),
+                     "evaluations": evals[0], "s": round(dt, 2),
+                     "ms_per_evaluation": round(dt / max(evals[0], 1) * 1e3, 1)}
+    return out
+
+
 def measure_screening(iqcc, H, th, ph):
     """The learned-screening perceptron (tensor cores, mma.sync BF16 / FP32)
     scoring every term of H as it stands: 2 (8 x 256 + 256 x 256 + 256) =
@@ -446,6 +488,7 @@ def run_gpu(args):
     adjoint = sort_variant = screening = plain_form = None
     if rank == 0 and not args.no_extras:
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
+        adjoint["joint_optimisation"] = measure_joint_optimisation(iqcc, H, th, ph)
         screening = measure_screening(iqcc, H, th, ph)
 
     # ---------------- end to end through host buffers (pinned), N = 1 path of a user
