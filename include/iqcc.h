@@ -304,6 +304,41 @@ const char* iqcc_last_error(const iqcc_ctx* ctx);
 void iqcc_free(iqcc_ctx* ctx);
 
 /* ------------------------------------------------------------------------
+ * Partitioned dressing (App. B's bit-wise partitioning, as a data layout).
+ * A Hamiltonian may be split over several contexts by the values of chosen
+ * key bits: one context per partition, on one GPU or one per GPU.  A
+ * generator P that flips none of those bits keeps every pair inside its
+ * partition: each context runs iqcc_dress.  A generator that flips some of
+ * them pairs every anticommuting row T of partition a with its partner
+ * T xor P in partition a xor (P's partition bits); the two contexts then
+ * exchange their anticommuting rows (iqcc_cross_rows) and each applies the
+ * dress to its own rows with the other's (iqcc_dress_cross).  Energies,
+ * A, B, C and DIS gradients are sums over the contexts.
+ * ------------------------------------------------------------------------ */
+
+/* The rows of H that anticommute with P (gx, gz: host [W]): *n = their count;
+ * min(cap, *n) of them written to x, z [cap][W] and coef [cap] (host), in no
+ * particular order.  cap = 0 is a size query.  H is not changed.  Errors:
+ * IQCC_ERR_ARG, IQCC_ERR_OOM, IQCC_ERR_CUDA. */
+iqcc_status iqcc_cross_rows(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, int64_t cap, int64_t* n,
+                            uint64_t* x, uint64_t* z, double* coef);
+
+/* Dress H by P at amplitude tau (Eq. 5, library sign) when the partner
+ * T xor P of every anticommuting row of H lives in the peer partition, whose
+ * anticommuting rows are given (px, pz [n_peer][W], pcoef [n_peer], host,
+ * distinct keys; the output of iqcc_cross_rows on the peer).  A local row K
+ * that anticommutes becomes C_K cos(tau) + s_T C_T sin(tau) when the peer
+ * holds T = K xor P (i T P = s_T P(K)), else C_K cos(tau); each peer row T
+ * whose partner K has no local row appends (K, s_T C_T sin(tau)).  With both
+ * sides of a pair of partitions called with the other's rows, the union is
+ * exactly iqcc_dress on the unsplit Hamiltonian.  Errors (H unchanged):
+ * IQCC_ERR_ARG (bad arguments, peer key bits above n_qubits),
+ * IQCC_ERR_CAPACITY (M + n_peer rows above capacity), IQCC_ERR_OOM;
+ * IQCC_ERR_HASH_FULL, IQCC_ERR_CUDA. */
+iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, double tau, int64_t n_peer,
+                             const uint64_t* px, const uint64_t* pz, const double* pcoef);
+
+/* ------------------------------------------------------------------------
  * Learned term screening (no counterpart in the paper, which limits terms by
  * magnitude).  A perceptron (8 features -> 256 -> 256 -> 1, ReLU, BF16
  * weights and activations with FP32 accumulation on the tensor cores) scores

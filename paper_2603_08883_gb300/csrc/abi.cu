@@ -956,6 +956,112 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
     return IQCC_OK;
 }
 
+iqcc_status iqcc_cross_rows(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, int64_t cap, int64_t* n,
+                            uint64_t* x, uint64_t* z, double* coef) {
+    GUARD(ctx);
+    if (!gx || !gz || !n) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    if (cap < 0) return fail(ctx, IQCC_ERR_ARG, "cap < 0");
+    if (bits_above_n(ctx, gx) || bits_above_n(ctx, gz)) return fail(ctx, IQCC_ERR_ARG, "generator bits above n_qubits");
+    *n = 0;
+    const int64_t M = ctx->M;
+    if (M == 0) return IQCC_OK;
+    const int64_t k = std::min(cap, M);
+    if (k > 0 && (!x || !z || !coef)) return fail(ctx, IQCC_ERR_ARG, "null output array");
+    uint64_t pk[8];
+    pad_key(ctx, gx, gz, pk);
+    const int W = ctx->W;
+    Carver cv;
+    cv.take<uint64_t>((size_t)k * W);
+    cv.take<uint64_t>((size_t)k * W);
+    cv.take<double>(k);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint64_t* dx = cv.take<uint64_t>((size_t)k * W);
+    uint64_t* dz = cv.take<uint64_t>((size_t)k * W);
+    double* dc = cv.take<double>(k);
+    DevCounters* c = dctr(ctx);
+    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    launch_cross_rows(ctx->Wd, ctx->rows(), ctx->c(), M, pk, W, k, dx, dz, dc, &c->aux, ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    *n = (int64_t)ctx->h_counters->aux;
+    const int64_t out = std::min(*n, k);
+    if (out > 0) {
+        CK(cudaMemcpyAsync(x, dx, sizeof(uint64_t) * out * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(z, dz, sizeof(uint64_t) * out * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(coef, dc, sizeof(double) * out, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+    }
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, double tau, int64_t n_peer,
+                             const uint64_t* px, const uint64_t* pz, const double* pcoef) {
+    GUARD(ctx);
+    if (!gx || !gz) return fail(ctx, IQCC_ERR_ARG, "null generator");
+    if (n_peer < 0) return fail(ctx, IQCC_ERR_ARG, "n_peer < 0");
+    if (n_peer > 0 && (!px || !pz || !pcoef)) return fail(ctx, IQCC_ERR_ARG, "null peer array");
+    if (!std::isfinite(tau)) return fail(ctx, IQCC_ERR_ARG, "non-finite amplitude");
+    if (bits_above_n(ctx, gx) || bits_above_n(ctx, gz)) return fail(ctx, IQCC_ERR_ARG, "generator bits above n_qubits");
+    uint64_t pk[8];
+    pad_key(ctx, gx, gz, pk);
+    const int64_t M = ctx->M;
+    const int64_t upper = M + n_peer;  // at most one appended row per received row
+    if (upper > ctx->capacity) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "dress would need up to %lld rows, capacity is %lld", (long long)upper,
+                 (long long)ctx->capacity);
+        return fail(ctx, IQCC_ERR_CAPACITY, buf);
+    }
+    iqcc_status st = reserve_rows(ctx, std::max<int64_t>(upper, 1));
+    if (st) return st;
+    const int W = ctx->W, Wd = ctx->Wd;
+    const uint64_t pslots = pow2_at_least((uint64_t)std::max<int64_t>(4 * n_peer, 64));  // load <= 1/4
+    Carver cv;
+    cv.take<uint64_t>((size_t)n_peer * W);
+    cv.take<uint64_t>((size_t)n_peer * W);
+    cv.take<uint64_t>((size_t)n_peer * 2 * Wd);
+    cv.take<double>(n_peer);
+    cv.take<uint64_t>(pslots);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint64_t* dx = cv.take<uint64_t>((size_t)n_peer * W);
+    uint64_t* dz = cv.take<uint64_t>((size_t)n_peer * W);
+    uint64_t* prow = cv.take<uint64_t>((size_t)n_peer * 2 * Wd);
+    double* pc = cv.take<double>(n_peer);
+    uint64_t* ps = cv.take<uint64_t>(pslots);
+    DevCounters* c = dctr(ctx);
+    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    HashView hp{ps, pslots / kBucketSlots - 1, ctx->max_probe};
+    if (n_peer > 0) {
+        CK(cudaMemcpyAsync(dx, px, sizeof(uint64_t) * n_peer * W, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(dz, pz, sizeof(uint64_t) * n_peer * W, cudaMemcpyHostToDevice, ctx->stream));
+        CK(cudaMemcpyAsync(pc, pcoef, sizeof(double) * n_peer, cudaMemcpyHostToDevice, ctx->stream));
+        const int r = ctx->n - 64 * (W - 1);
+        const uint64_t hi_mask = r >= 64 ? 0ull : ~((1ull << r) - 1);
+        launch_pack_rows(W, Wd, dx, dz, prow, n_peer, ctx->stream, hi_mask, &c->n_new);
+        launch_hash_clear(hp, pslots, ctx->stream);
+        launch_hash_insert(Wd, prow, 0, n_peer, hp, c, ctx->stream);
+        CK_LAUNCH();
+        st = read_counters(ctx);
+        if (st) return st;
+        if (ctx->h_counters->n_new != 0) return fail(ctx, IQCC_ERR_ARG, "peer key bits set above n_qubits");
+    }
+    launch_cross_dress(Wd, ctx->rows(), ctx->c(), M, pk, std::cos(tau), std::sin(tau), hash_view(ctx), hp, prow, pc,
+                       n_peer, c, ctx->stream);
+    CK_LAUNCH();
+    st = read_counters(ctx);
+    if (st) return st;
+    const int64_t n_new = (int64_t)ctx->h_counters->n_new;
+    ctx->M = M + n_new;
+    iqcc_stats& sx = ctx->stats;  // counted as a dress; its time is not in dress_kernel_ms
+    sx.n_dress++;
+    sx.dressed_terms += M;
+    sx.appended += n_new;
+    return IQCC_OK;
+}
+
 iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* tau,
                        int* n_applied) {
     if (n_applied) *n_applied = 0;

@@ -285,6 +285,15 @@ void launch_seg_abc(const uint64_t* rows, const double* coef, int64_t M, const u
                     const unsigned long long* best_key, double* partials, int blocks, cudaStream_t s);
 void launch_seg_tau(const double* abc, const unsigned long long* best_key, int B, double* tau, Gen<1>* gens,
                     cudaStream_t s);
+// partitioned dressing (k_dress.cu): the anticommuting rows of P appended to
+// ox/oz [.][Wout] and oc (at most cap; the count in *n_out), and the dress of
+// the local rows given the peer's anticommuting rows (prow/pcoef, indexed by hp)
+void launch_cross_rows(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, int Wout,
+                       int64_t cap, uint64_t* ox, uint64_t* oz, double* oc, unsigned long long* n_out,
+                       cudaStream_t s);
+void launch_cross_dress(int Wd, const uint64_t* rows, double* coef, int64_t M, const uint64_t* pkey, double cos_t,
+                        double sin_t, HashView h, HashView hp, const uint64_t* prow, const double* pcoef,
+                        int64_t n_peer, DevCounters* ctr, cudaStream_t s);
 void launch_dress_seg(const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M, const Gen<1>* gens, int B,
                       HashView h, DevCounters* ctr, cudaStream_t s);
 

@@ -310,6 +310,123 @@ __global__ void __launch_bounds__(kThreads) k_dress_count(const uint64_t* __rest
     if (lane == 0 && cnt) atomicAdd(&ctr->n_new, (unsigned long long)cnt);
 }
 
+// Partitioned dressing.  When H is split over several contexts by key bits
+// and P flips one of those bits, the partner Q = T xor P of every
+// anticommuting row T lies in the peer partition, so the pair rotation of
+// Eq. 5 takes one exchange: each side sends its anticommuting rows to the
+// peer (k_cross_rows), updates its own rows from the received ones
+// (k_cross_local: C_K <- C_K cos + s_T C_T sin for the received T = K xor P,
+// where i T P = s_T P(K)), and appends the partners that have no row on its
+// side (k_cross_append: (K, s_T C_T sin)).
+
+// The anticommuting rows, appended (warp-aggregated) as x [.][W], z [.][W], c.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_cross_rows(const uint64_t* __restrict__ rows,
+                                                         const double* __restrict__ coef, int64_t M, Key<W> p,
+                                                         int Wout, int64_t cap, uint64_t* ox, uint64_t* oz,
+                                                         double* oc, unsigned long long* n_out) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t M32 = (M + 31) & ~(int64_t)31;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M32; i += stride) {
+        Key<W> t{};
+        bool a = false;
+        if (i < M) {
+            t = load_key<W>(rows, i);
+            a = anticommutes<W>(t, p);
+        }
+        const unsigned m = __ballot_sync(FULL, a);
+        if (!m) continue;
+        const int leader = __ffs(m) - 1;
+        unsigned long long base = 0;
+        if (lane == leader) base = atomicAdd(n_out, (unsigned long long)__popc(m));
+        base = __shfl_sync(FULL, base, leader);
+        if (a) {
+            const int64_t r = (int64_t)base + __popc(m & ((1u << lane) - 1u));
+            if (r < cap) {
+                for (int j = 0; j < Wout; ++j) {
+                    ox[r * Wout + j] = t.x[j];
+                    oz[r * Wout + j] = t.z[j];
+                }
+                oc[r] = coef[i];
+            }
+        }
+    }
+}
+
+// Local rows: C_K <- C_K cos(tau) + s_T C_T sin(tau) when the peer holds
+// T = K xor P (looked up in the peer's rows through their own index).
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_cross_local(const uint64_t* __restrict__ rows, double* coef, int64_t M,
+                                                          Gen<W> g, HashView hp, const uint64_t* __restrict__ prow,
+                                                          const double* __restrict__ pcoef, DevCounters* ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const Key<W> k = load_key<W>(rows, i);
+        if (!anticommutes<W>(k, g.p)) continue;
+        const Key<W> t = key_xor<W>(k, g.p);
+        uint64_t fslot = 0;
+        double ct = 0.0;
+        const int64_t j = lookup_slot_coef<W>(t, hash_key<W>(t), hp, prow, pcoef, &fslot, &ct);
+        const double ck = coef[i];
+        if (j >= 0) {
+            const double s = (double)product_sign<W>(t, g.yP, g.p, k);
+            coef[i] = ck * g.cos_t + s * ct * g.sin_t;
+        } else if (j == -1) {
+            coef[i] = ck * g.cos_t;
+        } else {
+            set_error(ctr, IQCC_ERR_HASH_FULL, 60);
+        }
+    }
+}
+
+// Received rows T whose partner K = T xor P has no local row: append
+// (K, s_T C_T sin(tau)) behind the M local rows and index it.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_cross_append(const uint64_t* __restrict__ prow,
+                                                           const double* __restrict__ pcoef, int64_t n_peer, Gen<W> g,
+                                                           const uint64_t* __restrict__ rows, uint64_t* rows_app,
+                                                           double* coef, int64_t M, HashView h, DevCounters* ctr) {
+    const unsigned FULL = 0xFFFFFFFFu;
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t n32 = (n_peer + 31) & ~(int64_t)31;
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n32; j += stride) {
+        bool append = false;
+        Key<W> k{};
+        uint64_t hv = 0, fslot = 0;
+        double c_new = 0.0;
+        if (j < n_peer) {
+            const Key<W> t = load_key<W>(prow, j);
+            if (anticommutes<W>(t, g.p)) {
+                k = key_xor<W>(t, g.p);
+                hv = hash_key<W>(k);
+                const int64_t idx = lookup_slot<W>(k, hv, h, rows, &fslot);
+                if (idx == -1) {
+                    append = true;
+                    c_new = (double)product_sign<W>(t, g.yP, g.p, k) * pcoef[j] * g.sin_t;
+                } else if (idx == -2) {
+                    set_error(ctr, IQCC_ERR_HASH_FULL, 61);
+                }
+            }
+        }
+        const unsigned need = __ballot_sync(FULL, append);
+        if (!need) continue;
+        const int leader = __ffs(need) - 1;
+        unsigned long long slot0 = 0;
+        if (lane == leader) slot0 = atomicAdd(&ctr->n_new, (unsigned long long)__popc(need));
+        slot0 = __shfl_sync(FULL, slot0, leader);
+        if (append) {
+            const int64_t r = M + (int64_t)slot0 + __popc(need & lt);
+            store_key<W>(rows_app, r, k);
+            coef[r] = c_new;
+            if (!insert_from(hv, (uint32_t)r, fslot, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 62);
+        }
+    }
+}
+
 template <int W>
 Gen<W> make_gen(const uint64_t* pkey, double cos_t, double sin_t) {
     Gen<W> g{};
@@ -344,6 +461,47 @@ int grid_for_slots(uint64_t slots) {
 }
 
 }  // namespace
+
+void launch_cross_rows(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, int Wout,
+                       int64_t cap, uint64_t* ox, uint64_t* oz, double* oc, unsigned long long* n_out,
+                       cudaStream_t s) {
+    if (M <= 0) return;
+    const int grid = grid_for(M, 8);
+    switch (Wd) {
+        case 1: k_cross_rows<1><<<grid, kThreads, 0, s>>>(rows, coef, M, make_gen<1>(pkey, 1, 0).p, Wout, cap, ox, oz, oc, n_out); break;
+        case 2: k_cross_rows<2><<<grid, kThreads, 0, s>>>(rows, coef, M, make_gen<2>(pkey, 1, 0).p, Wout, cap, ox, oz, oc, n_out); break;
+        default: k_cross_rows<4><<<grid, kThreads, 0, s>>>(rows, coef, M, make_gen<4>(pkey, 1, 0).p, Wout, cap, ox, oz, oc, n_out); break;
+    }
+    note_launch();
+}
+
+void launch_cross_dress(int Wd, const uint64_t* rows, double* coef, int64_t M, const uint64_t* pkey, double cos_t,
+                        double sin_t, HashView h, HashView hp, const uint64_t* prow, const double* pcoef,
+                        int64_t n_peer, DevCounters* ctr, cudaStream_t s) {
+    const int g1 = grid_for(M, 8), g2 = grid_for(n_peer, 8);
+    uint64_t* rows_app = const_cast<uint64_t*>(rows);
+    switch (Wd) {
+        case 1: {
+            const Gen<1> g = make_gen<1>(pkey, cos_t, sin_t);
+            if (M > 0) k_cross_local<1><<<g1, kThreads, 0, s>>>(rows, coef, M, g, hp, prow, pcoef, ctr);
+            if (n_peer > 0) k_cross_append<1><<<g2, kThreads, 0, s>>>(prow, pcoef, n_peer, g, rows, rows_app, coef, M, h, ctr);
+            break;
+        }
+        case 2: {
+            const Gen<2> g = make_gen<2>(pkey, cos_t, sin_t);
+            if (M > 0) k_cross_local<2><<<g1, kThreads, 0, s>>>(rows, coef, M, g, hp, prow, pcoef, ctr);
+            if (n_peer > 0) k_cross_append<2><<<g2, kThreads, 0, s>>>(prow, pcoef, n_peer, g, rows, rows_app, coef, M, h, ctr);
+            break;
+        }
+        default: {
+            const Gen<4> g = make_gen<4>(pkey, cos_t, sin_t);
+            if (M > 0) k_cross_local<4><<<g1, kThreads, 0, s>>>(rows, coef, M, g, hp, prow, pcoef, ctr);
+            if (n_peer > 0) k_cross_append<4><<<g2, kThreads, 0, s>>>(prow, pcoef, n_peer, g, rows, rows_app, coef, M, h, ctr);
+            break;
+        }
+    }
+    note_launch((M > 0) + (n_peer > 0));
+}
 
 int sm_count() {
     static int n = 0;

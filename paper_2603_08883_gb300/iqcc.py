@@ -83,6 +83,9 @@ _c = ctypes.c_int
 _load = _sig("iqcc_load_hamiltonian", _c, [ctypes.POINTER(_vp), ctypes.POINTER(iqcc_opts), ctypes.c_int64, _u64p,
                                            _u64p, _f64p])
 _dress = _sig("iqcc_dress", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.POINTER(ctypes.c_int)])
+_cross_rows = _sig("iqcc_cross_rows", _c, [_vp, _u64p, _u64p, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
+_dress_cross = _sig("iqcc_dress_cross", _c, [_vp, _u64p, _u64p, ctypes.c_double, ctypes.c_int64, _u64p, _u64p,
+                                             _f64p])
 _set_model = _sig("iqcc_set_screening_model", _c, [_vp, _f32p, _f32p, _f32p, _f32p, _f32p, ctypes.c_float])
 _set_floor = _sig("iqcc_set_screening_floor", _c, [_vp, ctypes.c_double])
 _features = _sig("iqcc_term_features", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, _f64p, _f32p])
@@ -211,6 +214,31 @@ def iqcc_dress(H: Hamiltonian, gx, gz, tau) -> int:
     applied = ctypes.c_int(0)
     H._check(_dress(H._h, len(gxa), gxp, gzp, tp, ctypes.byref(applied)))
     return applied.value
+
+
+def iqcc_cross_rows(H: Hamiltonian, gx, gz):
+    """The rows that anticommute with P, for the peer partition: (x [k, W], z [k, W], c [k])."""
+    gxa, gxp = _u64(gx, (H.W,))
+    gza, gzp = _u64(gz, (H.W,))
+    n = ctypes.c_int64(0)
+    H._check(_cross_rows(H._h, gxp, gzp, 0, ctypes.byref(n), None, None, None))
+    k = n.value
+    x = np.zeros((max(k, 1), H.W), np.uint64)
+    z = np.zeros((max(k, 1), H.W), np.uint64)
+    c = np.zeros(max(k, 1))
+    H._check(_cross_rows(H._h, gxp, gzp, k, ctypes.byref(n), x.ctypes.data_as(_u64p), z.ctypes.data_as(_u64p),
+                         c.ctypes.data_as(_f64p)))
+    return x[:k], z[:k], c[:k]
+
+
+def iqcc_dress_cross(H: Hamiltonian, gx, gz, tau: float, px, pz, pc) -> None:
+    """Dress by P given the peer partition's anticommuting rows (from iqcc_cross_rows on the peer)."""
+    gxa, gxp = _u64(gx, (H.W,))
+    gza, gzp = _u64(gz, (H.W,))
+    pxa, pxp = _u64(px, (-1, H.W))
+    pza, pzp = _u64(pz, (-1, H.W))
+    pca, pcp = _f64(pc, len(pxa))
+    H._check(_dress_cross(H._h, gxp, gzp, float(tau), len(pxa), pxp, pzp, pcp))
 
 
 def iqcc_dress_sorted(H: Hamiltonian, gx, gz, tau, fuse: int = 1) -> int:

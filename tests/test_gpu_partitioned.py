@@ -1,0 +1,94 @@
+"""Partitioned dressing on one GPU (App. B's bit-wise partitioning): a
+Hamiltonian split over 2 or 4 contexts by key bits, dressed through
+iqcc_cross_rows / iqcc_dress_cross for generators that flip a partition bit
+and iqcc_dress otherwise, against the oracle dressing the whole H."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_08883_gb300 import partitioned as pt
+from paper_2603_08883_gb300 import synth
+from tests.compare import compare
+
+pytestmark = pytest.mark.gpu
+
+iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc")
+
+
+def _masks(n, parts):
+    W = (n + 63) // 64
+    mx = np.zeros(W, np.uint64)
+    mz = np.zeros(W, np.uint64)
+    mx[0] = np.uint64(1 << 3)
+    if parts == 4:
+        mz[W - 1] = np.uint64(1 << ((n - 1) % 64))  # the last qubit's z bit
+    return mx, mz
+
+
+@pytest.mark.parametrize("n,m,seed", [(24, 20_000, 1), (100, 30_011, 2), (200, 12_007, 3)])
+@pytest.mark.parametrize("parts", [2, 4])
+def test_partitioned_steps_match_the_oracle(n, m, seed, parts):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    _, x, z, c = synth.random_hamiltonian(n, m, 100 + seed, density=min(0.5, 12 / n))
+    th, ph = synth.qmf_angles(n, "uniform", seed=seed)
+    mx, mz = _masks(n, parts)
+    P = pt.PartitionedHamiltonian(n, x, z, c, mx, mz)
+    assert len(P.parts) == parts and len(P) == len(c)
+    o = oracle.Oracle(n, x, z, c)
+    shifts = []
+    for k in range(6):
+        gx, gz = synth.random_generator(n, rng, weight=3)
+        if k % 2 == 0:  # every other generator flips the first partition bit (x of qubit 3)
+            gx, gz = gx.copy(), gz.copy()
+            gx[0] |= np.uint64(1 << 3)
+            if sum(bin(int(a & b)).count("1") for a, b in zip(gx, gz)) % 2 == 0:
+                gz[0] ^= np.uint64(1 << 3)  # X <-> Y on qubit 3: keeps an odd number of Y letters
+        shifts.append(pt.generator_shift(gx, gz, mx, mz))
+        a, b, cc = o.abc(gx, gz, th, ph)
+        pa, pb, pc = P.abc(gx, gz, th, ph)
+        assert (pa, pb, pc) == pytest.approx((a, b, cc), abs=1e-10)
+        tau = P.step(gx, gz, th, ph)
+        o.dress(gx, gz, tau)
+    assert any(s != 0 for s in shifts)
+    bad = compare(P.export(), o.export())
+    assert not bad, bad[:5]
+    assert P.energy(th, ph) == pytest.approx(o.energy(th, ph), abs=1e-9)
+    P.close()
+
+
+def test_cross_rows_are_the_anticommuting_rows():
+    n = 100
+    rng = np.random.Generator(np.random.PCG64(9))
+    _, x, z, c = synth.random_hamiltonian(n, 5000, 19, density=0.2)
+    gx, gz = synth.random_generator(n, rng, weight=4)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    rx, rz, rc = iqcc.iqcc_cross_rows(H, gx, gz)
+    anti = [((bin(int(a[0] & gz[0])).count("1") + bin(int(a[1] & gz[1])).count("1")
+              + bin(int(b[0] & gx[0])).count("1") + bin(int(b[1] & gx[1])).count("1")) & 1) == 1
+            for a, b in zip(x, z)]
+    want = {(a.tobytes(), b.tobytes(), float(cc)) for a, b, cc, f in zip(x, z, c, anti) if f}
+    assert {(a.tobytes(), b.tobytes(), float(cc)) for a, b, cc in zip(rx, rz, rc)} == want
+    assert len(rc) == sum(anti) > 0
+
+
+def test_dress_cross_errors_leave_h_unchanged():
+    n = 30
+    _, x, z, c = synth.random_hamiltonian(n, 400, 5, density=0.3)
+    rng = np.random.Generator(np.random.PCG64(5))
+    gx, gz = synth.random_generator(n, rng, weight=2)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=450)
+    before = iqcc.iqcc_export(H)
+    px, pz, pc = x[:100], z[:100], c[:100]
+    with pytest.raises(iqcc.IqccError) as e:      # 400 + 100 rows above the capacity
+        iqcc.iqcc_dress_cross(H, gx, gz, 0.3, px, pz, pc)
+    assert e.value.status == 4
+    bad_z = pz.copy()
+    bad_z[7, 0] |= np.uint64(1 << 40)            # a bit above n_qubits
+    H2 = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_dress_cross(H2, gx, gz, 0.3, px, bad_z, pc)
+    assert e.value.status == 1
+    for got, want in zip(iqcc.iqcc_export(H), before):
+        assert np.array_equal(got, want)
+    for got, want in zip(iqcc.iqcc_export(H2), before):
+        assert np.array_equal(got, want)
