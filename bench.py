@@ -334,6 +334,48 @@ def measure_plain_form(iqcc, n, x, z, c, th, ph, n_gen=8, tau=0.1, max_rows=120_
             "speedup": round(sum(t_plain) / sum(t_lib), 2)}
 
 
+def measure_partitioned(iqcc, n, x, z, c, th, ph, n_gen=8, tau=0.1):
+    """The loaded Hamiltonian split in two contexts by the x bit of one qubit
+    (App. B's bit-wise partitioning on one GPU, paper_2603_08883_gb300/
+    partitioned.py), dressed by its top DIS candidates at tau; the qubit is
+    the one most of those generators flip, and each generator that flips it
+    exchanges the anticommuting rows of both parts through the host.  Wall
+    time with a device synchronize around the whole sequence, against the
+    same sequence on one context."""
+    import torch
+    from paper_2603_08883_gb300 import partitioned as pt
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 31)
+    gx, gz, _ = iqcc.iqcc_dis_gradients(H, th, ph, cap=n_gen)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    iqcc.iqcc_dress(H, gx, gz, np.full(len(gx), tau))
+    torch.cuda.synchronize()
+    t_one = time.perf_counter() - t0
+    m_one = len(H)
+    H.close()
+    W = (n + 63) // 64
+    flips = [sum((int(g[j // 64]) >> (j % 64)) & 1 for g in gx) for j in range(n)]
+    qubit = int(np.argmax(flips))
+    mx = np.zeros(W, np.uint64)
+    mz = np.zeros(W, np.uint64)
+    mx[qubit // 64] = np.uint64(1 << (qubit % 64))
+    P = pt.PartitionedHamiltonian(n, x, z, c, mx, mz, capacity=1 << 31)
+    parts_m0 = [len(h) for h in P.parts]
+    crossing = sum(pt.generator_shift(a, b, mx, mz) != 0 for a, b in zip(gx, gz))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for a, b in zip(gx, gz):
+        P.dress(a, b, tau)
+    torch.cuda.synchronize()
+    t_two = time.perf_counter() - t0
+    out = {"split": f"x bit of qubit {qubit}", "parts_M0": parts_m0,
+           "generators": f"top {len(gx)} DIS candidates of the loaded Hamiltonian, tau = {tau}",
+           "crossing_generators": int(crossing), "M_after": {"one_context": m_one, "partitioned": len(P)},
+           "ms_one_context": round(t_one * 1e3, 2), "ms_partitioned": round(t_two * 1e3, 2)}
+    P.close()
+    return out
+
+
 def measure_batch(iqcc, synth, n_problems=256, seed=1000, eps=1e-10, screens=20):
     """Many small Jordan-Wigner Hamiltonians (12..40 qubits, even, decay
     integrals, basis reference): one batched step against one single-problem
@@ -485,7 +527,7 @@ def run_gpu(args):
     t_max, total_dressed = reduce_over_ranks(dist, dev_s, dressed, "cuda")
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
-    adjoint = sort_variant = screening = plain_form = None
+    adjoint = sort_variant = screening = plain_form = partitioned = None
     if rank == 0 and not args.no_extras:
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
         adjoint["joint_optimisation"] = measure_joint_optimisation(iqcc, H, th, ph)
@@ -536,6 +578,7 @@ def run_gpu(args):
     if rank == 0 and not args.no_extras:  # after the capped Hamiltonian is released
         sort_variant = measure_sort_variant(iqcc, n, x, z, c, th, ph, stream)
         plain_form = measure_plain_form(iqcc, n, x, z, c, th, ph)
+        partitioned = measure_partitioned(iqcc, n, x, z, c, th, ph)
         batch_variant = measure_batch(iqcc, synth)
 
     if rank != 0:
@@ -561,7 +604,7 @@ def run_gpu(args):
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
                 "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant,
-                "learned_screening": screening, "plain_gpu_form": plain_form}
+                "learned_screening": screening, "plain_gpu_form": plain_form, "partitioned_variant": partitioned}
 
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None
