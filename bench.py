@@ -252,6 +252,32 @@ def measure_screening(iqcc, H, th, ph):
             "frac": round(tf / peak[0], 4) if peak[0] else None}
 
 
+def measure_random_access_peak(words=1 << 30, gathers=1 << 27, reps=3):
+    """Random-access rate of this GPU's HBM: torch.gather of 8-byte words at
+    uniformly random positions of an 8 GB table (every access its own DRAM
+    sector); the best of `reps` timed runs, CUDA events."""
+    import torch
+    table = torch.ones(words, dtype=torch.int64, device="cuda")
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    idx = torch.randint(0, words, (gathers,), device="cuda", generator=g)
+    out = torch.empty(gathers, dtype=torch.int64, device="cuda")
+    torch.gather(table, 0, idx, out=out)
+    best = None
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.gather(table, 0, idx, out=out)
+        e1.record()
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del table, idx, out
+    torch.cuda.empty_cache()
+    return gathers / (best / 1e3)
+
+
 def measured_peak_tensor():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -527,8 +553,21 @@ def run_gpu(args):
     t_max, total_dressed = reduce_over_ranks(dist, dev_s, dressed, "cuda")
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
-    adjoint = sort_variant = screening = plain_form = partitioned = None
+    adjoint = sort_variant = screening = plain_form = partitioned = random_access = None
     if rank == 0 and not args.no_extras:
+        # the dress kernel's random fetches per launch: every anticommuting row probes
+        # one bucket; a row whose partner is present also reads the partner's key, and
+        # the member that rotates the pair (half of them) its coefficient
+        n_d = max(stats["n_dress"], 1)
+        anti, new = stats["anticommuting"] / n_d, stats["appended"] / n_d
+        fetches = new + 2.5 * (anti - new)
+        launch_s = stats["dress_kernel_ms"] / 1e3 / n_d
+        peak_ra = measure_random_access_peak()
+        random_access = {"fetches_per_launch": fetches, "achieved_G_per_s": round(fetches / launch_s / 1e9, 2),
+                         "peak_G_per_s": round(peak_ra / 1e9, 2), "frac": round(fetches / launch_s / peak_ra, 4),
+                         "peak_kind": "measured here: torch.gather of 8-byte words at random from an 8 GB "
+                                      "table (random reads only)", "model": "bucket probe per anticommuting row; partner key "
+                                      "per row with a present partner; partner coefficient for the rotating half"}
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
         adjoint["joint_optimisation"] = measure_joint_optimisation(iqcc, H, th, ph)
         screening = measure_screening(iqcc, H, th, ph)
@@ -604,6 +643,7 @@ def run_gpu(args):
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
                 "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant,
+                "random_access": random_access,
                 "learned_screening": screening, "plain_gpu_form": plain_form, "partitioned_variant": partitioned}
 
     # ---------------- oracle on the host cores (N = 1 only)
