@@ -52,6 +52,54 @@ def test_energy_gradients_match_oracle(n, kind, with_gen):
         assert e == pytest.approx(a + b * np.cos(tau) + cc * np.sin(tau), rel=1e-12, abs=1e-13 * scale)
 
 
+def _chain_hamiltonian(n, m, rng):
+    """Jordan-Wigner-like strings: X or Y at p < q and Z on every qubit between
+    (runs of Z letters, many crossing the 64-qubit word boundary), some with a
+    second chain, plus random strings."""
+    W = (n + 63) // 64
+    xs, zs = [], []
+    for _ in range(m):
+        xb = np.zeros(n, bool)
+        zb = np.zeros(n, bool)
+        for _ in range(int(rng.integers(1, 3))):
+            p, q = sorted(rng.choice(n, 2, replace=False))
+            zb[p + 1:q] ^= True
+            for k in (p, q):
+                xb[k] = True
+                zb[k] = bool(rng.integers(0, 2))
+        xs.append(xb)
+        zs.append(zb)
+    pack = lambda b: np.array([[int("".join("1" if v else "0" for v in row[64 * w:64 * w + 64][::-1]) or "0", 2)
+                                for w in range(W)] for row in b], np.uint64)
+    x, z = pack(np.array(xs)), pack(np.array(zs))
+    keys = np.unique(np.concatenate([x, z], 1), axis=0)
+    c = rng.standard_normal(len(keys))
+    return keys[:, :W].copy(), keys[:, W:].copy(), c
+
+
+@pytest.mark.parametrize("n", [70, 100, 200])
+@pytest.mark.parametrize("with_gen", [False, True])
+def test_energy_gradients_of_z_chains_at_general_angles(n, with_gen):
+    """Long Z runs take the run-difference sums of the general path; runs
+    that cross a word boundary included."""
+    rng = np.random.Generator(np.random.PCG64(500 + n + with_gen))
+    x, z, c = _chain_hamiltonian(n, 2000, rng)
+    theta, phi = _angles(n, "general", rng)
+    gx = gz = None
+    tau = 0.0
+    if with_gen:
+        gx, gz = synth.random_generator(n, rng, weight=3)
+        tau = 0.7
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    o = oracle.Oracle(n, x, z, c)
+    got = iqcc.iqcc_energy_gradients(H, theta, phi, gx, gz, tau)
+    ref = o.energy_gradients(theta, phi, gx, gz, tau)
+    scale = float(np.abs(c).sum())
+    for g, r in zip(got, ref):
+        ok, worst = _close(g, r, scale)
+        assert ok, worst
+
+
 def test_energy_gradients_edge_cases():
     n = 6
     # identity only: constant energy, zero gradient
