@@ -32,6 +32,9 @@ sys.path.insert(0, ROOT)
 L2_BYTES = 129 * 1024 * 1024
 METRIC = "dressed Pauli terms/s, 100-qubit iQCC iteration"
 UNIT = "terms/s"
+# strings of the 100-qubit workload the oracle runs on per step (the reference arm and cpu_baseline);
+# fewer than about 4000 give no DIS candidate, hence nothing to dress
+REFERENCE_ROWS = 8000
 
 
 def parse():
@@ -471,7 +474,7 @@ def run_reference(args):
     w = synth.WORKLOADS[args.workload]
     n, x, z, c = synth.workload_hamiltonian(w)
     th, ph = synth.workload_angles(w)
-    rows = 4000
+    rows = REFERENCE_ROWS
     for _ in range(args.warmup):
         oracle_dressed(w, n, x, z, c, th, ph, rows)
     tot, dt = 0, 0.0
@@ -649,7 +652,7 @@ def run_gpu(args):
     # ---------------- oracle on the host cores (N = 1 only)
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
-        rows = 8000
+        rows = REFERENCE_ROWS
         d, t = oracle_dressed(w, n, x, z, c, th, ph, rows)
         cpu = {"value": d / t, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"one oracle iteration (DIS, {w.n_gen} x (A,B,C + dress + term limit), compression, "
