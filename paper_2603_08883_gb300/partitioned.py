@@ -159,7 +159,8 @@ def _send_recv(dist, peer: int, arrays):
     n_out = int(k[0])
     out = []
     for a in arrays:  # empty messages are skipped on both sides (each knows both counts)
-        flat = np.ascontiguousarray(a).reshape(a.shape[0], -1)
+        width = int(np.prod(a.shape[1:])) if a.ndim > 1 else 1
+        flat = np.ascontiguousarray(a).reshape(a.shape[0], width)
         as_i64 = flat.view(np.int64) if flat.dtype == np.uint64 else flat
         buf = torch.zeros((n_in, flat.shape[1]), dtype=torch.from_numpy(as_i64[:0]).dtype)
         req = dist.isend(torch.from_numpy(np.ascontiguousarray(as_i64)), peer) if n_out else None

@@ -160,3 +160,46 @@ def test_exchange_over_gloo_matches_the_oracle_on_the_whole_hamiltonian(world, m
     union = tuple(np.concatenate([r[1][i] for r in res]) for i in range(3))
     bad = compare(union, o.export())
     assert not bad, bad[:5]
+
+
+def _rank_empty_side(rank, world, port, q):
+    """Partition 1 starts empty: it sends no rows and receives every partner it must append."""
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        n = 6
+        mx = np.array([1 << 0], np.uint64)
+        mz = np.array([0], np.uint64)
+        x = np.array([[0], [2], [4]], np.uint64)          # all with x bit 0 clear: partition 0
+        z = np.array([[1], [3], [0]], np.uint64)
+        c = np.array([0.5, -1.25, 2.0])
+        sel = pt.partition_of(x, z, mx, mz) == rank
+        eng = DictEngine(n, x[sel], z[sel], c[sel])
+        gx, gz = np.array([1], np.uint64), np.array([1], np.uint64)  # Y on qubit 0: flips partition bit 0
+        pt.exchange_dress(eng, dist, rank, gx, gz, 0.4, mx, mz)
+        q.put((rank, eng.arrays()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_exchange_with_an_empty_partition():
+    port = _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_empty_side, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted((q.get(timeout=120) for _ in range(2)), key=lambda r: r[0])
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    x = np.array([[0], [2], [4]], np.uint64)
+    z = np.array([[1], [3], [0]], np.uint64)
+    c = np.array([0.5, -1.25, 2.0])
+    o = oracle.Oracle(6, x, z, c)
+    o.dress(np.array([1], np.uint64), np.array([1], np.uint64), 0.4)
+    union = tuple(np.concatenate([r[1][i] for r in res]) for i in range(3))
+    assert len(res[1][1][2]) > 0                        # the empty side received and appended partners
+    bad = compare(union, o.export())
+    assert not bad, bad[:5]
