@@ -1034,6 +1034,7 @@ iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* 
     DevCounters* c = dctr(ctx);
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
     HashView hp{ps, pslots / kBucketSlots - 1, ctx->max_probe};
+    launch_hash_clear(hp, pslots, ctx->stream);  // also when no row came: every local lookup then misses
     if (n_peer > 0) {
         CK(cudaMemcpyAsync(dx, px, sizeof(uint64_t) * n_peer * W, cudaMemcpyHostToDevice, ctx->stream));
         CK(cudaMemcpyAsync(dz, pz, sizeof(uint64_t) * n_peer * W, cudaMemcpyHostToDevice, ctx->stream));
@@ -1041,7 +1042,6 @@ iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* 
         const int r = ctx->n - 64 * (W - 1);
         const uint64_t hi_mask = r >= 64 ? 0ull : ~((1ull << r) - 1);
         launch_pack_rows(W, Wd, dx, dz, prow, n_peer, ctx->stream, hi_mask, &c->n_new);
-        launch_hash_clear(hp, pslots, ctx->stream);
         launch_hash_insert(Wd, prow, 0, n_peer, hp, c, ctx->stream);
         CK_LAUNCH();
         st = read_counters(ctx);

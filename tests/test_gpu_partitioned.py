@@ -92,3 +92,30 @@ def test_dress_cross_errors_leave_h_unchanged():
         assert np.array_equal(got, want)
     for got, want in zip(iqcc.iqcc_export(H2), before):
         assert np.array_equal(got, want)
+
+
+def test_partitioned_dress_with_an_empty_side():
+    """One partition empty: it sends no rows, scales nothing and appends every
+    partner; the other side rotates against an empty peer set (cos(tau) only)."""
+    n = 40
+    rng = np.random.Generator(np.random.PCG64(12))
+    _, x, z, c = synth.random_hamiltonian(n, 3000, 77, density=0.25)
+    x = x.copy()
+    x[:, 0] &= ~np.uint64(1 << 3)                    # every string in partition 0
+    keys = np.unique(np.concatenate([x, z], 1), axis=0, return_index=True)[1]
+    x, z, c = x[keys], z[keys], c[keys]
+    mx, mz = _masks(n, 2)
+    P = pt.PartitionedHamiltonian(n, x, z, c, mx, mz)
+    assert len(P.parts[1]) == 0
+    o = oracle.Oracle(n, x, z, c)
+    gx, gz = synth.random_generator(n, rng, weight=3)
+    gx, gz = gx.copy(), gz.copy()
+    gx[0] |= np.uint64(1 << 3)
+    if sum(bin(int(a & b)).count("1") for a, b in zip(gx, gz)) % 2 == 0:
+        gz[0] ^= np.uint64(1 << 3)
+    P.dress(gx, gz, 0.35)
+    o.dress(gx, gz, 0.35)
+    assert len(P.parts[1]) > 0
+    bad = compare(P.export(), o.export())
+    assert not bad, bad[:5]
+    P.close()
