@@ -787,17 +787,23 @@ iqcc_status prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_ge
             st = select_bucket(ctx, ctx->c(), flags, M, kept, &need, &prefix, &pmask);
             if (st) return st;
             CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-            launch_bucket_values(ctx->c(), flags, M, prefix, pmask, vals, &c->aux, ctx->stream);
+            launch_bucket_values(ctx->c(), flags, M, prefix, pmask, vals, &c->aux, 1 << 16, ctx->stream);
             CK_LAUNCH();
             st = read_counters(ctx);
             if (st) return st;
             const int64_t nb = (int64_t)ctx->h_counters->aux;
-            if (nb < need || nb > (1 << 16)) return fail(ctx, IQCC_ERR_STATE, "internal: floor bucket");
-            std::vector<uint64_t> hb((size_t)nb);
-            CK(cudaMemcpyAsync(hb.data(), vals, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
-            CK(cudaStreamSynchronize(ctx->stream));
-            std::nth_element(hb.begin(), hb.begin() + (need - 1), hb.end(), std::greater<uint64_t>());
-            t_bits = hb[(size_t)(need - 1)];
+            if (nb < need) return fail(ctx, IQCC_ERR_STATE, "internal: floor bucket");
+            if (nb > (1 << 16)) {
+                // more than 65,536 rows left in the bucket only when all 63 bits are
+                // fixed: they share one |C|, the threshold, and all of them are kept
+                t_bits = prefix;
+            } else {
+                std::vector<uint64_t> hb((size_t)nb);
+                CK(cudaMemcpyAsync(hb.data(), vals, sizeof(uint64_t) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+                CK(cudaStreamSynchronize(ctx->stream));
+                std::nth_element(hb.begin(), hb.begin() + (need - 1), hb.end(), std::greater<uint64_t>());
+                t_bits = hb[(size_t)(need - 1)];
+            }
         }
         launch_boost_rank(ctx->c(), flags, M, t_bits, 1e300, rank, ctx->stream);
         CK_LAUNCH();

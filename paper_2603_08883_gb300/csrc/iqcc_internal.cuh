@@ -416,9 +416,10 @@ void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n
                              uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s);
 void launch_bucket_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
                          uint32_t* cand, unsigned long long* n_cand, cudaStream_t s);
-// |c| bit patterns (as doubles) of the kept rows in a select bucket, appended to vals
+// |c| bit patterns (as doubles) of the kept rows in a select bucket, appended to
+// vals (at most cap; *n_vals counts all)
 void launch_bucket_values(const double* coef, const uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
-                          double* vals, unsigned long long* n_vals, cudaStream_t s);
+                          double* vals, unsigned long long* n_vals, int64_t cap, cudaStream_t s);
 // rank[i] = boost where flags[i] and the |c| bits reach t_bits
 void launch_boost_rank(const double* coef, const uint8_t* flags, int64_t n, uint64_t t_bits, double boost, double* rank,
                        cudaStream_t s);

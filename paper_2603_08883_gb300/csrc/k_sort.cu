@@ -500,14 +500,18 @@ __global__ void k_abs_digit_hist12(const double* __restrict__ coef, const uint8_
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
-// |C| of the kept rows inside the bucket (bits under prefix_mask equal prefix), appended to vals.
+// |C| of the kept rows inside the bucket (bits under prefix_mask equal prefix),
+// appended to vals (at most cap of them; *n_vals counts them all).
 __global__ void k_bucket_values(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
-                                uint64_t prefix, uint64_t prefix_mask, double* vals, unsigned long long* n_vals) {
+                                uint64_t prefix, uint64_t prefix_mask, double* vals, unsigned long long* n_vals,
+                                unsigned long long cap) {
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
         if (!flags[i]) continue;
         const uint64_t b = abs_bits(coef[i]);
-        if ((b & prefix_mask) == prefix) vals[atomicAdd(n_vals, 1ull)] = __longlong_as_double((long long)b);
+        if ((b & prefix_mask) != prefix) continue;
+        const unsigned long long k = atomicAdd(n_vals, 1ull);
+        if (k < cap) vals[k] = __longlong_as_double((long long)b);
     }
 }
 
@@ -810,9 +814,10 @@ void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n
 }
 
 void launch_bucket_values(const double* coef, const uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
-                          double* vals, unsigned long long* n_vals, cudaStream_t s) {
+                          double* vals, unsigned long long* n_vals, int64_t cap, cudaStream_t s) {
     if (n > 0) {
-        k_bucket_values<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, prefix, prefix_mask, vals, n_vals);
+        k_bucket_values<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, prefix, prefix_mask, vals, n_vals,
+                                                                   (unsigned long long)cap);
         note_launch();
     }
 }

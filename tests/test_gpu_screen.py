@@ -155,6 +155,26 @@ def test_learned_term_limit_keeps_its_magnitude_floor(m, floor):
     assert {(a.tobytes(), b.tobytes()) for a, b in zip(kx, kz)} == expect
 
 
+def test_magnitude_floor_with_more_equal_magnitudes_than_a_bucket_holds():
+    """150,000 terms of |C| = 1: the floor's threshold bucket cannot be narrowed
+    below 65,536 rows; every term ties at the threshold, so the limit keeps the
+    first terms in canonical order."""
+    n = 30
+    rng = np.random.Generator(np.random.PCG64(6))
+    _, x, z, c = synth.random_hamiltonian(n, 150_000, 36, density=0.3)
+    c = np.where(rng.integers(0, 2, len(c)) == 1, 1.0, -1.0)
+    th, ph = synth.qmf_angles(n, "basis")
+    gx, gz = synth.random_generator(n, rng, weight=3)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    iqcc.iqcc_set_screening_model(H, *_random_model(9))
+    ex, ez, ec = iqcc.iqcc_export(H)
+    keep = 40_000
+    removed = iqcc.iqcc_prune_learned(H, 0.0, keep, th, ph, gx, gz)
+    assert removed == len(ec) - keep and len(H) == keep
+    kx, kz, kc = iqcc.iqcc_export(H)
+    assert np.array_equal(kx, ex[:keep]) and np.array_equal(kz, ez[:keep]) and np.array_equal(kc, ec[:keep])
+
+
 def test_screening_floor_rejects_values_outside_the_unit_interval():
     _, x, z, c = synth.random_hamiltonian(10, 100, 3)
     H = iqcc.iqcc_load_hamiltonian(10, x, z, c)
