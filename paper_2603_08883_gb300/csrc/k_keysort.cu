@@ -14,11 +14,13 @@
 //
 // Rows keep their relative order through dressing and compaction, so a table
 // that was loaded in canonical order is still sorted up to its first appended
-// term.  The longest sorted prefix is found first; when it holds at least half
-// of the rows only the rest is radix sorted, and the two sorted runs are then
-// merged tile by tile straight into the export layout (merge path: the split of
-// every tile boundary by binary search, then inside a tile every element's
-// place is its index in its own run plus its rank in the other run).
+// term.  The longest sorted prefix is found first; only the rest is radix
+// sorted, and the two sorted runs are merged tile by tile straight into the
+// export layout (merge path: the split of every tile boundary by binary
+// search, then inside a tile every element's place is its index in its own run
+// plus its rank in the other run).  The merge writes page-locked host memory
+// directly when given it; into device scratch it needs the prefix to hold
+// about half of the rows (else all rows are sorted).
 #include <cuda_runtime.h>
 
 #include "iqcc_internal.cuh"
