@@ -274,14 +274,17 @@ iqcc_status iqcc_reset_stats(iqcc_ctx* ctx);
  * QMF energy (as iqcc_qmf_energy) of rows the caller already holds in device
  * memory, computed without allocating any device memory.  The paper has no
  * counterpart; it is for callers that cannot allocate when they need the
- * energy: code recording a CUDA stream capture, a plug-in whose host framework
- * owns all device memory, a service with a fixed footprint once started.
+ * energy: a plug-in whose host framework owns all device memory through its
+ * own allocator, a service that must keep a fixed footprint once started.
  *
  * d_rows: device [n_terms][2*Wd] uint64, x words then z words of each string,
  * Wd = 1 (n_qubits <= 64), 2 (<= 128) or 4 (<= 256), words above ceil(n/64)
  * zero; d_coef: device [n_terms] double.  Repeated strings simply add.
  * theta, phi: host [n_qubits]; energy: host double; stream: cudaStream_t or
- * NULL.  Returns after synchronising the stream.
+ * NULL.  Returns after synchronising the stream; the angles are copied from
+ * host memory and the result read back, so the call cannot be recorded in a
+ * CUDA graph: on a stream that is being captured it returns IQCC_ERR_ARG
+ * without issuing any work (the capture stays valid).
  *
  * Scratch is one fixed device array inside the library (234 kB per GPU that
  * loads it, held until the process exits), shared by every call: it limits
@@ -289,7 +292,7 @@ iqcc_status iqcc_reset_stats(iqcc_ctx* ctx);
  * to 4096 blocks.  Calls that overlap on the GPU (other streams, other host
  * threads) race on it and must be serialised by the caller.  The first call
  * on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.
+ * that device current.
  * Errors: IQCC_ERR_ARG, IQCC_ERR_CUDA; message in iqcc_last_error(NULL).
  */
 iqcc_status iqcc_qmf_energy_noalloc(int n_qubits, int64_t n_terms, const uint64_t* d_rows,

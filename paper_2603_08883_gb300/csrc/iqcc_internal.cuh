@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <string>
 
 #include "../../include/iqcc.h"
@@ -231,7 +232,12 @@ namespace iqcc {
 // ----------------------------------------------------------------------------
 
 int device_words(int n);
-int sm_count();
+int current_device();
+int sm_count();  // of the current device
+// True on the first call for the current device with this `seen` mask, and
+// for every call on devices past the 64th: per-device set-up such as
+// cudaFuncSetAttribute, whose settings belong to each device's context.
+bool first_on_device(std::atomic<unsigned long long>* seen);
 void note_launch();     // counts kernel launches of the library (all launchers call it)
 void note_launch(int k);  // k launches
 long long launches();

@@ -503,15 +503,37 @@ void launch_cross_dress(int Wd, const uint64_t* rows, double* coef, int64_t M, c
     note_launch((M > 0) + (n_peer > 0));
 }
 
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    return dev;
+}
+
+// Cached per device: a process may use several GPUs of different sizes.
 int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    constexpr int kDevices = 64;
+    static std::atomic<int> counts[kDevices];
+    const int dev = current_device();
+    int n = dev >= 0 && dev < kDevices ? counts[dev].load(std::memory_order_relaxed) : 0;
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            n = 0;
+        }
         if (n <= 0) n = 1;
+        if (dev >= 0 && dev < kDevices) counts[dev].store(n, std::memory_order_relaxed);
     }
     return n;
+}
+
+bool first_on_device(std::atomic<unsigned long long>* seen) {
+    const int dev = current_device();
+    if (dev < 0 || dev >= 64) return true;
+    const unsigned long long bit = 1ull << dev;
+    return (seen->fetch_or(bit, std::memory_order_relaxed) & bit) == 0;
 }
 
 int device_words(int n) { return n <= 64 ? 1 : (n <= 128 ? 2 : 4); }

@@ -364,11 +364,9 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
         k_abc<W, true><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
     } else {
         size_t smem = (size_t)n_groups * 256 * sizeof(double);
-        static bool attr = false;
-        if (!attr) {
+        static std::atomic<unsigned long long> attr{0};
+        if (first_on_device(&attr))
             cudaFuncSetAttribute(k_abc<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
-            attr = true;
-        }
         k_abc<W, false><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
     }
 }
@@ -376,11 +374,9 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
 template <int W>
 void grad_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* cand, int K,
                const double* tables, int n_groups, double* partials, int n_blocks, cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<unsigned long long> attr{0};
+    if (first_on_device(&attr))
         cudaFuncSetAttribute(k_grad_general<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
-        attr = true;
-    }
     size_t smem = (size_t)n_groups * 256 * sizeof(double);
     k_grad_general<W><<<n_blocks, kThreads, smem, s>>>(rows, coef, M, cand, K, tables, n_groups, partials); note_launch();
 }

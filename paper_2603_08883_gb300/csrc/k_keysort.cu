@@ -401,15 +401,14 @@ Cols radix_sort_cols(int Wd, const uint64_t* rows, const double* coef, int64_t n
 }
 
 void set_smem_limits() {
-    static bool done = false;
-    if (done) return;
+    static std::atomic<unsigned long long> done{0};
+    if (!first_on_device(&done)) return;
     cudaFuncSetAttribute(k_digit_scatter<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kTile * 8);
     cudaFuncSetAttribute(k_digit_scatter<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, 5 * kTile * 8);
     cudaFuncSetAttribute(k_digit_scatter<9>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * kTile * 8);
     cudaFuncSetAttribute(k_merge_export<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 3 * kMergeTile * 8);
     cudaFuncSetAttribute(k_merge_export<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 5 * kMergeTile * 8);
     cudaFuncSetAttribute(k_merge_export<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, 9 * kMergeTile * 8);
-    done = true;
 }
 
 }  // namespace

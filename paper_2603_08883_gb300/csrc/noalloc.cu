@@ -1,14 +1,18 @@
 // QMF energy without any device allocation.
 //
 // Some callers cannot allocate GPU memory at the moment they need an energy:
-// code recording a CUDA stream capture (cudaMalloc is not a capturable
-// operation), a plug-in hosted by a framework that owns every byte of device
-// memory through its own allocator, or a service that must keep a fixed memory
+// a plug-in hosted by a framework that owns every byte of device memory
+// through its own allocator, or a service that must keep a fixed memory
 // footprint once started.  For them iqcc_qmf_energy_noalloc evaluates the same
 // reduction as iqcc_qmf_energy (same kernels) on rows the caller already holds
 // on the device, with its scratch - the per-block partial sums, the QMF
 // product tables, the angles and the result - in the fixed array below, which
 // every GPU that loads this library keeps until the process exits.
+//
+// The call copies the angles from host memory and reads the result back
+// after synchronising its stream, so it cannot be recorded into a CUDA graph:
+// on a stream that is being captured it returns IQCC_ERR_ARG before issuing
+// any work, which leaves the caller's capture intact.
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -75,12 +79,21 @@ extern "C" iqcc_status iqcc_qmf_energy_noalloc(int n_qubits, int64_t n_terms, co
     if (n_terms < 0) return fail(IQCC_ERR_ARG, "iqcc_qmf_energy_noalloc: n_terms < 0");
     if (n_terms > 0 && (!d_rows || !d_coef)) return fail(IQCC_ERR_ARG, "iqcc_qmf_energy_noalloc: null row array");
     if (!theta || !phi || !energy) return fail(IQCC_ERR_ARG, "iqcc_qmf_energy_noalloc: null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(s, &cap);
+    if (e != cudaSuccess)
+        return fail(IQCC_ERR_CUDA, std::string("iqcc_qmf_energy_noalloc: cudaStreamIsCapturing: ") +
+                                       cudaGetErrorString(e));
+    if (cap != cudaStreamCaptureStatusNone)
+        return fail(IQCC_ERR_ARG, "iqcc_qmf_energy_noalloc: the stream is being captured; this call copies host "
+                                  "arrays and synchronises its stream, so it cannot be recorded in a graph");
     const int blocks = expect_blocks();
     if (blocks > kMaxBlocks)
         return fail(IQCC_ERR_ARG, "iqcc_qmf_energy_noalloc: this GPU needs more partial sums than the fixed "
                                   "scratch holds (4096 blocks)");
     double* sc = nullptr;
-    cudaError_t e = scratch_on_current_device(&sc);
+    e = scratch_on_current_device(&sc);
     if (e != cudaSuccess)
         return fail(IQCC_ERR_CUDA, std::string("iqcc_qmf_energy_noalloc: cudaGetSymbolAddress: ") +
                                        cudaGetErrorString(e));
@@ -88,7 +101,6 @@ extern "C" iqcc_status iqcc_qmf_energy_noalloc(int n_qubits, int64_t n_terms, co
     double* out3 = partials + kPartials;
     double* angles = out3 + kOut;
     double* tables = angles + kAngles;
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
 
     const int n = n_qubits;
     const int Wd = device_words(n);

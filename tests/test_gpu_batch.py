@@ -11,7 +11,7 @@ from tests.compare import compare
 
 pytestmark = pytest.mark.gpu
 
-iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc")
+iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc", exc_type=ImportError)
 
 
 def _problems(seed=0):

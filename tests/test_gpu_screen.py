@@ -10,7 +10,7 @@ from paper_2603_08883_gb300 import synth
 
 pytestmark = pytest.mark.gpu
 
-iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc")
+iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc", exc_type=ImportError)
 
 
 def _popc_rows(x):

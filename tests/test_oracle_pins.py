@@ -197,6 +197,28 @@ def test_dis_rule_brute_force(kind):
     assert all(mags[i] >= mags[i + 1] * (1 - 2 ** -30) for i in range(len(mags) - 1))
 
 
+def test_dis_ties_in_canonical_key_order():
+    """Exact ties of |g| are ordered by the canonical key (x as an unsigned
+    integer, then z), ascending.  H = 0.5 X0 + 0.5 X1 + 0.5 X0 X2 + 0.25 X2 +
+    0.3 Z0 at the z-eigenstate theta = (pi, 0, pi): the representatives Y0,
+    Y1 and Y0 X2 all have |g| = 0.5 exactly (from X Y = i Z and <Z> = -1, +1,
+    -1), Y2 has 0.25; so the order is Y0 (x = 1), Y1 (x = 2), Y0 X2 (x = 5),
+    then Y2.  A reversed tie order fails."""
+    n = 3
+    x, z, c = _from_words(n, {"XII": 0.5, "IXI": 0.5, "XIX": 0.5, "IIX": 0.25, "ZII": 0.3})
+    th = np.array([np.pi, 0.0, np.pi])
+    ph = np.zeros(n)
+    o = oracle.Oracle(n, x, z, c)
+    cx, cz, cg = o.dis(th, ph)
+    order = [dense.letters(n, cx[i], cz[i]) for i in range(len(cg))]
+    assert order == ["YII", "IYI", "YIX", "IIY"]
+    psi = dense.qmf_state(th, ph)
+    Hm = dense.dense(n, x, z, c)
+    for word, g in zip(order, cg):
+        assert g == pytest.approx(-dense.expval(Hm @ dense.pauli_matrix(word), psi).imag, abs=1e-14)
+    assert [abs(v) for v in cg] == pytest.approx([0.5, 0.5, 0.5, 0.25], abs=1e-15)
+
+
 # --------------------------------------------------------------------------- invariants
 
 
