@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--max-terms", type=int, default=0,
+                    help="profiling case: a lower term limit than the workload's (capacity twice it); the line "
+                         "then measures that smaller configuration and says so in its config")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the measurements of the adjoint pass, learned screening, sort-based dress and batches")
     return ap.parse_args()
@@ -509,6 +512,10 @@ def run_gpu(args):
     from paper_2603_08883_gb300 import iqcc, synth
 
     w = synth.WORKLOADS[args.workload]
+    if args.max_terms > 0:
+        import dataclasses
+        w = dataclasses.replace(w, max_terms=args.max_terms, capacity=2 * args.max_terms,
+                                notes=w.notes + f" (profiling case: term limit lowered to {args.max_terms})")
     if world > 1:
         w = workload_for_rank(w, rank)
     n, x, z, c = synth.workload_hamiltonian(w)

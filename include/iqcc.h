@@ -63,7 +63,8 @@ typedef enum {
 typedef struct {
     int n_qubits;          /* 1..256 */
     int64_t capacity;      /* maximum number of terms held; 0 -> 1<<30; at most 4294967294 */
-    int max_probe;         /* hash buckets probed per lookup before IQCC_ERR_HASH_FULL; 0 -> 64, at most 256 */
+    int max_probe;         /* hash buckets probed per lookup (DIS group table, key index of the
+                              partitioned dress) before IQCC_ERR_HASH_FULL; 0 -> 64, at most 256 */
     void* stream;          /* cudaStream_t to run on; NULL -> the legacy default stream */
     void* (*alloc)(size_t bytes, void* user); /* device allocator or NULL (cudaMalloc) */
     void (*free)(void* ptr, void* user);      /* matching free or NULL (cudaFree) */
@@ -91,13 +92,25 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
  * s sin(tau) C_T.  Commuting strings are untouched.  Nothing is pruned: exact
  * zeros stay until iqcc_prune.  *n_applied (may be NULL) receives the number
  * of generators applied.
+ * The merge (App. D Eq. 18, "insert if unique, else add") is a join: the
+ * anticommuting rows are partitioned by a hash of their pair key (of T and
+ * T xor P, the one whose bit at P's lowest set bit is clear) and each
+ * partition is matched in shared memory; the commuting rows stay in order, the
+ * dressed and appended rows follow them.  Device scratch: 16 Wd + 8 bytes per
+ * anticommuting row, plus small per-bin arrays.
+ * Errors: IQCC_ERR_ARG (bits above n_qubits, non-finite tau),
+ * IQCC_ERR_CAPACITY (H as after the previous generator), IQCC_ERR_OOM,
+ * IQCC_ERR_CUDA, IQCC_ERR_TIMEOUT (a device wait gave up),
+ * IQCC_ERR_HASH_FULL (more than 4096 rows fell into one partition group: far
+ * beyond any fluctuation of the hash).
  */
 iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz,
                        const double* tau, int* n_applied);
 
 /*
- * The dress of iqcc_dress by sorting instead of hashing (the alternative merge
- * of App. D: expansion, sort, segmented reduction).  Generators are taken in
+ * The dress of iqcc_dress by a global sort instead of the partitioned join
+ * (the alternative merge of App. D: expansion, sort, segmented reduction).
+ * Generators are taken in
  * groups of `fuse` (1..8, the last group may be shorter); each group expands
  * every term along every path through its generators (at generator j a path
  * keeps the current string, with factor cos(tau_j) when it anticommutes with
@@ -105,7 +118,7 @@ iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint6
  * the expanded terms in canonical key order, sums runs of equal keys in FP64
  * (exact zeros kept) and compacts them.  The result equals iqcc_dress up to
  * rounding (summation order); with fuse > 1 the intermediate merges are
- * skipped.  Terms end in canonical order; the index is rebuilt at the end.
+ * skipped.  Terms end in canonical order.
  * gx, gz: host [n_gen][W]; tau: host [n_gen].  Errors: IQCC_ERR_ARG (bad
  * fuse, bits above n_qubits, non-finite tau), IQCC_ERR_CAPACITY when a
  * group's expansion exceeds the capacity (H as after the previous group),
@@ -226,6 +239,27 @@ typedef struct {
 iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi,
                          const iqcc_iter_opts* opts, iqcc_iter_result* out);
 
+/*
+ * Device waits.  Two kinds of kernel wait on other blocks: the DIS grouping
+ * (a block that meets a group slot another block has claimed waits for the
+ * group's key to be published) and the stable compactions (a tile waits for
+ * its predecessors' counts, decoupled look-back).  Each wait polls at most
+ * `polls` times; then the kernel records IQCC_ERR_TIMEOUT and returns without
+ * writing out of bounds, the call that launched it returns IQCC_ERR_TIMEOUT,
+ * and the context refuses every later call (IQCC_ERR_STATE).  polls = 0
+ * restores the default of 2^24 polls (about a second).  The paper has no
+ * counterpart: this bounds every wait of the library.  Errors: IQCC_ERR_ARG.
+ */
+iqcc_status iqcc_set_wait_limit(iqcc_ctx* ctx, int polls);
+
+/*
+ * Self-test of that failure path: one device wait on a word that nothing
+ * writes.  Always returns IQCC_ERR_TIMEOUT (after the context's wait limit),
+ * and the context then refuses every later call with IQCC_ERR_STATE.  The
+ * paper has no counterpart.
+ */
+iqcc_status iqcc_wait_selftest(iqcc_ctx* ctx);
+
 /* Number of terms currently held. */
 iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms);
 
@@ -252,9 +286,9 @@ typedef struct {
     int64_t n_energy;          /* energy / A,B,C passes */
     double energy_kernel_ms;
     double energy_bytes;       /* (16W+8) M per pass */
-    double prune_ms;           /* device time of compression incl. hash rebuild */
+    double prune_ms;           /* device time of compression */
     double dis_ms;             /* device time of DIS screening */
-    double hash_ms;            /* device time of hash inserts and rebuilds */
+    double hash_ms;            /* device time of key-index builds (partitioned dress only) */
     int64_t hash_rebuilds;
     int64_t rows_allocated;    /* rows currently allocated on the device */
     int64_t hash_slots;        /* active hash slots */

@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstddef>
 #include <cstring>
 #include <functional>
 #include <string>
@@ -193,7 +194,7 @@ iqcc_status rebuild_hash(iqcc_ctx* ctx, uint64_t slots) {
     return read_counters(ctx);
 }
 
-// Rows and index able to hold `rows_needed` rows (current rows kept).
+// Rows able to hold `rows_needed` rows (current rows kept).
 iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
     if (rows_needed > ctx->rows_alloc) {
         int64_t want = std::max<int64_t>(rows_needed, ctx->rows_alloc + ctx->rows_alloc / 2);
@@ -206,11 +207,18 @@ iqcc_status reserve_rows(iqcc_ctx* ctx, int64_t rows_needed) {
         ctx->rows_alloc = want;
         ctx->stats.rows_allocated = want;
     }
-    // entries at most 1/2 of the slots once the rows are inserted (else a larger table)
-    if ((uint64_t)rows_needed * 2 > ctx->hash_slots) {
-        iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)rows_needed * 2));
-        if (st) return st;
-    }
+    return IQCC_OK;
+}
+
+// The key index over rows [0, M), with room for `rows_needed` entries at a
+// load of at most 1/2 (the partitioned dressing and the batches look keys up
+// in it; the single-Hamiltonian dress needs none).
+iqcc_status ensure_index(iqcc_ctx* ctx, int64_t rows_needed) {
+    const uint64_t want = pow2_at_least((uint64_t)std::max<int64_t>(rows_needed, 256) * 2);
+    if (ctx->index_valid && want <= ctx->hash_slots) return IQCC_OK;
+    iqcc_status st = rebuild_hash(ctx, std::max<uint64_t>(want, ctx->index_valid ? ctx->hash_slots : 0));
+    if (st) return st;
+    ctx->index_valid = true;
     return IQCC_OK;
 }
 
@@ -260,8 +268,11 @@ iqcc_status upload_tables(iqcc_ctx* ctx, const double* theta, const double* phi,
     return IQCC_OK;
 }
 
-// A, B, C of padded device-layout generator pkey (all zero: energy).
-iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, const double* phi, double* abc) {
+// A, B, C of padded device-layout generator pkey (all zero: energy).  With
+// pair_hist the same pass counts pkey's anticommuting rows by dress bin, for
+// the dress by pkey that follows (iqcc_iterate).
+iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, const double* phi, double* abc,
+                     bool pair_hist = false) {
     const bool basis = is_basis(ctx, theta);
     uint64_t occ[4];
     occ_words(ctx, theta, occ);
@@ -282,66 +293,161 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
         iqcc_status st = upload_tables(ctx, theta, phi, angles, tables);
         if (st) return st;
     }
+    ctx->pair_ready = false;
+    PairHistOut ph{nullptr, 0, dctr(ctx)};
+    if (pair_hist && ctx->M > 0) {
+        ph.log2_bins = pair_bins_log2(ctx->M);
+        const size_t bytes = sizeof(uint32_t) * (((size_t)1 << ph.log2_bins) + 1);
+        if (!ensure(ctx, ctx->pairbuf, bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        ph.counts = (uint32_t*)ctx->pairbuf.p + 1;
+        CK(cudaMemsetAsync(ctx->pairbuf.p, 0, bytes, ctx->stream));
+        CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_abc(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pkey, basis, occ, tables, n_groups(ctx), partials,
-               ctx->stream);
+               ctx->stream, ph.counts ? &ph : nullptr);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     launch_reduce3(partials, nb, out3, ctx->stream);
     CK_LAUNCH();
     double h3[3];
     CK(cudaMemcpyAsync(h3, out3, sizeof h3, cudaMemcpyDeviceToHost, ctx->stream));
+    if (ph.counts) {
+        iqcc_status st = read_counters(ctx);  // synchronises the stream
+        if (st) return st;
+        ctx->pair_n_anti = (int64_t)ctx->h_counters->n_anti;
+    }
     CK(cudaStreamSynchronize(ctx->stream));
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.n_energy++;
     ctx->stats.energy_kernel_ms += ms;
     ctx->stats.energy_bytes += (double)ctx->M * (16.0 * ctx->Wd + 8.0);
+    if (ph.counts) {
+        ctx->pair_ready = true;
+        ctx->pair_log2 = ph.log2_bins;
+        std::memcpy(ctx->pair_key, pkey, sizeof(uint64_t) * 2 * ctx->Wd);
+    }
     abc[0] = h3[0];
     abc[1] = h3[1];
     abc[2] = h3[2];
     return IQCC_OK;
 }
 
-// One generator (device-layout key); on IQCC_ERR_CAPACITY / OOM H is unchanged.
-iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
-    if (ctx->M == 0) {
-        ctx->stats.n_dress++;
-        return IQCC_OK;
-    }
+// One dress by pair partition (k_pairjoin.cu): bin histogram of the
+// anticommuting rows, split (commuting rows compacted in place, anticommuting
+// ones copied into their bins), join.  On IQCC_ERR_CAPACITY / OOM H is
+// unchanged.  Returns the counts in *n_anti_out / *n_new_out.
+iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, int64_t* n_new_out, float* ms_out) {
     const int64_t M = ctx->M;
-    int64_t upper = 2 * M;
+    *n_anti_out = *n_new_out = 0;
+    *ms_out = 0;
+    if (M == 0) return IQCC_OK;
+    // the bin counts of this dress were taken by the A, B, C pass that preceded it
+    bool ready = ctx->pair_ready && !d.gens && ctx->pair_log2 == pair_bins_log2(M) &&
+                 std::memcmp(ctx->pair_key, d.pkey, sizeof(uint64_t) * 2 * ctx->Wd) == 0;
+    ctx->pair_ready = false;
+    const int lb = pair_bins_log2(M);
+    const uint32_t NB = 1u << lb;
+    Carver cv;
+    cv.take<uint32_t>(1024);
+    cv.take<char>(pair_split_scratch_bytes(M));
+    cv.take<unsigned long long>(2);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint32_t* scan_tmp = cv.take<uint32_t>(1024);
+    char* tiles = cv.take<char>(pair_split_scratch_bytes(M));
+    unsigned long long* m_comm = cv.take<unsigned long long>(2);
+    unsigned long long* out_cursor = m_comm + 1;
+    if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+    const size_t arr_bytes = sizeof(uint32_t) * ((size_t)NB + 1);
+    if (!ready && !ensure(ctx, ctx->pairbuf, arr_bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    uint32_t* arr = (uint32_t*)ctx->pairbuf.p;  // [0] = 0, [1 + b]: count, then start, then end of bin b
     DevCounters* c = dctr(ctx);
-    if (upper > ctx->capacity) {
-        // exact admission count (probe only)
-        CK(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), ctx->stream));
-        launch_dress_count(ctx->Wd, ctx->rows(), M, pkey, hash_view(ctx), c, ctx->stream);
+    CK(cudaMemsetAsync(m_comm, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    if (!ready) {
+        CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        CK(cudaMemsetAsync(arr, 0, arr_bytes, ctx->stream));
+        launch_pair_hist(d, ctx->rows(), M, lb, arr + 1, c, ctx->stream);
+    }
+    launch_scan_u32_long(arr + 1, NB, scan_tmp, ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    const int64_t n_anti = ready ? ctx->pair_n_anti : (int64_t)ctx->h_counters->n_anti;
+    *n_anti_out = n_anti;
+    if (n_anti == 0) return IQCC_OK;  // P commutes with every term
+    // bin copies of the anticommuting rows
+    Carver rv;
+    rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
+    rv.take<double>(n_anti);
+    if (!ensure(ctx, ctx->aux, rv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    rv = Carver{(char*)ctx->aux.p, 0};
+    uint64_t* rk = rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
+    double* rc = rv.take<double>(n_anti);
+    if (rv.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+    const uint32_t bpb = pair_bins_per_block(n_anti, lb);
+    bool scattered = false;
+    if (M + n_anti > ctx->capacity) {
+        // exact admission: bin copies and a counting join first, H untouched
+        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c,
+                          ctx->stream);
+        launch_pair_join(d, false, rk, rc, arr, lb, bpb, ctx->rows(), ctx->c(), m_comm, out_cursor, c, ctx->stream);
         CK_LAUNCH();
-        iqcc_status st = read_counters(ctx);
+        st = read_counters(ctx);
         if (st) return st;
-        upper = M + (int64_t)ctx->h_counters->n_new;
+        const int64_t upper = M + (int64_t)ctx->h_counters->n_new;
         if (upper > ctx->capacity) {
             char buf[200];
             snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)upper,
                      (long long)ctx->capacity);
             return fail(ctx, IQCC_ERR_CAPACITY, buf);
         }
+        st = reserve_rows(ctx, upper);
+        if (st) return st;
+        CK(cudaMemsetAsync(&c->n_new, 0, sizeof(unsigned long long), ctx->stream));
+        scattered = true;
+    } else {
+        st = reserve_rows(ctx, M + n_anti);
+        if (st) return st;
     }
-    iqcc_status st = reserve_rows(ctx, upper);
-    if (st) return st;
-    CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));  // n_new .. aux
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    launch_dress(ctx->Wd, ctx->rows(), ctx->rows(), ctx->c(), M, pkey, std::cos(tau), std::sin(tau),
-                 hash_view(ctx), c, ctx->stream);
+    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c,
+                      ctx->stream);
+    launch_pair_join(d, true, rk, rc, arr, lb, bpb, ctx->rows(), ctx->c(), m_comm, out_cursor, c, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
     if (st) return st;
+    unsigned long long mc = 0, oc = 0;
+    CK(cudaMemcpyAsync(&mc, m_comm, sizeof mc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&oc, out_cursor, sizeof oc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
     const int64_t n_new = (int64_t)ctx->h_counters->n_new;
-    const int64_t n_anti = (int64_t)ctx->h_counters->n_anti;
+    if ((int64_t)mc + n_anti != M || (int64_t)oc != n_anti + n_new)
+        return fail(ctx, IQCC_ERR_STATE, "internal: pair dress row counts disagree");
+    cudaEventElapsedTime(ms_out, ctx->ev0, ctx->ev1);
+    ctx->M = M + n_new;
+    ctx->index_valid = false;
+    *n_new_out = n_new;
+    return IQCC_OK;
+}
+
+// One generator (device-layout key); on IQCC_ERR_CAPACITY / OOM H is unchanged.
+iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
+    const int64_t M = ctx->M;
+    bool identity = true;
+    for (int w = 0; w < 2 * ctx->Wd; ++w) identity &= pkey[w] == 0;
+    if (M == 0 || identity) {
+        ctx->stats.n_dress++;
+        ctx->stats.dressed_terms += M;
+        return IQCC_OK;
+    }
+    PairDress d{ctx->Wd, pkey, nullptr, 0, std::cos(tau), std::sin(tau)};
+    int64_t n_anti = 0, n_new = 0;
     float ms = 0;
-    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
-    ctx->M = M + n_new;  // the dress kernel indexed the appended rows itself
+    iqcc_status st = dress_pairs(ctx, d, &n_anti, &n_new, &ms);
+    if (st) return st;
     iqcc_stats& s = ctx->stats;
     s.n_dress++;
     s.dressed_terms += M;
@@ -425,6 +531,7 @@ iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags
 }
 
 iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed, const double* rank = nullptr) {
+    ctx->pair_ready = false;
     const int64_t M = ctx->M;
     *removed = 0;
     if (M == 0) return IQCC_OK;
@@ -433,7 +540,6 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     cv.take<unsigned long long>(256);
     cv.take<char>(compact_inplace_scratch_bytes(M));
     cv.take<uint32_t>(M);  // tie list
-    cv.take<uint32_t>(M);  // old row -> new row
     cv.off += sort_area_bytes(M);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
@@ -441,7 +547,6 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     unsigned long long* hist = cv.take<unsigned long long>(256);
     char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
-    uint32_t* new_row = cv.take<uint32_t>(M);
     SortArea sa = carve_sort(cv, M);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
@@ -494,7 +599,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
         }
     }
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream, new_row);
+    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
@@ -505,20 +610,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     const int64_t newM = (int64_t)ctx->h_counters->aux;
     ctx->M = newM;
     *removed = M - newM;
-    if (newM == M) return IQCC_OK;  // nothing moved
-    // rows moved: every partition of the index rebuilt from its own entries
-    // through the compaction map (removed rows dropped); a full build where the
-    // auxiliary buffer cannot hold the list of cross-partition probes
-    if (!ensure(ctx, ctx->aux, index_reindex_scratch_bytes(M))) return rebuild_hash(ctx, ctx->hash_slots);
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    launch_index_reindex(hash_view(ctx), ctx->hash_slots, new_row, M, ctx->aux.p, c, ctx->stream);
-    CK_LAUNCH();
-    CK(cudaEventRecord(ctx->ev1, ctx->stream));
-    st = read_counters(ctx);
-    if (st) return st;
-    float hms = 0;
-    cudaEventElapsedTime(&hms, ctx->ev0, ctx->ev1);
-    ctx->stats.hash_ms += hms;
+    if (newM != M) ctx->index_valid = false;  // rows moved: the index (when one is kept) is stale
     return IQCC_OK;
 }
 
@@ -808,7 +900,7 @@ iqcc_status prune_learned(iqcc_ctx* ctx, double eps, int64_t max_terms, int n_ge
         launch_boost_rank(ctx->c(), flags, M, t_bits, 1e300, rank, ctx->stream);
         CK_LAUNCH();
     }
-    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
     return compress(ctx, eps, max_terms, removed, rank);
 }
 
@@ -871,8 +963,12 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
         fail(ctx, IQCC_ERR_OOM, "counter allocation failed");
         return bail(IQCC_ERR_OOM);
     }
-    if (cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream) != cudaSuccess) {
-        fail_cuda(ctx, cudaGetLastError(), "memset", __LINE__);
+    *ctx->h_counters = DevCounters{};
+    ctx->h_counters->wait_limit = kDefaultWaitLimit;
+    if (cudaMemcpyAsync(ctx->counters.p, ctx->h_counters, sizeof(DevCounters), cudaMemcpyHostToDevice, ctx->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ctx->stream) != cudaSuccess) {
+        fail_cuda(ctx, cudaGetLastError(), "counter initialisation", __LINE__);
         return bail(IQCC_ERR_CUDA);
     }
     const int64_t rows0 = std::min<int64_t>(ctx->capacity, std::max<int64_t>(1024, 2 * n_terms));
@@ -953,11 +1049,8 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
         } while (0);
         if (st) return bail(st);
     }
-    iqcc_status st = rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
+    ctx->index_valid = false;  // built on demand by the calls that look keys up
     ctx->launch_base = launches();
-    if (st) return bail(st);
-    ctx->stats.hash_rebuilds = 0;
-    ctx->stats.hash_ms = 0;
     *out = ctx;
     return IQCC_OK;
 }
@@ -1012,6 +1105,7 @@ iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* 
     if (bits_above_n(ctx, gx) || bits_above_n(ctx, gz)) return fail(ctx, IQCC_ERR_ARG, "generator bits above n_qubits");
     uint64_t pk[8];
     pad_key(ctx, gx, gz, pk);
+    ctx->pair_ready = false;
     const int64_t M = ctx->M;
     const int64_t upper = M + n_peer;  // at most one appended row per received row
     if (upper > ctx->capacity) {
@@ -1021,6 +1115,8 @@ iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* 
         return fail(ctx, IQCC_ERR_CAPACITY, buf);
     }
     iqcc_status st = reserve_rows(ctx, std::max<int64_t>(upper, 1));
+    if (st) return st;
+    st = ensure_index(ctx, std::max<int64_t>(upper, 1));
     if (st) return st;
     const int W = ctx->W, Wd = ctx->Wd;
     const uint64_t pslots = pow2_at_least((uint64_t)std::max<int64_t>(4 * n_peer, 64));  // load <= 1/4
@@ -1079,7 +1175,7 @@ iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint6
             return fail(ctx, IQCC_ERR_ARG, "generator bits set above n_qubits");
         if (!std::isfinite(tau[k])) return fail(ctx, IQCC_ERR_ARG, "non-finite amplitude");
     }
-    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
     for (int k = 0; k < n_gen; ++k) {
         uint64_t pk[8];
         pad_key(ctx, gx + k * ctx->W, gz + k * ctx->W, pk);
@@ -1096,6 +1192,7 @@ iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint6
 // into the row buffer.  The index is not touched (rebuilt by the caller).  On
 // IQCC_ERR_CAPACITY / IQCC_ERR_OOM the Hamiltonian is unchanged.
 iqcc_status sorted_group(iqcc_ctx* ctx, const uint64_t* pkeys, const double* tau, int k) {
+    ctx->pair_ready = false;
     const int64_t M = ctx->M;
     if (M == 0) return IQCC_OK;
     const int Wd = ctx->Wd;
@@ -1170,7 +1267,7 @@ iqcc_status iqcc_dress_sorted(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, cons
             return fail(ctx, IQCC_ERR_ARG, "generator bits set above n_qubits");
         if (!std::isfinite(tau[k])) return fail(ctx, IQCC_ERR_ARG, "non-finite amplitude");
     }
-    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
     for (int g0 = 0; g0 < n_gen; g0 += fuse) {
         const int k = std::min(fuse, n_gen - g0);
         std::vector<uint64_t> pk((size_t)k * 2 * ctx->Wd);
@@ -1180,7 +1277,7 @@ iqcc_status iqcc_dress_sorted(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, cons
         if (st) return st;
         if (n_applied) *n_applied = g0 + k;
     }
-    if (n_gen > 0) return rebuild_hash(ctx, pow2_at_least((uint64_t)std::max<int64_t>(ctx->M, 256) * 4));
+    if (n_gen > 0) ctx->index_valid = false;  // rows rewritten in sorted order
     return IQCC_OK;
 }
 
@@ -1188,7 +1285,7 @@ iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_
     if (n_removed) *n_removed = 0;
     GUARD(ctx);
     if (std::isnan(eps)) return fail(ctx, IQCC_ERR_ARG, "eps is NaN");
-    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
     int64_t removed = 0;
     iqcc_status st = compress(ctx, eps, max_terms, &removed);
     if (st) return st;
@@ -1293,7 +1390,7 @@ iqcc_status iqcc_dis_gradients(iqcc_ctx* ctx, const double* theta, const double*
         return IQCC_OK;
     }
     if (cap > 0 && (!ox || !oz || !grad)) return fail(ctx, IQCC_ERR_ARG, "null output array");
-    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
     return dis_enumerate(ctx, theta, phi, cap, n_out, ox, oz, grad);
 }
 
@@ -1332,7 +1429,10 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     }
     for (int k = 0; k < used; ++k) {
         double abc[3];
-        iqcc_status st = iqcc_generator_abc(ctx, gx.data() + k * W, gz.data() + k * W, theta, phi, abc);
+        uint64_t pk[8];
+        pad_key(ctx, gx.data() + k * W, gz.data() + k * W, pk);
+        // A, B, C and the dress bins of the generator in one pass over H
+        iqcc_status st = abc_impl(ctx, pk, theta, phi, abc, true);
         if (st) return st;
         double tau;
         if (o->n_forced > 0 && o->forced_tau) tau = o->forced_tau[k];
@@ -1367,6 +1467,30 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
     out->n_removed += removed;
     out->n_terms = ctx->M;
     return iqcc_qmf_energy(ctx, theta, phi, &out->energy);
+}
+
+iqcc_status iqcc_set_wait_limit(iqcc_ctx* ctx, int polls) {
+    GUARD(ctx);
+    if (polls < 0) return fail(ctx, IQCC_ERR_ARG, "polls < 0");
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->h_counters->wait_limit = polls == 0 ? kDefaultWaitLimit : polls;
+    CK(cudaMemcpyAsync((char*)ctx->counters.p + offsetof(DevCounters, wait_limit), &ctx->h_counters->wait_limit,
+                       sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_wait_selftest(iqcc_ctx* ctx) {
+    GUARD(ctx);
+    Carver cv;
+    cv.take<unsigned long long>(1);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    unsigned long long* word = (unsigned long long*)ctx->scratch.p;
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
+    CK(cudaMemsetAsync(word, 0, sizeof(unsigned long long), ctx->stream));
+    launch_wait_selftest(word, dctr(ctx), ctx->stream);
+    CK_LAUNCH();
+    return read_counters(ctx);
 }
 
 iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms) {
@@ -1601,6 +1725,7 @@ void iqcc_free(iqcc_ctx* ctx) {
     release(ctx, ctx->aux);
     release(ctx, ctx->model);
     release(ctx, ctx->screen_rank);
+    release(ctx, ctx->pairbuf);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -1772,7 +1897,7 @@ iqcc_status batch_screen(iqcc_batch* b, const double* theta, const double* phi, 
     Carver cv{(char*)b->dev.p, 0};
     const BatchDev d = carve_batch(cv, B);
     CK(cudaStreamSynchronize(ctx->stream));
-    CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), b->gs));
+    CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, b->gs));
     if (b->graph && b->graph_M == ctx->M) {
         CK(cudaGraphLaunch(b->graph, b->gs));
         b->replays++;
@@ -1902,30 +2027,20 @@ iqcc_status iqcc_batch_step(iqcc_batch* b, const double* theta, const double* ph
     const BatchDev d = carve_batch(cv, b->B);
     const int64_t M = ctx->M;
     if (M > 0) {
-        // every anticommuting term appends at most one partner
-        st = reserve_rows(ctx, 2 * M);
-        if (st) return st;
-        DevCounters* c = dctr(ctx);
-        CK(cudaMemsetAsync(c, 0, sizeof(DevCounters), ctx->stream));
-        CK(cudaEventRecord(ctx->ev0, ctx->stream));
-        launch_dress_seg(ctx->rows(), ctx->rows(), ctx->c(), M, d.gens, b->B, hash_view(ctx), c, ctx->stream);
-        CK_LAUNCH();
-        CK(cudaEventRecord(ctx->ev1, ctx->stream));
-        st = read_counters(ctx);
-        if (st) return st;
-        const int64_t n_new = (int64_t)ctx->h_counters->n_new;
-        if (M + n_new > ctx->rows_alloc) return fail(ctx, IQCC_ERR_STATE, "internal: batch dress overran its rows");
-        ctx->M = M + n_new;
+        // each row dressed by its problem's generator, by pair partition
+        PairDress pd{1, nullptr, d.gens, b->B, 1.0, 0.0};
+        int64_t n_anti = 0, n_new = 0;
         float ms = 0;
-        cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+        st = dress_pairs(ctx, pd, &n_anti, &n_new, &ms);
+        if (st) return st;
         ctx->stats.n_dress++;
         ctx->stats.dressed_terms += M;
-        ctx->stats.anticommuting += (int64_t)ctx->h_counters->n_anti;
+        ctx->stats.anticommuting += n_anti;
         ctx->stats.appended += n_new;
         ctx->stats.dress_kernel_ms += ms;
     }
     if (eps > 0) {
-        CK(cudaMemsetAsync(ctx->counters.p, 0, sizeof(DevCounters), ctx->stream));
+        CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
         int64_t removed = 0;
         st = compress(ctx, eps, 0, &removed);
         if (st) return st;

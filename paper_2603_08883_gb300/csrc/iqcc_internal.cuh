@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <atomic>
@@ -127,6 +128,28 @@ __device__ __forceinline__ uint64_t hash_key(const Key<W>& k) {
     return h;
 }
 
+// Hash of the pair key of T for generator P whose lowest set bit is bit
+// `mask` of word `word` (0..2W-1, x words first): of T and its partner
+// T xor P, the one with that bit clear (exactly one of them), so the same for
+// both members of a pair.  Its top bits pick the dress bin.
+template <int W>
+__device__ __forceinline__ uint64_t pair_hash(const Key<W>& t, const Key<W>& p, int word, uint64_t mask) {
+    uint64_t v = 0;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        if (word == j) v = t.x[j];
+        if (word == W + j) v = t.z[j];
+    }
+    const uint64_t flip = (v & mask) ? ~0ull : 0ull;
+    Key<W> k;
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        k.x[j] = t.x[j] ^ (p.x[j] & flip);
+        k.z[j] = t.z[j] ^ (p.z[j] & flip);
+    }
+    return hash_key<W>(k);
+}
+
 // Device-side counters shared by the kernels of one call.
 struct DevCounters {
     unsigned long long n_new;      // rows appended by a dress
@@ -135,7 +158,12 @@ struct DevCounters {
     unsigned long long aux;        // scratch counter
     int err;                       // iqcc_status set by a kernel (first error wins)
     int err_where;                 // which kernel
+    int wait_limit;                // polls a device wait makes before it reports IQCC_ERR_TIMEOUT
+    int pad;
 };
+// Bytes of DevCounters cleared between calls (everything before wait_limit).
+constexpr size_t kCountersClear = offsetof(DevCounters, wait_limit);
+constexpr int kDefaultWaitLimit = 1 << 24;  // polls of about 32-64 ns: a wait gives up after about a second
 
 // First error wins; `where` names the raising site.
 __device__ __forceinline__ void set_error(DevCounters* ctr, int code, int where) {
@@ -170,10 +198,38 @@ template <int W>
 struct Gen {
     Key<W> p;
     int yP;          // popc(xP & zP) mod 4
-    int top_word;    // word index (0..2W-1, x words first) of P's highest set bit
-    uint64_t top_mask;
+    int top_word;    // word index (0..2W-1, x words first) of P's lowest set bit
+    uint64_t top_mask;  // that bit
     double cos_t, sin_t;
 };
+
+// Generator of a device-layout key pkey (x words then z words): P, its Y
+// count mod 4, the word and bit of P's lowest set bit (first non-zero word,
+// x words first), and the rotation.
+template <int W>
+inline Gen<W> make_gen(const uint64_t* pkey, double cos_t, double sin_t) {
+    Gen<W> g{};
+    int y = 0;
+    g.top_word = -1;
+    for (int j = 0; j < W; ++j) {
+        g.p.x[j] = pkey[j];
+        g.p.z[j] = pkey[W + j];
+        y += __builtin_popcountll(pkey[j] & pkey[W + j]);
+    }
+    for (int w = 0; w < 2 * W && g.top_word < 0; ++w)
+        if (pkey[w]) {
+            g.top_word = w;
+            g.top_mask = pkey[w] & (~pkey[w] + 1);
+        }
+    if (g.top_word < 0) {
+        g.top_word = 0;
+        g.top_mask = 0;
+    }
+    g.yP = y & 3;
+    g.cos_t = cos_t;
+    g.sin_t = sin_t;
+    return g;
+}
 
 // Batches of independent Hamiltonians (one word per x and z): problem b's
 // strings carry b in z bits kBatchTagShift.. (Z letters on virtual qubits).
@@ -205,8 +261,14 @@ struct iqcc_ctx {
     int64_t M = 0;                 // live rows
     int64_t rows_alloc = 0;        // rows allocated in the key/coef buffers
     iqcc::Buf keys, coef;
-    iqcc::Buf hash;                // slots
+    iqcc::Buf hash;                // slots of the key index (partitioned dressing and batches only)
     uint64_t hash_slots = 0;       // active slots (power of two)
+    bool index_valid = false;      // the index holds exactly rows [0, M)
+    iqcc::Buf pairbuf;             // dress bins: [0] = 0, then per bin its count, start, end
+    bool pair_ready = false;       // pairbuf holds the bin counts of pair_key's dress of the current H
+    int pair_log2 = 0;
+    int64_t pair_n_anti = 0;       // rows counted into those bins
+    uint64_t pair_key[8] = {0};    // device-layout key of that generator
     iqcc::Buf counters;            // DevCounters
     iqcc::DevCounters* h_counters = nullptr;  // pinned host mirror
     iqcc::Buf scratch;             // general scratch (grows)
@@ -321,6 +383,31 @@ void launch_mlp_score(int Wd, const uint64_t* rows, const double* coef, int64_t 
 void launch_future_energy(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkeys, const double* tau, int k,
                           const double* tab, int ts, int n, double* out, cudaStream_t s);
 
+// k_pairjoin.cu: dress by pair partition (histogram, split, shared-memory join).
+struct PairDress {
+    int Wd;
+    const uint64_t* pkey;    // host, device-layout key of the one generator (gens == nullptr)
+    const Gen<1>* gens;      // device, per-problem generators of a batch (Wd == 1), or nullptr
+    int B;
+    double cos_t, sin_t;
+};
+int pair_bins_log2(int64_t M);
+uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins);
+size_t pair_split_scratch_bytes(int64_t M);
+// counts: [2^log2_bins] zeroed; adds each anticommuting row to its bin and the total to ctr->n_anti
+void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
+                      DevCounters* ctr, cudaStream_t s);
+// cursor: bin starts in, bin ends out (when scattering); *m_comm: commuting rows (when compacting)
+void launch_pair_split(const PairDress& d, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M,
+                       int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, void* tile_scratch,
+                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s);
+// start: [2^log2_bins + 1] bin starts; rows without a partner counted in ctr->n_new; with `write` the
+// dressed rows and appended partners are written from row *m_comm + (*out_cursor, zeroed) on
+void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
+                      int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef,
+                      const unsigned long long* m_comm, unsigned long long* out_cursor, DevCounters* ctr,
+                      cudaStream_t s);
+
 // k_hash.cu / k_dress.cu
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
@@ -334,9 +421,16 @@ void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t*
 // k_expect.cu
 int expect_blocks();
 // Fills partials[block][3] with (A, B, C) sums; pkey may be all-zero (energy).
+// With `pair` the same pass also counts P's anticommuting rows by dress bin
+// (launch_pair_hist's output, for the dress by P that follows).
+struct PairHistOut {
+    uint32_t* counts;   // [2^log2_bins], zeroed
+    int log2_bins;
+    DevCounters* ctr;   // n_anti (zeroed) receives the total
+};
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,
                 bool basis, const uint64_t* occ, const double* tables, int n_groups, double* partials,
-                cudaStream_t s);
+                cudaStream_t s, const PairHistOut* pair = nullptr);
 void launch_reduce3(const double* partials, int n, double* out3, cudaStream_t s);
 void launch_qmf_tables(const double* theta, const double* phi, int n, int n_groups, double* tables,
                        cudaStream_t s);
@@ -385,6 +479,9 @@ size_t compact_inplace_scratch_bytes(int64_t n);
 void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double* coef, int64_t n, void* scratch,
                             unsigned long long* count, DevCounters* ctr, cudaStream_t s,
                             uint32_t* new_row = nullptr);
+
+// one bounded wait on *word (zero, never written): records IQCC_ERR_TIMEOUT once ctr->wait_limit is spent
+void launch_wait_selftest(const unsigned long long* word, DevCounters* ctr, cudaStream_t s);
 
 // DIS top-k: coarse |g| radix select, collect, sort of the collected subset
 void launch_coarse_digit_hist(const double* g, int64_t G, int shift, uint64_t prefix, uint64_t prefix_mask,

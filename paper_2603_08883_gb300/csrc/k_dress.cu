@@ -427,25 +427,6 @@ __global__ void __launch_bounds__(kThreads) k_cross_append(const uint64_t* __res
     }
 }
 
-template <int W>
-Gen<W> make_gen(const uint64_t* pkey, double cos_t, double sin_t) {
-    Gen<W> g{};
-    int y = 0;
-    g.top_word = -1;
-    for (int j = 0; j < W; ++j) {
-        g.p.x[j] = pkey[j];
-        g.p.z[j] = pkey[W + j];
-        y += __builtin_popcountll(pkey[j] & pkey[W + j]);
-    }
-    for (int w = 0; w < 2 * W && g.top_word < 0; ++w)
-        if (pkey[w]) { g.top_word = w; g.top_mask = pkey[w] & (~pkey[w] + 1); }
-    if (g.top_word < 0) { g.top_word = 0; g.top_mask = 0; }
-    g.yP = y & 3;
-    g.cos_t = cos_t;
-    g.sin_t = sin_t;
-    return g;
-}
-
 int grid_for(int64_t n, int per_sm) {
     int64_t want = (n + kThreads - 1) / kThreads;
     int64_t cap = (int64_t)sm_count() * per_sm;

@@ -90,22 +90,37 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* out) 
     }
 }
 
-// A, B, C for generator p (p = 0: energy in A).
-template <int W, bool BASIS>
+// Dress-bin counting folded into the A, B, C pass (see launch_abc).
+struct PairCount {
+    uint32_t* counts;
+    int shift;
+    int top_word;
+    uint64_t top_mask;
+    DevCounters* ctr;
+};
+
+// A, B, C for generator p (p = 0: energy in A).  HIST: also counts the
+// anticommuting rows by dress bin of p (k_pairjoin.cu), one key read for both.
+template <int W, bool BASIS, bool HIST>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
                                                   int yP, Key<W> occ, const double* __restrict__ tables,
-                                                  int n_groups, double* partials) {
+                                                  int n_groups, double* partials, PairCount pc) {
     extern __shared__ double s_tab[];
     if (!BASIS) {
         for (int i = threadIdx.x; i < n_groups * 256; i += blockDim.x) s_tab[i] = tables[i];
         __syncthreads();
     }
     double acc[3] = {0.0, 0.0, 0.0};
+    unsigned n_anti = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
         Key<W> t = load_key<W>(rows, i);
         const int anti = anticommutes<W>(t, p);
+        if (HIST && anti) {
+            atomicAdd(&pc.counts[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
+            ++n_anti;
+        }
         if (BASIS) {
             const bool diag = x_is_zero<W>(t);
             const bool cross = anti && x_equal<W>(t, p);
@@ -135,6 +150,11 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
                 acc[0] += c * et;
             }
         }
+    }
+    if (HIST) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
+        if ((threadIdx.x & 31) == 0 && n_anti) atomicAdd(&pc.ctr->n_anti, (unsigned long long)n_anti);
     }
     block_reduce_store<3>(acc, partials + 3 * blockIdx.x);
 }
@@ -254,7 +274,7 @@ __global__ void __launch_bounds__(kThreads) k_dis_group(const uint64_t* __restri
                 if ((uint32_t)(cur >> 32) != fp) continue;
                 int spins = 0;
                 while ((uint32_t)cur == kPendingGroup) {
-                    if (++spins > (1 << 22)) { set_error(ctr, IQCC_ERR_TIMEOUT, 10); break; }
+                    if (++spins > ctr->wait_limit) { set_error(ctr, IQCC_ERR_TIMEOUT, 10); break; }
                     __nanosleep(64);
                     cur = *(volatile unsigned long long*)slot;
                 }
@@ -351,23 +371,40 @@ int abc_grid(int64_t M) {
     return (int)(want < 1 ? 1 : want);
 }
 
+template <int W, bool HIST>
+void abc_launch(const uint64_t* rows, const double* coef, int64_t M, const Key<W>& p, int y, const Key<W>& occ,
+                bool basis, const double* tables, int n_groups, double* partials, const PairCount& pc,
+                cudaStream_t s) {
+    const int grid = expect_blocks();
+    if (basis) {
+        k_abc<W, true, HIST><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, pc);
+    } else {
+        size_t smem = (size_t)n_groups * 256 * sizeof(double);
+        static std::atomic<unsigned long long> attr{0};
+        if (first_on_device(&attr))
+            cudaFuncSetAttribute(k_abc<W, false, HIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
+        k_abc<W, false, HIST><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials,
+                                                            pc);
+    }
+    note_launch();
+}
+
 template <int W>
 void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, bool basis,
-              const uint64_t* occ_words, const double* tables, int n_groups, double* partials, cudaStream_t s) {
+              const uint64_t* occ_words, const double* tables, int n_groups, double* partials, cudaStream_t s,
+              const PairHistOut* pair) {
     Key<W> p = key_from<W>(pkey);
     int y = 0;
     for (int j = 0; j < W; ++j) y += __builtin_popcountll(p.x[j] & p.z[j]);
     Key<W> occ{};
     for (int j = 0; j < W; ++j) { occ.x[j] = occ_words[j]; occ.z[j] = 0; }
-    const int grid = expect_blocks();
-    if (basis) {
-        k_abc<W, true><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
+    PairCount pc{};
+    if (pair) {
+        const Gen<W> g = make_gen<W>(pkey, 1.0, 0.0);
+        pc = PairCount{pair->counts, 64 - pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
+        abc_launch<W, true>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, s);
     } else {
-        size_t smem = (size_t)n_groups * 256 * sizeof(double);
-        static std::atomic<unsigned long long> attr{0};
-        if (first_on_device(&attr))
-            cudaFuncSetAttribute(k_abc<W, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
-        k_abc<W, false><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials); note_launch();
+        abc_launch<W, false>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, s);
     }
 }
 
@@ -386,11 +423,12 @@ void grad_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64
 int expect_blocks() { return sm_count() * 4; }
 
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, bool basis,
-                const uint64_t* occ, const double* tables, int n_groups, double* partials, cudaStream_t s) {
+                const uint64_t* occ, const double* tables, int n_groups, double* partials, cudaStream_t s,
+                const PairHistOut* pair) {
     switch (Wd) {
-        case 1: abc_impl<1>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s); break;
-        case 2: abc_impl<2>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s); break;
-        default: abc_impl<4>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s); break;
+        case 1: abc_impl<1>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair); break;
+        case 2: abc_impl<2>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair); break;
+        default: abc_impl<4>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair); break;
     }
 }
 

@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
             const int stop = pref ? __ffs(pref) - 1 : 31;  // last lane that counts
             const unsigned upto = stop == 31 ? 0xFFFFFFFFu : ((2u << stop) - 1u);
             if (zero & upto) {  // a predecessor within the window has not published yet
-                if (++spins > (1 << 24)) {
+                if (++spins > ctr->wait_limit) {
                     if (lane == 0 && atomicCAS(&ctr->err, 0, (int)IQCC_ERR_TIMEOUT) == 0) ctr->err_where = 20;
                     break;
                 }
@@ -292,6 +292,21 @@ __global__ void __launch_bounds__(kThreads) k_compact_inplace(const uint8_t* __r
             coef[out + rank[r]] = c[r];
         }
         if (new_row && i < n) new_row[i] = keep[r] ? (uint32_t)(out + rank[r]) : kRowRemoved;
+    }
+}
+
+// One bounded device wait on a word that nothing writes: polls until the
+// context's wait limit is spent, then records IQCC_ERR_TIMEOUT and returns
+// (the failure path every device wait of the library takes).
+__global__ void k_wait_selftest(const unsigned long long* word, DevCounters* ctr) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int spins = 0;
+    while (*(const volatile unsigned long long*)word == 0) {
+        if (++spins > ctr->wait_limit) {
+            set_error(ctr, IQCC_ERR_TIMEOUT, 90);
+            return;
+        }
+        __nanosleep(32);
     }
 }
 
@@ -700,6 +715,11 @@ void launch_compact_inplace(int Wd, const uint8_t* flags, uint64_t* rows, double
                                                                   new_row);
             break;
     }
+    note_launch();
+}
+
+void launch_wait_selftest(const unsigned long long* word, DevCounters* ctr, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(word, ctr);
     note_launch();
 }
 

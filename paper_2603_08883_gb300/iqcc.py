@@ -110,6 +110,8 @@ _stats = _sig("iqcc_get_stats", _c, [_vp, ctypes.POINTER(iqcc_stats)])
 _reset = _sig("iqcc_reset_stats", _c, [_vp])
 _err = _sig("iqcc_last_error", ctypes.c_char_p, [_vp])
 _free = _sig("iqcc_free", None, [_vp])
+_set_wait = _sig("iqcc_set_wait_limit", _c, [_vp, ctypes.c_int])
+_wait_selftest = _sig("iqcc_wait_selftest", _c, [_vp])
 _energy_noalloc = _sig("iqcc_qmf_energy_noalloc", _c, [ctypes.c_int, ctypes.c_int64, _vp, _vp, _f64p, _f64p, _vp,
                                                        _f64p])
 
@@ -439,6 +441,16 @@ def iqcc_get_stats(H: Hamiltonian) -> dict:
 
 def iqcc_reset_stats(H: Hamiltonian) -> None:
     H._check(_reset(H._h))
+
+
+def iqcc_set_wait_limit(H: Hamiltonian, polls: int) -> None:
+    """Polls a device wait makes before it gives up with IQCC_ERR_TIMEOUT (0: the default)."""
+    H._check(_set_wait(H._h, int(polls)))
+
+
+def iqcc_wait_selftest(H: Hamiltonian) -> None:
+    """One device wait on a word nothing writes: always raises IQCC_ERR_TIMEOUT."""
+    H._check(_wait_selftest(H._h))
 
 
 def iqcc_last_error(H: Hamiltonian | None = None) -> str:

@@ -49,6 +49,11 @@ def compare(gpu, ref, eps=0.0, rel=REL, abs_=ABS, scale=None, thresholds=()):
         abs_ = abs_ * max(1.0, scale)
     gk, rk = _keys(gx, gz), _keys(rx, rz)
     bad = []
+    for kind, keys in (("repeated_gpu_key", gk), ("repeated_oracle_key", rk)):
+        u, cnt = np.unique(keys, return_counts=True)
+        bad += [(kind, k.tobytes(), int(m)) for k, m in zip(u[cnt > 1], cnt[cnt > 1])]
+    if bad:
+        return bad
     if len(gk) == len(rk) and np.array_equal(gk, rk):
         ig = ir = np.arange(len(gk))
     else:

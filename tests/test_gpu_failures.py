@@ -1,0 +1,116 @@
+"""Failure paths of the device code, made to happen without faulting the GPU.
+
+* Every device wait (the DIS grouping's wait for a published group key, the
+  stable compactions' decoupled look-back) polls a bounded number of times,
+  then records IQCC_ERR_TIMEOUT and returns; the call fails with that status
+  and the context refuses every later call (IQCC_ERR_STATE).  The self-test
+  waits on a word that nothing writes; a one-poll limit on real work shows that
+  every wait gives up and returns instead of hanging.
+* A probe bound of one bucket in the DIS group table makes a crowded table
+  overflow: IQCC_ERR_HASH_FULL, then IQCC_ERR_STATE.
+In every case a fresh context on the same GPU still works.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2603_08883_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+iqcc = pytest.importorskip("paper_2603_08883_gb300.iqcc", exc_type=ImportError)
+
+TIMEOUT, HASH_FULL, STATE = 6, 5, 7
+
+
+def _fresh_context_still_works():
+    n = 12
+    _, x, z, c = synth.random_hamiltonian(n, 500, 3)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    th, ph = synth.qmf_angles(n, "basis")
+    assert iqcc.iqcc_qmf_energy(H, th, ph) == pytest.approx(oracle.Oracle(n, x, z, c).energy(th, ph), abs=1e-9)
+    H.close()
+
+
+def test_device_wait_on_a_word_nothing_writes_times_out():
+    n = 10
+    _, x, z, c = synth.random_hamiltonian(n, 100, 1)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    iqcc.iqcc_set_wait_limit(H, 1000)
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_wait_selftest(H)
+    assert e.value.status == TIMEOUT
+    assert "device error 6" in iqcc.iqcc_last_error(H)
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_qmf_energy(H, np.zeros(n), np.zeros(n))
+    assert e.value.status == STATE
+    H.close()
+    _fresh_context_still_works()
+
+
+def test_default_wait_limit_is_restored_and_bounded():
+    """With the default limit (2^24 polls) the self-test still gives up (about a second)."""
+    n = 10
+    _, x, z, c = synth.random_hamiltonian(n, 100, 2)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+    iqcc.iqcc_set_wait_limit(H, 5)
+    iqcc.iqcc_set_wait_limit(H, 0)
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_wait_selftest(H)
+    assert e.value.status == TIMEOUT
+    H.close()
+
+
+def test_one_poll_waits_give_up_or_finish_correctly():
+    """A one-poll limit on work that waits for real (a compaction of about
+    10^6 rows in about 1,000 tiles; DIS grouping with many rows per group): each
+    call either completes with the right result or fails with IQCC_ERR_TIMEOUT
+    and leaves the context refusing further calls.  Nothing hangs."""
+    n = 40
+    _, x, z, c = synth.random_hamiltonian(n, 1_200_000, 9, density=0.1)
+    x[: len(x) // 2] &= np.uint64(0xF)             # few flip sets: many rows share a DIS group
+    eps = float(np.quantile(np.abs(c), 0.5))
+    R = iqcc.iqcc_load_hamiltonian(n, x, z, c)     # the same calls with the default limit
+    iqcc.iqcc_prune(R, eps)
+    ref = iqcc.iqcc_export(R)
+    R.close()
+    outcomes = []
+    for call in ("prune", "dis"):
+        H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
+        iqcc.iqcc_set_wait_limit(H, 1)
+        th, ph = synth.qmf_angles(n, "basis")
+        try:
+            if call == "prune":
+                iqcc.iqcc_prune(H, eps)
+                iqcc.iqcc_set_wait_limit(H, 0)
+                got = iqcc.iqcc_export(H)
+                assert all(np.array_equal(a, b) for a, b in zip(got, ref))
+            else:
+                iqcc.iqcc_dis_gradients(H, th, ph, cap=4)
+            outcomes.append("ok")
+        except iqcc.IqccError as e:
+            assert e.status == TIMEOUT
+            outcomes.append("timeout")
+            with pytest.raises(iqcc.IqccError) as e2:
+                iqcc.iqcc_qmf_energy(H, th, ph)
+            assert e2.value.status == STATE
+        H.close()
+    print("one-poll outcomes:", outcomes)
+    _fresh_context_still_works()
+
+
+def test_dis_group_table_full_then_context_refuses():
+    """A one-bucket probe bound (max_probe = 1) and about 10^5 distinct flip
+    sets: some buckets of the DIS group table overflow."""
+    n = 40
+    _, x, z, c = synth.random_hamiltonian(n, 100_000, 4, density=0.3)
+    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, max_probe=1)
+    th, ph = synth.qmf_angles(n, "basis")
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_dis_gradients(H, th, ph, cap=4)
+    assert e.value.status == HASH_FULL
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_dress(H, x[0], z[0] ^ np.uint64(1), [0.1])
+    assert e.value.status == STATE
+    H.close()
+    _fresh_context_still_works()
