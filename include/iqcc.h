@@ -184,8 +184,11 @@ iqcc_status iqcc_energy_gradients(iqcc_ctx* ctx, const uint64_t* gx, const uint6
  *   distinct non-empty flip set F (the x vector) of the terms of H, with Y on
  *   the lowest qubit of F and X on the rest (odd Y count, matching flip set).
  *   When Omega is a basis state (all theta in {0, pi}) only terms with flip
- *   set F contribute (Eq. 14-15) and the pass is one stream over H; otherwise
- *   every term is summed for every candidate (cost M x G).  Candidates are
+ *   set F contribute (Eq. 14-15): the terms are grouped by flip set in a
+ *   partition join (a hash partition of the rows by F, each partition summed
+ *   in shared memory); otherwise every term is summed for every candidate
+ *   (cost M x G).  Device scratch: 32 bytes (64 when Wd = 4) per term with
+ *   a non-empty flip set, and (8 Wd + 8) per candidate.  Candidates are
  *   ordered by |g| with its 20 low mantissa bits cleared (relative tie
  *   tolerance 2^-32), descending, then canonical key ascending.  *n_out = G
  *   (the total); min(cap, G) candidates are written to ox, oz [cap][W] and grad
@@ -240,10 +243,9 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi,
                          const iqcc_iter_opts* opts, iqcc_iter_result* out);
 
 /*
- * Device waits.  Two kinds of kernel wait on other blocks: the DIS grouping
- * (a block that meets a group slot another block has claimed waits for the
- * group's key to be published) and the stable compactions (a tile waits for
- * its predecessors' counts, decoupled look-back).  Each wait polls at most
+ * Device waits.  The stable in-place compactions (the dress's split of the
+ * commuting rows, the compression) wait on other blocks: a tile waits for its
+ * predecessors' counts (decoupled look-back).  Each wait polls at most
  * `polls` times; then the kernel records IQCC_ERR_TIMEOUT and returns without
  * writing out of bounds, the call that launched it returns IQCC_ERR_TIMEOUT,
  * and the context refuses every later call (IQCC_ERR_STATE).  polls = 0

@@ -142,6 +142,12 @@ HashView hash_view(const iqcc_ctx* ctx) {
 
 DevCounters* dctr(iqcc_ctx* ctx) { return (DevCounters*)ctx->counters.p; }
 
+// Terms of H: the rows, less those a pending term-limit cut drops.
+int64_t live_terms(const iqcc_ctx* ctx) { return ctx->pending ? ctx->live : ctx->M; }
+
+// The pending cut's flags for kernels that skip dropped rows (NULL: none pending).
+const uint8_t* live_flags(const iqcc_ctx* ctx) { return ctx->pending ? (const uint8_t*)ctx->dropflags.p : nullptr; }
+
 iqcc_status read_counters(iqcc_ctx* ctx) {
     CK(cudaMemcpyAsync(ctx->h_counters, ctx->counters.p, sizeof(DevCounters), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
@@ -305,7 +311,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     launch_abc(ctx->Wd, ctx->rows(), ctx->c(), ctx->M, pkey, basis, occ, tables, n_groups(ctx), partials,
-               ctx->stream, ph.counts ? &ph : nullptr);
+               ctx->stream, ph.counts ? &ph : nullptr, live_flags(ctx));
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     launch_reduce3(partials, nb, out3, ctx->stream);
@@ -322,7 +328,7 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.n_energy++;
     ctx->stats.energy_kernel_ms += ms;
-    ctx->stats.energy_bytes += (double)ctx->M * (16.0 * ctx->Wd + 8.0);
+    ctx->stats.energy_bytes += (double)live_terms(ctx) * (16.0 * ctx->Wd + 8.0);
     if (ph.counts) {
         ctx->pair_ready = true;
         ctx->pair_log2 = ph.log2_bins;
@@ -333,6 +339,8 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
     abc[2] = h3[2];
     return IQCC_OK;
 }
+
+iqcc_status apply_pending_cut(iqcc_ctx* ctx);
 
 // One dress by pair partition (k_pairjoin.cu): bin histogram of the
 // anticommuting rows, split (commuting rows compacted in place, anticommuting
@@ -369,7 +377,7 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     if (!ready) {
         CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
         CK(cudaMemsetAsync(arr, 0, arr_bytes, ctx->stream));
-        launch_pair_hist(d, ctx->rows(), M, lb, arr + 1, c, ctx->stream);
+        launch_pair_hist(d, ctx->rows(), M, lb, arr + 1, c, ctx->stream, live_flags(ctx));
     }
     launch_scan_u32_long(arr + 1, NB, scan_tmp, ctx->stream);
     CK_LAUNCH();
@@ -377,7 +385,7 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     if (st) return st;
     const int64_t n_anti = ready ? ctx->pair_n_anti : (int64_t)ctx->h_counters->n_anti;
     *n_anti_out = n_anti;
-    if (n_anti == 0) return IQCC_OK;  // P commutes with every term
+    if (n_anti == 0) return apply_pending_cut(ctx);  // P commutes with every term
     // bin copies of the anticommuting rows
     Carver rv;
     rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
@@ -388,16 +396,17 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     double* rc = rv.take<double>(n_anti);
     if (rv.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
     const uint32_t bpb = pair_bins_per_block(n_anti, lb);
+    const int64_t live = live_terms(ctx);  // the rows a pending cut keeps: the input of this dress
     bool scattered = false;
-    if (M + n_anti > ctx->capacity) {
+    if (live + n_anti > ctx->capacity) {
         // exact admission: bin copies and a counting join first, H untouched
-        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c,
-                          ctx->stream);
+        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c, ctx->stream,
+                          live_flags(ctx));
         launch_pair_join(d, false, rk, rc, arr, lb, bpb, ctx->rows(), ctx->c(), m_comm, out_cursor, c, ctx->stream);
         CK_LAUNCH();
         st = read_counters(ctx);
         if (st) return st;
-        const int64_t upper = M + (int64_t)ctx->h_counters->n_new;
+        const int64_t upper = live + (int64_t)ctx->h_counters->n_new;
         if (upper > ctx->capacity) {
             char buf[200];
             snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)upper,
@@ -409,11 +418,11 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
         CK(cudaMemsetAsync(&c->n_new, 0, sizeof(unsigned long long), ctx->stream));
         scattered = true;
     } else {
-        st = reserve_rows(ctx, M + n_anti);
+        st = reserve_rows(ctx, std::max(M, live + n_anti));
         if (st) return st;
     }
     launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c,
-                      ctx->stream);
+                      ctx->stream, live_flags(ctx));
     launch_pair_join(d, true, rk, rc, arr, lb, bpb, ctx->rows(), ctx->c(), m_comm, out_cursor, c, ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
@@ -424,10 +433,11 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     CK(cudaMemcpyAsync(&oc, out_cursor, sizeof oc, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const int64_t n_new = (int64_t)ctx->h_counters->n_new;
-    if ((int64_t)mc + n_anti != M || (int64_t)oc != n_anti + n_new)
+    if ((int64_t)mc + n_anti != live || (int64_t)oc != n_anti + n_new)
         return fail(ctx, IQCC_ERR_STATE, "internal: pair dress row counts disagree");
     cudaEventElapsedTime(ms_out, ctx->ev0, ctx->ev1);
-    ctx->M = M + n_new;
+    ctx->M = live + n_new;
+    ctx->pending = false;  // the split dropped the rows of the pending cut
     ctx->index_valid = false;
     *n_new_out = n_new;
     return IQCC_OK;
@@ -435,13 +445,13 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
 
 // One generator (device-layout key); on IQCC_ERR_CAPACITY / OOM H is unchanged.
 iqcc_status dress_one(iqcc_ctx* ctx, const uint64_t* pkey, double tau) {
-    const int64_t M = ctx->M;
+    const int64_t M = live_terms(ctx);
     bool identity = true;
     for (int w = 0; w < 2 * ctx->Wd; ++w) identity &= pkey[w] == 0;
     if (M == 0 || identity) {
         ctx->stats.n_dress++;
         ctx->stats.dressed_terms += M;
-        return IQCC_OK;
+        return apply_pending_cut(ctx);
     }
     PairDress d{ctx->Wd, pkey, nullptr, 0, std::cos(tau), std::sin(tau)};
     int64_t n_anti = 0, n_new = 0;
@@ -530,24 +540,115 @@ iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags
     return IQCC_OK;
 }
 
+// The rows of a term limit's threshold bucket (ties, n_cand of them, with
+// `need` still to keep) kept in order of (key value desc, canonical key asc):
+// their flags set.
+iqcc_status keep_bucket_head(iqcc_ctx* ctx, const double* key, const uint32_t* ties, int64_t n_cand, int64_t need,
+                             uint8_t* flags) {
+    if (need >= n_cand) {
+        launch_set_flags(ties, n_cand, flags, ctx->stream);
+        CK_LAUNCH();
+        return IQCC_OK;
+    }
+    const int stride = 2 * ctx->Wd + 1;
+    Carver dry;
+    dry.take<uint64_t>((size_t)n_cand * stride);
+    carve_sort(dry, n_cand);
+    if (!ensure(ctx, ctx->aux, dry.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    Carver cv2{(char*)ctx->aux.p, 0};
+    uint64_t* skeys = cv2.take<uint64_t>((size_t)n_cand * stride);
+    SortArea ca = carve_sort(cv2, n_cand);
+    if (cv2.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+    launch_candidate_keys(ctx->Wd, ctx->rows(), key, ties, n_cand, skeys, ctx->stream);
+    launch_iota(ca.a, n_cand, ctx->stream);
+    SortPlan plan{};
+    plan.n_words = stride;
+    plan.n_order = stride;
+    for (int w = 0; w < stride; ++w) plan.order[w] = w;
+    uint32_t* sorted = nullptr;
+    radix_sort_indirect(skeys, stride, plan, ca.a, ca.b, n_cand, &sorted, ca.tmp, ca.tmp_bytes, ctx->stream);
+    CK_LAUNCH();
+    launch_set_flags_sorted(ties, sorted, need, flags, ctx->stream);
+    CK_LAUNCH();
+    return IQCC_OK;
+}
+
+// Applies a pending term-limit cut: the rows it drops are compacted away.
+iqcc_status apply_pending_cut(iqcc_ctx* ctx) {
+    if (!ctx->pending) return IQCC_OK;
+    const int64_t M = ctx->M;
+    Carver cv;
+    cv.take<char>(compact_inplace_scratch_bytes(M));
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    DevCounters* c = dctr(ctx);
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_compact_inplace(ctx->Wd, (const uint8_t*)ctx->dropflags.p, ctx->rows(), ctx->c(), M, ctx->scratch.p,
+                           &c->aux, c, ctx->stream);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    ctx->M = (int64_t)ctx->h_counters->aux;
+    ctx->pending = false;
+    ctx->index_valid = false;
+    return IQCC_OK;
+}
+
+// The term limit of App. A / Tables 2-3 (keep the max_terms largest |C|,
+// ties in canonical key order) as flags only: the rows stay in place and the
+// next dress drops the others while it moves rows anyway (its split), so the
+// cut costs no compaction.  Only iqcc_iterate defers a cut, and only when a
+// dress follows it.
+iqcc_status cut_deferred(iqcc_ctx* ctx, int64_t max_terms, int64_t* removed) {
+    *removed = 0;
+    const int64_t M = ctx->M;
+    if (ctx->pending || max_terms <= 0 || M <= max_terms) return IQCC_OK;
+    ctx->pair_ready = false;
+    Carver cv;
+    cv.take<uint32_t>(M);  // rows of the threshold bucket
+    if (!ensure(ctx, ctx->scratch, cv.off) || !ensure(ctx, ctx->dropflags, (size_t)M))
+        return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    uint32_t* ties = (uint32_t*)ctx->scratch.p;
+    uint8_t* flags = (uint8_t*)ctx->dropflags.p;
+    DevCounters* c = dctr(ctx);
+    CK(cudaEventRecord(ctx->ev0, ctx->stream));
+    int64_t need = max_terms;
+    uint64_t prefix = 0, pmask = 0;
+    iqcc_status st = select_bucket(ctx, ctx->c(), nullptr, M, M, &need, &prefix, &pmask);
+    if (st) return st;
+    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+    launch_cut_flags(ctx->c(), flags, M, prefix, pmask, ties, &c->aux, ctx->stream);
+    CK_LAUNCH();
+    st = read_counters(ctx);
+    if (st) return st;
+    st = keep_bucket_head(ctx, ctx->c(), ties, (int64_t)ctx->h_counters->aux, need, flags);
+    if (st) return st;
+    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0;
+    cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+    ctx->stats.prune_ms += ms;
+    ctx->pending = true;
+    ctx->live = max_terms;
+    *removed = M - max_terms;
+    return IQCC_OK;
+}
+
 iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* removed, const double* rank = nullptr) {
     ctx->pair_ready = false;
-    const int64_t M = ctx->M;
     *removed = 0;
+    iqcc_status st = apply_pending_cut(ctx);
+    if (st) return st;
+    const int64_t M = ctx->M;
     if (M == 0) return IQCC_OK;
     Carver cv;
     cv.take<uint8_t>(M);
-    cv.take<unsigned long long>(256);
     cv.take<char>(compact_inplace_scratch_bytes(M));
     cv.take<uint32_t>(M);  // tie list
-    cv.off += sort_area_bytes(M);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
     uint8_t* flags = cv.take<uint8_t>(M);
-    unsigned long long* hist = cv.take<unsigned long long>(256);
     char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
     uint32_t* ties = cv.take<uint32_t>(M);
-    SortArea sa = carve_sort(cv, M);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
     DevCounters* c = dctr(ctx);
@@ -555,7 +656,7 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
     launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, flags, &c->aux, ctx->stream);
     CK_LAUNCH();
-    iqcc_status st = read_counters(ctx);
+    st = read_counters(ctx);
     if (st) return st;
     const int64_t kept = (int64_t)ctx->h_counters->aux;
     if (max_terms > 0 && kept > max_terms) {
@@ -571,32 +672,8 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
         CK_LAUNCH();
         st = read_counters(ctx);
         if (st) return st;
-        const int64_t n_cand = (int64_t)ctx->h_counters->aux;
-        if (need >= n_cand) {
-            launch_set_flags(ties, n_cand, flags, ctx->stream);
-            CK_LAUNCH();
-        } else {
-            const int stride = 2 * ctx->Wd + 1;
-            Carver dry;
-            dry.take<uint64_t>((size_t)n_cand * stride);
-            carve_sort(dry, n_cand);
-            if (!ensure(ctx, ctx->aux, dry.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-            Carver cv2{(char*)ctx->aux.p, 0};
-            uint64_t* skeys = cv2.take<uint64_t>((size_t)n_cand * stride);
-            SortArea ca = carve_sort(cv2, n_cand);
-            if (cv2.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-            launch_candidate_keys(ctx->Wd, ctx->rows(), rank ? rank : ctx->c(), ties, n_cand, skeys, ctx->stream);
-            launch_iota(ca.a, n_cand, ctx->stream);
-            SortPlan plan{};
-            plan.n_words = stride;
-            plan.n_order = stride;
-            for (int w = 0; w < stride; ++w) plan.order[w] = w;
-            uint32_t* sorted = nullptr;
-            radix_sort_indirect(skeys, stride, plan, ca.a, ca.b, n_cand, &sorted, ca.tmp, ca.tmp_bytes, ctx->stream);
-            CK_LAUNCH();
-            launch_set_flags_sorted(ties, sorted, need, flags, ctx->stream);
-            CK_LAUNCH();
-        }
+        st = keep_bucket_head(ctx, rank ? rank : ctx->c(), ties, (int64_t)ctx->h_counters->aux, need, flags);
+        if (st) return st;
     }
     CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
     launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
@@ -625,11 +702,13 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     occ_words(ctx, theta, occ);
     // groups (distinct flip sets) are at most the rows
     const int64_t Mg = std::max<int64_t>(M, 1);
-    const uint64_t gslots = pow2_at_least((uint64_t)Mg * 2);
     const int nblk = expect_blocks();
     constexpr int64_t kHeadLimit = 1 << 16;  // the top-k path orders at most this many candidates
+    ctx->pair_ready = false;                 // the bins below reuse the dress-bin buffer
+    const int lb = pair_bins_log2(M);
+    const uint32_t NB = 1u << lb;
     Carver cv;
-    cv.take<uint64_t>(gslots);
+    cv.take<uint32_t>(1024);
     cv.take<uint64_t>((size_t)Mg * Wd);
     cv.take<double>(Mg);
     cv.take<uint32_t>(kHeadLimit);
@@ -640,7 +719,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     cv.take<double>(16);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
-    uint64_t* slots = cv.take<uint64_t>(gslots);
+    uint32_t* scan_tmp = cv.take<uint32_t>(1024);
     uint64_t* gkeys = cv.take<uint64_t>((size_t)Mg * Wd);
     double* gsum = cv.take<double>(Mg);
     uint32_t* head = cv.take<uint32_t>(kHeadLimit);
@@ -652,16 +731,29 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
     DevCounters* c = dctr(ctx);
+    const size_t arr_bytes = sizeof(uint32_t) * ((size_t)NB + 1);
+    if (!ensure(ctx, ctx->pairbuf, arr_bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    uint32_t* arr = (uint32_t*)ctx->pairbuf.p;  // [0] = 0, [1 + b]: count, then start, then end of bin b
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    HashView gh{slots, gslots / kBucketSlots - 1, ctx->max_probe};
-    launch_hash_clear(gh, gslots, ctx->stream);
-    CK_LAUNCH();
+    // one candidate per distinct flip set: the rows grouped by flip set in a
+    // partition join (k_disgroup.cu), with the z-eigenstate gradient sums
     CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
-    launch_dis_group(Wd, ctx->rows(), ctx->c(), M, occ, basis, slots, gh.bucket_mask, ctx->max_probe, gkeys, gsum, c,
-                     ctx->stream, Mg);
+    CK(cudaMemsetAsync(arr, 0, arr_bytes, ctx->stream));
+    launch_flip_hist(Wd, ctx->rows(), M, lb, arr + 1, c, ctx->stream);
+    launch_scan_u32_long(arr + 1, NB, scan_tmp, ctx->stream);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
+    const int64_t n_flip = (int64_t)ctx->h_counters->aux;
+    if (n_flip > 0) {
+        if (!ensure(ctx, ctx->aux, (size_t)n_flip * flip_record_bytes(Wd)))
+            return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        launch_flip_group(Wd, ctx->rows(), ctx->c(), M, occ, basis, lb, arr, (uint64_t*)ctx->aux.p, n_flip, gkeys,
+                          gsum, Mg, c, ctx->stream);
+        CK_LAUNCH();
+        st = read_counters(ctx);
+        if (st) return st;
+    }
     const int64_t G = (int64_t)ctx->h_counters->n_groups;
     if (!basis && G > 0) {
         // general angles: every term against every candidate, 16 candidates per pass
@@ -1427,22 +1519,29 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         const int64_t avail = std::min<int64_t>(G, n_gen);
         while (used < avail && std::fabs(g[used]) > gmin) ++used;
     }
+    // A term limit cut followed by another dress only marks the rows it keeps;
+    // that dress drops the others as it moves rows (cut_deferred).  On an error
+    // the marks are applied before returning, so H is left in one piece.
+    auto fail_iter = [&](iqcc_status st) {
+        if (ctx->pending && !ctx->broken) apply_pending_cut(ctx);
+        return st;
+    };
     for (int k = 0; k < used; ++k) {
         double abc[3];
         uint64_t pk[8];
         pad_key(ctx, gx.data() + k * W, gz.data() + k * W, pk);
         // A, B, C and the dress bins of the generator in one pass over H
         iqcc_status st = abc_impl(ctx, pk, theta, phi, abc, true);
-        if (st) return st;
+        if (st) return fail_iter(st);
         double tau;
         if (o->n_forced > 0 && o->forced_tau) tau = o->forced_tau[k];
         else tau = (abc[1] == 0.0 && abc[2] == 0.0) ? 0.0 : std::atan2(-abc[2], -abc[1]);
-        out->dressed_terms += ctx->M;
+        out->dressed_terms += live_terms(ctx);
         int applied = 0;
         st = iqcc_dress(ctx, 1, gx.data() + k * W, gz.data() + k * W, &tau, &applied);
         if (st) {
             out->n_applied = k;
-            return st;
+            return fail_iter(st);
         }
         std::memcpy(out->gx + k * W, gx.data() + k * W, sizeof(uint64_t) * W);
         std::memcpy(out->gz + k * W, gz.data() + k * W, sizeof(uint64_t) * W);
@@ -1453,9 +1552,14 @@ iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi, 
         out->n_terms_peak = std::max(out->n_terms_peak, ctx->M);
         if (o->max_terms > 0 && ctx->M > o->max_terms) {
             int64_t cut = 0;
-            st = o->screening == 1 ? prune_learned(ctx, 0.0, o->max_terms, used, gx.data(), gz.data(), theta, phi, &cut)
-                                   : iqcc_prune(ctx, 0.0, o->max_terms, &cut);
-            if (st) return st;
+            if (o->screening == 1)
+                st = prune_learned(ctx, 0.0, o->max_terms, used, gx.data(), gz.data(), theta, phi, &cut);
+            else if (k + 1 < used)
+                st = cut_deferred(ctx, o->max_terms, &cut);
+            // else: the compression below applies the same term limit (keeping the
+            // max_terms largest |C| and then dropping |C| < eps keeps the same rows
+            // as dropping |C| < eps and then keeping the max_terms largest)
+            if (st) return fail_iter(st);
             out->n_removed += cut;
         }
     }

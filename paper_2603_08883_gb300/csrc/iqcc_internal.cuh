@@ -20,7 +20,6 @@ namespace iqcc {
 
 constexpr uint64_t kEmptySlot = ~0ull;        // hash slot never used
 constexpr uint32_t kRowRemoved = 0xFFFFFFFFu; // compaction map entry of a removed row
-constexpr uint32_t kPendingGroup = 0xFFFFFFFEu;  // group slot claimed, key not yet published
 constexpr int kBucketSlots = 4;               // 4 x 8-byte slots = one 32-byte sector
 
 template <int W>
@@ -264,6 +263,9 @@ struct iqcc_ctx {
     iqcc::Buf hash;                // slots of the key index (partitioned dressing and batches only)
     uint64_t hash_slots = 0;       // active slots (power of two)
     bool index_valid = false;      // the index holds exactly rows [0, M)
+    iqcc::Buf dropflags;           // a deferred term-limit cut: 1 for the rows it keeps
+    bool pending = false;          // dropflags applies to rows [0, M); the next dress drops the rest
+    int64_t live = 0;              // rows kept by the pending cut (M when none is pending)
     iqcc::Buf pairbuf;             // dress bins: [0] = 0, then per bin its count, start, end
     bool pair_ready = false;       // pairbuf holds the bin counts of pair_key's dress of the current H
     int pair_log2 = 0;
@@ -311,13 +313,6 @@ size_t index_build_scratch_bytes(int64_t n, uint64_t n_slots);
 void launch_scan_u32_long(uint32_t* data, int64_t n, uint32_t* tmp, cudaStream_t s);
 void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView h, uint64_t n_slots, void* scratch,
                         DevCounters* ctr, cudaStream_t s);
-// After an in-place compaction with map new_row (old row -> new row or
-// kRowRemoved): the index rebuilt partition by partition from its own entries
-// (no key is read), removed rows dropped.  n_entries: rows indexed before.
-size_t index_reindex_scratch_bytes(int64_t n_entries);
-void launch_index_reindex(HashView h, uint64_t n_slots, const uint32_t* new_row, int64_t n_entries, void* scratch,
-                          DevCounters* ctr, cudaStream_t s);
-
 // k_grad.cu: adjoint of the dressed QMF energy.  tab: energy_grad_table_doubles(n)
 // per-qubit values; partials: [blocks][energy_grad_cols(n)]; the column sums go
 // through launch_grad_combine to out[2n + 3] = (dE/dtheta, dE/dphi, A, B, C).
@@ -362,8 +357,6 @@ void launch_cross_rows(int Wd, const uint64_t* rows, const double* coef, int64_t
 void launch_cross_dress(int Wd, const uint64_t* rows, double* coef, int64_t M, const uint64_t* pkey, double cos_t,
                         double sin_t, HashView h, HashView hp, const uint64_t* prow, const double* pcoef,
                         int64_t n_peer, DevCounters* ctr, cudaStream_t s);
-void launch_dress_seg(const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M, const Gen<1>* gens, int B,
-                      HashView h, DevCounters* ctr, cudaStream_t s);
 
 // k_screen.cu: learned term screening (features, perceptron scores).  gsup:
 // union of the generators' supports (Wd words); ev: per-qubit <sigma> at
@@ -394,13 +387,15 @@ struct PairDress {
 int pair_bins_log2(int64_t M);
 uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins);
 size_t pair_split_scratch_bytes(int64_t M);
-// counts: [2^log2_bins] zeroed; adds each anticommuting row to its bin and the total to ctr->n_anti
+// counts: [2^log2_bins] zeroed; adds each anticommuting row to its bin and the total to ctr->n_anti.
+// live (may be NULL): rows with live[i] == 0 are dropped (a pending term-limit cut), here and in the split.
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
-                      DevCounters* ctr, cudaStream_t s);
+                      DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
 // cursor: bin starts in, bin ends out (when scattering); *m_comm: commuting rows (when compacting)
+// rk [n_anti][2 Wd] keys and rc [n_anti] coefficients of the anticommuting rows, by bin
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M,
                        int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, void* tile_scratch,
-                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s);
+                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
 // start: [2^log2_bins + 1] bin starts; rows without a partner counted in ctr->n_new; with `write` the
 // dressed rows and appended partners are written from row *m_comm + (*out_cursor, zeroed) on
 void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
@@ -408,14 +403,9 @@ void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const 
                       const unsigned long long* m_comm, unsigned long long* out_cursor, DevCounters* ctr,
                       cudaStream_t s);
 
-// k_hash.cu / k_dress.cu
+// k_dress.cu: the key index (partitioned dress only)
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,
-                        DevCounters* ctr, cudaStream_t s);
-void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
-                  const uint64_t* pkey, double cos_t, double sin_t, HashView h, DevCounters* ctr,
-                  cudaStream_t s);
-void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,
                         DevCounters* ctr, cudaStream_t s);
 
 // k_expect.cu
@@ -428,16 +418,27 @@ struct PairHistOut {
     int log2_bins;
     DevCounters* ctr;   // n_anti (zeroed) receives the total
 };
+// live (may be NULL: every row): rows with live[i] == 0 are skipped (a pending term-limit cut).
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,
                 bool basis, const uint64_t* occ, const double* tables, int n_groups, double* partials,
-                cudaStream_t s, const PairHistOut* pair = nullptr);
+                cudaStream_t s, const PairHistOut* pair = nullptr, const uint8_t* live = nullptr);
 void launch_reduce3(const double* partials, int n, double* out3, cudaStream_t s);
 void launch_qmf_tables(const double* theta, const double* phi, int n, int n_groups, double* tables,
                        cudaStream_t s);
-// DIS basis path: group by x, sum signed contributions.
-void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ,
-                      bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe,
-                      uint64_t* gkeys, double* gsum, DevCounters* ctr, cudaStream_t s, int64_t max_groups);
+// k_disgroup.cu: DIS candidates by partition.  launch_flip_hist counts the rows
+// with a non-empty flip set into 2^log2_bins bins (counts zeroed; total to
+// ctr->aux); after an exclusive scan of counts, launch_flip_group copies them
+// into their bins (flip sets and, when `values`, z-eigenstate
+// contributions) and writes one (flip set, summed
+// contribution) per distinct flip set to gkeys [.][Wd] / gsum, counted in
+// ctr->n_groups (at most max_groups).  arr: [0] = 0, then the bin starts;
+// rr: flip_record_bytes(Wd) per row with a non-empty flip set.
+void launch_flip_hist(int Wd, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts, DevCounters* ctr,
+                      cudaStream_t s);
+size_t flip_record_bytes(int Wd);
+void launch_flip_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ_words,
+                       bool values, int log2_bins, uint32_t* arr, uint64_t* rr, int64_t n_flip, uint64_t* gkeys,
+                       double* gsum, int64_t max_groups, DevCounters* ctr, cudaStream_t s);
 // General-angle gradients of K candidates: partials[block][K].
 void launch_grad_general(int Wd, const uint64_t* rows, const double* coef, int64_t M,
                          const uint64_t* cand, int K, const double* tables, int n_groups,
@@ -526,6 +527,9 @@ void launch_bucket_values(const double* coef, const uint8_t* flags, int64_t n, u
 // rank[i] = boost where flags[i] and the |c| bits reach t_bits
 void launch_boost_rank(const double* coef, const uint8_t* flags, int64_t n, uint64_t t_bits, double boost, double* rank,
                        cudaStream_t s);
+// flags[i] = |c| bits above the bucket (every row live); bucket rows listed in cand
+void launch_cut_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
+                      uint32_t* cand, unsigned long long* n_cand, cudaStream_t s);
 void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, const uint32_t* cand, int64_t k,
                            uint64_t* skeys, cudaStream_t s);
 void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s);

@@ -226,73 +226,6 @@ __global__ void __launch_bounds__(kThreads) k_part_build(const uint64_t* __restr
     for (uint32_t k = threadIdx.x; k < part_slots / 2; k += blockDim.x) out[k] = src[k];
 }
 
-// After an in-place compaction: one block per partition reads its slots, drops
-// the entries of removed rows, gives the others their new row, and places
-// those whose home bucket lies in the partition into a fresh shared-memory
-// copy (the home is the slot's bucket minus the stored distance).  Entries
-// whose home lies in another partition (probes that ran in from an earlier
-// one) or whose new probe runs past the end are listed with their home slot.
-// Blocks read and write only their own partition.  In each round a thread
-// first issues its slot loads and then its row-map gathers, so that the
-// random gathers of a block are in flight together.
-// Shape chosen by measurement on the 100-qubit workload (2^32 slots): 8
-// entries per thread in one round and 2 blocks per SM (47.7 ms) beat 4 per
-// thread in two rounds (53 ms), 1 block per SM (61 ms) and 512-thread blocks
-// (58-65 ms): gathers in flight matter more than the few spilled registers.
-constexpr int kReindexThreads = 1024;
-constexpr int kReindexPairs = 4;  // slot pairs per thread and round
-constexpr int kReindexRounds = (1 << kPartLog2) / 2 / kReindexThreads / kReindexPairs;
-
-__global__ void __launch_bounds__(kReindexThreads, 2) k_part_reindex(uint64_t* slots, uint64_t bmask, int pshift,
-                                                                  int max_slots, const uint32_t* __restrict__ new_row,
-                                                                  uint64_t* ovf_entry, uint64_t* ovf_home,
-                                                                  unsigned long long* n_ovf, int64_t ovf_cap,
-                                                                  DevCounters* ctr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    unsigned long long* tab = reinterpret_cast<unsigned long long*>(smem_raw);
-    const uint32_t part_slots = 1u << pshift;
-    const uint32_t pairs = part_slots / 2;
-    for (uint32_t k = threadIdx.x; k < part_slots; k += blockDim.x) tab[k] = kEmptySlot;
-    __syncthreads();
-    const uint64_t first = (uint64_t)blockIdx.x << pshift;
-    const ulonglong2* in = reinterpret_cast<const ulonglong2*>(slots + first);
-#pragma unroll 1
-    for (int round = 0; round < kReindexRounds; ++round) {
-        uint64_t e[2 * kReindexPairs];
-#pragma unroll
-        for (int t = 0; t < kReindexPairs; ++t) {
-            const uint32_t k2 = threadIdx.x + (uint32_t)(round * kReindexPairs + t) * kReindexThreads;
-            ulonglong2 v = make_ulonglong2(kEmptySlot, kEmptySlot);
-            if (k2 < pairs) v = __ldcs(in + k2);
-            e[2 * t] = v.x;
-            e[2 * t + 1] = v.y;
-        }
-#pragma unroll
-        for (int t = 0; t < 2 * kReindexPairs; ++t) {  // the new row replaces the old (empty when removed)
-            if (e[t] == kEmptySlot) continue;
-            const uint32_t nr = __ldg(new_row + (uint32_t)e[t]);
-            e[t] = (nr == kRowRemoved) ? kEmptySlot : ((e[t] & 0xFFFFFFFF00000000ull) | nr);
-        }
-#pragma unroll
-        for (int t = 0; t < 2 * kReindexPairs; ++t) {
-            if (e[t] == kEmptySlot) continue;
-            const uint32_t k2 = threadIdx.x + (uint32_t)(round * kReindexPairs + t / 2) * kReindexThreads;
-            const uint64_t slot = first + 2 * (uint64_t)k2 + (t & 1);
-            const uint64_t home_slot = ((slot / kBucketSlots - entry_disp(e[t])) & bmask) * kBucketSlots;
-            int res = 0;
-            if ((home_slot >> pshift) == blockIdx.x)
-                res = place_local(tab, part_slots, (uint32_t)(home_slot - first), e[t], (uint32_t)e[t], max_slots);
-            if (res < 0) set_error(ctr, IQCC_ERR_HASH_FULL, 43);
-            else if (res == 0)
-                list_overflow(e[t], (uint32_t)e[t], home_slot, ovf_entry, ovf_home, n_ovf, ovf_cap, ctr, 44);
-        }
-    }
-    __syncthreads();
-    ulonglong2* out = reinterpret_cast<ulonglong2*>(slots + first);
-    const ulonglong2* src = reinterpret_cast<const ulonglong2*>(tab);
-    for (uint32_t k = threadIdx.x; k < pairs; k += blockDim.x) out[k] = src[k];
-}
-
 // The listed entries, inserted into the written table by global CAS: linear
 // probing from the home slot (wrapping at the table end), within the probe
 // bound, the stored distance set to the slot found.
@@ -502,30 +435,6 @@ void launch_index_build(int Wd, const uint64_t* rows, int64_t n, HashView hv, ui
     k_part_overflow<<<64, kThreads, 0, s>>>(ovf_e, ovf_h, n_ovf, b.ovf_cap, hv.slots, n_slots,
                                             hv.max_probe * kBucketSlots, ctr);
     note_launch(3);
-}
-
-size_t index_reindex_scratch_bytes(int64_t n_entries) {
-    const int64_t cap = n_entries / 16 + 4096;
-    return align_up((size_t)cap * 8) * 2 + 256;
-}
-
-void launch_index_reindex(HashView hv, uint64_t n_slots, const uint32_t* new_row, int64_t n_entries, void* scratch,
-                          DevCounters* ctr, cudaStream_t s) {
-    const BuildPlan b = plan_for(0, n_slots);
-    const int64_t cap = n_entries / 16 + 4096;
-    char* p = (char*)scratch;
-    uint64_t* ovf_e = (uint64_t*)p; p += align_up((size_t)cap * 8);
-    uint64_t* ovf_h = (uint64_t*)p; p += align_up((size_t)cap * 8);
-    unsigned long long* n_ovf = (unsigned long long*)p;
-    cudaMemsetAsync(n_ovf, 0, sizeof(unsigned long long), s);
-    cudaFuncSetAttribute(k_part_reindex, cudaFuncAttributeMaxDynamicSharedMemorySize, 8 << kPartLog2);
-    cudaFuncSetAttribute(k_part_reindex, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
-    k_part_reindex<<<b.parts, kReindexThreads, (size_t)8 << b.pshift, s>>>(hv.slots, hv.bucket_mask, b.pshift,
-                                                                    hv.max_probe * kBucketSlots, new_row, ovf_e,
-                                                                    ovf_h, n_ovf, cap, ctr);
-    k_part_overflow<<<64, kThreads, 0, s>>>(ovf_e, ovf_h, n_ovf, cap, hv.slots, n_slots, hv.max_probe * kBucketSlots,
-                                            ctr);
-    note_launch(2);
 }
 
 }  // namespace iqcc

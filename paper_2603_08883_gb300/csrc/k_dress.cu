@@ -1,23 +1,12 @@
-// Dressing of the resident Hamiltonian by one generator (Eq. 5 in the
-// library convention, Eq. 6) and the open-addressing index it relies on.
+// The key index and the partitioned dressing (App. B's bit-wise partitions).
 //
 // Index: 2^k buckets of 4 eight-byte slots (one 32-byte sector), linear
 // probing bucket by bucket; a slot holds an entry (fingerprint, distance from
 // the home bucket, row; see make_entry) or kEmptySlot.  Lookups stop at the
-// first empty slot.  Compression does not touch the keys of the index: it
-// rebuilds each partition of slots from the entries themselves (k_build.cu),
-// which the stored distances make possible, so the table never holds
-// tombstones.
-//
-// Dress: one streaming pass over the M rows.  For a row T that anticommutes
-// with P (popcount parity of (xT & zP) ^ (zT & xP)), its partner Q = T xor P is
-// looked up.  Exactly one member of each present pair - the one with a zero at
-// P's lowest set bit - rotates both coefficients; a row whose partner is
-// absent scales itself by cos(tau) and appends (Q, s sin(tau) C_T) behind the
-// M input rows, indexing it in the same pass.  q -> q xor P is a bijection, so
-// appended keys are distinct and absent from H: no duplicate merge is needed
-// within one generator (the "insert if unique, else add" merge of App. D,
-// Eq. 18, done as a lookup).
+// first empty slot.  A context builds it only for the partitioned dress, which
+// looks its own rows up by key (the single-Hamiltonian and batched dresses
+// join by pair partition instead, k_pairjoin.cu); any change of the rows
+// invalidates it and the next partitioned dress rebuilds it (k_build.cu).
 #include <cuda_runtime.h>
 
 #include <atomic>
@@ -34,7 +23,8 @@ constexpr int kThreads = 256;
 // When absent, *free_slot is the empty slot that ended the probe: where q
 // would be inserted.  Read-only use of the slots through the non-coherent
 // path: a slot read stale can only be an empty slot since filled with a key
-// that no lookup of this pass seeks (see k_dress).
+// that no lookup of the same pass seeks (an appended key is the partner of
+// exactly one received row).
 template <int W>
 __device__ __forceinline__ int64_t lookup_slot(const Key<W>& q, uint64_t hv, const HashView& h,
                                                const uint64_t* __restrict__ rows, uint64_t* free_slot) {
@@ -79,17 +69,6 @@ __device__ __forceinline__ bool insert_from(uint64_t hv, uint32_t row, uint64_t 
         b = (b + 1) & h.bucket_mask;
     }
     return false;
-}
-
-template <int W>
-__device__ __forceinline__ bool bit_of(const Key<W>& k, int word, uint64_t mask) {
-    uint64_t v = 0;
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        if (word == j) v = k.x[j];
-        if (word == W + j) v = k.z[j];
-    }
-    return (v & mask) != 0;
 }
 
 __global__ void k_hash_clear(uint64_t* slots, uint64_t n) {
@@ -151,163 +130,6 @@ __device__ __forceinline__ int64_t lookup_slot_coef(const Key<W>& q, uint64_t hv
         b = (b + 1) & h.bucket_mask;
     }
     return -2;
-}
-
-constexpr int kWarpTile = 64;  // rows classified per warp before the probes
-#ifndef IQCC_DRESS_MIN_BLOCKS
-#define IQCC_DRESS_MIN_BLOCKS 4     // resident 256-thread blocks per SM the register budget targets (5 spills)
-#endif
-
-// One pass of Eq. 5 over rows [0, M).  Each warp classifies a tile of 64 rows
-// (two per lane) and queues the anticommuting ones in shared memory, so that
-// every lane then works on one queued row: partner lookup, pair rotation or
-// append.  An appended partner is inserted into the index at the empty slot
-// its lookup ended on (or the next one).  Concurrent inserts leave every
-// lookup correct: a key present before the pass has no empty slot ahead of it
-// in its probe sequence, and a slot filled during the pass was empty (a lookup
-// that read it so stops there) and receives a key no lookup seeks (an
-// appended key is the partner of exactly one row, q -> q xor P being a
-// bijection).  rows_app is the same buffer as rows;
-// appended rows land at M + slot and are not visited by this pass.
-template <int W, class GenOf>
-__device__ __forceinline__ void dress_body(const uint64_t* __restrict__ rows, uint64_t* rows_app, double* coef,
-                                           int64_t M, const GenOf& gen_of, HashView h, DevCounters* ctr) {
-    __shared__ uint32_t s_queue[kThreads / 32][kWarpTile];
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const unsigned lt = (1u << lane) - 1u;
-    uint32_t* queue = s_queue[wid];
-    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    unsigned n_anti = 0;
-    for (int64_t base = warp * kWarpTile; base < M; base += n_warps * kWarpTile) {
-        int nq = 0;
-#pragma unroll
-        for (int r = 0; r < kWarpTile / 32; ++r) {
-            const int64_t i = base + r * 32 + lane;
-            bool a = false;
-            if (i < M) {
-                const Key<W> t = load_key<W>(rows, i);
-                a = anticommutes<W>(t, gen_of(t).p);
-            }
-            const unsigned m = __ballot_sync(FULL, a);
-            if (a) queue[nq + __popc(m & lt)] = (uint32_t)(r * 32 + lane);
-            nq += __popc(m);
-        }
-        __syncwarp();
-        n_anti += (lane == 0) ? (unsigned)nq : 0u;
-        for (int e0 = 0; e0 < nq; e0 += 32) {
-            const int e = e0 + lane;
-            bool append = false;
-            Key<W> q;
-            double c_new = 0.0;
-            uint64_t hv = 0, fslot = 0;
-            if (e < nq) {
-                const int64_t i = base + queue[e];
-                const double ct = coef[i];  // independent of the lookup: issued first
-                const Key<W> t = load_key<W>(rows, i);
-                const Gen<W>& g = gen_of(t);
-                q = key_xor<W>(t, g.p);
-                const double s = (double)product_sign<W>(t, g.yP, g.p, q);
-                const bool upper = bit_of<W>(t, g.top_word, g.top_mask);
-                hv = hash_key<W>(q);
-                double cq = 0.0;
-                // only the member that rotates a present pair needs its partner's coefficient
-                const int64_t j = upper ? lookup_slot<W>(q, hv, h, rows, &fslot)
-                                        : lookup_slot_coef<W>(q, hv, h, rows, coef, &fslot, &cq);
-                if (j == -1) {
-                    coef[i] = ct * g.cos_t;
-                    c_new = s * ct * g.sin_t;
-                    append = true;
-                } else if (j >= 0) {
-                    if (!upper) {
-                        coef[i] = ct * g.cos_t - s * cq * g.sin_t;
-                        coef[j] = cq * g.cos_t + s * ct * g.sin_t;
-                    }
-                } else {
-                    set_error(ctr, IQCC_ERR_HASH_FULL, 2);
-                }
-            }
-            const unsigned need = __ballot_sync(FULL, append);
-            if (need) {
-                const int leader = __ffs(need) - 1;
-                unsigned long long slot0 = 0;
-                if (lane == leader) slot0 = atomicAdd(&ctr->n_new, (unsigned long long)__popc(need));
-                slot0 = __shfl_sync(FULL, slot0, leader);
-                if (append) {
-                    const int64_t r = M + (int64_t)slot0 + __popc(need & lt);
-                    store_key<W>(rows_app, r, q);
-                    coef[r] = c_new;
-                    if (!insert_from(hv, (uint32_t)r, fslot, h)) set_error(ctr, IQCC_ERR_HASH_FULL, 4);
-                }
-            }
-        }
-        __syncwarp();
-    }
-    if (lane == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
-}
-
-
-template <int W>
-struct FixedGen {
-    Gen<W> g;
-    __device__ __forceinline__ const Gen<W>& operator()(const Key<W>&) const { return g; }
-};
-
-template <int W>
-__global__ void __launch_bounds__(kThreads, W == 4 ? 4 : IQCC_DRESS_MIN_BLOCKS) k_dress(const uint64_t* __restrict__ rows,
-                                                                    uint64_t* rows_app, double* coef, int64_t M,
-                                                                    Gen<W> g, HashView h, DevCounters* ctr) {
-    dress_body<W>(rows, rows_app, coef, M, FixedGen<W>{g}, h, ctr);
-}
-
-// Generator of a row of a batch: its problem's (tag in z bits 48..63), from a
-// shared-memory table; the identity (nothing anticommutes) past the table.
-struct TagGen {
-    const Gen<1>* table;
-    int B;
-    Gen<1> none;
-    __device__ __forceinline__ const Gen<1>& operator()(const Key<1>& t) const {
-        const int b = (int)(t.z[0] >> kBatchTagShift);
-        return b < B ? table[b] : none;
-    }
-};
-
-// Per-problem dress of a batch (one 64-bit word per x and z): as k_dress, each
-// row with the generator of its problem.
-__global__ void __launch_bounds__(kThreads, IQCC_DRESS_MIN_BLOCKS) k_dress_seg(const uint64_t* __restrict__ rows,
-                                                                             uint64_t* rows_app, double* coef,
-                                                                             int64_t M, const Gen<1>* gens, int B,
-                                                                             HashView h, DevCounters* ctr) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    Gen<1>* table = reinterpret_cast<Gen<1>*>(smem_raw);
-    for (int b = threadIdx.x; b < B; b += blockDim.x) table[b] = gens[b];
-    __syncthreads();
-    TagGen tg{table, B, Gen<1>{}};
-    dress_body<1>(rows, rows_app, coef, M, tg, h, ctr);
-}
-
-// Admission count: how many partners a dress would append (no writes to H).
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_dress_count(const uint64_t* __restrict__ rows, int64_t M,
-                                                          Gen<W> g, HashView h, DevCounters* ctr) {
-    const unsigned FULL = 0xFFFFFFFFu;
-    const int lane = threadIdx.x & 31;
-    unsigned cnt = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        Key<W> t = load_key<W>(rows, i);
-        if (anticommutes<W>(t, g.p)) {
-            Key<W> q = key_xor<W>(t, g.p);
-            uint64_t fslot;
-            int64_t j = lookup_slot<W>(q, hash_key<W>(q), h, rows, &fslot);
-            if (j == -1) ++cnt;
-            else if (j == -2) set_error(ctr, IQCC_ERR_HASH_FULL, 3);
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(FULL, cnt, o);
-    if (lane == 0 && cnt) atomicAdd(&ctr->n_new, (unsigned long long)cnt);
 }
 
 // Partitioned dressing.  When H is split over several contexts by key bits
@@ -536,38 +358,6 @@ void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, Ha
         case 1: k_hash_insert<1><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
         case 2: k_hash_insert<2><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
         default: k_hash_insert<4><<<grid, kThreads, 0, s>>>(rows, lo, hi, h, ctr); note_launch(); break;
-    }
-}
-
-void launch_dress(int Wd, const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M,
-                  const uint64_t* pkey, double cos_t, double sin_t, HashView h, DevCounters* ctr,
-                  cudaStream_t s) {
-    if (M <= 0) return;
-    int grid = grid_for(M, 8);
-    switch (Wd) {
-        case 1: k_dress<1><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<1>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
-        case 2: k_dress<2><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<2>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
-        default: k_dress<4><<<grid, kThreads, 0, s>>>(rows_in, rows, coef, M, make_gen<4>(pkey, cos_t, sin_t), h, ctr); note_launch(); break;
-    }
-}
-
-void launch_dress_seg(const uint64_t* rows_in, uint64_t* rows, double* coef, int64_t M, const Gen<1>* gens, int B,
-                      HashView h, DevCounters* ctr, cudaStream_t s) {
-    if (M <= 0) return;
-    const size_t smem = (size_t)B * sizeof(Gen<1>);
-    cudaFuncSetAttribute(k_dress_seg, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_dress_seg<<<grid_for(M, 8), kThreads, smem, s>>>(rows_in, rows, coef, M, gens, B, h, ctr);
-    note_launch();
-}
-
-void launch_dress_count(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkey, HashView h,
-                        DevCounters* ctr, cudaStream_t s) {
-    if (M <= 0) return;
-    int grid = grid_for(M, 8);
-    switch (Wd) {
-        case 1: k_dress_count<1><<<grid, kThreads, 0, s>>>(rows, M, make_gen<1>(pkey, 1, 0), h, ctr); note_launch(); break;
-        case 2: k_dress_count<2><<<grid, kThreads, 0, s>>>(rows, M, make_gen<2>(pkey, 1, 0), h, ctr); note_launch(); break;
-        default: k_dress_count<4><<<grid, kThreads, 0, s>>>(rows, M, make_gen<4>(pkey, 1, 0), h, ctr); note_launch(); break;
     }
 }
 

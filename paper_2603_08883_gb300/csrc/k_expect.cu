@@ -3,20 +3,22 @@
 //   A, B, C  of E(tau) = A + B cos tau + C sin tau for one generator P
 //            (Eq. 5 inserted into Eq. 12): A over commuting T, B over
 //            anticommuting T, C = sum_anti C_T <i T P>
-//   DIS      gradients g = dE/dtau at 0 (Eq. 7 / Eq. 13) of candidate generators.
+//   DIS      gradients g = dE/dtau at 0 (Eq. 7 / Eq. 13) of given candidate
+//            generators at general angles (the candidates themselves and their
+//            z-eigenstate gradients come from the flip-set grouping of
+//            k_disgroup.cu).
 //
 // Two evaluation modes.
 //  * Basis state (every theta_j in {0, pi}): <T> = 0 unless T has no X/Y, and
 //    then <T> = (-1)^{popc(zT & occ)}.  No FP64 multiplies; only rows that can
-//    contribute read their coefficient.  For DIS this is the flip-set grouping
-//    of Eq. 14-15: a candidate with flip set F only sees terms with x = F.
+//    contribute read their coefficient.
 //  * General angles: per 4-qubit group a 256-entry table of products of the
 //    single-qubit expectations <I>=1, <X>=sin th cos ph, <Y>=sin th sin ph,
 //    <Z>=cos th, indexed by (x nibble << 4 | z nibble), kept in shared memory.
 //
 // Sums: per-thread FP64 accumulation, warp-shuffle and shared-memory block
 // reduction, one partial per block, and a final fixed-order compensated sum -
-// deterministic for a given launch shape.  DIS group sums use FP64 atomics.
+// deterministic for a given launch shape.
 #include <cuda_runtime.h>
 
 #include "iqcc_internal.cuh"
@@ -105,7 +107,8 @@ template <int W, bool BASIS, bool HIST>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
                                                   int yP, Key<W> occ, const double* __restrict__ tables,
-                                                  int n_groups, double* partials, PairCount pc) {
+                                                  int n_groups, double* partials, PairCount pc,
+                                                  const uint8_t* __restrict__ live) {
     extern __shared__ double s_tab[];
     if (!BASIS) {
         for (int i = threadIdx.x; i < n_groups * 256; i += blockDim.x) s_tab[i] = tables[i];
@@ -115,6 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
     unsigned n_anti = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        if (live && !live[i]) continue;  // dropped by a pending term-limit cut
         Key<W> t = load_key<W>(rows, i);
         const int anti = anticommutes<W>(t, p);
         if (HIST && anti) {
@@ -227,91 +231,6 @@ __global__ void k_qmf_tables(const double* theta, const double* phi, int n, int 
     tables[idx] = v;
 }
 
-// DIS grouping by flip set x (basis state: with the signed contribution of
-// Eq. 14-15; otherwise keys only).  Group slots: (fp32 << 32) | gid32, with
-// gid = kPendingGroup while the claiming thread publishes the group key.
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_dis_group(const uint64_t* __restrict__ rows,
-                                                        const double* __restrict__ coef, int64_t M, Key<W> occ,
-                                                        bool with_values, uint64_t* gslots, uint64_t bucket_mask,
-                                                        int max_probe, uint64_t* gkeys, double* gsum,
-                                                        DevCounters* ctr, int64_t max_groups) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        Key<W> t = load_key<W>(rows, i);
-        if (x_is_zero<W>(t)) continue;
-        // group key: the flip set (x words, z = 0)
-        Key<W> kx;
-#pragma unroll
-        for (int j = 0; j < W; ++j) { kx.x[j] = t.x[j]; kx.z[j] = 0; }
-        uint64_t hv = hash_key<W>(kx);
-        uint32_t fp = (uint32_t)(hv >> 32);
-        uint64_t b = hv & bucket_mask;
-        int64_t gid = -1;
-        for (int p = 0; p < max_probe && gid < 0; ++p) {
-            for (int s = 0; s < 4 && gid < 0; ++s) {
-                unsigned long long* slot = reinterpret_cast<unsigned long long*>(gslots + b * 4 + s);
-                unsigned long long cur = *(volatile unsigned long long*)slot;
-                if (cur == kEmptySlot) {
-                    unsigned long long claim = ((unsigned long long)fp << 32) | kPendingGroup;
-                    unsigned long long prev = atomicCAS(slot, (unsigned long long)kEmptySlot, claim);
-                    if (prev == kEmptySlot) {
-                        unsigned long long g = atomicAdd(&ctr->n_groups, 1ull);
-                        if ((int64_t)g >= max_groups) {  // cannot happen: groups <= rows
-                            set_error(ctr, IQCC_ERR_STATE, 12);
-                            g = 0;
-                        }
-#pragma unroll
-                        for (int j = 0; j < W; ++j) gkeys[g * W + j] = t.x[j];
-                        if (with_values) gsum[g] = 0.0;
-                        __threadfence();
-                        atomicExch(slot, ((unsigned long long)fp << 32) | (unsigned long long)g);
-                        gid = (int64_t)g;
-                        break;
-                    }
-                    cur = prev;
-                }
-                if ((uint32_t)(cur >> 32) != fp) continue;
-                int spins = 0;
-                while ((uint32_t)cur == kPendingGroup) {
-                    if (++spins > ctr->wait_limit) { set_error(ctr, IQCC_ERR_TIMEOUT, 10); break; }
-                    __nanosleep(64);
-                    cur = *(volatile unsigned long long*)slot;
-                }
-                if ((uint32_t)cur == kPendingGroup) { gid = -2; break; }
-                uint32_t g = (uint32_t)cur;
-                bool same = true;
-#pragma unroll
-                for (int j = 0; j < W; ++j) same &= (__ldcg(gkeys + (size_t)g * W + j) == t.x[j]);
-                if (same) gid = g;
-            }
-            b = (b + 1) & bucket_mask;
-        }
-        if (gid < 0) {
-            if (gid == -1) set_error(ctr, IQCC_ERR_HASH_FULL, 11);
-            continue;
-        }
-        if (with_values) {
-            // candidate alpha: x = F, z = lowest bit of F (single Y)
-            Key<W> a;
-            bool found = false;
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                a.x[j] = t.x[j];
-                uint64_t low = found ? 0ull : (t.x[j] & (~t.x[j] + 1));
-                a.z[j] = low;
-                found |= (t.x[j] != 0);
-            }
-            if (!anticommutes<W>(t, a)) continue;
-            Key<W> q = key_xor<W>(t, a);
-            const int s = product_sign<W>(t, 1, a, q);
-            const double c = coef[i];
-            const bool neg = (s < 0) ^ odd_occ<W>(q, occ.x);
-            atomicAdd(gsum + gid, neg ? -c : c);
-        }
-    }
-}
-
 constexpr int kGradTile = 16;
 
 // General-angle gradients of K (<= kGradTile) candidates:
@@ -374,17 +293,18 @@ int abc_grid(int64_t M) {
 template <int W, bool HIST>
 void abc_launch(const uint64_t* rows, const double* coef, int64_t M, const Key<W>& p, int y, const Key<W>& occ,
                 bool basis, const double* tables, int n_groups, double* partials, const PairCount& pc,
-                cudaStream_t s) {
+                const uint8_t* live, cudaStream_t s) {
     const int grid = expect_blocks();
     if (basis) {
-        k_abc<W, true, HIST><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, pc);
+        k_abc<W, true, HIST><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, pc,
+                                                        live);
     } else {
         size_t smem = (size_t)n_groups * 256 * sizeof(double);
         static std::atomic<unsigned long long> attr{0};
         if (first_on_device(&attr))
             cudaFuncSetAttribute(k_abc<W, false, HIST>, cudaFuncAttributeMaxDynamicSharedMemorySize, 64 * 256 * 8);
         k_abc<W, false, HIST><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials,
-                                                            pc);
+                                                            pc, live);
     }
     note_launch();
 }
@@ -392,7 +312,7 @@ void abc_launch(const uint64_t* rows, const double* coef, int64_t M, const Key<W
 template <int W>
 void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, bool basis,
               const uint64_t* occ_words, const double* tables, int n_groups, double* partials, cudaStream_t s,
-              const PairHistOut* pair) {
+              const PairHistOut* pair, const uint8_t* live) {
     Key<W> p = key_from<W>(pkey);
     int y = 0;
     for (int j = 0; j < W; ++j) y += __builtin_popcountll(p.x[j] & p.z[j]);
@@ -402,9 +322,9 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
     if (pair) {
         const Gen<W> g = make_gen<W>(pkey, 1.0, 0.0);
         pc = PairCount{pair->counts, 64 - pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
-        abc_launch<W, true>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, s);
+        abc_launch<W, true>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
     } else {
-        abc_launch<W, false>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, s);
+        abc_launch<W, false>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
     }
 }
 
@@ -424,11 +344,11 @@ int expect_blocks() { return sm_count() * 4; }
 
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey, bool basis,
                 const uint64_t* occ, const double* tables, int n_groups, double* partials, cudaStream_t s,
-                const PairHistOut* pair) {
+                const PairHistOut* pair, const uint8_t* live) {
     switch (Wd) {
-        case 1: abc_impl<1>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair); break;
-        case 2: abc_impl<2>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair); break;
-        default: abc_impl<4>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair); break;
+        case 1: abc_impl<1>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair, live); break;
+        case 2: abc_impl<2>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair, live); break;
+        default: abc_impl<4>(rows, coef, M, pkey, basis, occ, tables, n_groups, partials, s, pair, live); break;
     }
 }
 
@@ -444,30 +364,6 @@ void launch_qmf_tables(const double* theta, const double* phi, int n, int n_grou
                        cudaStream_t s) {
     int total = n_groups * 256;
     k_qmf_tables<<<(total + 255) / 256, 256, 0, s>>>(theta, phi, n, n_groups, tables); note_launch();
-}
-
-void launch_dis_group(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* occ_words,
-                      bool with_values, uint64_t* gslots, uint64_t gbucket_mask, int max_probe, uint64_t* gkeys,
-                      double* gsum, DevCounters* ctr, cudaStream_t s, int64_t max_groups) {
-    if (M <= 0) return;
-    int grid = abc_grid(M) * 2;
-    switch (Wd) {
-        case 1: {
-            Key<1> o{}; o.x[0] = occ_words[0];
-            k_dis_group<1><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, max_groups); note_launch();
-            break;
-        }
-        case 2: {
-            Key<2> o{}; for (int j = 0; j < 2; ++j) o.x[j] = occ_words[j];
-            k_dis_group<2><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, max_groups); note_launch();
-            break;
-        }
-        default: {
-            Key<4> o{}; for (int j = 0; j < 4; ++j) o.x[j] = occ_words[j];
-            k_dis_group<4><<<grid, kThreads, 0, s>>>(rows, coef, M, o, with_values, gslots, gbucket_mask, max_probe, gkeys, gsum, ctr, max_groups); note_launch();
-            break;
-        }
-    }
 }
 
 void launch_grad_general(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* cand,

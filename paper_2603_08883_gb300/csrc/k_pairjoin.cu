@@ -68,11 +68,13 @@ struct ProblemGen {
 
 template <int W, class G>
 __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restrict__ rows, int64_t M, G gen_of,
-                                                        int shift, uint32_t* counts, DevCounters* ctr) {
+                                                        int shift, uint32_t* counts, DevCounters* ctr,
+                                                        const uint8_t* __restrict__ live) {
     const int lane = threadIdx.x & 31;
     unsigned n_anti = 0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        if (live && !live[i]) continue;
         const Key<W> t = load_key<W>(rows, i);
         const auto& g = gen_of(t);
         if (anticommutes<W>(t, g.p)) {
@@ -90,13 +92,39 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
 // order by a tile counter, offsets by a decoupled look-back: a tile writes
 // only after every earlier tile has read its rows, and below the end of its
 // own rows), their count to *total.  SCATTER: rows that anticommute are copied
-// (key, coefficient) to their bin.
+// (key, coefficient) to their bin.  Warps 1.. copy theirs while warp 0 looks
+// back, so the look-back's latency is hidden behind the bin writes.  live
+// (may be NULL): rows with live[i] == 0 (dropped by a pending term-limit cut)
+// are neither kept nor copied.
+template <int W, class G, bool SCATTER>
+__device__ __forceinline__ void scatter_rows(const Key<W>* key, const double* c, const bool* anti, const G& gen_of,
+                                             int shift, uint32_t* cursor, uint64_t* rk, double* rc) {
+    if constexpr (!SCATTER) return;
+    uint32_t pos[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {  // the four positions first: their round trips overlap
+        if (anti[r]) {
+            const auto& g = gen_of(key[r]);
+            pos[r] = atomicAdd(&cursor[pair_hash<W>(key[r], g.p, g.top_word, g.top_mask) >> shift], 1u);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        if (anti[r]) {
+            store_key<W>(rk, pos[r], key[r]);
+            rc[pos[r]] = c[r];
+        }
+    }
+}
+
 template <int W, class G, bool COMPACT, bool SCATTER>
 __global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double* coef, int64_t n, G gen_of, int shift,
                                                          uint32_t* cursor, uint64_t* rk, double* rc,
                                                          unsigned long long* state, unsigned int* tile_counter,
-                                                         unsigned long long* total, DevCounters* ctr) {
+                                                         unsigned long long* total, DevCounters* ctr,
+                                                         const uint8_t* __restrict__ live) {
     constexpr int kPer = kSplitTile / kThreads;
+    static_assert(kPer == 4, "scatter_rows handles 4 rows per thread");
     __shared__ uint32_t s_w[kThreads / 32];
     __shared__ unsigned int s_tile;
     __shared__ unsigned long long s_prefix;
@@ -115,23 +143,18 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double*
     Key<W> key[kPer];
     double c[kPer];
     uint32_t rank[kPer];
-    bool keep[kPer];
+    bool keep[kPer], anti[kPer];
     uint32_t wcount = 0;
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
         const int64_t i = wbase + (int64_t)r * 32 + lane;
-        keep[r] = false;
-        if (i < n) {
+        keep[r] = anti[r] = false;
+        if (i < n && (!live || live[i])) {  // rows dropped by a pending cut are neither kept nor copied
             key[r] = load_key<W>(rows, i);
             c[r] = coef[i];
             const auto& g = gen_of(key[r]);
-            const bool a = anticommutes<W>(key[r], g.p);
-            keep[r] = !a;
-            if (SCATTER && a) {
-                const uint32_t p = atomicAdd(&cursor[pair_hash<W>(key[r], g.p, g.top_word, g.top_mask) >> shift], 1u);
-                store_key<W>(rk, p, key[r]);
-                rc[p] = c[r];
-            }
+            anti[r] = anticommutes<W>(key[r], g.p);
+            keep[r] = !anti[r];
         }
         if (COMPACT) {
             const unsigned b = __ballot_sync(0xFFFFFFFFu, keep[r]);
@@ -139,7 +162,10 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double*
             wcount += __popc(b);
         }
     }
-    if (!COMPACT) return;
+    if (!COMPACT) {
+        scatter_rows<W, G, SCATTER>(key, c, anti, gen_of, shift, cursor, rk, rc);
+        return;
+    }
     if (lane == 0) s_w[wid] = wcount;
     __syncthreads();
     if (wid == 0) {
@@ -172,7 +198,6 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double*
                     if (lane == 0) set_error(ctr, IQCC_ERR_TIMEOUT, 71);
                     break;
                 }
-                __nanosleep(32);
                 continue;
             }
             unsigned long long part = lane <= stop ? (v2 & kStMask) : 0ull;
@@ -187,8 +212,11 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double*
             s_prefix = prefix;
             if (base + kSplitTile >= n) *total = prefix + count;
         }
+    } else {
+        scatter_rows<W, G, SCATTER>(key, c, anti, gen_of, shift, cursor, rk, rc);
     }
     __syncthreads();
+    if (wid == 0) scatter_rows<W, G, SCATTER>(key, c, anti, gen_of, shift, cursor, rk, rc);
     const unsigned long long out = s_prefix + s_w[wid];
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
@@ -199,11 +227,11 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double*
     }
 }
 
-// Block j joins bins [j*bpb, (j+1)*bpb): rows [start[b0], start[b1]) of the
-// bin copies.  WRITE: the dressed rows go to rows/coef from *m_comm on (the
-// commuting rows end there), each block's at the position it reserves on
-// out_cursor; appended partners follow the block's own rows.  Always: the
-// number of rows without a partner is added to ctr->n_new.
+// Block j joins bins [j*bpb, (j+1)*bpb): records [start[b0], start[b1]).
+// WRITE: the dressed rows go to rows/coef from *m_comm on (the commuting rows
+// end there), each block's at the position it reserves on out_cursor;
+// appended partners follow the block's own rows.  Always: the number of rows
+// without a partner is added to ctr->n_new.
 template <int W, class G, bool WRITE>
 __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restrict__ rk, const double* __restrict__ rc,
                                                         const uint32_t* __restrict__ start, uint32_t n_bins,
@@ -306,25 +334,26 @@ int grid_cap(int64_t items, int per_sm) {
 template <int W, class G>
 struct PairLaunch {
     static void hist(const G& g, const uint64_t* rows, int64_t M, int shift, uint32_t* counts, DevCounters* ctr,
-                     cudaStream_t s) {
-        k_pair_hist<W, G><<<grid_cap(M, 8), kThreads, 0, s>>>(rows, M, g, shift, counts, ctr);
+                     const uint8_t* live, cudaStream_t s) {
+        k_pair_hist<W, G><<<grid_cap(M, 8), kThreads, 0, s>>>(rows, M, g, shift, counts, ctr, live);
     }
     static void split(const G& g, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M, int shift,
-                      uint32_t* cursor, uint64_t* rk, double* rc, unsigned long long* state, unsigned int* tile_counter,
-                      unsigned long long* total, DevCounters* ctr, cudaStream_t s) {
+                      uint32_t* cursor, uint64_t* rk, double* rc, unsigned long long* state,
+                      unsigned int* tile_counter, unsigned long long* total, DevCounters* ctr, const uint8_t* live,
+                      cudaStream_t s) {
         const unsigned nt = (unsigned)((M + kSplitTile - 1) / kSplitTile);
         if (compact && scatter)
             k_pair_split<W, G, true, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, state,
-                                                                    tile_counter, total, ctr);
+                                                                    tile_counter, total, ctr, live);
         else if (compact)
             k_pair_split<W, G, true, false><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, state,
-                                                                     tile_counter, total, ctr);
+                                                                     tile_counter, total, ctr, live);
         else
             k_pair_split<W, G, false, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, state,
-                                                                     tile_counter, total, ctr);
+                                                                     tile_counter, total, ctr, live);
     }
-    static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
-                     uint32_t n_bins, uint32_t bpb, uint64_t* rows, double* coef, const unsigned long long* m_comm,
+    static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start, uint32_t n_bins,
+                     uint32_t bpb, uint64_t* rows, double* coef, const unsigned long long* m_comm,
                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s) {
         const unsigned blocks = (n_bins + bpb - 1) / bpb;
         if (write)
@@ -374,15 +403,15 @@ size_t pair_split_scratch_bytes(int64_t M) {
 }
 
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
-                      DevCounters* ctr, cudaStream_t s) {
+                      DevCounters* ctr, cudaStream_t s, const uint8_t* live) {
     if (M <= 0) return;
-    with_provider(d, [&](auto L, auto g) { decltype(L)::hist(g, rows, M, 64 - log2_bins, counts, ctr, s); });
+    with_provider(d, [&](auto L, auto g) { decltype(L)::hist(g, rows, M, 64 - log2_bins, counts, ctr, live, s); });
     note_launch();
 }
 
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M,
                        int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, void* tile_scratch,
-                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s) {
+                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s, const uint8_t* live) {
     if (M <= 0 || !(compact || scatter)) return;
     const int64_t nt = (M + kSplitTile - 1) / kSplitTile;
     unsigned long long* state = (unsigned long long*)tile_scratch;
@@ -390,7 +419,7 @@ void launch_pair_split(const PairDress& d, bool compact, bool scatter, uint64_t*
     if (compact) cudaMemsetAsync(tile_scratch, 0, (size_t)(nt + 1) * sizeof(unsigned long long), s);
     with_provider(d, [&](auto L, auto g) {
         decltype(L)::split(g, compact, scatter, rows, coef, M, 64 - log2_bins, cursor, rk, rc, state, tile_counter,
-                           m_comm, ctr, s);
+                           m_comm, ctr, live, s);
     });
     note_launch();
 }

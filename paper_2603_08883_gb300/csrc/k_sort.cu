@@ -496,8 +496,8 @@ __global__ void k_set_flags(const uint32_t* __restrict__ idx, int64_t k, uint8_t
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) flags[idx[i]] = 1;
 }
 
-// 12-bit digit histogram of |C| bit patterns among kept rows whose higher bits
-// equal `prefix` (bits under `prefix_mask`).
+// 12-bit digit histogram of |C| bit patterns among kept rows (every row when
+// flags is NULL) whose higher bits equal `prefix` (bits under `prefix_mask`).
 __global__ void k_abs_digit_hist12(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
                                    int shift, uint64_t prefix, uint64_t prefix_mask, unsigned long long* hist) {
     __shared__ unsigned int h[4096];
@@ -505,7 +505,7 @@ __global__ void k_abs_digit_hist12(const double* __restrict__ coef, const uint8_
     __syncthreads();
     const int64_t s = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
-        if (!flags[i]) continue;
+        if (flags && !flags[i]) continue;
         const uint64_t b = abs_bits(coef[i]);
         if ((b & prefix_mask) != prefix) continue;
         atomicAdd(&h[(b >> shift) & 4095u], 1u);
@@ -548,6 +548,18 @@ __global__ void k_bucket_flags(const double* __restrict__ coef, uint8_t* flags, 
         const uint64_t b = abs_bits(coef[i]) & prefix_mask;
         if (b > prefix) continue;
         flags[i] = 0;
+        if (b == prefix) cand[atomicAdd(n_cand, 1ull)] = (uint32_t)i;
+    }
+}
+
+// The term limit's cut with every row live: flags[i] = 1 above the threshold
+// bucket, 0 in and below it; the bucket's rows are listed as candidates.
+__global__ void k_cut_flags(const double* __restrict__ coef, uint8_t* flags, int64_t n, uint64_t prefix,
+                            uint64_t prefix_mask, uint32_t* cand, unsigned long long* n_cand) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        const uint64_t b = abs_bits(coef[i]) & prefix_mask;
+        flags[i] = b > prefix;
         if (b == prefix) cand[atomicAdd(n_cand, 1ull)] = (uint32_t)i;
     }
 }
@@ -854,6 +866,14 @@ void launch_bucket_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t
                          uint32_t* cand, unsigned long long* n_cand, cudaStream_t s) {
     if (n > 0) {
         k_bucket_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, prefix, prefix_mask, cand, n_cand);
+        note_launch();
+    }
+}
+
+void launch_cut_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
+                      uint32_t* cand, unsigned long long* n_cand, cudaStream_t s) {
+    if (n > 0) {
+        k_cut_flags<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, prefix, prefix_mask, cand, n_cand);
         note_launch();
     }
 }

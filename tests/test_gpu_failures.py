@@ -6,8 +6,8 @@
   and the context refuses every later call (IQCC_ERR_STATE).  The self-test
   waits on a word that nothing writes; a one-poll limit on real work shows that
   every wait gives up and returns instead of hanging.
-* A probe bound of one bucket in the DIS group table makes a crowded table
-  overflow: IQCC_ERR_HASH_FULL, then IQCC_ERR_STATE.
+* A probe bound of one bucket in the batched screening's group table makes a
+  crowded table overflow: IQCC_ERR_HASH_FULL, then IQCC_ERR_STATE.
 In every case a fresh context on the same GPU still works.
 """
 import numpy as np
@@ -15,6 +15,7 @@ import pytest
 
 import oracle
 from paper_2603_08883_gb300 import synth
+from tests.compare import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -62,31 +63,37 @@ def test_default_wait_limit_is_restored_and_bounded():
 
 
 def test_one_poll_waits_give_up_or_finish_correctly():
-    """A one-poll limit on work that waits for real (a compaction of about
-    10^6 rows in about 1,000 tiles; DIS grouping with many rows per group): each
-    call either completes with the right result or fails with IQCC_ERR_TIMEOUT
-    and leaves the context refusing further calls.  Nothing hangs."""
+    """A one-poll limit on work that waits for real (the compression's and
+    the dress's in-place compactions of about 10^6 rows in about 1,000 tiles):
+    each call either completes with the right result or fails with
+    IQCC_ERR_TIMEOUT and leaves the context refusing further calls.  Nothing
+    hangs."""
     n = 40
     _, x, z, c = synth.random_hamiltonian(n, 1_200_000, 9, density=0.1)
     x[: len(x) // 2] &= np.uint64(0xF)             # few flip sets: many rows share a DIS group
     eps = float(np.quantile(np.abs(c), 0.5))
-    R = iqcc.iqcc_load_hamiltonian(n, x, z, c)     # the same calls with the default limit
-    iqcc.iqcc_prune(R, eps)
-    ref = iqcc.iqcc_export(R)
-    R.close()
+    P = (np.array([0b1011], np.uint64), np.array([0b0001], np.uint64))
+    refs = {}
+    for call in ("prune", "dress"):
+        R = iqcc.iqcc_load_hamiltonian(n, x, z, c)     # the same call with the default limit
+        if call == "prune":
+            iqcc.iqcc_prune(R, eps)
+        else:
+            iqcc.iqcc_dress(R, P[0], P[1], [0.3])
+        refs[call] = iqcc.iqcc_export(R)
+        R.close()
     outcomes = []
-    for call in ("prune", "dis"):
+    th, ph = synth.qmf_angles(n, "basis")
+    for call in ("prune", "dress"):
         H = iqcc.iqcc_load_hamiltonian(n, x, z, c)
         iqcc.iqcc_set_wait_limit(H, 1)
-        th, ph = synth.qmf_angles(n, "basis")
         try:
             if call == "prune":
                 iqcc.iqcc_prune(H, eps)
-                iqcc.iqcc_set_wait_limit(H, 0)
-                got = iqcc.iqcc_export(H)
-                assert all(np.array_equal(a, b) for a, b in zip(got, ref))
             else:
-                iqcc.iqcc_dis_gradients(H, th, ph, cap=4)
+                iqcc.iqcc_dress(H, P[0], P[1], [0.3])
+            iqcc.iqcc_set_wait_limit(H, 0)
+            assert not compare(iqcc.iqcc_export(H), refs[call])
             outcomes.append("ok")
         except iqcc.IqccError as e:
             assert e.status == TIMEOUT
@@ -99,18 +106,23 @@ def test_one_poll_waits_give_up_or_finish_correctly():
     _fresh_context_still_works()
 
 
-def test_dis_group_table_full_then_context_refuses():
-    """A one-bucket probe bound (max_probe = 1) and about 10^5 distinct flip
-    sets: some buckets of the DIS group table overflow."""
-    n = 40
-    _, x, z, c = synth.random_hamiltonian(n, 100_000, 4, density=0.3)
-    H = iqcc.iqcc_load_hamiltonian(n, x, z, c, max_probe=1)
-    th, ph = synth.qmf_angles(n, "basis")
+def test_group_table_full_then_context_refuses():
+    """A one-bucket probe bound (max_probe = 1) on the batched screening's
+    (flip set, problem) group table, with about 1.2 x 10^5 distinct groups:
+    some buckets of the table overflow."""
+    probs = []
+    for k in range(4):
+        n = 40
+        _, x, z, c = synth.random_hamiltonian(n, 30_000, 40 + k, density=0.3)
+        probs.append((n, x.reshape(-1), z.reshape(-1), c))
+    batch = iqcc.iqcc_batch_load(probs, max_probe=1)
+    th = [np.where(np.arange(n) < n // 2, np.pi, 0.0) for n, *_ in probs]
+    ph = [np.zeros(n) for n, *_ in probs]
     with pytest.raises(iqcc.IqccError) as e:
-        iqcc.iqcc_dis_gradients(H, th, ph, cap=4)
+        iqcc.iqcc_batch_screen(batch, th, ph)
     assert e.value.status == HASH_FULL
     with pytest.raises(iqcc.IqccError) as e:
-        iqcc.iqcc_dress(H, x[0], z[0] ^ np.uint64(1), [0.1])
+        iqcc.iqcc_batch_screen(batch, th, ph)
     assert e.value.status == STATE
-    H.close()
+    batch.close()
     _fresh_context_still_works()
