@@ -274,6 +274,41 @@ iqcc_status upload_tables(iqcc_ctx* ctx, const double* theta, const double* phi,
     return IQCC_OK;
 }
 
+// The other row buffer, holding at least `rows` rows (contents not kept).
+iqcc_status ensure_second_rows(iqcc_ctx* ctx, int64_t rows) {
+    const size_t rb = row_bytes(ctx);
+    if (ctx->keys2.bytes >= (size_t)rows * rb && ctx->coef2.bytes >= (size_t)rows * 8) return IQCC_OK;
+    const int64_t want = std::max<int64_t>(rows, std::min<int64_t>(ctx->capacity, ctx->rows_alloc));
+    release(ctx, ctx->keys2);
+    release(ctx, ctx->coef2);
+    if (!ensure(ctx, ctx->keys2, (size_t)want * rb) || !ensure(ctx, ctx->coef2, (size_t)want * 8))
+        return fail(ctx, IQCC_ERR_OOM, "row allocation failed");
+    return IQCC_OK;
+}
+
+// The dress-bin counts ([0] = 0, then one count per bin: later their starts,
+// then their ends) and the per-tile kept counts (one per tile of kDressTile
+// rows and a zero: later their offsets and the total) for a dress of M rows,
+// in ctx->pairbuf.
+struct PairCounts {
+    uint32_t* bins;
+    uint32_t* tiles;
+    int log2_bins;
+    int64_t n_tiles;
+    size_t bytes;
+};
+
+PairCounts pair_counts_layout(iqcc_ctx* ctx, int64_t M) {
+    PairCounts pc;
+    pc.log2_bins = pair_bins_log2(M);
+    pc.n_tiles = (M + kDressTile - 1) / kDressTile;
+    const size_t nb = ((size_t)1 << pc.log2_bins) + 1;
+    pc.bytes = sizeof(uint32_t) * (nb + (size_t)pc.n_tiles + 1);
+    pc.bins = (uint32_t*)ctx->pairbuf.p;
+    pc.tiles = pc.bins ? pc.bins + nb : nullptr;
+    return pc;
+}
+
 // A, B, C of padded device-layout generator pkey (all zero: energy).  With
 // pair_hist the same pass counts pkey's anticommuting rows by dress bin, for
 // the dress by pkey that follows (iqcc_iterate).
@@ -300,13 +335,15 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
         if (st) return st;
     }
     ctx->pair_ready = false;
-    PairHistOut ph{nullptr, 0, dctr(ctx)};
+    PairHistOut ph{nullptr, nullptr, 0, dctr(ctx)};
     if (pair_hist && ctx->M > 0) {
-        ph.log2_bins = pair_bins_log2(ctx->M);
-        const size_t bytes = sizeof(uint32_t) * (((size_t)1 << ph.log2_bins) + 1);
-        if (!ensure(ctx, ctx->pairbuf, bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-        ph.counts = (uint32_t*)ctx->pairbuf.p + 1;
-        CK(cudaMemsetAsync(ctx->pairbuf.p, 0, bytes, ctx->stream));
+        PairCounts pc = pair_counts_layout(ctx, ctx->M);
+        if (!ensure(ctx, ctx->pairbuf, pc.bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        pc = pair_counts_layout(ctx, ctx->M);
+        ph.log2_bins = pc.log2_bins;
+        ph.counts = pc.bins + 1;
+        ph.tile_kept = pc.tiles;
+        CK(cudaMemsetAsync(pc.bins, 0, pc.bytes, ctx->stream));
         CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
     }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -346,40 +383,45 @@ iqcc_status apply_pending_cut(iqcc_ctx* ctx);
 // anticommuting rows, split (commuting rows compacted in place, anticommuting
 // ones copied into their bins), join.  On IQCC_ERR_CAPACITY / OOM H is
 // unchanged.  Returns the counts in *n_anti_out / *n_new_out.
+// One dress by pair partition (k_pairjoin.cu): bin and tile counts (taken by
+// the A, B, C pass that preceded the dress, or here), split of H into the
+// other row buffer (commuting rows at offsets known per tile, anticommuting
+// rows copied into their bins), join behind the commuting rows; then the two
+// row buffers swap.  On IQCC_ERR_CAPACITY / OOM H is unchanged.  Returns the
+// counts in *n_anti_out / *n_new_out.
 iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, int64_t* n_new_out, float* ms_out) {
     const int64_t M = ctx->M;
     *n_anti_out = *n_new_out = 0;
     *ms_out = 0;
     if (M == 0) return IQCC_OK;
-    // the bin counts of this dress were taken by the A, B, C pass that preceded it
-    bool ready = ctx->pair_ready && !d.gens && ctx->pair_log2 == pair_bins_log2(M) &&
-                 std::memcmp(ctx->pair_key, d.pkey, sizeof(uint64_t) * 2 * ctx->Wd) == 0;
+    // the counts of this dress were taken by the A, B, C pass that preceded it
+    const bool ready = ctx->pair_ready && !d.gens && ctx->pair_log2 == pair_bins_log2(M) &&
+                       std::memcmp(ctx->pair_key, d.pkey, sizeof(uint64_t) * 2 * ctx->Wd) == 0;
     ctx->pair_ready = false;
-    const int lb = pair_bins_log2(M);
-    const uint32_t NB = 1u << lb;
+    PairCounts pc = pair_counts_layout(ctx, M);
+    const uint32_t NB = 1u << pc.log2_bins;
+    if (!ready) {
+        if (!ensure(ctx, ctx->pairbuf, pc.bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        pc = pair_counts_layout(ctx, M);
+    }
     Carver cv;
     cv.take<uint32_t>(1024);
-    cv.take<char>(pair_split_scratch_bytes(M));
-    cv.take<unsigned long long>(2);
+    cv.take<unsigned long long>(1);
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
     uint32_t* scan_tmp = cv.take<uint32_t>(1024);
-    char* tiles = cv.take<char>(pair_split_scratch_bytes(M));
-    unsigned long long* m_comm = cv.take<unsigned long long>(2);
-    unsigned long long* out_cursor = m_comm + 1;
+    unsigned long long* out_cursor = cv.take<unsigned long long>(1);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    const size_t arr_bytes = sizeof(uint32_t) * ((size_t)NB + 1);
-    if (!ready && !ensure(ctx, ctx->pairbuf, arr_bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-    uint32_t* arr = (uint32_t*)ctx->pairbuf.p;  // [0] = 0, [1 + b]: count, then start, then end of bin b
     DevCounters* c = dctr(ctx);
-    CK(cudaMemsetAsync(m_comm, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CK(cudaMemsetAsync(out_cursor, 0, sizeof(unsigned long long), ctx->stream));
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (!ready) {
         CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
-        CK(cudaMemsetAsync(arr, 0, arr_bytes, ctx->stream));
-        launch_pair_hist(d, ctx->rows(), M, lb, arr + 1, c, ctx->stream, live_flags(ctx));
+        CK(cudaMemsetAsync(pc.bins, 0, pc.bytes, ctx->stream));
+        launch_pair_hist(d, ctx->rows(), M, pc.log2_bins, pc.bins + 1, pc.tiles, c, ctx->stream, live_flags(ctx));
     }
-    launch_scan_u32_long(arr + 1, NB, scan_tmp, ctx->stream);
+    launch_scan_u32_long(pc.bins + 1, NB, scan_tmp, ctx->stream);
+    launch_scan_u32_long(pc.tiles, pc.n_tiles + 1, scan_tmp, ctx->stream);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
     if (st) return st;
@@ -395,47 +437,55 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     uint64_t* rk = rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
     double* rc = rv.take<double>(n_anti);
     if (rv.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    const uint32_t bpb = pair_bins_per_block(n_anti, lb);
+    const uint32_t bpb = pair_bins_per_block(n_anti, pc.log2_bins);
     const int64_t live = live_terms(ctx);  // the rows a pending cut keeps: the input of this dress
+    const uint32_t* kept = pc.tiles + pc.n_tiles;  // rows the split keeps, after the scan
     bool scattered = false;
+    int64_t need = live + n_anti;
     if (live + n_anti > ctx->capacity) {
         // exact admission: bin copies and a counting join first, H untouched
-        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c, ctx->stream,
-                          live_flags(ctx));
-        launch_pair_join(d, false, rk, rc, arr, lb, bpb, ctx->rows(), ctx->c(), m_comm, out_cursor, c, ctx->stream);
+        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.bins + 1, rk, rc, pc.tiles,
+                          nullptr, nullptr, ctx->stream, live_flags(ctx));
+        launch_pair_join(d, false, rk, rc, pc.bins, pc.log2_bins, bpb, nullptr, nullptr, kept, out_cursor, c,
+                         ctx->stream);
         CK_LAUNCH();
         st = read_counters(ctx);
         if (st) return st;
-        const int64_t upper = live + (int64_t)ctx->h_counters->n_new;
-        if (upper > ctx->capacity) {
+        need = live + (int64_t)ctx->h_counters->n_new;
+        if (need > ctx->capacity) {
             char buf[200];
-            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)upper,
+            snprintf(buf, sizeof buf, "dress would need %lld rows, capacity is %lld", (long long)need,
                      (long long)ctx->capacity);
             return fail(ctx, IQCC_ERR_CAPACITY, buf);
         }
-        st = reserve_rows(ctx, upper);
-        if (st) return st;
         CK(cudaMemsetAsync(&c->n_new, 0, sizeof(unsigned long long), ctx->stream));
         scattered = true;
-    } else {
-        st = reserve_rows(ctx, std::max(M, live + n_anti));
-        if (st) return st;
     }
-    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, lb, arr + 1, rk, rc, tiles, m_comm, c,
-                      ctx->stream, live_flags(ctx));
-    launch_pair_join(d, true, rk, rc, arr, lb, bpb, ctx->rows(), ctx->c(), m_comm, out_cursor, c, ctx->stream);
+    st = ensure_second_rows(ctx, std::max<int64_t>(need, 1));
+    if (st) return st;
+    uint64_t* rows_out = (uint64_t*)ctx->keys2.p;
+    double* coef_out = (double*)ctx->coef2.p;
+    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.bins + 1, rk, rc, pc.tiles,
+                      rows_out, coef_out, ctx->stream, live_flags(ctx));
+    launch_pair_join(d, true, rk, rc, pc.bins, pc.log2_bins, bpb, rows_out, coef_out, kept, out_cursor, c,
+                     ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
     if (st) return st;
-    unsigned long long mc = 0, oc = 0;
-    CK(cudaMemcpyAsync(&mc, m_comm, sizeof mc, cudaMemcpyDeviceToHost, ctx->stream));
+    uint32_t mc = 0;
+    unsigned long long oc = 0;
+    CK(cudaMemcpyAsync(&mc, kept, sizeof mc, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaMemcpyAsync(&oc, out_cursor, sizeof oc, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     const int64_t n_new = (int64_t)ctx->h_counters->n_new;
     if ((int64_t)mc + n_anti != live || (int64_t)oc != n_anti + n_new)
         return fail(ctx, IQCC_ERR_STATE, "internal: pair dress row counts disagree");
     cudaEventElapsedTime(ms_out, ctx->ev0, ctx->ev1);
+    std::swap(ctx->keys, ctx->keys2);
+    std::swap(ctx->coef, ctx->coef2);
+    ctx->rows_alloc = (int64_t)std::min(ctx->keys.bytes / row_bytes(ctx), ctx->coef.bytes / 8);
+    ctx->stats.rows_allocated = ctx->rows_alloc;
     ctx->M = live + n_new;
     ctx->pending = false;  // the split dropped the rows of the pending cut
     ctx->index_valid = false;
@@ -1830,6 +1880,9 @@ void iqcc_free(iqcc_ctx* ctx) {
     release(ctx, ctx->model);
     release(ctx, ctx->screen_rank);
     release(ctx, ctx->pairbuf);
+    release(ctx, ctx->keys2);
+    release(ctx, ctx->coef2);
+    release(ctx, ctx->dropflags);
     if (ctx->h_counters) cudaFreeHost(ctx->h_counters);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);

@@ -260,6 +260,7 @@ struct iqcc_ctx {
     int64_t M = 0;                 // live rows
     int64_t rows_alloc = 0;        // rows allocated in the key/coef buffers
     iqcc::Buf keys, coef;
+    iqcc::Buf keys2, coef2;        // the other row buffer: a dress writes H there and the two swap
     iqcc::Buf hash;                // slots of the key index (partitioned dressing and batches only)
     uint64_t hash_slots = 0;       // active slots (power of two)
     bool index_valid = false;      // the index holds exactly rows [0, M)
@@ -377,6 +378,11 @@ void launch_future_energy(int Wd, const uint64_t* rows, int64_t M, const uint64_
                           const double* tab, int ts, int n, double* out, cudaStream_t s);
 
 // k_pairjoin.cu: dress by pair partition (histogram, split, shared-memory join).
+// The split works on tiles of kDressTile rows (256 threads, 4 rows each); the
+// counting pass before it (launch_pair_hist, or the A, B, C pass of
+// iqcc_iterate) counts per tile the rows the split keeps, so that each tile's
+// output offset is known in advance.
+constexpr int kDressTile = 1024;
 struct PairDress {
     int Wd;
     const uint64_t* pkey;    // host, device-layout key of the one generator (gens == nullptr)
@@ -386,22 +392,22 @@ struct PairDress {
 };
 int pair_bins_log2(int64_t M);
 uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins);
-size_t pair_split_scratch_bytes(int64_t M);
-// counts: [2^log2_bins] zeroed; adds each anticommuting row to its bin and the total to ctr->n_anti.
+// counts: [2^log2_bins] zeroed; adds each anticommuting row to its bin and the total to ctr->n_anti;
+// tile_kept[t]: the rows of tile t the split keeps (commuting, live).
 // live (may be NULL): rows with live[i] == 0 are dropped (a pending term-limit cut), here and in the split.
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
-                      DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
-// cursor: bin starts in, bin ends out (when scattering); *m_comm: commuting rows (when compacting)
-// rk [n_anti][2 Wd] keys and rc [n_anti] coefficients of the anticommuting rows, by bin
-void launch_pair_split(const PairDress& d, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M,
-                       int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, void* tile_scratch,
-                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
+                      uint32_t* tile_kept, DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
+// From rows/coef (M rows) into rows_out/coef_out: the kept rows of tile t from tile_off[t] on (compact);
+// rk [n_anti][2 Wd] keys and rc [n_anti] coefficients of the anticommuting rows, by bin (scatter;
+// cursor: bin starts in, bin ends out).
+void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
+                       int64_t M, int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
+                       uint64_t* rows_out, double* coef_out, cudaStream_t s, const uint8_t* live = nullptr);
 // start: [2^log2_bins + 1] bin starts; rows without a partner counted in ctr->n_new; with `write` the
-// dressed rows and appended partners are written from row *m_comm + (*out_cursor, zeroed) on
+// dressed rows and appended partners are written to rows/coef from row *kept + (*out_cursor, zeroed) on
 void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
-                      int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef,
-                      const unsigned long long* m_comm, unsigned long long* out_cursor, DevCounters* ctr,
-                      cudaStream_t s);
+                      int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef, const uint32_t* kept,
+                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s);
 
 // k_dress.cu: the key index (partitioned dress only)
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
@@ -414,9 +420,10 @@ int expect_blocks();
 // With `pair` the same pass also counts P's anticommuting rows by dress bin
 // (launch_pair_hist's output, for the dress by P that follows).
 struct PairHistOut {
-    uint32_t* counts;   // [2^log2_bins], zeroed
+    uint32_t* counts;     // [2^log2_bins], zeroed
+    uint32_t* tile_kept;  // [ceil(M / kDressTile)]: rows per tile the split keeps (commuting, live)
     int log2_bins;
-    DevCounters* ctr;   // n_anti (zeroed) receives the total
+    DevCounters* ctr;     // n_anti (zeroed) receives the total
 };
 // live (may be NULL: every row): rows with live[i] == 0 are skipped (a pending term-limit cut).
 void launch_abc(int Wd, const uint64_t* rows, const double* coef, int64_t M, const uint64_t* pkey,

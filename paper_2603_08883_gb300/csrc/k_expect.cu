@@ -92,17 +92,58 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* out) 
     }
 }
 
-// Dress-bin counting folded into the A, B, C pass (see launch_abc).
+// Dress-bin and per-tile counting folded into the A, B, C pass (see launch_abc).
 struct PairCount {
     uint32_t* counts;
+    uint32_t* tile_kept;
     int shift;
     int top_word;
     uint64_t top_mask;
     DevCounters* ctr;
 };
 
-// A, B, C for generator p (p = 0: energy in A).  HIST: also counts the
-// anticommuting rows by dress bin of p (k_pairjoin.cu), one key read for both.
+// One row of the A, B, C pass: adds its share to acc; returns whether it
+// anticommutes with p.
+template <int W, bool BASIS>
+__device__ __forceinline__ bool abc_row(const Key<W>& t, const double* __restrict__ coef, int64_t i, const Key<W>& p,
+                                        int yP, const Key<W>& occ, const double* s_tab, int n_groups, double* acc) {
+    const int anti = anticommutes<W>(t, p);
+    if (BASIS) {
+        const bool diag = x_is_zero<W>(t);
+        const bool cross = anti && x_equal<W>(t, p);
+        if (diag || cross) {
+            const double c = coef[i];
+            if (diag) {
+                const double e = odd_occ<W>(t, occ.x) ? -c : c;
+                if (anti) acc[1] += e;
+                else acc[0] += e;
+            }
+            if (cross) {
+                Key<W> q = key_xor<W>(t, p);
+                const int s = product_sign<W>(t, yP, p, q);
+                const bool neg = (s < 0) ^ odd_occ<W>(q, occ.x);
+                acc[2] += neg ? -c : c;
+            }
+        }
+    } else {
+        const double c = coef[i];
+        const double et = expect_tab<W>(t, s_tab, n_groups);
+        if (anti) {
+            acc[1] += c * et;
+            Key<W> q = key_xor<W>(t, p);
+            const int s = product_sign<W>(t, yP, p, q);
+            acc[2] += (double)s * c * expect_tab<W>(q, s_tab, n_groups);
+        } else {
+            acc[0] += c * et;
+        }
+    }
+    return anti != 0;
+}
+
+// A, B, C for generator p (p = 0: energy in A).  HIST: the same pass also
+// counts, for the dress by p that follows (k_pairjoin.cu), the anticommuting
+// rows by dress bin and the commuting rows per tile of kDressTile rows (the
+// blocks then walk whole tiles); one read of the keys for both.
 template <int W, bool BASIS, bool HIST>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
@@ -115,50 +156,37 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
         __syncthreads();
     }
     double acc[3] = {0.0, 0.0, 0.0};
-    unsigned n_anti = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        if (live && !live[i]) continue;  // dropped by a pending term-limit cut
-        Key<W> t = load_key<W>(rows, i);
-        const int anti = anticommutes<W>(t, p);
-        if (HIST && anti) {
-            atomicAdd(&pc.counts[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
-            ++n_anti;
-        }
-        if (BASIS) {
-            const bool diag = x_is_zero<W>(t);
-            const bool cross = anti && x_equal<W>(t, p);
-            if (diag || cross) {
-                const double c = coef[i];
-                if (diag) {
-                    const double e = odd_occ<W>(t, occ.x) ? -c : c;
-                    if (anti) acc[1] += e;
-                    else acc[0] += e;
-                }
-                if (cross) {
-                    Key<W> q = key_xor<W>(t, p);
-                    const int s = product_sign<W>(t, yP, p, q);
-                    const bool neg = (s < 0) ^ odd_occ<W>(q, occ.x);
-                    acc[2] += neg ? -c : c;
-                }
-            }
-        } else {
-            const double c = coef[i];
-            const double et = expect_tab<W>(t, s_tab, n_groups);
-            if (anti) {
-                acc[1] += c * et;
-                Key<W> q = key_xor<W>(t, p);
-                const int s = product_sign<W>(t, yP, p, q);
-                acc[2] += (double)s * c * expect_tab<W>(q, s_tab, n_groups);
-            } else {
-                acc[0] += c * et;
-            }
-        }
-    }
     if (HIST) {
+        unsigned n_anti = 0;
+        const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            int kept = 0;
+#pragma unroll
+            for (int r = 0; r < kDressTile / kThreads; ++r) {
+                const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
+                bool k = false;
+                if (i < M && (!live || live[i])) {  // rows dropped by a pending term-limit cut are skipped
+                    const Key<W> t = load_key<W>(rows, i);
+                    if (abc_row<W, BASIS>(t, coef, i, p, yP, occ, s_tab, n_groups, acc)) {
+                        atomicAdd(&pc.counts[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
+                        ++n_anti;
+                    } else {
+                        k = true;
+                    }
+                }
+                kept += __syncthreads_count(k);
+            }
+            if (threadIdx.x == 0) pc.tile_kept[tile] = (uint32_t)kept;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
         if ((threadIdx.x & 31) == 0 && n_anti) atomicAdd(&pc.ctr->n_anti, (unsigned long long)n_anti);
+    } else {
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+            if (live && !live[i]) continue;  // dropped by a pending term-limit cut
+            abc_row<W, BASIS>(load_key<W>(rows, i), coef, i, p, yP, occ, s_tab, n_groups, acc);
+        }
     }
     block_reduce_store<3>(acc, partials + 3 * blockIdx.x);
 }
@@ -321,7 +349,7 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
     PairCount pc{};
     if (pair) {
         const Gen<W> g = make_gen<W>(pkey, 1.0, 0.0);
-        pc = PairCount{pair->counts, 64 - pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
+        pc = PairCount{pair->counts, pair->tile_kept, 64 - pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
         abc_launch<W, true>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
     } else {
         abc_launch<W, false>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);

@@ -11,13 +11,15 @@
 //
 //   1. k_pair_hist   one pass over the keys: how many anticommuting rows fall
 //                    in each of 2^k bins (the top k bits of the pair key's
-//                    hash); an exclusive scan turns the counts into bin starts.
-//   2. k_pair_split  one pass over the rows: the commuting rows are compacted
-//                    in place (stable, decoupled look-back), the anticommuting
-//                    ones are copied with their coefficients into their bins.
+//                    hash), and how many commuting rows each tile of 1024 rows
+//                    holds; exclusive scans turn both into starts.
+//   2. k_pair_split  one pass over the rows into the other row buffer: the
+//                    commuting rows are copied to offsets known per tile (the
+//                    counting pass counted them), the anticommuting ones with
+//                    their coefficients into their bins.
 //   3. k_pair_join   one block per group of consecutive bins: the group's
 //                    rows are matched by pair key in a shared-memory table,
-//                    each row is written back behind the commuting rows with
+//                    each row is written behind the commuting rows with
 //                    C_T cos(tau) - s_T C_Q sin(tau) (partner present, i T P =
 //                    s_T Q) or C_T cos(tau) (partner absent), and each row
 //                    without a partner appends (Q, s_T C_T sin(tau)).
@@ -30,6 +32,8 @@
 // no duplicate merge is needed.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "iqcc_internal.cuh"
 
 namespace iqcc {
@@ -37,14 +41,11 @@ namespace iqcc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSplitTile = 1024;           // rows per split tile (4 per thread)
 constexpr int kJoinCap = 4096;             // rows one join block can hold
 constexpr int kJoinSlots = 8192;           // its shared-memory table (load <= 1/2)
 constexpr uint32_t kJoinEmpty = 0xFFFFFFFFu;
 constexpr uint16_t kNoPartner = 0xFFFFu;
 constexpr int kJoinTarget = 2048;          // rows per join block on average
-constexpr unsigned long long kStAgg = 1ull << 62, kStPrefix = 2ull << 62;
-constexpr unsigned long long kStMask = (1ull << 62) - 1;
 
 // One generator for every row.
 template <int W>
@@ -68,167 +69,114 @@ struct ProblemGen {
 
 template <int W, class G>
 __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restrict__ rows, int64_t M, G gen_of,
-                                                        int shift, uint32_t* counts, DevCounters* ctr,
-                                                        const uint8_t* __restrict__ live) {
-    const int lane = threadIdx.x & 31;
+                                                        int shift, uint32_t* counts, uint32_t* tile_kept,
+                                                        DevCounters* ctr, const uint8_t* __restrict__ live) {
     unsigned n_anti = 0;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        if (live && !live[i]) continue;
-        const Key<W> t = load_key<W>(rows, i);
-        const auto& g = gen_of(t);
-        if (anticommutes<W>(t, g.p)) {
-            atomicAdd(&counts[pair_hash<W>(t, g.p, g.top_word, g.top_mask) >> shift], 1u);
-            ++n_anti;
+    const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        int kept = 0;
+#pragma unroll
+        for (int r = 0; r < kDressTile / kThreads; ++r) {
+            const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
+            bool k = false;
+            if (i < M && (!live || live[i])) {
+                const Key<W> t = load_key<W>(rows, i);
+                const auto& g = gen_of(t);
+                if (anticommutes<W>(t, g.p)) {
+                    atomicAdd(&counts[pair_hash<W>(t, g.p, g.top_word, g.top_mask) >> shift], 1u);
+                    ++n_anti;
+                } else {
+                    k = true;
+                }
+            }
+            kept += __syncthreads_count(k);
         }
+        if (threadIdx.x == 0) tile_kept[tile] = (uint32_t)kept;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
-    if (lane == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
+    if ((threadIdx.x & 31) == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
 }
 
-// cursor[b]: on entry the start of bin b, on exit its end.  COMPACT: rows
-// that commute with their generator are compacted in place, stably (tile
-// order by a tile counter, offsets by a decoupled look-back: a tile writes
-// only after every earlier tile has read its rows, and below the end of its
-// own rows), their count to *total.  SCATTER: rows that anticommute are copied
-// (key, coefficient) to their bin.  Warps 1.. copy theirs while warp 0 looks
-// back, so the look-back's latency is hidden behind the bin writes.  live
-// (may be NULL): rows with live[i] == 0 (dropped by a pending term-limit cut)
-// are neither kept nor copied.
-template <int W, class G, bool SCATTER>
-__device__ __forceinline__ void scatter_rows(const Key<W>* key, const double* c, const bool* anti, const G& gen_of,
-                                             int shift, uint32_t* cursor, uint64_t* rk, double* rc) {
-    if constexpr (!SCATTER) return;
-    uint32_t pos[4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {  // the four positions first: their round trips overlap
-        if (anti[r]) {
-            const auto& g = gen_of(key[r]);
-            pos[r] = atomicAdd(&cursor[pair_hash<W>(key[r], g.p, g.top_word, g.top_mask) >> shift], 1u);
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        if (anti[r]) {
-            store_key<W>(rk, pos[r], key[r]);
-            rc[pos[r]] = c[r];
-        }
-    }
-}
-
+// The split, one 1024-row tile per block, from the rows into the other row
+// buffer: COMPACT copies the rows that commute with their generator to
+// rows_out / coef_out from tile_off[t] on (the counting pass that preceded
+// this one counted them per tile, and the offsets are the exclusive scan of
+// those counts, so no block waits on another); SCATTER copies the
+// anticommuting rows (key, coefficient) to their bins, their positions taken
+// first so that the round trips of the four positions of a thread overlap
+// with the ranking of the kept rows.  cursor[b]: the start of bin b on entry,
+// its end on exit.  live (may be NULL): rows with live[i] == 0 (dropped by a
+// pending term-limit cut) are neither kept nor copied.
 template <int W, class G, bool COMPACT, bool SCATTER>
-__global__ void __launch_bounds__(kThreads) k_pair_split(uint64_t* rows, double* coef, int64_t n, G gen_of, int shift,
-                                                         uint32_t* cursor, uint64_t* rk, double* rc,
-                                                         unsigned long long* state, unsigned int* tile_counter,
-                                                         unsigned long long* total, DevCounters* ctr,
-                                                         const uint8_t* __restrict__ live) {
-    constexpr int kPer = kSplitTile / kThreads;
-    static_assert(kPer == 4, "scatter_rows handles 4 rows per thread");
+__global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restrict__ rows,
+                                                         const double* __restrict__ coef, int64_t n, G gen_of,
+                                                         int shift, uint32_t* cursor, uint64_t* rk, double* rc,
+                                                         const uint32_t* __restrict__ tile_off, uint64_t* rows_out,
+                                                         double* coef_out, const uint8_t* __restrict__ live) {
+    constexpr int kPer = kDressTile / kThreads;
     __shared__ uint32_t s_w[kThreads / 32];
-    __shared__ unsigned int s_tile;
-    __shared__ unsigned long long s_prefix;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    unsigned int t;
-    if (COMPACT) {
-        if (threadIdx.x == 0) s_tile = atomicAdd(tile_counter, 1u);
-        __syncthreads();
-        t = s_tile;
-    } else {
-        t = blockIdx.x;
-    }
-    const int64_t base = (int64_t)t * kSplitTile;
-    const int64_t wbase = base + (int64_t)wid * (kPer * 32);
+    const int64_t t = blockIdx.x;
+    const int64_t wbase = t * kDressTile + (int64_t)wid * (kPer * 32);
     Key<W> key[kPer];
     double c[kPer];
-    uint32_t rank[kPer];
+    uint32_t rank[kPer], pos[kPer];
     bool keep[kPer], anti[kPer];
-    uint32_t wcount = 0;
 #pragma unroll
     for (int r = 0; r < kPer; ++r) {
         const int64_t i = wbase + (int64_t)r * 32 + lane;
         keep[r] = anti[r] = false;
-        if (i < n && (!live || live[i])) {  // rows dropped by a pending cut are neither kept nor copied
+        if (i < n && (!live || live[i])) {
             key[r] = load_key<W>(rows, i);
             c[r] = coef[i];
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = wbase + (int64_t)r * 32 + lane;
+        if (i < n && (!live || live[i])) {
             const auto& g = gen_of(key[r]);
             anti[r] = anticommutes<W>(key[r], g.p);
             keep[r] = !anti[r];
+            if (SCATTER && anti[r])
+                pos[r] = atomicAdd(&cursor[pair_hash<W>(key[r], g.p, g.top_word, g.top_mask) >> shift], 1u);
         }
-        if (COMPACT) {
+    }
+    if (COMPACT) {
+        uint32_t wcount = 0;
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
             const unsigned b = __ballot_sync(0xFFFFFFFFu, keep[r]);
             rank[r] = wcount + __popc(b & lt);
             wcount += __popc(b);
         }
-    }
-    if (!COMPACT) {
-        scatter_rows<W, G, SCATTER>(key, c, anti, gen_of, shift, cursor, rk, rc);
-        return;
-    }
-    if (lane == 0) s_w[wid] = wcount;
-    __syncthreads();
-    if (wid == 0) {
-        const uint32_t v = lane < kThreads / 32 ? s_w[lane] : 0u;
-        uint32_t incl = v;
+        if (lane == 0) s_w[wid] = wcount;
+        __syncthreads();
+        uint32_t off = tile_off[t];
+        for (int w = 0; w < wid; ++w) off += s_w[w];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        const uint32_t count = __shfl_sync(0xFFFFFFFFu, incl, 31);
-        if (lane < kThreads / 32) s_w[lane] = incl - v;
-        if (lane == 0) {
-            __threadfence();
-            atomicExch(state + t, (t == 0 ? kStPrefix : kStAgg) | count);
-        }
-        unsigned long long prefix = 0;
-        int64_t p = (int64_t)t - 1;
-        int spins = 0;
-        while (p >= 0) {
-            const int64_t q = p - lane;
-            unsigned long long v2 = kStPrefix;  // before tile 0: a prefix of 0
-            if (q >= 0) v2 = *(volatile unsigned long long*)(state + q);
-            const unsigned pref = __ballot_sync(0xFFFFFFFFu, (v2 & ~kStMask) == kStPrefix);
-            const unsigned zero = __ballot_sync(0xFFFFFFFFu, v2 == 0);
-            const int stop = pref ? __ffs(pref) - 1 : 31;
-            const unsigned upto = stop == 31 ? 0xFFFFFFFFu : ((2u << stop) - 1u);
-            if (zero & upto) {
-                if (++spins > ctr->wait_limit) {
-                    if (lane == 0) set_error(ctr, IQCC_ERR_TIMEOUT, 71);
-                    break;
-                }
-                continue;
+        for (int r = 0; r < kPer; ++r) {
+            if (keep[r]) {
+                store_key<W>(rows_out, (int64_t)(off + rank[r]), key[r]);
+                coef_out[off + rank[r]] = c[r];
             }
-            unsigned long long part = lane <= stop ? (v2 & kStMask) : 0ull;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) part += __shfl_down_sync(0xFFFFFFFFu, part, o);
-            prefix += __shfl_sync(0xFFFFFFFFu, part, 0);
-            if (pref) break;
-            p -= 32;
         }
-        if (lane == 0) {
-            if (t != 0) atomicExch(state + t, kStPrefix | (prefix + count));
-            s_prefix = prefix;
-            if (base + kSplitTile >= n) *total = prefix + count;
-        }
-    } else {
-        scatter_rows<W, G, SCATTER>(key, c, anti, gen_of, shift, cursor, rk, rc);
     }
-    __syncthreads();
-    if (wid == 0) scatter_rows<W, G, SCATTER>(key, c, anti, gen_of, shift, cursor, rk, rc);
-    const unsigned long long out = s_prefix + s_w[wid];
+    if (SCATTER) {
 #pragma unroll
-    for (int r = 0; r < kPer; ++r) {
-        if (keep[r]) {
-            store_key<W>(rows, (int64_t)(out + rank[r]), key[r]);
-            coef[out + rank[r]] = c[r];
+        for (int r = 0; r < kPer; ++r) {
+            if (anti[r]) {
+                store_key<W>(rk, pos[r], key[r]);
+                rc[pos[r]] = c[r];
+            }
         }
     }
 }
 
 // Block j joins bins [j*bpb, (j+1)*bpb): records [start[b0], start[b1]).
-// WRITE: the dressed rows go to rows/coef from *m_comm on (the commuting rows
+// WRITE: the dressed rows go to rows/coef from *kept on (the commuting rows
 // end there), each block's at the position it reserves on out_cursor;
 // appended partners follow the block's own rows.  Always: the number of rows
 // without a partner is added to ctr->n_new.
@@ -236,7 +184,7 @@ template <int W, class G, bool WRITE>
 __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restrict__ rk, const double* __restrict__ rc,
                                                         const uint32_t* __restrict__ start, uint32_t n_bins,
                                                         uint32_t bins_per_block, G gen_of, uint64_t* rows,
-                                                        double* coef, const unsigned long long* __restrict__ m_comm,
+                                                        double* coef, const uint32_t* __restrict__ kept,
                                                         unsigned long long* out_cursor, DevCounters* ctr) {
     __shared__ uint32_t table[kJoinSlots];
     __shared__ uint16_t partner[kJoinCap];
@@ -297,7 +245,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
     const unsigned n_single = s_single;
     if (threadIdx.x == 0) {
         if (n_single) atomicAdd(&ctr->n_new, (unsigned long long)n_single);
-        if (WRITE) s_base = *m_comm + atomicAdd(out_cursor, (unsigned long long)(n + n_single));
+        if (WRITE) s_base = (unsigned long long)*kept + atomicAdd(out_cursor, (unsigned long long)(n + n_single));
     }
     if (!WRITE) return;
     __syncthreads();
@@ -333,34 +281,35 @@ int grid_cap(int64_t items, int per_sm) {
 // The three launches for one provider type.
 template <int W, class G>
 struct PairLaunch {
-    static void hist(const G& g, const uint64_t* rows, int64_t M, int shift, uint32_t* counts, DevCounters* ctr,
-                     const uint8_t* live, cudaStream_t s) {
-        k_pair_hist<W, G><<<grid_cap(M, 8), kThreads, 0, s>>>(rows, M, g, shift, counts, ctr, live);
+    static void hist(const G& g, const uint64_t* rows, int64_t M, int shift, uint32_t* counts, uint32_t* tile_kept,
+                     DevCounters* ctr, const uint8_t* live, cudaStream_t s) {
+        const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
+        const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sm_count() * 8);
+        k_pair_hist<W, G><<<grid, kThreads, 0, s>>>(rows, M, g, shift, counts, tile_kept, ctr, live);
     }
-    static void split(const G& g, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M, int shift,
-                      uint32_t* cursor, uint64_t* rk, double* rc, unsigned long long* state,
-                      unsigned int* tile_counter, unsigned long long* total, DevCounters* ctr, const uint8_t* live,
-                      cudaStream_t s) {
-        const unsigned nt = (unsigned)((M + kSplitTile - 1) / kSplitTile);
+    static void split(const G& g, bool compact, bool scatter, const uint64_t* rows, const double* coef, int64_t M,
+                      int shift, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
+                      uint64_t* rows_out, double* coef_out, const uint8_t* live, cudaStream_t s) {
+        const unsigned nt = (unsigned)((M + kDressTile - 1) / kDressTile);
         if (compact && scatter)
-            k_pair_split<W, G, true, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, state,
-                                                                    tile_counter, total, ctr, live);
+            k_pair_split<W, G, true, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, tile_off,
+                                                                    rows_out, coef_out, live);
         else if (compact)
-            k_pair_split<W, G, true, false><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, state,
-                                                                     tile_counter, total, ctr, live);
+            k_pair_split<W, G, true, false><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, tile_off,
+                                                                     rows_out, coef_out, live);
         else
-            k_pair_split<W, G, false, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, state,
-                                                                     tile_counter, total, ctr, live);
+            k_pair_split<W, G, false, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, tile_off,
+                                                                     rows_out, coef_out, live);
     }
-    static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start, uint32_t n_bins,
-                     uint32_t bpb, uint64_t* rows, double* coef, const unsigned long long* m_comm,
+    static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
+                     uint32_t n_bins, uint32_t bpb, uint64_t* rows, double* coef, const uint32_t* kept,
                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s) {
         const unsigned blocks = (n_bins + bpb - 1) / bpb;
         if (write)
-            k_pair_join<W, G, true><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, m_comm,
+            k_pair_join<W, G, true><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, kept,
                                                                  out_cursor, ctr);
         else
-            k_pair_join<W, G, false><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, m_comm,
+            k_pair_join<W, G, false><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, kept,
                                                                   out_cursor, ctr);
     }
 };
@@ -398,39 +347,32 @@ uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins) {
     return bpb;
 }
 
-size_t pair_split_scratch_bytes(int64_t M) {
-    return ((size_t)((M + kSplitTile - 1) / kSplitTile) + 1) * sizeof(unsigned long long) + 256;
-}
-
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
-                      DevCounters* ctr, cudaStream_t s, const uint8_t* live) {
+                      uint32_t* tile_kept, DevCounters* ctr, cudaStream_t s, const uint8_t* live) {
     if (M <= 0) return;
-    with_provider(d, [&](auto L, auto g) { decltype(L)::hist(g, rows, M, 64 - log2_bins, counts, ctr, live, s); });
+    with_provider(d, [&](auto L, auto g) {
+        decltype(L)::hist(g, rows, M, 64 - log2_bins, counts, tile_kept, ctr, live, s);
+    });
     note_launch();
 }
 
-void launch_pair_split(const PairDress& d, bool compact, bool scatter, uint64_t* rows, double* coef, int64_t M,
-                       int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, void* tile_scratch,
-                       unsigned long long* m_comm, DevCounters* ctr, cudaStream_t s, const uint8_t* live) {
+void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
+                       int64_t M, int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
+                       uint64_t* rows_out, double* coef_out, cudaStream_t s, const uint8_t* live) {
     if (M <= 0 || !(compact || scatter)) return;
-    const int64_t nt = (M + kSplitTile - 1) / kSplitTile;
-    unsigned long long* state = (unsigned long long*)tile_scratch;
-    unsigned int* tile_counter = (unsigned int*)(state + nt);
-    if (compact) cudaMemsetAsync(tile_scratch, 0, (size_t)(nt + 1) * sizeof(unsigned long long), s);
     with_provider(d, [&](auto L, auto g) {
-        decltype(L)::split(g, compact, scatter, rows, coef, M, 64 - log2_bins, cursor, rk, rc, state, tile_counter,
-                           m_comm, ctr, live, s);
+        decltype(L)::split(g, compact, scatter, rows, coef, M, 64 - log2_bins, cursor, rk, rc, tile_off, rows_out,
+                           coef_out, live, s);
     });
     note_launch();
 }
 
 void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
-                      int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef,
-                      const unsigned long long* m_comm, unsigned long long* out_cursor, DevCounters* ctr,
-                      cudaStream_t s) {
+                      int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef, const uint32_t* kept,
+                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s) {
     const uint32_t n_bins = 1u << log2_bins;
     with_provider(d, [&](auto L, auto g) {
-        decltype(L)::join(g, write, rk, rc, start, n_bins, bins_per_block, rows, coef, m_comm, out_cursor, ctr, s);
+        decltype(L)::join(g, write, rk, rc, start, n_bins, bins_per_block, rows, coef, kept, out_cursor, ctr, s);
     });
     note_launch();
 }
