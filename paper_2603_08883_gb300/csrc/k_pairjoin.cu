@@ -120,6 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
     const unsigned lt = (1u << lane) - 1u;
     const int64_t t = blockIdx.x;
     const int64_t wbase = t * kDressTile + (int64_t)wid * (kPer * 32);
+    const uint32_t off0 = COMPACT ? tile_off[t] : 0u;  // loaded with the rows
     Key<W> key[kPer];
     double c[kPer];
     uint32_t rank[kPer], pos[kPer];
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
         }
         if (lane == 0) s_w[wid] = wcount;
         __syncthreads();
-        uint32_t off = tile_off[t];
+        uint32_t off = off0;
         for (int w = 0; w < wid; ++w) off += s_w[w];
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
