@@ -258,32 +258,6 @@ def measure_screening(iqcc, H, th, ph):
             "frac": round(tf / peak[0], 4) if peak[0] else None}
 
 
-def measure_random_access_peak(words=1 << 30, gathers=1 << 27, reps=3):
-    """Random-access rate of this GPU's HBM: torch.gather of 8-byte words at
-    uniformly random positions of an 8 GB table (every access its own DRAM
-    sector); the best of `reps` timed runs, CUDA events."""
-    import torch
-    table = torch.ones(words, dtype=torch.int64, device="cuda")
-    g = torch.Generator(device="cuda")
-    g.manual_seed(7)
-    idx = torch.randint(0, words, (gathers,), device="cuda", generator=g)
-    out = torch.empty(gathers, dtype=torch.int64, device="cuda")
-    torch.gather(table, 0, idx, out=out)
-    best = None
-    for _ in range(reps):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        torch.gather(table, 0, idx, out=out)
-        e1.record()
-        e1.synchronize()
-        ms = e0.elapsed_time(e1)
-        best = ms if best is None else min(best, ms)
-    del table, idx, out
-    torch.cuda.empty_cache()
-    return gathers / (best / 1e3)
-
-
 def measured_peak_tensor():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -453,10 +427,11 @@ def measure_batch(iqcc, synth, n_problems=256, seed=1000, eps=1e-10, screens=20)
 
 
 def profile_traffic(avg_rows):
-    """DRAM bytes per dressed term of the dress kernel from the committed ncu
-    summary (profiles/dress_kernel_jw100.md, line 'dram_bytes_per_dressed_term:'),
-    scaled to a launch of avg_rows rows; None when absent."""
-    path = os.path.join(ROOT, "profiles", "dress_kernel_jw100.md")
+    """DRAM bytes per dressed term of one dress (split + join) from the
+    committed ncu summary (profiles/dress_pairs_jw100.md, line
+    'dram_bytes_per_dressed_term:'), scaled to a dress of avg_rows rows; None
+    when absent."""
+    path = os.path.join(ROOT, "profiles", "dress_pairs_jw100.md")
     try:
         for line in open(path):
             if line.startswith("dram_bytes_per_dressed_term:"):
@@ -563,21 +538,8 @@ def run_gpu(args):
     t_max, total_dressed = reduce_over_ranks(dist, dev_s, dressed, "cuda")
 
     # ---------------- adjoint pass (dE/dtheta, dE/dphi, dE/dtau) on the capped H, after the timed region
-    adjoint = sort_variant = screening = plain_form = partitioned = random_access = None
+    adjoint = sort_variant = screening = plain_form = partitioned = None
     if rank == 0 and not args.no_extras:
-        # the dress kernel's random fetches per launch: every anticommuting row probes
-        # one bucket; a row whose partner is present also reads the partner's key, and
-        # the member that rotates the pair (half of them) its coefficient
-        n_d = max(stats["n_dress"], 1)
-        anti, new = stats["anticommuting"] / n_d, stats["appended"] / n_d
-        fetches = new + 2.5 * (anti - new)
-        launch_s = stats["dress_kernel_ms"] / 1e3 / n_d
-        peak_ra = measure_random_access_peak()
-        random_access = {"fetches_per_launch": fetches, "achieved_G_per_s": round(fetches / launch_s / 1e9, 2),
-                         "peak_G_per_s": round(peak_ra / 1e9, 2), "frac": round(fetches / launch_s / peak_ra, 4),
-                         "peak_kind": "measured here: torch.gather of 8-byte words at random from an 8 GB "
-                                      "table (random reads only)", "model": "bucket probe per anticommuting row; partner key "
-                                      "per row with a present partner; partner coefficient for the rotating half"}
         adjoint = measure_adjoint(iqcc, H, n, th, ph, stream)
         adjoint["joint_optimisation"] = measure_joint_optimisation(iqcc, H, th, ph)
         screening = measure_screening(iqcc, H, th, ph)
@@ -635,25 +597,38 @@ def run_gpu(args):
             dist.destroy_process_group()
         return
 
-    # ---------------- roofline of the dress kernel
+    # ---------------- roofline of the dress (split + join of one generator)
     peak, peak_kind = measured_peak()
     n_dress = max(stats["n_dress"], 1)
     dress_s = stats["dress_kernel_ms"] / 1e3
     achieved = stats["dress_bytes"] / dress_s / 1e9 if dress_s > 0 else 0.0
     avg_rows = stats["dressed_terms"] / n_dress
-    shares = {"dress": stats["dress_kernel_ms"], "hash_insert_rebuild": stats["hash_ms"],
+    # bytes the pair-partition dress itself moves: the split reads and writes
+    # every live row (commuting rows to the other buffer, anticommuting rows to
+    # their bins); the join reads the bins and writes the rotated rows and the
+    # appended partners
+    row_b = 16 * (1 if n <= 64 else 2 if n <= 128 else 4) + 8
+    moved = row_b * (2 * stats["dressed_terms"] + 2 * stats["anticommuting"] + stats["appended"])
+    shares = {"dress": stats["dress_kernel_ms"], "key_index": stats["hash_ms"],
               "compression": stats["prune_ms"], "dis_screening": stats["dis_ms"],
               "energy_abc": stats["energy_kernel_ms"]}
     tot_ms = sum(shares.values())
-    roofline = {"bound": "hbm", "kernel": "k_dress (classify, partner lookup, rotate/append)",
+    roofline = {"bound": "hbm", "kernel": "dress of one generator: k_pair_split + k_pair_join (bin and tile "
+                                          "counts from the preceding A,B,C pass)",
                 "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                 "frac": round(achieved / peak, 4), "peak_kind": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)",
                 "traffic": profile_traffic(avg_rows),
                 "bytes_per_launch": stats["dress_bytes"] / n_dress, "launches": stats["n_dress"],
                 "avg_launch_ms": stats["dress_kernel_ms"] / n_dress,
+                "bytes_model": "16W M_in + 16 M_anti + (16W+8) M_new per dress (the method's own bytes)",
+                "moved_bytes_per_launch": moved / n_dress,
+                "moved_frac": round(moved / dress_s / 1e9 / peak, 4) if dress_s > 0 else None,
+                "moved_model": "(16W+8)(2 M_in + 2 M_anti + M_new): split copies every row once, "
+                               "join reads the bins and writes rotated and appended rows",
+                "anticommuting_per_launch": stats["anticommuting"] / n_dress,
+                "appended_per_launch": stats["appended"] / n_dress,
                 "device_ms_share": {k: round(v / tot_ms, 4) for k, v in shares.items()} if tot_ms else {},
                 "adjoint_pass": adjoint, "sort_variant": sort_variant, "batch_variant": batch_variant,
-                "random_access": random_access,
                 "learned_screening": screening, "plain_gpu_form": plain_form, "partitioned_variant": partitioned}
 
     # ---------------- oracle on the host cores (N = 1 only)

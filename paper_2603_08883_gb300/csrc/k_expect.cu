@@ -96,7 +96,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* out) 
 struct PairCount {
     uint32_t* counts;
     uint32_t* tile_kept;
-    int shift;
+    int L;
     int top_word;
     uint64_t top_mask;
     DevCounters* ctr;
@@ -141,9 +141,10 @@ __device__ __forceinline__ bool abc_row(const Key<W>& t, const double* __restric
 }
 
 // A, B, C for generator p (p = 0: energy in A).  HIST: the same pass also
-// counts, for the dress by p that follows (k_pairjoin.cu), the anticommuting
-// rows by dress bin and the commuting rows per tile of kDressTile rows (the
-// blocks then walk whole tiles); one read of the keys for both.
+// does the counting for the dress by p that follows (k_pairjoin.cu): per tile
+// of kDressTile rows (the blocks then walk whole tiles) the commuting rows the
+// split keeps and the anticommuting rows per level-1 partition, counted in
+// shared memory; one read of the keys for both.
 template <int W, bool BASIS, bool HIST>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
@@ -151,32 +152,47 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
                                                   int n_groups, double* partials, PairCount pc,
                                                   const uint8_t* __restrict__ live) {
     extern __shared__ double s_tab[];
+    __shared__ uint32_t s_h[HIST ? (1 << kPairL1Max) : 1];
+    __shared__ uint32_t s_kept;
     if (!BASIS) {
         for (int i = threadIdx.x; i < n_groups * 256; i += blockDim.x) s_tab[i] = tables[i];
         __syncthreads();
     }
     double acc[3] = {0.0, 0.0, 0.0};
     if (HIST) {
+        const int L1 = pair_l1(pc.L), F1 = 1 << L1, shift1 = 64 - L1;
         unsigned n_anti = 0;
         const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
+        for (int d = threadIdx.x; d < F1; d += blockDim.x) s_h[d] = 0;
+        if (threadIdx.x == 0) s_kept = 0;
+        __syncthreads();
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-            int kept = 0;
-#pragma unroll
-            for (int r = 0; r < kDressTile / kThreads; ++r) {
-                const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
-                bool k = false;
-                if (i < M && (!live || live[i])) {  // rows dropped by a pending term-limit cut are skipped
-                    const Key<W> t = load_key<W>(rows, i);
-                    if (abc_row<W, BASIS>(t, coef, i, p, yP, occ, s_tab, n_groups, acc)) {
-                        atomicAdd(&pc.counts[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
-                        ++n_anti;
-                    } else {
-                        k = true;
-                    }
+            unsigned kept = 0;
+            const int64_t end = min(M, (tile + 1) * kDressTile);
+#pragma unroll 4
+            for (int64_t i = tile * kDressTile + threadIdx.x; i < end; i += blockDim.x) {
+                if (live && !live[i]) continue;  // rows dropped by a pending term-limit cut are skipped
+                const Key<W> t = load_key<W>(rows, i);
+                if (abc_row<W, BASIS>(t, coef, i, p, yP, occ, s_tab, n_groups, acc)) {
+                    atomicAdd(&s_h[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> shift1], 1u);
+                    ++n_anti;
+                } else {
+                    ++kept;
                 }
-                kept += __syncthreads_count(k);
             }
-            if (threadIdx.x == 0) pc.tile_kept[tile] = (uint32_t)kept;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(0xFFFFFFFFu, kept, o);
+            if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&s_kept, kept);
+            __syncthreads();
+            for (int d = threadIdx.x; d < F1; d += blockDim.x) {
+                pc.counts[(int64_t)d * n_tiles + tile] = s_h[d];
+                s_h[d] = 0;
+            }
+            if (threadIdx.x == 0) {
+                pc.tile_kept[tile] = s_kept;
+                s_kept = 0;
+            }
+            __syncthreads();
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
@@ -349,7 +365,7 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
     PairCount pc{};
     if (pair) {
         const Gen<W> g = make_gen<W>(pkey, 1.0, 0.0);
-        pc = PairCount{pair->counts, pair->tile_kept, 64 - pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
+        pc = PairCount{pair->counts, pair->tile_kept, pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
         abc_launch<W, true>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
     } else {
         abc_launch<W, false>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
