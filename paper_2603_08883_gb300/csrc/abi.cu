@@ -463,7 +463,7 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     if (live + n_anti > ctx->capacity) {
         // exact admission: partitioned copies and a counting join first, H untouched
         launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, rk1, rc1, rb1, pc.tiles,
-                          nullptr, nullptr, ctx->stream, live_flags(ctx));
+                          nullptr, nullptr, c, ctx->stream, live_flags(ctx));
         launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, rk1, rc1, rb1, rk, rc, pc.start, ctx->stream);
         launch_pair_join(d, false, rk, rc, pc.start, pc.log2_bins, bpb, nullptr, nullptr, kept, out_cursor, c,
                          ctx->stream);
@@ -485,7 +485,7 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     uint64_t* rows_out = (uint64_t*)ctx->keys2.p;
     double* coef_out = (double*)ctx->coef2.p;
     launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, rk1, rc1, rb1, pc.tiles,
-                      rows_out, coef_out, ctx->stream, live_flags(ctx));
+                      rows_out, coef_out, c, ctx->stream, live_flags(ctx));
     if (!scattered) launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, rk1, rc1, rb1, rk, rc, pc.start, ctx->stream);
     launch_pair_join(d, true, rk, rc, pc.start, pc.log2_bins, bpb, rows_out, coef_out, kept, out_cursor, c,
                      ctx->stream);

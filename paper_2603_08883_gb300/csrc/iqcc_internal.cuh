@@ -408,8 +408,8 @@ void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int l
 // grouped by level-1 partition (scatter; base1: exclusive scan of the counting pass's matrix).
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
                        int64_t M, int log2_bins, const uint32_t* base1, uint64_t* rk1, double* rc1, uint32_t* rb1,
-                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, cudaStream_t s,
-                       const uint8_t* live = nullptr);
+                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
+                       cudaStream_t s, const uint8_t* live = nullptr);
 // The split's output ordered by bin into rk / rc; start: [2^log2_bins + 1] bin starts (all written).
 void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* rk1,
                        const double* rc1, const uint32_t* rb1, uint64_t* rk, double* rc, uint32_t* start,

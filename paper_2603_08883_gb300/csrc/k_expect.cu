@@ -169,15 +169,30 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             unsigned kept = 0;
             const int64_t end = min(M, (tile + 1) * kDressTile);
-#pragma unroll 4
-            for (int64_t i = tile * kDressTile + threadIdx.x; i < end; i += blockDim.x) {
-                if (live && !live[i]) continue;  // rows dropped by a pending term-limit cut are skipped
-                const Key<W> t = load_key<W>(rows, i);
-                if (abc_row<W, BASIS>(t, coef, i, p, yP, occ, s_tab, n_groups, acc)) {
-                    atomicAdd(&s_h[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> shift1], 1u);
-                    ++n_anti;
-                } else {
-                    ++kept;
+            // four rows per thread in flight: their live flags, then their keys
+            constexpr int kU = 4;
+            for (int64_t i0 = tile * kDressTile + threadIdx.x; i0 < end; i0 += (int64_t)kU * kThreads) {
+                bool v[kU];
+                Key<W> tk[kU];
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    const int64_t i = i0 + (int64_t)u * kThreads;
+                    v[u] = i < end;
+                    if (v[u] && live) v[u] = live[i] != 0;  // rows dropped by a pending term-limit cut are skipped
+                }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (v[u]) tk[u] = load_key<W>(rows, i0 + (int64_t)u * kThreads);
+#pragma unroll
+                for (int u = 0; u < kU; ++u) {
+                    if (!v[u]) continue;
+                    const int64_t i = i0 + (int64_t)u * kThreads;
+                    if (abc_row<W, BASIS>(tk[u], coef, i, p, yP, occ, s_tab, n_groups, acc)) {
+                        atomicAdd(&s_h[pair_hash<W>(tk[u], p, pc.top_word, pc.top_mask) >> shift1], 1u);
+                        ++n_anti;
+                    } else {
+                        ++kept;
+                    }
                 }
             }
 #pragma unroll

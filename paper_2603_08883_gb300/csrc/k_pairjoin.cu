@@ -41,6 +41,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 
 #include "iqcc_internal.cuh"
 
@@ -144,58 +145,217 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
     if ((threadIdx.x & 31) == 0 && n_anti) atomicAdd(&ctr->n_anti, (unsigned long long)n_anti);
 }
 
-// The split, one tile of kDressTile rows per block, in chunks of 1024 rows
-// (256 threads, 4 rows each), from the rows into the other row buffer:
-// COMPACT copies the rows that commute with their generator to rows_out /
-// coef_out from tile_off[t] on, in order (ranked by warp ballots); SCATTER
-// copies each anticommuting row's key, coefficient and bin (the top L bits
-// of its pair hash) to rk1 / rc1 / rb1 at its level-1 partition's offset for
-// this tile (base1: the exclusive scan of the counting pass's matrix), ranked
-// by a shared-memory counter per partition.  No block waits on another and no
+// ---------------------------------------------------------------------------
+// The split as a persistent kernel whose rows arrive by bulk copies.  Each
+// block takes the tiles t = blockIdx.x, blockIdx.x + gridDim.x, ... and walks
+// them in chunks of 1024 rows; the chunks (keys, coefficients and, under a
+// pending cut, live flags) are copied into a ring of kSplitStages shared-memory
+// stages by cp.async.bulk with completion counted on one mbarrier per stage,
+// kSplitStages - 1 chunks ahead of the one being worked on.  So the loads of
+// later chunks are in flight while a chunk is ranked and written, which a
+// one-shot tile (loads, then ranking, then stores) cannot do.  A partial chunk
+// (the end of H) is read from global memory directly.  Every wait on an
+// mbarrier is bounded by ctr->wait_limit polls; a wait that gives up records
+// IQCC_ERR_TIMEOUT, waits (bounded again) for the copies still in flight, and
+// the block returns.
+
+constexpr int kSplitChunk = 1024;
+constexpr int kSplitStages = 2;
+constexpr int kSplitChunks = kDressTile / kSplitChunk;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init_fence() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n"
+        ".reg .pred p;\n"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        "selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int limit) {
+    for (int k = 0; k < limit; ++k)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+// Generic-proxy accesses of shared memory ordered before later async-proxy ones.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// bytes (a multiple of 16) from 16-byte aligned global src to 16-byte aligned
+// shared dst, counted on bar
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int W>
+struct SplitStage {
+    static constexpr size_t kKeys = (size_t)kSplitChunk * 16 * W;
+    static constexpr size_t kCoefs = (size_t)kSplitChunk * 8;
+    static constexpr size_t kLive = kSplitChunk;
+    static constexpr size_t kBytes = kKeys + kCoefs + kLive;  // a multiple of 16
+};
+
+template <int W>
+constexpr size_t split_smem_bytes() {
+    return kSplitStages * SplitStage<W>::kBytes;
+}
+
+// Job j of a block: chunk j % kSplitChunks of its (j / kSplitChunks)-th tile.
+// Thread 0 starts its copies into stage `st` (a full chunk), or, for a
+// partial chunk or a job past the end, arrives on the stage's barrier without
+// a copy.
+template <int W>
+__device__ __forceinline__ void split_issue(unsigned char* stage, uint64_t* bar, const uint64_t* rows,
+                                            const double* coef, const uint8_t* live, int64_t n, int64_t r0) {
+    if (r0 + kSplitChunk > n) {
+        mbar_arrive(bar);
+        return;
+    }
+    const uint32_t bytes =
+        (uint32_t)(SplitStage<W>::kKeys + SplitStage<W>::kCoefs + (live ? SplitStage<W>::kLive : 0));
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, bytes);
+    bulk_load(stage, rows + (size_t)r0 * 2 * W, (uint32_t)SplitStage<W>::kKeys, bar);
+    bulk_load(stage + SplitStage<W>::kKeys, coef + r0, (uint32_t)SplitStage<W>::kCoefs, bar);
+    if (live) bulk_load(stage + SplitStage<W>::kKeys + SplitStage<W>::kCoefs, live + r0, (uint32_t)SplitStage<W>::kLive, bar);
+}
+
+template <int W>
+__device__ __forceinline__ Key<W> smem_key(const unsigned char* stage, int r) {
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(stage) + (size_t)r * W;
+    Key<W> k;
+    uint64_t w[2 * W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const ulonglong2 v = p[j];
+        w[2 * j] = v.x;
+        w[2 * j + 1] = v.y;
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        k.x[j] = w[j];
+        k.z[j] = w[W + j];
+    }
+    return k;
+}
+
+// The split, from the rows into the other row buffer: COMPACT copies the
+// rows that commute with their generator to rows_out / coef_out from
+// tile_off[t] on, in order (ranked by warp ballots); SCATTER copies each
+// anticommuting row's key, coefficient and bin (the top L bits of its pair
+// hash) to rk1 / rc1 / rb1 at its level-1 partition's offset for the tile
+// (base1: the exclusive scan of the counting pass's matrix), ranked by a
+// shared-memory counter per partition.  No block waits on another and no
 // position comes from a global atomic.  live (may be NULL): rows with
 // live[i] == 0 (dropped by a pending term-limit cut) are neither kept nor
 // copied.
 template <int W, class G, bool COMPACT, bool SCATTER>
 __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restrict__ rows,
-                                                         const double* __restrict__ coef, int64_t n, G gen_of,
-                                                         int L, const uint32_t* __restrict__ base1, uint64_t* rk1,
-                                                         double* rc1, uint32_t* rb1,
-                                                         const uint32_t* __restrict__ tile_off, uint64_t* rows_out,
-                                                         double* coef_out, const uint8_t* __restrict__ live) {
-    constexpr int kPer = 1024 / kThreads;
+                                                              const double* __restrict__ coef, int64_t n, G gen_of,
+                                                              int L, const uint32_t* __restrict__ base1,
+                                                              uint64_t* rk1, double* rc1, uint32_t* rb1,
+                                                              const uint32_t* __restrict__ tile_off,
+                                                              uint64_t* rows_out, double* coef_out,
+                                                              const uint8_t* __restrict__ live, DevCounters* ctr) {
+    extern __shared__ __align__(128) unsigned char s_stage[];
+    __shared__ __align__(8) uint64_t s_bar[kSplitStages];
     __shared__ uint32_t s_cur[SCATTER ? (1 << kPairL1Max) : 1];
     __shared__ uint32_t s_w[kThreads / 32];
+    constexpr int kPer = kSplitChunk / kThreads;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const unsigned lt = (1u << lane) - 1u;
-    const int64_t t = blockIdx.x;
     const int64_t n_tiles = (n + kDressTile - 1) / kDressTile;
+    const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t jobs = my_tiles * kSplitChunks;
     const int L1 = pair_l1(L);
     const int shift1 = 64 - L1, shiftL = 64 - L;
-    if (SCATTER)
-        for (int d = threadIdx.x; d < (1 << L1); d += blockDim.x) s_cur[d] = base1[(int64_t)d * n_tiles + t];
-    uint32_t koff = COMPACT ? tile_off[t] : 0u;
+    const int limit = ctr->wait_limit;
+    auto job_row = [&](int64_t j) {
+        return ((int64_t)blockIdx.x + (j / kSplitChunks) * gridDim.x) * kDressTile + (j % kSplitChunks) * kSplitChunk;
+    };
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < kSplitStages; ++st) mbar_init(&s_bar[st], 1);
+        mbar_init_fence();
+    }
     __syncthreads();
-    for (int ch = 0; ch < kDressTile / 1024; ++ch) {
-        const int64_t cbase = t * kDressTile + (int64_t)ch * 1024;
-        if (cbase >= n) break;  // the same for the whole block
-        const int64_t wbase = cbase + (int64_t)wid * (kPer * 32);
+    if (threadIdx.x == 0)
+        for (int64_t j = 0; j < kSplitStages - 1 && j < jobs; ++j)
+            split_issue<W>(s_stage + (size_t)j * SplitStage<W>::kBytes, &s_bar[j], rows, coef, live, n, job_row(j));
+    uint32_t koff = 0;
+    for (int64_t j = 0; j < jobs; ++j) {
+        const int st = (int)(j % kSplitStages);
+        const int64_t r0 = job_row(j);
+        if (r0 >= n) break;  // the same for the whole block (only the last tile can end early)
+        const int64_t t = r0 / kDressTile;
+        if (threadIdx.x == 0 && j + kSplitStages - 1 < jobs) {
+            const int64_t jn = j + kSplitStages - 1;
+            const int sn = (int)(jn % kSplitStages);
+            split_issue<W>(s_stage + (size_t)sn * SplitStage<W>::kBytes, &s_bar[sn], rows, coef, live, n,
+                           job_row(jn));
+        }
+        if (j % kSplitChunks == 0) {  // a new tile: its offsets
+            if (SCATTER)
+                for (int d = threadIdx.x; d < (1 << L1); d += blockDim.x) s_cur[d] = base1[(int64_t)d * n_tiles + t];
+            if (COMPACT) koff = tile_off[t];
+            __syncthreads();
+        }
+        const bool ok = mbar_wait_bounded(&s_bar[st], (uint32_t)((j / kSplitStages) & 1), limit);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                set_error(ctr, IQCC_ERR_TIMEOUT, 75);
+                // the copies still in flight land before the block's shared memory is released
+                for (int64_t jj = j; jj < jobs && jj < j + kSplitStages; ++jj)
+                    mbar_wait_bounded(&s_bar[jj % kSplitStages], (uint32_t)((jj / kSplitStages) & 1), limit);
+            }
+            return;
+        }
+        const unsigned char* stage = s_stage + (size_t)st * SplitStage<W>::kBytes;
+        const bool full = r0 + kSplitChunk <= n;
+        const double* s_coef = reinterpret_cast<const double*>(stage + SplitStage<W>::kKeys);
+        const uint8_t* s_live = stage + SplitStage<W>::kKeys + SplitStage<W>::kCoefs;
         Key<W> key[kPer];
         double c[kPer];
         uint32_t pos[kPer], bin[kPer];
         bool keep[kPer], anti[kPer];
 #pragma unroll
         for (int r = 0; r < kPer; ++r) {
-            const int64_t i = wbase + (int64_t)r * 32 + lane;
+            const int rr = wid * (kPer * 32) + r * 32 + lane;
+            const int64_t i = r0 + rr;
             keep[r] = anti[r] = false;
-            if (i < n && (!live || live[i])) {
-                key[r] = load_key<W>(rows, i);
-                c[r] = coef[i];
-            }
-        }
-#pragma unroll
-        for (int r = 0; r < kPer; ++r) {
-            const int64_t i = wbase + (int64_t)r * 32 + lane;
-            if (i < n && (!live || live[i])) {
+            bool in = i < n;
+            if (in && live) in = full ? s_live[rr] != 0 : live[i] != 0;
+            if (in) {
+                if (full) {
+                    key[r] = smem_key<W>(stage, rr);
+                    c[r] = s_coef[rr];
+                } else {
+                    key[r] = load_key<W>(rows, i);
+                    c[r] = coef[i];
+                }
                 const auto& g = gen_of(key[r]);
                 anti[r] = anticommutes<W>(key[r], g.p);
                 keep[r] = !anti[r];
@@ -242,8 +402,8 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
                 }
             }
             koff += tot;
-            __syncthreads();  // s_w is rewritten by the next chunk
         }
+        __syncthreads();  // stage st and s_w are reused
     }
 }
 
@@ -268,7 +428,28 @@ __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, i
     const int64_t s = base1[p * n_tiles], e = base1[(p + 1) * n_tiles];
     for (uint32_t d = threadIdx.x; d < F2; d += blockDim.x) s_h[d] = 0;
     __syncthreads();
-    for (int64_t i = s + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&s_h[rb1[i] & mask], 1u);
+    {  // histogram of the bins: 16-byte loads over the aligned middle, two per thread in flight
+        const int64_t a0 = min(e, (s + 3) & ~(int64_t)3), a1 = max(a0, e & ~(int64_t)3);
+        for (int64_t i = s + threadIdx.x; i < a0; i += blockDim.x) atomicAdd(&s_h[rb1[i] & mask], 1u);
+        for (int64_t i = a1 + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&s_h[rb1[i] & mask], 1u);
+        const uint4* v = reinterpret_cast<const uint4*>(rb1 + a0);
+        const int64_t nv = (a1 - a0) / 4;
+        for (int64_t k = threadIdx.x; k < nv; k += 2 * (int64_t)blockDim.x) {
+            const uint4 x = v[k];
+            const bool two = k + blockDim.x < nv;
+            const uint4 y = two ? v[k + blockDim.x] : make_uint4(0, 0, 0, 0);
+            atomicAdd(&s_h[x.x & mask], 1u);
+            atomicAdd(&s_h[x.y & mask], 1u);
+            atomicAdd(&s_h[x.z & mask], 1u);
+            atomicAdd(&s_h[x.w & mask], 1u);
+            if (two) {
+                atomicAdd(&s_h[y.x & mask], 1u);
+                atomicAdd(&s_h[y.y & mask], 1u);
+                atomicAdd(&s_h[y.z & mask], 1u);
+                atomicAdd(&s_h[y.w & mask], 1u);
+            }
+        }
+    }
     __syncthreads();
     // exclusive scan of the F2 counters: each thread takes a run of `per`
     const uint32_t per = (F2 + blockDim.x - 1) / blockDim.x;
@@ -425,17 +606,26 @@ struct PairLaunch {
     static void split(const G& g, bool compact, bool scatter, const uint64_t* rows, const double* coef, int64_t M,
                       int L, const uint32_t* base1, uint64_t* rk1, double* rc1, uint32_t* rb1,
                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, const uint8_t* live,
-                      cudaStream_t s) {
-        const unsigned nt = (unsigned)((M + kDressTile - 1) / kDressTile);
+                      DevCounters* ctr, cudaStream_t s) {
+        const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
+        constexpr size_t smem = split_smem_bytes<W>();
+        const int per_sm = std::max(1, (int)((200 * 1024) / (smem + 9 * 1024)));
+        const int grid = (int)std::min<int64_t>(n_tiles, (int64_t)sm_count() * per_sm);
+        static std::atomic<unsigned long long> attr{0};
+        if (first_on_device(&attr)) {
+            cudaFuncSetAttribute(k_pair_split<W, G, true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_pair_split<W, G, true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            cudaFuncSetAttribute(k_pair_split<W, G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        }
         if (compact && scatter)
-            k_pair_split<W, G, true, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
-                                                                    tile_off, rows_out, coef_out, live);
+            k_pair_split<W, G, true, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
+                                                                       tile_off, rows_out, coef_out, live, ctr);
         else if (compact)
-            k_pair_split<W, G, true, false><<<nt, kThreads, 0, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
-                                                                     tile_off, rows_out, coef_out, live);
+            k_pair_split<W, G, true, false><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
+                                                                        tile_off, rows_out, coef_out, live, ctr);
         else
-            k_pair_split<W, G, false, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
-                                                                     tile_off, rows_out, coef_out, live);
+            k_pair_split<W, G, false, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
+                                                                        tile_off, rows_out, coef_out, live, ctr);
     }
     static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
                      uint32_t n_bins, uint32_t bpb, uint64_t* rows, double* coef, const uint32_t* kept,
@@ -492,12 +682,12 @@ void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int l
 
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
                        int64_t M, int log2_bins, const uint32_t* base1, uint64_t* rk1, double* rc1, uint32_t* rb1,
-                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, cudaStream_t s,
-                       const uint8_t* live) {
+                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
+                       cudaStream_t s, const uint8_t* live) {
     if (M <= 0 || !(compact || scatter)) return;
     with_provider(d, [&](auto L, auto g) {
         decltype(L)::split(g, compact, scatter, rows, coef, M, log2_bins, base1, rk1, rc1, rb1, tile_off, rows_out,
-                           coef_out, live, s);
+                           coef_out, live, ctr, s);
     });
     note_launch();
 }
