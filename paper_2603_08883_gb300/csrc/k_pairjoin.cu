@@ -159,6 +159,49 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
 // IQCC_ERR_TIMEOUT, waits (bounded again) for the copies still in flight, and
 // the block returns.
 
+// A level-1 record: the key (x words, then z words), then one whole 32-byte
+// sector holding the coefficient, the bin and zeros, so that every record is
+// written as whole sectors (a partial sector written by one block and
+// completed by another much later would be read back from DRAM first).
+template <int W>
+__device__ __forceinline__ void store_rec(uint64_t* rec, uint32_t pos, const Key<W>& k, double c, uint32_t bin) {
+    constexpr int RW = pair_rec_words(W);
+    uint64_t w[RW];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        w[j] = k.x[j];
+        w[W + j] = k.z[j];
+    }
+    w[2 * W] = (uint64_t)__double_as_longlong(c);
+    w[2 * W + 1] = bin;
+#pragma unroll
+    for (int j = 2 * W + 2; j < RW; ++j) w[j] = 0;
+    ulonglong2* p = reinterpret_cast<ulonglong2*>(rec + (size_t)pos * RW);
+#pragma unroll
+    for (int j = 0; j < RW / 2; ++j) p[j] = make_ulonglong2(w[2 * j], w[2 * j + 1]);
+}
+
+template <int W>
+__device__ __forceinline__ void load_rec(const uint64_t* __restrict__ rec, int64_t i, Key<W>& k, double& c,
+                                         uint32_t& bin) {
+    constexpr int RW = pair_rec_words(W);
+    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(rec + (size_t)i * RW);
+    uint64_t w[2 * W + 2];
+#pragma unroll
+    for (int j = 0; j < W + 1; ++j) {
+        const ulonglong2 v = __ldg(p + j);
+        w[2 * j] = v.x;
+        w[2 * j + 1] = v.y;
+    }
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        k.x[j] = w[j];
+        k.z[j] = w[W + j];
+    }
+    c = __longlong_as_double((long long)w[2 * W]);
+    bin = (uint32_t)w[2 * W + 1];
+}
+
 constexpr int kSplitChunk = 1024;
 constexpr int kSplitStages = 2;
 constexpr int kSplitChunks = kDressTile / kSplitChunk;
@@ -267,7 +310,7 @@ __device__ __forceinline__ Key<W> smem_key(const unsigned char* stage, int r) {
 // rows that commute with their generator to rows_out / coef_out from
 // tile_off[t] on, in order (ranked by warp ballots); SCATTER copies each
 // anticommuting row's key, coefficient and bin (the top L bits of its pair
-// hash) to rk1 / rc1 / rb1 at its level-1 partition's offset for the tile
+// hash) as one record (store_rec) to rec1 at its level-1 partition's offset for the tile
 // (base1: the exclusive scan of the counting pass's matrix), ranked by a
 // shared-memory counter per partition.  No block waits on another and no
 // position comes from a global atomic.  live (may be NULL): rows with
@@ -277,7 +320,7 @@ template <int W, class G, bool COMPACT, bool SCATTER>
 __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restrict__ rows,
                                                               const double* __restrict__ coef, int64_t n, G gen_of,
                                                               int L, const uint32_t* __restrict__ base1,
-                                                              uint64_t* rk1, double* rc1, uint32_t* rb1,
+                                                              uint64_t* rec1,
                                                               const uint32_t* __restrict__ tile_off,
                                                               uint64_t* rows_out, double* coef_out,
                                                               const uint8_t* __restrict__ live, DevCounters* ctr) {
@@ -370,9 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
                 if (anti[r]) {
-                    store_key<W>(rk1, pos[r], key[r]);
-                    rc1[pos[r]] = c[r];
-                    rb1[pos[r]] = bin[r];
+                    store_rec<W>(rec1, pos[r], key[r], c[r], bin[r]);
                 }
             }
         }
@@ -407,19 +448,19 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
     }
 }
 
-// The second level: block p orders level-1 partition p (rows [base1[p *
-// n_tiles], base1[(p + 1) * n_tiles]) of rk1 / rc1 / rb1) by the low L2 =
-// L - L1 bits of each row's bin into rk / rc, and writes the starts of its
+// The second level: block p orders level-1 partition p (records
+// [base1[p * n_tiles], base1[(p + 1) * n_tiles]) of rec1) by the low L2 =
+// L - L1 bits of each record's bin into rk / rc, and writes the starts of its
 // 2^L2 bins to start[(p << L2) ...] (the last block also start[2^L]).  Two
 // reads of the bins (histogram, then placement through shared-memory
-// counters) and one of the rows.
+// counters) and one of the keys and coefficients.
 template <int W>
 __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, int L,
                                                               const uint32_t* __restrict__ base1,
-                                                              const uint64_t* __restrict__ rk1,
-                                                              const double* __restrict__ rc1,
-                                                              const uint32_t* __restrict__ rb1, uint64_t* rk,
+                                                              const uint64_t* __restrict__ rec1, uint64_t* rk,
                                                               double* rc, uint32_t* start) {
+    constexpr int RW = pair_rec_words(W);
+    constexpr int kU = 4;
     __shared__ uint32_t s_h[1 << kPairL2Max];
     __shared__ uint32_t s_warp[kPart2Threads / 32];
     const int L1 = pair_l1(L), L2 = L - L1;
@@ -428,27 +469,16 @@ __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, i
     const int64_t s = base1[p * n_tiles], e = base1[(p + 1) * n_tiles];
     for (uint32_t d = threadIdx.x; d < F2; d += blockDim.x) s_h[d] = 0;
     __syncthreads();
-    {  // histogram of the bins: 16-byte loads over the aligned middle, two per thread in flight
-        const int64_t a0 = min(e, (s + 3) & ~(int64_t)3), a1 = max(a0, e & ~(int64_t)3);
-        for (int64_t i = s + threadIdx.x; i < a0; i += blockDim.x) atomicAdd(&s_h[rb1[i] & mask], 1u);
-        for (int64_t i = a1 + threadIdx.x; i < e; i += blockDim.x) atomicAdd(&s_h[rb1[i] & mask], 1u);
-        const uint4* v = reinterpret_cast<const uint4*>(rb1 + a0);
-        const int64_t nv = (a1 - a0) / 4;
-        for (int64_t k = threadIdx.x; k < nv; k += 2 * (int64_t)blockDim.x) {
-            const uint4 x = v[k];
-            const bool two = k + blockDim.x < nv;
-            const uint4 y = two ? v[k + blockDim.x] : make_uint4(0, 0, 0, 0);
-            atomicAdd(&s_h[x.x & mask], 1u);
-            atomicAdd(&s_h[x.y & mask], 1u);
-            atomicAdd(&s_h[x.z & mask], 1u);
-            atomicAdd(&s_h[x.w & mask], 1u);
-            if (two) {
-                atomicAdd(&s_h[y.x & mask], 1u);
-                atomicAdd(&s_h[y.y & mask], 1u);
-                atomicAdd(&s_h[y.z & mask], 1u);
-                atomicAdd(&s_h[y.w & mask], 1u);
-            }
+    for (int64_t i0 = s + threadIdx.x; i0 < e; i0 += (int64_t)blockDim.x * kU) {
+        uint32_t b[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int64_t i = i0 + (int64_t)u * blockDim.x;
+            b[u] = i < e ? (uint32_t)__ldg(rec1 + (size_t)i * RW + 2 * W + 1) : 0u;
         }
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + (int64_t)u * blockDim.x < e) atomicAdd(&s_h[b[u] & mask], 1u);
     }
     __syncthreads();
     // exclusive scan of the F2 counters: each thread takes a run of `per`
@@ -465,7 +495,6 @@ __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, i
     }
     if (p == (int64_t)gridDim.x - 1 && threadIdx.x == 0) start[(int64_t)gridDim.x << L2] = (uint32_t)e;
     __syncthreads();
-    constexpr int kU = 4;
     for (int64_t i0 = s + threadIdx.x; i0 < e; i0 += (int64_t)blockDim.x * kU) {
         Key<W> key[kU];
         double c[kU];
@@ -473,11 +502,7 @@ __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, i
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x;
-            if (i < e) {
-                key[u] = load_key<W>(rk1, i);
-                c[u] = rc1[i];
-                b[u] = rb1[i];
-            }
+            if (i < e) load_rec<W>(rec1, i, key[u], c[u], b[u]);
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -604,7 +629,7 @@ struct PairLaunch {
         k_pair_hist<W, G><<<grid, kThreads, 0, s>>>(rows, M, g, L, counts, tile_kept, ctr, live);
     }
     static void split(const G& g, bool compact, bool scatter, const uint64_t* rows, const double* coef, int64_t M,
-                      int L, const uint32_t* base1, uint64_t* rk1, double* rc1, uint32_t* rb1,
+                      int L, const uint32_t* base1, uint64_t* rec1,
                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, const uint8_t* live,
                       DevCounters* ctr, cudaStream_t s) {
         const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
@@ -618,13 +643,13 @@ struct PairLaunch {
             cudaFuncSetAttribute(k_pair_split<W, G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         }
         if (compact && scatter)
-            k_pair_split<W, G, true, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
+            k_pair_split<W, G, true, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rec1,
                                                                        tile_off, rows_out, coef_out, live, ctr);
         else if (compact)
-            k_pair_split<W, G, true, false><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
+            k_pair_split<W, G, true, false><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rec1,
                                                                         tile_off, rows_out, coef_out, live, ctr);
         else
-            k_pair_split<W, G, false, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rk1, rc1, rb1,
+            k_pair_split<W, G, false, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rec1,
                                                                         tile_off, rows_out, coef_out, live, ctr);
     }
     static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
@@ -681,26 +706,26 @@ void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int l
 }
 
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
-                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* rk1, double* rc1, uint32_t* rb1,
+                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* rec1,
                        const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
                        cudaStream_t s, const uint8_t* live) {
     if (M <= 0 || !(compact || scatter)) return;
     with_provider(d, [&](auto L, auto g) {
-        decltype(L)::split(g, compact, scatter, rows, coef, M, log2_bins, base1, rk1, rc1, rb1, tile_off, rows_out,
+        decltype(L)::split(g, compact, scatter, rows, coef, M, log2_bins, base1, rec1, tile_off, rows_out,
                            coef_out, live, ctr, s);
     });
     note_launch();
 }
 
-void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* rk1,
-                       const double* rc1, const uint32_t* rb1, uint64_t* rk, double* rc, uint32_t* start,
+void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* rec1,
+                       uint64_t* rk, double* rc, uint32_t* start,
                        cudaStream_t s) {
     const int64_t n_tiles = (std::max<int64_t>(M, 1) + kDressTile - 1) / kDressTile;
     const unsigned parts = 1u << pair_l1(log2_bins);
     switch (Wd) {
-        case 1: k_pair_part2<1><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rk1, rc1, rb1, rk, rc, start); break;
-        case 2: k_pair_part2<2><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rk1, rc1, rb1, rk, rc, start); break;
-        default: k_pair_part2<4><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rk1, rc1, rb1, rk, rc, start); break;
+        case 1: k_pair_part2<1><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rec1, rk, rc, start); break;
+        case 2: k_pair_part2<2><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rec1, rk, rc, start); break;
+        default: k_pair_part2<4><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rec1, rk, rc, start); break;
     }
     note_launch();
 }
