@@ -438,16 +438,18 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     const int64_t n_anti = ready ? ctx->pair_n_anti : (int64_t)ctx->h_counters->n_anti;
     *n_anti_out = n_anti;
     if (n_anti == 0) return apply_pending_cut(ctx);  // P commutes with every term
-    // the anticommuting rows grouped by level-1 partition (records of key,
+    // the anticommuting rows grouped by level-1 partition (keys, and tails of
     // coefficient and bin), then ordered by bin (keys, coefficients)
     const size_t kw = (size_t)n_anti * 2 * ctx->Wd;
     Carver rv;
-    rv.take<uint64_t>((size_t)n_anti * pair_rec_words(ctx->Wd));
+    rv.take<uint64_t>((size_t)n_anti * pair_key_words(ctx->Wd));
+    rv.take<uint64_t>((size_t)n_anti * 4);
     rv.take<uint64_t>(kw);
     rv.take<double>(n_anti);
     if (!ensure(ctx, ctx->aux, rv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     rv = Carver{(char*)ctx->aux.p, 0};
-    uint64_t* rec1 = rv.take<uint64_t>((size_t)n_anti * pair_rec_words(ctx->Wd));
+    uint64_t* k1 = rv.take<uint64_t>((size_t)n_anti * pair_key_words(ctx->Wd));
+    uint64_t* t1 = rv.take<uint64_t>((size_t)n_anti * 4);
     uint64_t* rk = rv.take<uint64_t>(kw);
     double* rc = rv.take<double>(n_anti);
     if (rv.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
@@ -458,9 +460,9 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     int64_t need = live + n_anti;
     if (live + n_anti > ctx->capacity) {
         // exact admission: partitioned copies and a counting join first, H untouched
-        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, rec1, pc.tiles,
+        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, k1, t1, pc.tiles,
                           nullptr, nullptr, c, ctx->stream, live_flags(ctx));
-        launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, rec1, rk, rc, pc.start, ctx->stream);
+        launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, k1, t1, rk, rc, pc.start, ctx->stream);
         launch_pair_join(d, false, rk, rc, pc.start, pc.log2_bins, bpb, nullptr, nullptr, kept, out_cursor, c,
                          ctx->stream);
         CK_LAUNCH();
@@ -480,9 +482,9 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     if (st) return st;
     uint64_t* rows_out = (uint64_t*)ctx->keys2.p;
     double* coef_out = (double*)ctx->coef2.p;
-    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, rec1, pc.tiles,
+    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, k1, t1, pc.tiles,
                       rows_out, coef_out, c, ctx->stream, live_flags(ctx));
-    if (!scattered) launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, rec1, rk, rc, pc.start, ctx->stream);
+    if (!scattered) launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, k1, t1, rk, rc, pc.start, ctx->stream);
     launch_pair_join(d, true, rk, rc, pc.start, pc.log2_bins, bpb, rows_out, coef_out, kept, out_cursor, c,
                      ctx->stream);
     CK_LAUNCH();

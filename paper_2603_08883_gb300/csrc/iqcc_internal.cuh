@@ -388,9 +388,8 @@ constexpr int kDressTile = 16384;
 constexpr int kPairL1Max = 11;
 constexpr int kPairL2Max = 12;
 __host__ __device__ inline int pair_l1(int L) { return L < kPairL1Max ? L : kPairL1Max; }
-// 64-bit words of a level-1 record: the key, then a 32-byte sector with the
-// coefficient and the bin (whole sectors only).
-__host__ __device__ constexpr int pair_rec_words(int Wd) { return (2 * Wd + 2 + 3) / 4 * 4; }
+// 64-bit words of a key in the split's level-1 copy: whole 32-byte sectors.
+__host__ __device__ constexpr int pair_key_words(int Wd) { return 2 * Wd < 4 ? 4 : 2 * Wd; }
 struct PairDress {
     int Wd;
     const uint64_t* pkey;    // host, device-layout key of the one generator (gens == nullptr)
@@ -407,15 +406,16 @@ uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins);
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
                       uint32_t* tile_kept, DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
 // From rows/coef (M rows) into rows_out/coef_out: the kept rows of tile t from tile_off[t] on (compact);
-// rec1 [n_anti][pair_rec_words(Wd)]: key, coefficient and bin of each anticommuting row, grouped by
-// level-1 partition (scatter; base1: exclusive scan of the counting pass's matrix).
+// k1 [n_anti][pair_key_words(Wd)] keys and t1 [n_anti][4] (coefficient, bin, 0, 0) of the
+// anticommuting rows, grouped by level-1 partition (scatter; base1: exclusive scan of the counting
+// pass's matrix).
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
-                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* rec1,
+                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* k1, uint64_t* t1,
                        const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
                        cudaStream_t s, const uint8_t* live = nullptr);
 // The split's output ordered by bin into rk / rc; start: [2^log2_bins + 1] bin starts (all written).
-void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* rec1,
-                       uint64_t* rk, double* rc, uint32_t* start,
+void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* k1,
+                       const uint64_t* t1, uint64_t* rk, double* rc, uint32_t* start,
                        cudaStream_t s);
 // start: [2^log2_bins + 1] bin starts; rows without a partner counted in ctr->n_new; with `write` the
 // dressed rows and appended partners are written to rows/coef from row *kept + (*out_cursor, zeroed) on

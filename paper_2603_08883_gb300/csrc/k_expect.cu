@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
             unsigned kept = 0;
             const int64_t end = min(M, (tile + 1) * kDressTile);
-            // four rows per thread in flight: keys and live flags in one round
+            // four rows per thread in flight: their live flags, then their keys
             constexpr int kU = 4;
             for (int64_t i0 = tile * kDressTile + threadIdx.x; i0 < end; i0 += (int64_t)kU * kThreads) {
                 bool v[kU];
@@ -178,11 +178,11 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
                 for (int u = 0; u < kU; ++u) {
                     const int64_t i = i0 + (int64_t)u * kThreads;
                     v[u] = i < end;
-                    if (v[u]) {
-                        tk[u] = load_key<W>(rows, i);
-                        if (live) v[u] = live[i] != 0;  // rows dropped by a pending term-limit cut are skipped
-                    }
+                    if (v[u] && live) v[u] = live[i] != 0;  // rows dropped by a pending term-limit cut are skipped
                 }
+#pragma unroll
+                for (int u = 0; u < kU; ++u)
+                    if (v[u]) tk[u] = load_key<W>(rows, i0 + (int64_t)u * kThreads);
 #pragma unroll
                 for (int u = 0; u < kU; ++u) {
                     if (!v[u]) continue;

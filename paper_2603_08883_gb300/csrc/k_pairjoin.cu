@@ -159,47 +159,74 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
 // IQCC_ERR_TIMEOUT, waits (bounded again) for the copies still in flight, and
 // the block returns.
 
-// A level-1 record: the key (x words, then z words), then one whole 32-byte
-// sector holding the coefficient, the bin and zeros, so that every record is
-// written as whole sectors (a partial sector written by one block and
-// completed by another much later would be read back from DRAM first).
+// 32-byte global accesses (one sector per thread; 32-byte aligned addresses).
+__device__ __forceinline__ void st256(uint64_t* p, uint64_t a, uint64_t b, uint64_t c, uint64_t d) {
+    asm volatile("st.global.v4.u64 [%0], {%1, %2, %3, %4};" ::"l"(p), "l"(a), "l"(b), "l"(c), "l"(d) : "memory");
+}
+
+__device__ __forceinline__ void ld256(const uint64_t* p, uint64_t& a, uint64_t& b, uint64_t& c, uint64_t& d) {
+    asm volatile("ld.global.nc.v4.u64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+
+// The level-1 copy of an anticommuting row is two whole-sector items: its key
+// in k1 (stride pair_key_words(W), zero-padded to a sector) and a tail
+// (coefficient, bin, 0, 0) in t1.  Written as whole sectors, no item is left
+// partly written in L2 for another block to complete much later (which would
+// make DRAM read the sector back first); the tails alone serve the second
+// pass's histogram.
 template <int W>
-__device__ __forceinline__ void store_rec(uint64_t* rec, uint32_t pos, const Key<W>& k, double c, uint32_t bin) {
-    constexpr int RW = pair_rec_words(W);
-    uint64_t w[RW];
+__device__ __forceinline__ void store_l1(uint64_t* k1, uint64_t* t1, uint32_t pos, const Key<W>& k, double c,
+                                         uint32_t bin) {
+    constexpr int KS = pair_key_words(W);
+    uint64_t w[KS];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         w[j] = k.x[j];
         w[W + j] = k.z[j];
     }
-    w[2 * W] = (uint64_t)__double_as_longlong(c);
-    w[2 * W + 1] = bin;
 #pragma unroll
-    for (int j = 2 * W + 2; j < RW; ++j) w[j] = 0;
-    ulonglong2* p = reinterpret_cast<ulonglong2*>(rec + (size_t)pos * RW);
+    for (int j = 2 * W; j < KS; ++j) w[j] = 0;
+    uint64_t* p = k1 + (size_t)pos * KS;
 #pragma unroll
-    for (int j = 0; j < RW / 2; ++j) p[j] = make_ulonglong2(w[2 * j], w[2 * j + 1]);
+    for (int j = 0; j < KS / 4; ++j) st256(p + 4 * j, w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    st256(t1 + (size_t)pos * 4, (uint64_t)__double_as_longlong(c), bin, 0, 0);
 }
 
 template <int W>
-__device__ __forceinline__ void load_rec(const uint64_t* __restrict__ rec, int64_t i, Key<W>& k, double& c,
-                                         uint32_t& bin) {
-    constexpr int RW = pair_rec_words(W);
-    const ulonglong2* p = reinterpret_cast<const ulonglong2*>(rec + (size_t)i * RW);
-    uint64_t w[2 * W + 2];
+__device__ __forceinline__ void load_l1(const uint64_t* k1, const uint64_t* t1, int64_t i, Key<W>& k, double& c,
+                                        uint32_t& bin) {
+    constexpr int KS = pair_key_words(W);
+    uint64_t w[KS];
+    const uint64_t* p = k1 + (size_t)i * KS;
 #pragma unroll
-    for (int j = 0; j < W + 1; ++j) {
-        const ulonglong2 v = __ldg(p + j);
-        w[2 * j] = v.x;
-        w[2 * j + 1] = v.y;
-    }
+    for (int j = 0; j < KS / 4; ++j) ld256(p + 4 * j, w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         k.x[j] = w[j];
         k.z[j] = w[W + j];
     }
-    c = __longlong_as_double((long long)w[2 * W]);
-    bin = (uint32_t)w[2 * W + 1];
+    uint64_t a, b, u, v;
+    ld256(t1 + (size_t)i * 4, a, b, u, v);
+    c = __longlong_as_double((long long)a);
+    bin = (uint32_t)b;
+}
+
+// A row's key as whole sectors to rows_out (16 W bytes, a multiple of 32 for W >= 2).
+template <int W>
+__device__ __forceinline__ void store_row(uint64_t* rows, int64_t i, const Key<W>& k) {
+    if constexpr (W == 1) {
+        store_key<W>(rows, i, k);
+    } else {
+        uint64_t w[2 * W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            w[j] = k.x[j];
+            w[W + j] = k.z[j];
+        }
+        uint64_t* p = rows + (size_t)i * 2 * W;
+#pragma unroll
+        for (int j = 0; j < W / 2; ++j) st256(p + 4 * j, w[4 * j], w[4 * j + 1], w[4 * j + 2], w[4 * j + 3]);
+    }
 }
 
 constexpr int kSplitChunk = 1024;
@@ -310,7 +337,7 @@ __device__ __forceinline__ Key<W> smem_key(const unsigned char* stage, int r) {
 // rows that commute with their generator to rows_out / coef_out from
 // tile_off[t] on, in order (ranked by warp ballots); SCATTER copies each
 // anticommuting row's key, coefficient and bin (the top L bits of its pair
-// hash) as one record (store_rec) to rec1 at its level-1 partition's offset for the tile
+// hash) to k1 / t1 (store_l1) at its level-1 partition's offset for the tile
 // (base1: the exclusive scan of the counting pass's matrix), ranked by a
 // shared-memory counter per partition.  No block waits on another and no
 // position comes from a global atomic.  live (may be NULL): rows with
@@ -320,7 +347,7 @@ template <int W, class G, bool COMPACT, bool SCATTER>
 __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restrict__ rows,
                                                               const double* __restrict__ coef, int64_t n, G gen_of,
                                                               int L, const uint32_t* __restrict__ base1,
-                                                              uint64_t* rec1,
+                                                              uint64_t* k1, uint64_t* t1,
                                                               const uint32_t* __restrict__ tile_off,
                                                               uint64_t* rows_out, double* coef_out,
                                                               const uint8_t* __restrict__ live, DevCounters* ctr) {
@@ -413,7 +440,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
                 if (anti[r]) {
-                    store_rec<W>(rec1, pos[r], key[r], c[r], bin[r]);
+                    store_l1<W>(k1, t1, pos[r], key[r], c[r], bin[r]);
                 }
             }
         }
@@ -438,7 +465,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
 #pragma unroll
             for (int r = 0; r < kPer; ++r) {
                 if (keep[r]) {
-                    store_key<W>(rows_out, (int64_t)(off + rank[r]), key[r]);
+                    store_row<W>(rows_out, (int64_t)(off + rank[r]), key[r]);
                     coef_out[off + rank[r]] = c[r];
                 }
             }
@@ -448,8 +475,8 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
     }
 }
 
-// The second level: block p orders level-1 partition p (records
-// [base1[p * n_tiles], base1[(p + 1) * n_tiles]) of rec1) by the low L2 =
+// The second level: block p orders level-1 partition p (items
+// [base1[p * n_tiles], base1[(p + 1) * n_tiles]) of k1 / t1) by the low L2 =
 // L - L1 bits of each record's bin into rk / rc, and writes the starts of its
 // 2^L2 bins to start[(p << L2) ...] (the last block also start[2^L]).  Two
 // reads of the bins (histogram, then placement through shared-memory
@@ -457,9 +484,9 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
 template <int W>
 __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, int L,
                                                               const uint32_t* __restrict__ base1,
-                                                              const uint64_t* __restrict__ rec1, uint64_t* rk,
+                                                              const uint64_t* __restrict__ k1,
+                                                              const uint64_t* __restrict__ t1, uint64_t* rk,
                                                               double* rc, uint32_t* start) {
-    constexpr int RW = pair_rec_words(W);
     constexpr int kU = 4;
     __shared__ uint32_t s_h[1 << kPairL2Max];
     __shared__ uint32_t s_warp[kPart2Threads / 32];
@@ -474,7 +501,7 @@ __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, i
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x;
-            b[u] = i < e ? (uint32_t)__ldg(rec1 + (size_t)i * RW + 2 * W + 1) : 0u;
+            b[u] = i < e ? (uint32_t)__ldg(t1 + (size_t)i * 4 + 1) : 0u;
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u)
@@ -502,7 +529,7 @@ __global__ void __launch_bounds__(kPart2Threads) k_pair_part2(int64_t n_tiles, i
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
             const int64_t i = i0 + (int64_t)u * blockDim.x;
-            if (i < e) load_rec<W>(rec1, i, key[u], c[u], b[u]);
+            if (i < e) load_l1<W>(k1, t1, i, key[u], c[u], b[u]);
         }
 #pragma unroll
         for (int u = 0; u < kU; ++u) {
@@ -629,7 +656,7 @@ struct PairLaunch {
         k_pair_hist<W, G><<<grid, kThreads, 0, s>>>(rows, M, g, L, counts, tile_kept, ctr, live);
     }
     static void split(const G& g, bool compact, bool scatter, const uint64_t* rows, const double* coef, int64_t M,
-                      int L, const uint32_t* base1, uint64_t* rec1,
+                      int L, const uint32_t* base1, uint64_t* k1, uint64_t* t1,
                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, const uint8_t* live,
                       DevCounters* ctr, cudaStream_t s) {
         const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
@@ -643,13 +670,13 @@ struct PairLaunch {
             cudaFuncSetAttribute(k_pair_split<W, G, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         }
         if (compact && scatter)
-            k_pair_split<W, G, true, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rec1,
+            k_pair_split<W, G, true, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, k1, t1,
                                                                        tile_off, rows_out, coef_out, live, ctr);
         else if (compact)
-            k_pair_split<W, G, true, false><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rec1,
+            k_pair_split<W, G, true, false><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, k1, t1,
                                                                         tile_off, rows_out, coef_out, live, ctr);
         else
-            k_pair_split<W, G, false, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, rec1,
+            k_pair_split<W, G, false, true><<<grid, kThreads, smem, s>>>(rows, coef, M, g, L, base1, k1, t1,
                                                                         tile_off, rows_out, coef_out, live, ctr);
     }
     static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
@@ -706,26 +733,26 @@ void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int l
 }
 
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
-                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* rec1,
+                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* k1, uint64_t* t1,
                        const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
                        cudaStream_t s, const uint8_t* live) {
     if (M <= 0 || !(compact || scatter)) return;
     with_provider(d, [&](auto L, auto g) {
-        decltype(L)::split(g, compact, scatter, rows, coef, M, log2_bins, base1, rec1, tile_off, rows_out,
+        decltype(L)::split(g, compact, scatter, rows, coef, M, log2_bins, base1, k1, t1, tile_off, rows_out,
                            coef_out, live, ctr, s);
     });
     note_launch();
 }
 
-void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* rec1,
-                       uint64_t* rk, double* rc, uint32_t* start,
+void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* k1,
+                       const uint64_t* t1, uint64_t* rk, double* rc, uint32_t* start,
                        cudaStream_t s) {
     const int64_t n_tiles = (std::max<int64_t>(M, 1) + kDressTile - 1) / kDressTile;
     const unsigned parts = 1u << pair_l1(log2_bins);
     switch (Wd) {
-        case 1: k_pair_part2<1><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rec1, rk, rc, start); break;
-        case 2: k_pair_part2<2><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rec1, rk, rc, start); break;
-        default: k_pair_part2<4><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, rec1, rk, rc, start); break;
+        case 1: k_pair_part2<1><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, k1, t1, rk, rc, start); break;
+        case 2: k_pair_part2<2><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, k1, t1, rk, rc, start); break;
+        default: k_pair_part2<4><<<parts, kPart2Threads, 0, s>>>(n_tiles, log2_bins, base1, k1, t1, rk, rc, start); break;
     }
     note_launch();
 }
