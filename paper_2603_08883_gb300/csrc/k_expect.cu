@@ -21,6 +21,7 @@
 // deterministic for a given launch shape.
 #include <cuda_runtime.h>
 
+#include "bulk.cuh"
 #include "iqcc_internal.cuh"
 
 namespace iqcc {
@@ -222,6 +223,130 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
     block_reduce_store<3>(acc, partials + 3 * blockIdx.x);
 }
 
+// The counting A, B, C pass at a z-eigenstate reference, persistent and fed
+// by bulk copies: each block takes the tiles blockIdx.x, blockIdx.x +
+// gridDim.x, ... and streams their chunks of 1024 rows (keys and, under a
+// pending cut, live flags) through a ring of kAbcStages shared-memory stages
+// (cp.async.bulk, one mbarrier per stage), kAbcStages - 1 chunks ahead of the
+// chunk being counted; a partial chunk is read from global memory.  The sums
+// and counts are those of k_abc<W, true, true>.  Every wait is bounded by
+// ctr->wait_limit polls (IQCC_ERR_TIMEOUT, site 76).
+constexpr int kAbcChunk = 1024;
+constexpr int kAbcStages = 3;
+
+template <int W>
+struct AbcStage {
+    static constexpr size_t kKeys = (size_t)kAbcChunk * 16 * W;
+    static constexpr size_t kBytes = kKeys + kAbcChunk;  // keys, then live flags
+};
+
+template <int W>
+__device__ __forceinline__ void abc_issue(unsigned char* stage, uint64_t* bar, const uint64_t* rows,
+                                          const uint8_t* live, int64_t n, int64_t r0) {
+    if (r0 + kAbcChunk > n) {
+        mbar_arrive(bar);
+        return;
+    }
+    fence_proxy_async_smem();
+    mbar_expect_tx(bar, (uint32_t)(AbcStage<W>::kKeys + (live ? kAbcChunk : 0)));
+    bulk_load(stage, rows + (size_t)r0 * 2 * W, (uint32_t)AbcStage<W>::kKeys, bar);
+    if (live) bulk_load(stage + AbcStage<W>::kKeys, live + r0, (uint32_t)kAbcChunk, bar);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_abc_hist_bulk(const uint64_t* __restrict__ rows,
+                                                            const double* __restrict__ coef, int64_t M, Key<W> p,
+                                                            int yP, Key<W> occ, double* partials, PairCount pc,
+                                                            const uint8_t* __restrict__ live) {
+    extern __shared__ __align__(128) unsigned char s_stage[];
+    __shared__ __align__(8) uint64_t s_bar[kAbcStages];
+    __shared__ uint32_t s_h[1 << kPairL1Max];
+    __shared__ uint32_t s_kept;
+    __shared__ int s_fail;
+    constexpr int kChunks = kDressTile / kAbcChunk;
+    constexpr int kPer = kAbcChunk / kThreads;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int L1 = pair_l1(pc.L), F1 = 1 << L1, shift1 = 64 - L1;
+    const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
+    const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const int64_t jobs = my_tiles * kChunks;
+    const int limit = pc.ctr->wait_limit;
+    auto job_row = [&](int64_t j) {
+        return ((int64_t)blockIdx.x + (j / kChunks) * gridDim.x) * kDressTile + (j % kChunks) * kAbcChunk;
+    };
+    double acc[3] = {0.0, 0.0, 0.0};
+    unsigned n_anti = 0, kept = 0;
+    for (int d = threadIdx.x; d < F1; d += blockDim.x) s_h[d] = 0;
+    if (threadIdx.x == 0) {
+        s_kept = 0;
+        s_fail = 0;
+        for (int st = 0; st < kAbcStages; ++st) mbar_init(&s_bar[st], 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (int64_t j = 0; j < kAbcStages - 1 && j < jobs; ++j)
+            abc_issue<W>(s_stage + (size_t)j * AbcStage<W>::kBytes, &s_bar[j], rows, live, M, job_row(j));
+    int64_t j = 0;
+    for (; j < jobs; ++j) {
+        const int64_t r0 = job_row(j);
+        if (r0 >= M) break;  // the same for the whole block (only the last tile can end early)
+        const int st = (int)(j % kAbcStages);
+        if (threadIdx.x == 0 && j + kAbcStages - 1 < jobs) {
+            const int64_t jn = j + kAbcStages - 1;
+            abc_issue<W>(s_stage + (size_t)(jn % kAbcStages) * AbcStage<W>::kBytes, &s_bar[jn % kAbcStages], rows,
+                         live, M, job_row(jn));
+        }
+        const bool ok = mbar_wait_bounded(&s_bar[st], (uint32_t)((j / kAbcStages) & 1), limit);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                set_error(pc.ctr, IQCC_ERR_TIMEOUT, 76);
+                for (int64_t jj = j; jj < jobs && jj < j + kAbcStages; ++jj)
+                    mbar_wait_bounded(&s_bar[jj % kAbcStages], (uint32_t)((jj / kAbcStages) & 1), limit);
+            }
+            return;
+        }
+        const unsigned char* stage = s_stage + (size_t)st * AbcStage<W>::kBytes;
+        const uint8_t* s_live = stage + AbcStage<W>::kKeys;
+        const bool full = r0 + kAbcChunk <= M;
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int rr = wid * (kPer * 32) + r * 32 + lane;
+            const int64_t i = r0 + rr;
+            if (i >= M) continue;
+            if (live && !(full ? s_live[rr] : live[i])) continue;  // dropped by a pending term-limit cut
+            const Key<W> t = full ? smem_key<W>(stage, rr) : load_key<W>(rows, i);
+            if (abc_row<W, true>(t, coef, i, p, yP, occ, nullptr, 0, acc)) {
+                atomicAdd(&s_h[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> shift1], 1u);
+                ++n_anti;
+            } else {
+                ++kept;
+            }
+        }
+        if ((j + 1) % kChunks == 0 || job_row(j + 1) >= M) {  // the tile is complete: its counts
+            const int64_t t = r0 / kDressTile;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(0xFFFFFFFFu, kept, o);
+            if (lane == 0 && kept) atomicAdd(&s_kept, kept);
+            kept = 0;
+            __syncthreads();
+            for (int d = threadIdx.x; d < F1; d += blockDim.x) {
+                pc.counts[(int64_t)d * n_tiles + t] = s_h[d];
+                s_h[d] = 0;
+            }
+            if (threadIdx.x == 0) {
+                pc.tile_kept[t] = s_kept;
+                s_kept = 0;
+            }
+        }
+        __syncthreads();  // stage st, s_h and s_kept are reused
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
+    if (lane == 0 && n_anti) atomicAdd(&pc.ctr->n_anti, (unsigned long long)n_anti);
+    block_reduce_store<3>(acc, partials + 3 * blockIdx.x);
+}
+
 // Fixed-order compensated sum of partials[n][3] -> out3.
 __global__ void k_reduce3(const double* partials, int n, double* out3) {
     __shared__ double ss[kThreads][3];
@@ -353,8 +478,14 @@ template <int W, bool HIST>
 void abc_launch(const uint64_t* rows, const double* coef, int64_t M, const Key<W>& p, int y, const Key<W>& occ,
                 bool basis, const double* tables, int n_groups, double* partials, const PairCount& pc,
                 const uint8_t* live, cudaStream_t s) {
-    const int grid = expect_blocks();
-    if (basis) {
+    const int grid = expect_blocks();  // every one of these blocks writes its partials
+    if (basis && HIST) {
+        constexpr size_t smem = kAbcStages * AbcStage<W>::kBytes;
+        static std::atomic<unsigned long long> attr{0};
+        if (first_on_device(&attr))
+            cudaFuncSetAttribute(k_abc_hist_bulk<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_abc_hist_bulk<W><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, partials, pc, live);
+    } else if (basis) {
         k_abc<W, true, HIST><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, pc,
                                                         live);
     } else {
