@@ -286,40 +286,27 @@ iqcc_status ensure_second_rows(iqcc_ctx* ctx, int64_t rows) {
     return IQCC_OK;
 }
 
-// The counts of a dress of M rows, in ctx->pairbuf: the counting pass's
-// partition-major matrix (2^L1 level-1 partitions x n_tiles tiles, and a zero:
-// after the exclusive scan the split's offsets and the total), the per-tile
-// kept counts (n_tiles and a zero: later their offsets and the total) and the
-// bin starts written by the second partition pass (2^L + 1).
+// The dress-bin counts ([0] = 0, then one count per bin: later their starts,
+// then their ends) and the per-tile kept counts (one per tile of kDressTile
+// rows and a zero: later their offsets and the total) for a dress of M rows,
+// in ctx->pairbuf.
 struct PairCounts {
-    uint32_t* c1;
+    uint32_t* bins;
     uint32_t* tiles;
-    uint32_t* start;
     int log2_bins;
     int64_t n_tiles;
-    int64_t n_c1;  // entries of c1 including the trailing zero
     size_t bytes;
 };
 
 PairCounts pair_counts_layout(iqcc_ctx* ctx, int64_t M) {
     PairCounts pc;
     pc.log2_bins = pair_bins_log2(M);
-    pc.n_tiles = (std::max<int64_t>(M, 1) + kDressTile - 1) / kDressTile;
-    pc.n_c1 = ((int64_t)1 << pair_l1(pc.log2_bins)) * pc.n_tiles + 1;
+    pc.n_tiles = (M + kDressTile - 1) / kDressTile;
     const size_t nb = ((size_t)1 << pc.log2_bins) + 1;
-    pc.bytes = sizeof(uint32_t) * ((size_t)pc.n_c1 + (size_t)pc.n_tiles + 1 + nb);
-    pc.c1 = (uint32_t*)ctx->pairbuf.p;
-    pc.tiles = pc.c1 ? pc.c1 + pc.n_c1 : nullptr;
-    pc.start = pc.c1 ? pc.tiles + pc.n_tiles + 1 : nullptr;
+    pc.bytes = sizeof(uint32_t) * (nb + (size_t)pc.n_tiles + 1);
+    pc.bins = (uint32_t*)ctx->pairbuf.p;
+    pc.tiles = pc.bins ? pc.bins + nb : nullptr;
     return pc;
-}
-
-// The trailing zeros of the two count arrays (the counting pass writes every
-// other entry).
-iqcc_status clear_count_tails(iqcc_ctx* ctx, const PairCounts& pc) {
-    CK(cudaMemsetAsync(pc.c1 + pc.n_c1 - 1, 0, sizeof(uint32_t), ctx->stream));
-    CK(cudaMemsetAsync(pc.tiles + pc.n_tiles, 0, sizeof(uint32_t), ctx->stream));
-    return IQCC_OK;
 }
 
 // A, B, C of padded device-layout generator pkey (all zero: energy).  With
@@ -354,10 +341,9 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
         if (!ensure(ctx, ctx->pairbuf, pc.bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
         pc = pair_counts_layout(ctx, ctx->M);
         ph.log2_bins = pc.log2_bins;
-        ph.counts = pc.c1;
+        ph.counts = pc.bins + 1;
         ph.tile_kept = pc.tiles;
-        iqcc_status st = clear_count_tails(ctx, pc);
-        if (st) return st;
+        CK(cudaMemsetAsync(pc.bins, 0, pc.bytes, ctx->stream));
         CK(cudaMemsetAsync(ctx->counters.p, 0, 4 * sizeof(unsigned long long), ctx->stream));
     }
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
@@ -393,12 +379,16 @@ iqcc_status abc_impl(iqcc_ctx* ctx, const uint64_t* pkey, const double* theta, c
 
 iqcc_status apply_pending_cut(iqcc_ctx* ctx);
 
-// One dress by pair partition (k_pairjoin.cu): counts per tile (taken by the
-// A, B, C pass that preceded the dress, or here), split of H into the other
-// row buffer (commuting rows at offsets known per tile, anticommuting rows to
-// their level-1 partitions), the second partition pass by bin, join behind the
-// commuting rows; then the two row buffers swap.  On IQCC_ERR_CAPACITY / OOM H
-// is unchanged.  Returns the counts in *n_anti_out / *n_new_out.
+// One dress by pair partition (k_pairjoin.cu): bin histogram of the
+// anticommuting rows, split (commuting rows compacted in place, anticommuting
+// ones copied into their bins), join.  On IQCC_ERR_CAPACITY / OOM H is
+// unchanged.  Returns the counts in *n_anti_out / *n_new_out.
+// One dress by pair partition (k_pairjoin.cu): bin and tile counts (taken by
+// the A, B, C pass that preceded the dress, or here), split of H into the
+// other row buffer (commuting rows at offsets known per tile, anticommuting
+// rows copied into their bins), join behind the commuting rows; then the two
+// row buffers swap.  On IQCC_ERR_CAPACITY / OOM H is unchanged.  Returns the
+// counts in *n_anti_out / *n_new_out.
 iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, int64_t* n_new_out, float* ms_out) {
     const int64_t M = ctx->M;
     *n_anti_out = *n_new_out = 0;
@@ -409,6 +399,7 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
                        std::memcmp(ctx->pair_key, d.pkey, sizeof(uint64_t) * 2 * ctx->Wd) == 0;
     ctx->pair_ready = false;
     PairCounts pc = pair_counts_layout(ctx, M);
+    const uint32_t NB = 1u << pc.log2_bins;
     if (!ready) {
         if (!ensure(ctx, ctx->pairbuf, pc.bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
         pc = pair_counts_layout(ctx, M);
@@ -426,11 +417,10 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     CK(cudaEventRecord(ctx->ev0, ctx->stream));
     if (!ready) {
         CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
-        iqcc_status st = clear_count_tails(ctx, pc);
-        if (st) return st;
-        launch_pair_hist(d, ctx->rows(), M, pc.log2_bins, pc.c1, pc.tiles, c, ctx->stream, live_flags(ctx));
+        CK(cudaMemsetAsync(pc.bins, 0, pc.bytes, ctx->stream));
+        launch_pair_hist(d, ctx->rows(), M, pc.log2_bins, pc.bins + 1, pc.tiles, c, ctx->stream, live_flags(ctx));
     }
-    launch_scan_u32_long(pc.c1, pc.n_c1, scan_tmp, ctx->stream);
+    launch_scan_u32_long(pc.bins + 1, NB, scan_tmp, ctx->stream);
     launch_scan_u32_long(pc.tiles, pc.n_tiles + 1, scan_tmp, ctx->stream);
     CK_LAUNCH();
     iqcc_status st = read_counters(ctx);
@@ -438,19 +428,13 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     const int64_t n_anti = ready ? ctx->pair_n_anti : (int64_t)ctx->h_counters->n_anti;
     *n_anti_out = n_anti;
     if (n_anti == 0) return apply_pending_cut(ctx);  // P commutes with every term
-    // the anticommuting rows grouped by level-1 partition (keys, and tails of
-    // coefficient and bin), then ordered by bin (keys, coefficients)
-    const size_t kw = (size_t)n_anti * 2 * ctx->Wd;
+    // bin copies of the anticommuting rows
     Carver rv;
-    rv.take<uint64_t>((size_t)n_anti * pair_key_words(ctx->Wd));
-    rv.take<uint64_t>((size_t)n_anti * 4);
-    rv.take<uint64_t>(kw);
+    rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
     rv.take<double>(n_anti);
     if (!ensure(ctx, ctx->aux, rv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     rv = Carver{(char*)ctx->aux.p, 0};
-    uint64_t* k1 = rv.take<uint64_t>((size_t)n_anti * pair_key_words(ctx->Wd));
-    uint64_t* t1 = rv.take<uint64_t>((size_t)n_anti * 4);
-    uint64_t* rk = rv.take<uint64_t>(kw);
+    uint64_t* rk = rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
     double* rc = rv.take<double>(n_anti);
     if (rv.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
     const uint32_t bpb = pair_bins_per_block(n_anti, pc.log2_bins);
@@ -459,11 +443,10 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     bool scattered = false;
     int64_t need = live + n_anti;
     if (live + n_anti > ctx->capacity) {
-        // exact admission: partitioned copies and a counting join first, H untouched
-        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, k1, t1, pc.tiles,
-                          nullptr, nullptr, c, ctx->stream, live_flags(ctx));
-        launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, k1, t1, rk, rc, pc.start, ctx->stream);
-        launch_pair_join(d, false, rk, rc, pc.start, pc.log2_bins, bpb, nullptr, nullptr, kept, out_cursor, c,
+        // exact admission: bin copies and a counting join first, H untouched
+        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.bins + 1, rk, rc, pc.tiles,
+                          nullptr, nullptr, ctx->stream, live_flags(ctx));
+        launch_pair_join(d, false, rk, rc, pc.bins, pc.log2_bins, bpb, nullptr, nullptr, kept, out_cursor, c,
                          ctx->stream);
         CK_LAUNCH();
         st = read_counters(ctx);
@@ -482,10 +465,9 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     if (st) return st;
     uint64_t* rows_out = (uint64_t*)ctx->keys2.p;
     double* coef_out = (double*)ctx->coef2.p;
-    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.c1, k1, t1, pc.tiles,
-                      rows_out, coef_out, c, ctx->stream, live_flags(ctx));
-    if (!scattered) launch_pair_part2(ctx->Wd, M, pc.log2_bins, pc.c1, k1, t1, rk, rc, pc.start, ctx->stream);
-    launch_pair_join(d, true, rk, rc, pc.start, pc.log2_bins, bpb, rows_out, coef_out, kept, out_cursor, c,
+    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.bins + 1, rk, rc, pc.tiles,
+                      rows_out, coef_out, ctx->stream, live_flags(ctx));
+    launch_pair_join(d, true, rk, rc, pc.bins, pc.log2_bins, bpb, rows_out, coef_out, kept, out_cursor, c,
                      ctx->stream);
     CK_LAUNCH();
     CK(cudaEventRecord(ctx->ev1, ctx->stream));

@@ -377,19 +377,12 @@ void launch_mlp_score(int Wd, const uint64_t* rows, const double* coef, int64_t 
 void launch_future_energy(int Wd, const uint64_t* rows, int64_t M, const uint64_t* pkeys, const double* tau, int k,
                           const double* tab, int ts, int n, double* out, cudaStream_t s);
 
-// k_pairjoin.cu: dress by pair partition (two-level partition, shared-memory
-// join).  The counting pass (launch_pair_hist, or the A, B, C pass of
-// iqcc_iterate) works on tiles of kDressTile rows: per tile the rows the split
-// keeps and the anticommuting rows per level-1 partition (the top
-// pair_l1(L) bits of a row's bin), so that every output offset of the split is
-// known in advance; launch_pair_part2 orders each partition by the remaining
-// bits of the bin.
-constexpr int kDressTile = 16384;
-constexpr int kPairL1Max = 11;
-constexpr int kPairL2Max = 12;
-__host__ __device__ inline int pair_l1(int L) { return L < kPairL1Max ? L : kPairL1Max; }
-// 64-bit words of a key in the split's level-1 copy: whole 32-byte sectors.
-__host__ __device__ constexpr int pair_key_words(int Wd) { return 2 * Wd < 4 ? 4 : 2 * Wd; }
+// k_pairjoin.cu: dress by pair partition (histogram, split, shared-memory join).
+// The split works on tiles of kDressTile rows (256 threads, 4 rows each); the
+// counting pass before it (launch_pair_hist, or the A, B, C pass of
+// iqcc_iterate) counts per tile the rows the split keeps, so that each tile's
+// output offset is known in advance.
+constexpr int kDressTile = 1024;
 struct PairDress {
     int Wd;
     const uint64_t* pkey;    // host, device-layout key of the one generator (gens == nullptr)
@@ -399,24 +392,17 @@ struct PairDress {
 };
 int pair_bins_log2(int64_t M);
 uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins);
-// counts: [2^pair_l1(L) * n_tiles] (partition-major: counts[d * n_tiles + tile]), every entry written;
-// tile_kept[t]: the rows of tile t the split keeps (commuting, live); the anticommuting total is added to
-// ctr->n_anti.  live (may be NULL): rows with live[i] == 0 are dropped (a pending term-limit cut), here
-// and in the split.
+// counts: [2^log2_bins] zeroed; adds each anticommuting row to its bin and the total to ctr->n_anti;
+// tile_kept[t]: the rows of tile t the split keeps (commuting, live).
+// live (may be NULL): rows with live[i] == 0 are dropped (a pending term-limit cut), here and in the split.
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
                       uint32_t* tile_kept, DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
 // From rows/coef (M rows) into rows_out/coef_out: the kept rows of tile t from tile_off[t] on (compact);
-// k1 [n_anti][pair_key_words(Wd)] keys and t1 [n_anti][4] (coefficient, bin, 0, 0) of the
-// anticommuting rows, grouped by level-1 partition (scatter; base1: exclusive scan of the counting
-// pass's matrix).
+// rk [n_anti][2 Wd] keys and rc [n_anti] coefficients of the anticommuting rows, by bin (scatter;
+// cursor: bin starts in, bin ends out).
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
-                       int64_t M, int log2_bins, const uint32_t* base1, uint64_t* k1, uint64_t* t1,
-                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
-                       cudaStream_t s, const uint8_t* live = nullptr);
-// The split's output ordered by bin into rk / rc; start: [2^log2_bins + 1] bin starts (all written).
-void launch_pair_part2(int Wd, int64_t M, int log2_bins, const uint32_t* base1, const uint64_t* k1,
-                       const uint64_t* t1, uint64_t* rk, double* rc, uint32_t* start,
-                       cudaStream_t s);
+                       int64_t M, int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
+                       uint64_t* rows_out, double* coef_out, cudaStream_t s, const uint8_t* live = nullptr);
 // start: [2^log2_bins + 1] bin starts; rows without a partner counted in ctr->n_new; with `write` the
 // dressed rows and appended partners are written to rows/coef from row *kept + (*out_cursor, zeroed) on
 void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
@@ -434,8 +420,8 @@ int expect_blocks();
 // With `pair` the same pass also counts P's anticommuting rows by dress bin
 // (launch_pair_hist's output, for the dress by P that follows).
 struct PairHistOut {
-    uint32_t* counts;     // [2^pair_l1(log2_bins) * n_tiles], as launch_pair_hist
-    uint32_t* tile_kept;  // [n_tiles = ceil(M / kDressTile)]: rows per tile the split keeps (commuting, live)
+    uint32_t* counts;     // [2^log2_bins], zeroed
+    uint32_t* tile_kept;  // [ceil(M / kDressTile)]: rows per tile the split keeps (commuting, live)
     int log2_bins;
     DevCounters* ctr;     // n_anti (zeroed) receives the total
 };

@@ -21,7 +21,6 @@
 // deterministic for a given launch shape.
 #include <cuda_runtime.h>
 
-#include "bulk.cuh"
 #include "iqcc_internal.cuh"
 
 namespace iqcc {
@@ -97,7 +96,7 @@ __device__ __forceinline__ void block_reduce_store(double (&v)[N], double* out) 
 struct PairCount {
     uint32_t* counts;
     uint32_t* tile_kept;
-    int L;
+    int shift;
     int top_word;
     uint64_t top_mask;
     DevCounters* ctr;
@@ -142,10 +141,9 @@ __device__ __forceinline__ bool abc_row(const Key<W>& t, const double* __restric
 }
 
 // A, B, C for generator p (p = 0: energy in A).  HIST: the same pass also
-// does the counting for the dress by p that follows (k_pairjoin.cu): per tile
-// of kDressTile rows (the blocks then walk whole tiles) the commuting rows the
-// split keeps and the anticommuting rows per level-1 partition, counted in
-// shared memory; one read of the keys for both.
+// counts, for the dress by p that follows (k_pairjoin.cu), the anticommuting
+// rows by dress bin and the commuting rows per tile of kDressTile rows (the
+// blocks then walk whole tiles); one read of the keys for both.
 template <int W, bool BASIS, bool HIST>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
@@ -153,62 +151,32 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
                                                   int n_groups, double* partials, PairCount pc,
                                                   const uint8_t* __restrict__ live) {
     extern __shared__ double s_tab[];
-    __shared__ uint32_t s_h[HIST ? (1 << kPairL1Max) : 1];
-    __shared__ uint32_t s_kept;
     if (!BASIS) {
         for (int i = threadIdx.x; i < n_groups * 256; i += blockDim.x) s_tab[i] = tables[i];
         __syncthreads();
     }
     double acc[3] = {0.0, 0.0, 0.0};
     if (HIST) {
-        const int L1 = pair_l1(pc.L), F1 = 1 << L1, shift1 = 64 - L1;
         unsigned n_anti = 0;
         const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
-        for (int d = threadIdx.x; d < F1; d += blockDim.x) s_h[d] = 0;
-        if (threadIdx.x == 0) s_kept = 0;
-        __syncthreads();
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-            unsigned kept = 0;
-            const int64_t end = min(M, (tile + 1) * kDressTile);
-            // four rows per thread in flight: their live flags, then their keys
-            constexpr int kU = 4;
-            for (int64_t i0 = tile * kDressTile + threadIdx.x; i0 < end; i0 += (int64_t)kU * kThreads) {
-                bool v[kU];
-                Key<W> tk[kU];
+            int kept = 0;
 #pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    const int64_t i = i0 + (int64_t)u * kThreads;
-                    v[u] = i < end;
-                    if (v[u] && live) v[u] = live[i] != 0;  // rows dropped by a pending term-limit cut are skipped
-                }
-#pragma unroll
-                for (int u = 0; u < kU; ++u)
-                    if (v[u]) tk[u] = load_key<W>(rows, i0 + (int64_t)u * kThreads);
-#pragma unroll
-                for (int u = 0; u < kU; ++u) {
-                    if (!v[u]) continue;
-                    const int64_t i = i0 + (int64_t)u * kThreads;
-                    if (abc_row<W, BASIS>(tk[u], coef, i, p, yP, occ, s_tab, n_groups, acc)) {
-                        atomicAdd(&s_h[pair_hash<W>(tk[u], p, pc.top_word, pc.top_mask) >> shift1], 1u);
+            for (int r = 0; r < kDressTile / kThreads; ++r) {
+                const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
+                bool k = false;
+                if (i < M && (!live || live[i])) {  // rows dropped by a pending term-limit cut are skipped
+                    const Key<W> t = load_key<W>(rows, i);
+                    if (abc_row<W, BASIS>(t, coef, i, p, yP, occ, s_tab, n_groups, acc)) {
+                        atomicAdd(&pc.counts[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
                         ++n_anti;
                     } else {
-                        ++kept;
+                        k = true;
                     }
                 }
+                kept += __syncthreads_count(k);
             }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(0xFFFFFFFFu, kept, o);
-            if ((threadIdx.x & 31) == 0 && kept) atomicAdd(&s_kept, kept);
-            __syncthreads();
-            for (int d = threadIdx.x; d < F1; d += blockDim.x) {
-                pc.counts[(int64_t)d * n_tiles + tile] = s_h[d];
-                s_h[d] = 0;
-            }
-            if (threadIdx.x == 0) {
-                pc.tile_kept[tile] = s_kept;
-                s_kept = 0;
-            }
-            __syncthreads();
+            if (threadIdx.x == 0) pc.tile_kept[tile] = (uint32_t)kept;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
@@ -220,130 +188,6 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
             abc_row<W, BASIS>(load_key<W>(rows, i), coef, i, p, yP, occ, s_tab, n_groups, acc);
         }
     }
-    block_reduce_store<3>(acc, partials + 3 * blockIdx.x);
-}
-
-// The counting A, B, C pass at a z-eigenstate reference, persistent and fed
-// by bulk copies: each block takes the tiles blockIdx.x, blockIdx.x +
-// gridDim.x, ... and streams their chunks of 1024 rows (keys and, under a
-// pending cut, live flags) through a ring of kAbcStages shared-memory stages
-// (cp.async.bulk, one mbarrier per stage), kAbcStages - 1 chunks ahead of the
-// chunk being counted; a partial chunk is read from global memory.  The sums
-// and counts are those of k_abc<W, true, true>.  Every wait is bounded by
-// ctr->wait_limit polls (IQCC_ERR_TIMEOUT, site 76).
-constexpr int kAbcChunk = 1024;
-constexpr int kAbcStages = 3;
-
-template <int W>
-struct AbcStage {
-    static constexpr size_t kKeys = (size_t)kAbcChunk * 16 * W;
-    static constexpr size_t kBytes = kKeys + kAbcChunk;  // keys, then live flags
-};
-
-template <int W>
-__device__ __forceinline__ void abc_issue(unsigned char* stage, uint64_t* bar, const uint64_t* rows,
-                                          const uint8_t* live, int64_t n, int64_t r0) {
-    if (r0 + kAbcChunk > n) {
-        mbar_arrive(bar);
-        return;
-    }
-    fence_proxy_async_smem();
-    mbar_expect_tx(bar, (uint32_t)(AbcStage<W>::kKeys + (live ? kAbcChunk : 0)));
-    bulk_load(stage, rows + (size_t)r0 * 2 * W, (uint32_t)AbcStage<W>::kKeys, bar);
-    if (live) bulk_load(stage + AbcStage<W>::kKeys, live + r0, (uint32_t)kAbcChunk, bar);
-}
-
-template <int W>
-__global__ void __launch_bounds__(kThreads) k_abc_hist_bulk(const uint64_t* __restrict__ rows,
-                                                            const double* __restrict__ coef, int64_t M, Key<W> p,
-                                                            int yP, Key<W> occ, double* partials, PairCount pc,
-                                                            const uint8_t* __restrict__ live) {
-    extern __shared__ __align__(128) unsigned char s_stage[];
-    __shared__ __align__(8) uint64_t s_bar[kAbcStages];
-    __shared__ uint32_t s_h[1 << kPairL1Max];
-    __shared__ uint32_t s_kept;
-    __shared__ int s_fail;
-    constexpr int kChunks = kDressTile / kAbcChunk;
-    constexpr int kPer = kAbcChunk / kThreads;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int L1 = pair_l1(pc.L), F1 = 1 << L1, shift1 = 64 - L1;
-    const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
-    const int64_t my_tiles = n_tiles > (int64_t)blockIdx.x ? (n_tiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-    const int64_t jobs = my_tiles * kChunks;
-    const int limit = pc.ctr->wait_limit;
-    auto job_row = [&](int64_t j) {
-        return ((int64_t)blockIdx.x + (j / kChunks) * gridDim.x) * kDressTile + (j % kChunks) * kAbcChunk;
-    };
-    double acc[3] = {0.0, 0.0, 0.0};
-    unsigned n_anti = 0, kept = 0;
-    for (int d = threadIdx.x; d < F1; d += blockDim.x) s_h[d] = 0;
-    if (threadIdx.x == 0) {
-        s_kept = 0;
-        s_fail = 0;
-        for (int st = 0; st < kAbcStages; ++st) mbar_init(&s_bar[st], 1);
-        mbar_init_fence();
-    }
-    __syncthreads();
-    if (threadIdx.x == 0)
-        for (int64_t j = 0; j < kAbcStages - 1 && j < jobs; ++j)
-            abc_issue<W>(s_stage + (size_t)j * AbcStage<W>::kBytes, &s_bar[j], rows, live, M, job_row(j));
-    int64_t j = 0;
-    for (; j < jobs; ++j) {
-        const int64_t r0 = job_row(j);
-        if (r0 >= M) break;  // the same for the whole block (only the last tile can end early)
-        const int st = (int)(j % kAbcStages);
-        if (threadIdx.x == 0 && j + kAbcStages - 1 < jobs) {
-            const int64_t jn = j + kAbcStages - 1;
-            abc_issue<W>(s_stage + (size_t)(jn % kAbcStages) * AbcStage<W>::kBytes, &s_bar[jn % kAbcStages], rows,
-                         live, M, job_row(jn));
-        }
-        const bool ok = mbar_wait_bounded(&s_bar[st], (uint32_t)((j / kAbcStages) & 1), limit);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                set_error(pc.ctr, IQCC_ERR_TIMEOUT, 76);
-                for (int64_t jj = j; jj < jobs && jj < j + kAbcStages; ++jj)
-                    mbar_wait_bounded(&s_bar[jj % kAbcStages], (uint32_t)((jj / kAbcStages) & 1), limit);
-            }
-            return;
-        }
-        const unsigned char* stage = s_stage + (size_t)st * AbcStage<W>::kBytes;
-        const uint8_t* s_live = stage + AbcStage<W>::kKeys;
-        const bool full = r0 + kAbcChunk <= M;
-#pragma unroll
-        for (int r = 0; r < kPer; ++r) {
-            const int rr = wid * (kPer * 32) + r * 32 + lane;
-            const int64_t i = r0 + rr;
-            if (i >= M) continue;
-            if (live && !(full ? s_live[rr] : live[i])) continue;  // dropped by a pending term-limit cut
-            const Key<W> t = full ? smem_key<W>(stage, rr) : load_key<W>(rows, i);
-            if (abc_row<W, true>(t, coef, i, p, yP, occ, nullptr, 0, acc)) {
-                atomicAdd(&s_h[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> shift1], 1u);
-                ++n_anti;
-            } else {
-                ++kept;
-            }
-        }
-        if ((j + 1) % kChunks == 0 || job_row(j + 1) >= M) {  // the tile is complete: its counts
-            const int64_t t = r0 / kDressTile;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) kept += __shfl_down_sync(0xFFFFFFFFu, kept, o);
-            if (lane == 0 && kept) atomicAdd(&s_kept, kept);
-            kept = 0;
-            __syncthreads();
-            for (int d = threadIdx.x; d < F1; d += blockDim.x) {
-                pc.counts[(int64_t)d * n_tiles + t] = s_h[d];
-                s_h[d] = 0;
-            }
-            if (threadIdx.x == 0) {
-                pc.tile_kept[t] = s_kept;
-                s_kept = 0;
-            }
-        }
-        __syncthreads();  // stage st, s_h and s_kept are reused
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) n_anti += __shfl_down_sync(0xFFFFFFFFu, n_anti, o);
-    if (lane == 0 && n_anti) atomicAdd(&pc.ctr->n_anti, (unsigned long long)n_anti);
     block_reduce_store<3>(acc, partials + 3 * blockIdx.x);
 }
 
@@ -478,14 +322,8 @@ template <int W, bool HIST>
 void abc_launch(const uint64_t* rows, const double* coef, int64_t M, const Key<W>& p, int y, const Key<W>& occ,
                 bool basis, const double* tables, int n_groups, double* partials, const PairCount& pc,
                 const uint8_t* live, cudaStream_t s) {
-    const int grid = expect_blocks();  // every one of these blocks writes its partials
-    if (basis && HIST) {
-        constexpr size_t smem = kAbcStages * AbcStage<W>::kBytes;
-        static std::atomic<unsigned long long> attr{0};
-        if (first_on_device(&attr))
-            cudaFuncSetAttribute(k_abc_hist_bulk<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        k_abc_hist_bulk<W><<<grid, kThreads, smem, s>>>(rows, coef, M, p, y & 3, occ, partials, pc, live);
-    } else if (basis) {
+    const int grid = expect_blocks();
+    if (basis) {
         k_abc<W, true, HIST><<<grid, kThreads, 0, s>>>(rows, coef, M, p, y & 3, occ, tables, n_groups, partials, pc,
                                                         live);
     } else {
@@ -511,7 +349,7 @@ void abc_impl(const uint64_t* rows, const double* coef, int64_t M, const uint64_
     PairCount pc{};
     if (pair) {
         const Gen<W> g = make_gen<W>(pkey, 1.0, 0.0);
-        pc = PairCount{pair->counts, pair->tile_kept, pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
+        pc = PairCount{pair->counts, pair->tile_kept, 64 - pair->log2_bins, g.top_word, g.top_mask, pair->ctr};
         abc_launch<W, true>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
     } else {
         abc_launch<W, false>(rows, coef, M, p, y, occ, basis, tables, n_groups, partials, pc, live, s);
