@@ -137,6 +137,23 @@ iqcc_status iqcc_dress_sorted(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, cons
 iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_removed);
 
 /*
+ * iqcc_prune over the union of several contexts on one device, the
+ * partitions of one Hamiltonian (App. B): |C| < eps is dropped in every part,
+ * then, when max_terms > 0 and more terms remain in all, the max_terms
+ * largest |C| of the union are kept, ties at the threshold in ascending
+ * canonical key order across the parts (the parts hold distinct keys).  The
+ * threshold is found on the device: the radix select's histograms are summed
+ * over the parts and the threshold bucket's rows of all parts are ordered
+ * together; nothing is copied to the host but the histograms and counts.
+ * parts: n_parts distinct contexts created on the same CUDA device with the
+ * same n_qubits.  *n_removed (may be NULL): rows removed in all.  Errors:
+ * IQCC_ERR_ARG (no, null, repeated or mismatched contexts, NaN eps),
+ * IQCC_ERR_OOM, IQCC_ERR_CUDA; IQCC_ERR_STATE when a context is broken.
+ */
+iqcc_status iqcc_prune_parts(iqcc_ctx* const* parts, int n_parts, double eps, int64_t max_terms,
+                             int64_t* n_removed);
+
+/*
  * QMF energy E = sum_k C_k <Omega|P_k|Omega> for the product state of Eq. 3
  * (Eq. 10), theta/phi: host [n_qubits].  <X> = sin(th) cos(ph),
  * <Y> = sin(th) sin(ph), <Z> = cos(th) per qubit.  When every theta_j is

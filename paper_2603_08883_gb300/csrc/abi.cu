@@ -46,6 +46,14 @@ iqcc_status fail_cuda(iqcc_ctx* ctx, cudaError_t e, const char* what, int line) 
 
 #define CK_LAUNCH() CK(cudaGetLastError())
 
+// As CK / CK_LAUNCH for a named context (calls over several contexts).
+#define CK_CTX(c, call)                                                     \
+    do {                                                                    \
+        cudaError_t e_ = (call);                                            \
+        if (e_ != cudaSuccess) return fail_cuda((c), e_, #call, __LINE__);  \
+    } while (0)
+#define CK_LAUNCH_CTX(c) CK_CTX((c), cudaGetLastError())
+
 #define GUARD(ctx)                                                                 \
     do {                                                                           \
         if (!(ctx)) return fail(nullptr, IQCC_ERR_ARG, "null context");            \
@@ -1074,6 +1082,7 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
     ctx->capacity = opts->capacity ? opts->capacity : (int64_t)1 << 30;
     ctx->max_probe = opts->max_probe > 0 ? opts->max_probe : 64;
     ctx->stream = (cudaStream_t)opts->stream;
+    ctx->device = current_device();
     ctx->alloc = opts->alloc;
     ctx->dfree = opts->free;
     ctx->alloc_user = opts->alloc_user;
@@ -1430,6 +1439,196 @@ iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_
     CK(cudaMemsetAsync(ctx->counters.p, 0, kCountersClear, ctx->stream));
     int64_t removed = 0;
     iqcc_status st = compress(ctx, eps, max_terms, &removed);
+    if (st) return st;
+    if (n_removed) *n_removed = removed;
+    return IQCC_OK;
+}
+
+// The term limit over several contexts on one device (partitions of one
+// Hamiltonian): the radix select of compress() with every pass's 12-bit
+// histogram summed over the parts (each part's kernel adds into one
+// histogram), the threshold bucket's rows of all parts ordered together by
+// (|C| desc, canonical key asc), and each part compacted with its own flags.
+iqcc_status prune_parts_impl(iqcc_ctx* const* parts, int np, double eps, int64_t max_terms, int64_t* removed) {
+    iqcc_ctx* c0 = parts[0];
+    cudaStream_t s0 = c0->stream;
+    struct PartArea {
+        uint8_t* flags;
+        char* cscratch;
+        uint32_t* ties;
+        int64_t M, kept, n_cand;
+    };
+    std::vector<PartArea> pa(np);
+    int64_t total = 0;
+    for (int p = 0; p < np; ++p) {
+        iqcc_ctx* ctx = parts[p];
+        ctx->pair_ready = false;
+        iqcc_status st = apply_pending_cut(ctx);
+        if (st) return st;
+        const int64_t M = ctx->M;
+        Carver cv;
+        cv.take<uint8_t>(std::max<int64_t>(M, 1));
+        cv.take<char>(compact_inplace_scratch_bytes(std::max<int64_t>(M, 1)));
+        cv.take<uint32_t>(std::max<int64_t>(M, 1));
+        if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        cv = Carver{(char*)ctx->scratch.p, 0};
+        pa[p].flags = cv.take<uint8_t>(std::max<int64_t>(M, 1));
+        pa[p].cscratch = cv.take<char>(compact_inplace_scratch_bytes(std::max<int64_t>(M, 1)));
+        pa[p].ties = cv.take<uint32_t>(std::max<int64_t>(M, 1));
+        pa[p].M = M;
+        DevCounters* c = dctr(ctx);
+        CK_CTX(ctx, cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
+        if (M > 0) {
+            launch_prune_flags(ctx->c(), M, eps > 0 ? eps : 0.0, pa[p].flags, &c->aux, ctx->stream);
+            CK_LAUNCH_CTX(ctx);
+        }
+        st = read_counters(ctx);
+        if (st) return st;
+        pa[p].kept = (int64_t)ctx->h_counters->aux;
+        total += pa[p].kept;
+    }
+    if (max_terms > 0 && total > max_terms) {
+        // radix select over all parts: one histogram per 12-bit pass
+        constexpr int64_t kBucketLimit = 1 << 16;
+        int64_t need = max_terms, bucket = total;
+        uint64_t prefix = 0, pmask = 0;
+        int hi = 63;
+        if (!ensure(c0, c0->aux, 4096 * sizeof(unsigned long long)))
+            return fail(c0, IQCC_ERR_OOM, "scratch allocation failed");
+        unsigned long long* hist12 = (unsigned long long*)c0->aux.p;
+        std::vector<unsigned long long> h(4096);
+        while (bucket > kBucketLimit && hi > 0) {
+            const int shift = std::max(0, hi - 12);
+            CK_CTX(c0, cudaMemsetAsync(hist12, 0, 4096 * sizeof(unsigned long long), s0));
+            CK_CTX(c0, cudaStreamSynchronize(s0));
+            for (int p = 0; p < np; ++p) {
+                if (pa[p].M == 0) continue;
+                launch_abs_digit_hist12(parts[p]->c(), pa[p].flags, pa[p].M, shift, prefix, pmask, hist12,
+                                        parts[p]->stream);
+                CK_LAUNCH_CTX(parts[p]);
+            }
+            for (int p = 0; p < np; ++p) CK_CTX(parts[p], cudaStreamSynchronize(parts[p]->stream));
+            CK_CTX(c0, cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                       s0));
+            CK_CTX(c0, cudaStreamSynchronize(s0));
+            int64_t cum = 0;
+            int sel = 0;
+            for (int d = 4095; d >= 0; --d) {
+                if (cum + (int64_t)h[d] >= need) {
+                    sel = d;
+                    break;
+                }
+                cum += (int64_t)h[d];
+            }
+            need -= cum;
+            bucket = (int64_t)h[sel];
+            prefix |= (uint64_t)sel << shift;
+            pmask |= (uint64_t)4095 << shift;
+            hi = shift;
+        }
+        pmask &= 0x7FFFFFFFFFFFFFFFull;
+        // the threshold bucket's rows of every part
+        int64_t n_cand = 0;
+        std::vector<int64_t> offs(np + 1, 0);
+        for (int p = 0; p < np; ++p) {
+            iqcc_ctx* ctx = parts[p];
+            DevCounters* c = dctr(ctx);
+            CK_CTX(ctx, cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+            if (pa[p].M > 0) {
+                launch_bucket_flags(ctx->c(), pa[p].flags, pa[p].M, prefix, pmask, pa[p].ties, &c->aux, ctx->stream);
+                CK_LAUNCH_CTX(ctx);
+            }
+            iqcc_status st = read_counters(ctx);
+            if (st) return st;
+            pa[p].n_cand = (int64_t)ctx->h_counters->aux;
+            offs[p] = n_cand;
+            n_cand += pa[p].n_cand;
+        }
+        offs[np] = n_cand;
+        if (need >= n_cand) {
+            for (int p = 0; p < np; ++p) {
+                launch_set_flags(pa[p].ties, pa[p].n_cand, pa[p].flags, parts[p]->stream);
+                CK_LAUNCH_CTX(parts[p]);
+            }
+        } else {
+            // order the candidates of all parts together, keep the first `need`
+            const int stride = 2 * c0->Wd + 1;
+            Carver dry;
+            dry.take<uint64_t>((size_t)n_cand * stride);
+            dry.take<uint32_t>(n_cand);
+            dry.take<int64_t>(np + 1);
+            dry.take<uint8_t*>(np);
+            carve_sort(dry, n_cand);
+            if (!ensure(c0, c0->aux, dry.off)) return fail(c0, IQCC_ERR_OOM, "scratch allocation failed");
+            Carver cv{(char*)c0->aux.p, 0};
+            uint64_t* skeys = cv.take<uint64_t>((size_t)n_cand * stride);
+            uint32_t* cand = cv.take<uint32_t>(n_cand);
+            int64_t* d_offs = cv.take<int64_t>(np + 1);
+            uint8_t** d_flags = cv.take<uint8_t*>(np);
+            SortArea ca = carve_sort(cv, n_cand);
+            if (cv.off > c0->aux.bytes) return fail(c0, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
+            for (int p = 0; p < np; ++p) {
+                if (pa[p].n_cand == 0) continue;
+                launch_candidate_keys(c0->Wd, parts[p]->rows(), parts[p]->c(), pa[p].ties, pa[p].n_cand,
+                                      skeys + (size_t)offs[p] * stride, parts[p]->stream);
+                CK_LAUNCH_CTX(parts[p]);
+                CK_CTX(parts[p], cudaMemcpyAsync(cand + offs[p], pa[p].ties, sizeof(uint32_t) * pa[p].n_cand,
+                                                 cudaMemcpyDeviceToDevice, parts[p]->stream));
+            }
+            for (int p = 0; p < np; ++p) CK_CTX(parts[p], cudaStreamSynchronize(parts[p]->stream));
+            std::vector<uint8_t*> hflags(np);
+            for (int p = 0; p < np; ++p) hflags[p] = pa[p].flags;
+            CK_CTX(c0, cudaMemcpyAsync(d_offs, offs.data(), sizeof(int64_t) * (np + 1), cudaMemcpyHostToDevice, s0));
+            CK_CTX(c0, cudaMemcpyAsync(d_flags, hflags.data(), sizeof(uint8_t*) * np, cudaMemcpyHostToDevice, s0));
+            launch_iota(ca.a, n_cand, s0);
+            SortPlan plan{};
+            plan.n_words = stride;
+            plan.n_order = stride;
+            for (int w = 0; w < stride; ++w) plan.order[w] = w;
+            uint32_t* sorted = nullptr;
+            radix_sort_indirect(skeys, stride, plan, ca.a, ca.b, n_cand, &sorted, ca.tmp, ca.tmp_bytes, s0);
+            launch_set_flags_sorted_parts(cand, sorted, need, d_offs, d_flags, np, s0);
+            CK_LAUNCH_CTX(c0);
+            CK_CTX(c0, cudaStreamSynchronize(s0));  // the host arrays copied above live until here
+        }
+    }
+    // each part keeps its flagged rows
+    *removed = 0;
+    for (int p = 0; p < np; ++p) {
+        iqcc_ctx* ctx = parts[p];
+        if (pa[p].M == 0) continue;
+        DevCounters* c = dctr(ctx);
+        CK_CTX(ctx, cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
+        launch_compact_inplace(ctx->Wd, pa[p].flags, ctx->rows(), ctx->c(), pa[p].M, pa[p].cscratch, &c->aux, c,
+                               ctx->stream);
+        CK_LAUNCH_CTX(ctx);
+        iqcc_status st = read_counters(ctx);
+        if (st) return st;
+        const int64_t newM = (int64_t)ctx->h_counters->aux;
+        *removed += pa[p].M - newM;
+        if (newM != ctx->M) ctx->index_valid = false;
+        ctx->M = newM;
+    }
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_prune_parts(iqcc_ctx* const* parts, int n_parts, double eps, int64_t max_terms,
+                             int64_t* n_removed) {
+    if (n_removed) *n_removed = 0;
+    if (!parts || n_parts <= 0) return fail(nullptr, IQCC_ERR_ARG, "no contexts");
+    for (int p = 0; p < n_parts; ++p) {
+        if (!parts[p]) return fail(nullptr, IQCC_ERR_ARG, "null context");
+        if (parts[p]->broken) return IQCC_ERR_STATE;
+        for (int q = 0; q < p; ++q)
+            if (parts[q] == parts[p]) return fail(parts[p], IQCC_ERR_ARG, "a context is listed twice");
+        if (parts[p]->device != parts[0]->device || parts[p]->n != parts[0]->n)
+            return fail(parts[p], IQCC_ERR_ARG, "contexts on different devices or of different qubit counts");
+    }
+    if (std::isnan(eps)) return fail(parts[0], IQCC_ERR_ARG, "eps is NaN");
+    for (int p = 0; p < n_parts; ++p)
+        CK_CTX(parts[p], cudaMemsetAsync(parts[p]->counters.p, 0, kCountersClear, parts[p]->stream));
+    int64_t removed = 0;
+    iqcc_status st = prune_parts_impl(parts, n_parts, eps, max_terms, &removed);
     if (st) return st;
     if (n_removed) *n_removed = removed;
     return IQCC_OK;

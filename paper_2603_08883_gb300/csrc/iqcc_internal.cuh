@@ -252,6 +252,7 @@ struct iqcc_ctx {
     int Wd = 0;           // device words (1, 2, 4)
     int64_t capacity = 0; // admission limit (rows)
     int max_probe = 64;
+    int device = 0;       // the CUDA device the context lives on
     cudaStream_t stream = nullptr;
     void* (*alloc)(size_t, void*) = nullptr;
     void (*dfree)(void*, void*) = nullptr;
@@ -540,6 +541,10 @@ void launch_cut_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t pr
 void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, const uint32_t* cand, int64_t k,
                            uint64_t* skeys, cudaStream_t s);
 void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s);
+// cand: candidates of all parts concatenated (part p's at [offs[p], offs[p + 1])); flags: device array of
+// the parts' flag arrays; the first k in `order` set in their owner's flags.
+void launch_set_flags_sorted_parts(const uint32_t* cand, const uint32_t* order, int64_t k, const int64_t* offs,
+                                   uint8_t* const* flags, int n_parts, cudaStream_t s);
 
 // DIS candidate keys for the sort: [coarse |g| complement, x words...]
 void launch_dis_sort_keys(int Wd, const uint64_t* gkeys, const double* gsum, int64_t G, uint64_t* skeys,

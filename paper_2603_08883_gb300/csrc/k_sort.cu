@@ -589,6 +589,21 @@ __global__ void k_set_flags_sorted(const uint32_t* __restrict__ cand, const uint
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) flags[cand[order[i]]] = 1;
 }
 
+// Multi-part term limit: the first k candidates in sorted order, each owned
+// by the part whose range [offs[p], offs[p + 1]) holds its index, flagged in
+// that part's flags.
+__global__ void k_set_flags_sorted_parts(const uint32_t* __restrict__ cand, const uint32_t* __restrict__ order,
+                                         int64_t k, const int64_t* __restrict__ offs, uint8_t* const* flags,
+                                         int n_parts) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) {
+        const int64_t g = order[i];
+        int p = 0;
+        while (p + 1 < n_parts && offs[p + 1] <= g) ++p;
+        flags[p][cand[g]] = 1;
+    }
+}
+
 // ---------------------------------------------------------------- DIS ordering
 
 // skeys[g] = [~coarse(|g|), x[Wd-1], ..., x[0]]: ascending order of these words
@@ -892,6 +907,14 @@ void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, con
 void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s) {
     if (k > 0) {
         k_set_flags_sorted<<<grid_stride_blocks(k), kThreads, 0, s>>>(cand, order, k, flags);
+        note_launch();
+    }
+}
+
+void launch_set_flags_sorted_parts(const uint32_t* cand, const uint32_t* order, int64_t k, const int64_t* offs,
+                                   uint8_t* const* flags, int n_parts, cudaStream_t s) {
+    if (k > 0) {
+        k_set_flags_sorted_parts<<<grid_stride_blocks(k), kThreads, 0, s>>>(cand, order, k, offs, flags, n_parts);
         note_launch();
     }
 }

@@ -96,6 +96,8 @@ _prune_learned = _sig("iqcc_prune_learned", _c, [_vp, ctypes.c_double, ctypes.c_
 _dress_sorted = _sig("iqcc_dress_sorted", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)])
 _prune = _sig("iqcc_prune", _c, [_vp, ctypes.c_double, ctypes.c_int64, _i64p])
+_prune_parts = _sig("iqcc_prune_parts", _c, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double, ctypes.c_int64,
+                                               _i64p])
 _energy = _sig("iqcc_qmf_energy", _c, [_vp, _f64p, _f64p, _f64p])
 _abc = _sig("iqcc_generator_abc", _c, [_vp, _u64p, _u64p, _f64p, _f64p, _f64p])
 _egrad = _sig("iqcc_energy_gradients", _c, [_vp, _u64p, _u64p, ctypes.c_double, _f64p, _f64p, _f64p, _f64p, _f64p,
@@ -316,6 +318,20 @@ def iqcc_prune_learned(H: Hamiltonian, eps: float, max_terms: int, theta, phi, g
 def iqcc_prune(H: Hamiltonian, eps: float, max_terms: int = 0) -> int:
     removed = ctypes.c_int64(0)
     H._check(_prune(H._h, float(eps), int(max_terms), ctypes.byref(removed)))
+    return removed.value
+
+
+def iqcc_prune_parts(parts, eps: float, max_terms: int = 0) -> int:
+    """iqcc_prune_parts: the term limit over the union of several Hamiltonians
+    (the partitions of one) on one device; returns the rows removed in all."""
+    parts = list(parts)
+    arr = (_vp * max(len(parts), 1))(*[H._h for H in parts])
+    removed = ctypes.c_int64(0)
+    st = _prune_parts(arr, len(parts), float(eps), int(max_terms), ctypes.byref(removed))
+    if st != 0:
+        msgs = [_err(H._h).decode() for H in parts if H._h]
+        msg = next((m for m in msgs if m != "no error"), _err(None).decode())
+        raise IqccError(st, msg)
     return removed.value
 
 

@@ -130,22 +130,11 @@ class PartitionedHamiltonian:
         return tau
 
     def prune(self, eps: float, max_terms: int = 0) -> int:
-        """|C| < eps dropped in every part (no exchange needed); with a term
-        limit, the max_terms largest |C| of the whole Hamiltonian are kept,
-        ties at the threshold in canonical key order across the parts (the
-        threshold is found on the host from every part's coefficients)."""
-        if max_terms <= 0:
-            return sum(_lib().iqcc_prune(H, eps, 0) for H in self.parts)
-        exports = [_lib().iqcc_export(H) for H in self.parts]
-        removed = 0
-        for H, k in zip(self.parts, term_limit_quotas(exports, eps, max_terms, self.W)):
-            if k is None:
-                removed += _lib().iqcc_prune(H, eps, 0)
-            elif k == 0:  # a limit of 0 means none to the library: drop every term by magnitude
-                removed += _lib().iqcc_prune(H, float(np.finfo(np.float64).max), 0)
-            else:
-                removed += _lib().iqcc_prune(H, eps, int(k))
-        return removed
+        """|C| < eps dropped in every part; with a term limit, the max_terms
+        largest |C| of the whole Hamiltonian kept, ties at the threshold in
+        canonical key order across the parts (iqcc_prune_parts: the threshold
+        is found on the device over all parts)."""
+        return _lib().iqcc_prune_parts(self.parts, eps, max_terms)
 
     def export(self):
         """All parts in canonical order (x as an integer, last word most significant, then z)."""
@@ -158,40 +147,6 @@ class PartitionedHamiltonian:
         for H in self.parts:
             H.close()
         self.parts = []
-
-
-def _canonical_rank(x, z, W: int) -> np.ndarray:
-    """Position of every key in canonical order (x as an integer, last word most significant, then z)."""
-    order = np.lexsort([z[:, w] for w in range(W)] + [x[:, w] for w in range(W)])
-    rank = np.empty(len(order), np.int64)
-    rank[order] = np.arange(len(order))
-    return rank
-
-
-def term_limit_quotas(exports, eps: float, max_terms: int, W: int):
-    """Rows each part keeps so that together they hold the max_terms largest
-    |C| with |C| >= eps, ties at the threshold in canonical key order across
-    the parts; None for a part that needs no limit.  exports: (x, z, c) of
-    every part."""
-    cs = [np.abs(np.asarray(c, np.float64)) for _, _, c in exports]
-    kept = [a >= eps if eps > 0 else np.ones(len(a), bool) for a in cs]
-    total = sum(int(k.sum()) for k in kept)
-    if total <= max_terms:
-        return [None] * len(exports)
-    vals = np.concatenate([a[k] for a, k in zip(cs, kept)])
-    t = np.partition(vals, len(vals) - max_terms)[len(vals) - max_terms]  # the max_terms-th largest
-    above = [int(((a > t) & k).sum()) for a, k in zip(cs, kept)]
-    need = max_terms - sum(above)
-    tx, tz, part = [], [], []
-    for i, ((x, z, _), a, k) in enumerate(zip(exports, cs, kept)):
-        tie = (a == t) & k
-        tx.append(np.asarray(x, np.uint64).reshape(-1, W)[tie])
-        tz.append(np.asarray(z, np.uint64).reshape(-1, W)[tie])
-        part.append(np.full(int(tie.sum()), i))
-    tx, tz, part = np.concatenate(tx), np.concatenate(tz), np.concatenate(part)
-    first = np.argsort(_canonical_rank(tx, tz, W))[:need]  # the canonical-first ties
-    quota = np.bincount(part[first], minlength=len(exports))
-    return [above[i] + int(quota[i]) for i in range(len(exports))]
 
 
 def _send_recv(dist, peer: int, arrays):

@@ -121,20 +121,22 @@ def test_partitioned_dress_with_an_empty_side():
     P.close()
 
 
-@pytest.mark.parametrize("eps,limit", [(0.0, 9000), (1e-3, 5000), (0.0, 3)])
-def test_partitioned_term_limit_matches_the_oracle(eps, limit):
-    """The term limit over the whole split Hamiltonian (threshold from every
-    part's coefficients, ties in canonical order across parts) against the
-    oracle's compression of the unsplit one; coefficients rounded to create
-    ties at the threshold."""
-    n = 64
-    rng = np.random.Generator(np.random.PCG64(31))
-    _, x, z, c = synth.random_hamiltonian(n, 20_000, 91, density=0.2)
+@pytest.mark.parametrize("n,rows,eps,limit", [(64, 20_000, 0.0, 9000), (64, 20_000, 1e-3, 5000), (64, 20_000, 0.0, 3),
+                                              (100, 200_000, 0.0, 120_000), (200, 200_000, 1e-3, 70_001)])
+def test_partitioned_term_limit_matches_the_oracle(n, rows, eps, limit):
+    """The term limit over the whole split Hamiltonian (iqcc_prune_parts:
+    threshold from every part's coefficients, ties in canonical order across
+    parts) against the oracle's compression of the unsplit one; coefficients
+    rounded to create ties at the threshold.  The 200,000-row cases need
+    several 12-bit select passes before the threshold bucket is small."""
+    rng = np.random.Generator(np.random.PCG64(31 + n))
+    _, x, z, c = synth.random_hamiltonian(n, rows, 91 + n, density=0.2)
     c = np.round(c, 2)
     keep = c != 0
     x, z, c = x[keep], z[keep], c[keep]
     mx, mz = _masks(n, 4)
     P = pt.PartitionedHamiltonian(n, x, z, c, mx, mz)
+    assert min(len(H) for H in P.parts) > 0
     o = oracle.Oracle(n, x, z, c)
     removed = P.prune(eps, limit)
     assert removed == o.prune(eps, limit)

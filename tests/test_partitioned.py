@@ -203,25 +203,3 @@ def test_exchange_with_an_empty_partition():
     assert len(res[1][1][2]) > 0                        # the empty side received and appended partners
     bad = compare(union, o.export())
     assert not bad, bad[:5]
-
-
-@pytest.mark.parametrize("eps", [0.0, 0.3])
-def test_term_limit_quotas_match_a_global_selection(eps):
-    """Per-part row counts of a global term limit (ties at the threshold in
-    canonical key order across the parts) against sorting the whole set."""
-    rng = np.random.Generator(np.random.PCG64(int(eps * 10) + 3))
-    W, parts, m = 2, 4, 3000
-    keys = np.unique(rng.integers(0, 2**62, (m, 2 * W), dtype=np.uint64), axis=0)
-    c = rng.choice([0.1, 0.25, 0.5, -0.5, 1.0, -1.0, 2.0], len(keys))   # many exact ties
-    owner = rng.integers(0, parts, len(keys))
-    exports = [(keys[owner == a, :W], keys[owner == a, W:], c[owner == a]) for a in range(parts)]
-    for limit in (1, 500, 1200, len(keys) - 1):
-        quotas = pt.term_limit_quotas(exports, eps, limit, W)
-        alive = np.abs(c) >= eps if eps > 0 else np.ones(len(c), bool)
-        if alive.sum() <= limit:
-            assert quotas == [None] * parts
-            continue
-        canon = pt._canonical_rank(keys[:, :W], keys[:, W:], W)
-        idx = np.flatnonzero(alive)
-        chosen = idx[np.lexsort([canon[idx], -np.abs(c[idx])])][:limit]
-        assert quotas == [int(np.sum(owner[chosen] == a)) for a in range(parts)]
