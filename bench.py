@@ -564,13 +564,22 @@ def run_gpu(args):
         H.close()
         h2d = d2h = 0
         e_dressed = 0
+        phases = {"load_s": 0.0, "iterate_s": 0.0, "export_s": 0.0}
         barrier()
         t0 = time.perf_counter()
         for k in range(args.e2e_steps):
             src, dst = bufs[k % 2], bufs[(k + 1) % 2]
+            ta = time.perf_counter()
             Hk = iqcc.iqcc_load_hamiltonian(n, src[0][:m], src[1][:m], src[2][:m], capacity=capacity)
+            torch.cuda.synchronize()
+            tb = time.perf_counter()
             r = iqcc.iqcc_iterate(Hk, th, ph, w.n_gen, w.eps, w.max_terms)
+            torch.cuda.synchronize()
+            tc = time.perf_counter()
             ox, oz, oc = iqcc.iqcc_export(Hk, out=dst)
+            phases["load_s"] += tb - ta
+            phases["iterate_s"] += tc - tb
+            phases["export_s"] += time.perf_counter() - tc
             h2d += m * (2 * W * 8 + 8) + 2 * n * 8
             d2h += len(oc) * (2 * W * 8 + 8) + 8
             m = len(oc)
@@ -581,6 +590,7 @@ def run_gpu(args):
         e_wall = time.perf_counter() - t0
         e2e = {"value": e_dressed / e_wall, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
                "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps,
+               "phases_s_per_step": {k: round(v / args.e2e_steps, 4) for k, v in phases.items()},
                "path": "per step: iqcc_load_hamiltonian from pinned host arrays, iqcc_iterate, iqcc_export to "
                        "pinned host arrays (the next step's input); wall clock"}
     else:

@@ -173,6 +173,16 @@ iqcc_status iqcc_generator_abc(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t
                                const double* theta, const double* phi, double abc[3]);
 
 /*
+ * iqcc_generator_abc summed over several contexts (the partitions of one
+ * Hamiltonian, App. B: A, B and C are sums over the parts), in part order;
+ * with all-zero gx, gz, A is the energy.  tau (may be NULL): the minimiser
+ * atan2(-C, -B) of the summed E(tau), 0 when B = C = 0.  Errors as
+ * iqcc_generator_abc; IQCC_ERR_ARG also for no or mismatched contexts.
+ */
+iqcc_status iqcc_generator_abc_parts(iqcc_ctx* const* parts, int n_parts, const uint64_t* gx, const uint64_t* gz,
+                                     const double* theta, const double* phi, double abc[3], double* tau);
+
+/*
  * Derivatives of the dressed QMF energy (the adjoint of Eq. 3 / Eq. 12 after
  * Eq. 5), for joint optimisation of the product-state angles and one
  * generator's amplitude.  With a generator (gx, gz: host [W] words each, both
@@ -371,6 +381,25 @@ void iqcc_free(iqcc_ctx* ctx);
  * dress to its own rows with the other's (iqcc_dress_cross).  Energies,
  * A, B, C and DIS gradients are sums over the contexts.
  * ------------------------------------------------------------------------ */
+
+/* Dress two partitions a and b of one Hamiltonian, held by two contexts on
+ * the same device, by P at amplitude tau (Eq. 5, library sign) as if they
+ * were one context: the anticommuting rows of both go into one set of pair
+ * bins (the merge of App. D Eq. 18 as in iqcc_dress), and every output row
+ * goes to the partition that owns its key, so a generator that flips the
+ * partition bits moves the new partners T xor P to the other context without
+ * a copy through the host (App. B's pairwise exchange, on one device).
+ * mx, mz: host [W] partition masks; ax, az: host [W], a's bits under them (a
+ * key k belongs to a iff k & mask == (ax, az), to b otherwise; every row of
+ * a and b must satisfy its side's rule).  All work runs on a's stream; b's
+ * stream is synchronised first.  Errors (both unchanged): IQCC_ERR_ARG (same
+ * context twice, different devices or qubit counts, bits above n_qubits or
+ * outside the masks, non-finite tau), IQCC_ERR_CAPACITY (a context could
+ * receive more rows than its capacity: M_a + anticommuting rows of b, and
+ * likewise for b), IQCC_ERR_OOM, IQCC_ERR_CUDA; IQCC_ERR_HASH_FULL as
+ * iqcc_dress. */
+iqcc_status iqcc_dress_pair(iqcc_ctx* a, iqcc_ctx* b, const uint64_t* gx, const uint64_t* gz, double tau,
+                            const uint64_t* mx, const uint64_t* mz, const uint64_t* ax, const uint64_t* az);
 
 /* The rows of H that anticommute with P (gx, gz: host [W]): *n = their count;
  * min(cap, *n) of them written to x, z [cap][W] and coef [cap] (host), in no

@@ -1315,6 +1315,163 @@ iqcc_status iqcc_dress_cross(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* 
     return IQCC_OK;
 }
 
+// One generator over two partitions a, b of one Hamiltonian on one device
+// (k_pairjoin.cu, both partitions' anticommuting rows in one set of bins):
+// counts of both into one bin histogram, each partition split into its own
+// other row buffer and into the shared bins, one join whose outputs go to the
+// partition that owns each key; then both swap their row buffers.  All work
+// runs on a's stream.  On IQCC_ERR_CAPACITY / OOM both are unchanged.
+static iqcc_status dress_pair_impl(iqcc_ctx* a, iqcc_ctx* b, const uint64_t* pk, double tau, const uint64_t* dmask,
+                            const uint64_t* daval) {
+    iqcc_ctx* ctx = a;  // CK reports on a
+    cudaStream_t s = a->stream;
+    iqcc_status st = apply_pending_cut(a);
+    if (st) return st;
+    st = apply_pending_cut(b);
+    if (st) return st;
+    CK(cudaStreamSynchronize(b->stream));
+    a->pair_ready = b->pair_ready = false;
+    const int64_t Ma = a->M, Mb = b->M;
+    if (Ma + Mb == 0) return IQCC_OK;
+    PairDress d{a->Wd, pk, nullptr, 0, std::cos(tau), std::sin(tau)};
+    const int L = pair_bins_log2(Ma + Mb);
+    const uint32_t NB = 1u << L;
+    const int64_t nta = (Ma + kDressTile - 1) / kDressTile, ntb = (Mb + kDressTile - 1) / kDressTile;
+    if (!ensure(a, a->pairbuf, sizeof(uint32_t) * ((size_t)NB + 1 + (size_t)nta + 1)) ||
+        !ensure(b, b->pairbuf, sizeof(uint32_t) * ((size_t)ntb + 1)))
+        return fail(a, IQCC_ERR_OOM, "scratch allocation failed");
+    uint32_t* bins = (uint32_t*)a->pairbuf.p;
+    uint32_t* ta = bins + NB + 1;
+    uint32_t* tb = (uint32_t*)b->pairbuf.p;
+    Carver cv;
+    cv.take<uint32_t>(1024);
+    cv.take<unsigned long long>(2);
+    if (!ensure(a, a->scratch, cv.off)) return fail(a, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)a->scratch.p, 0};
+    uint32_t* scan_tmp = cv.take<uint32_t>(1024);
+    unsigned long long* cursors = cv.take<unsigned long long>(2);
+    DevCounters* ca = dctr(a);
+    DevCounters* cb = dctr(b);
+    CK(cudaEventRecord(a->ev0, s));
+    CK(cudaMemsetAsync(cursors, 0, 2 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ca, 0, 4 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(cb, 0, 4 * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(bins, 0, sizeof(uint32_t) * ((size_t)NB + 1 + (size_t)nta + 1), s));
+    CK(cudaMemsetAsync(tb, 0, sizeof(uint32_t) * ((size_t)ntb + 1), s));
+    if (Ma) launch_pair_hist(d, a->rows(), Ma, L, bins + 1, ta, ca, s);
+    if (Mb) launch_pair_hist(d, b->rows(), Mb, L, bins + 1, tb, cb, s);
+    launch_scan_u32_long(bins + 1, NB, scan_tmp, s);
+    launch_scan_u32_long(ta, nta + 1, scan_tmp, s);
+    launch_scan_u32_long(tb, ntb + 1, scan_tmp, s);
+    CK_LAUNCH();
+    CK(cudaStreamSynchronize(s));
+    st = read_counters(a);
+    if (st) return st;
+    const int64_t na = (int64_t)a->h_counters->n_anti;
+    st = read_counters(b);
+    if (st) return st;
+    const int64_t nb = (int64_t)b->h_counters->n_anti;
+    const int64_t n_anti = na + nb;
+    if (n_anti == 0) return IQCC_OK;
+    // a partition receives at most its own anticommuting rows and one partner per row of the other
+    const int64_t need_a = Ma + nb, need_b = Mb + na;
+    if (need_a > a->capacity || need_b > b->capacity) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "dress may need %lld and %lld rows, capacities are %lld and %lld",
+                 (long long)need_a, (long long)need_b, (long long)a->capacity, (long long)b->capacity);
+        return fail(a, IQCC_ERR_CAPACITY, buf);
+    }
+    Carver rv;
+    rv.take<uint64_t>((size_t)n_anti * 2 * a->Wd);
+    rv.take<double>(n_anti);
+    if (!ensure(a, a->aux, rv.off)) return fail(a, IQCC_ERR_OOM, "scratch allocation failed");
+    rv = Carver{(char*)a->aux.p, 0};
+    uint64_t* rk = rv.take<uint64_t>((size_t)n_anti * 2 * a->Wd);
+    double* rc = rv.take<double>(n_anti);
+    st = ensure_second_rows(a, std::max<int64_t>(need_a, 1));
+    if (st) return st;
+    st = ensure_second_rows(b, std::max<int64_t>(need_b, 1));
+    if (st) return st;
+    if (Ma)
+        launch_pair_split(d, true, true, a->rows(), a->c(), Ma, L, bins + 1, rk, rc, ta, (uint64_t*)a->keys2.p,
+                          (double*)a->coef2.p, s);
+    if (Mb)
+        launch_pair_split(d, true, true, b->rows(), b->c(), Mb, L, bins + 1, rk, rc, tb, (uint64_t*)b->keys2.p,
+                          (double*)b->coef2.p, s);
+    PairTwo two{};
+    for (int w = 0; w < 2 * a->Wd; ++w) {
+        two.mask[w] = dmask[w];
+        two.aval[w] = daval[w];
+    }
+    two.rows[0] = (uint64_t*)a->keys2.p;
+    two.rows[1] = (uint64_t*)b->keys2.p;
+    two.coef[0] = (double*)a->coef2.p;
+    two.coef[1] = (double*)b->coef2.p;
+    two.kept[0] = ta + nta;
+    two.kept[1] = tb + ntb;
+    two.cursor[0] = cursors;
+    two.cursor[1] = cursors + 1;
+    launch_pair_join2(d, rk, rc, bins, L, pair_bins_per_block(n_anti, L), two, ca, s);
+    CK_LAUNCH();
+    CK(cudaEventRecord(a->ev1, s));
+    uint32_t kept[2] = {0, 0};
+    unsigned long long got[2] = {0, 0};
+    CK(cudaMemcpyAsync(&kept[0], ta + nta, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&kept[1], tb + ntb, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(got, cursors, sizeof got, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    st = read_counters(a);
+    if (st) return st;
+    st = read_counters(b);
+    if (st) return st;
+    const int64_t n_new = (int64_t)a->h_counters->n_new;
+    if ((int64_t)kept[0] + na != Ma || (int64_t)kept[1] + nb != Mb ||
+        (int64_t)(got[0] + got[1]) != n_anti + n_new)
+        return fail(a, IQCC_ERR_STATE, "internal: two-partition dress row counts disagree");
+    float ms = 0;
+    cudaEventElapsedTime(&ms, a->ev0, a->ev1);
+    iqcc_ctx* parts[2] = {a, b};
+    const int64_t in[2] = {Ma, Mb}, anti[2] = {na, nb};
+    for (int k = 0; k < 2; ++k) {
+        iqcc_ctx* c = parts[k];
+        std::swap(c->keys, c->keys2);
+        std::swap(c->coef, c->coef2);
+        c->rows_alloc = (int64_t)std::min(c->keys.bytes / row_bytes(c), c->coef.bytes / 8);
+        c->stats.rows_allocated = c->rows_alloc;
+        c->M = (int64_t)kept[k] + (int64_t)got[k];
+        c->index_valid = false;
+        c->stats.n_dress++;
+        c->stats.dressed_terms += in[k];
+        c->stats.anticommuting += anti[k];
+        c->stats.appended += c->M - in[k];
+    }
+    a->stats.dress_kernel_ms += ms;
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_dress_pair(iqcc_ctx* a, iqcc_ctx* b, const uint64_t* gx, const uint64_t* gz, double tau,
+                            const uint64_t* mx, const uint64_t* mz, const uint64_t* ax, const uint64_t* az) {
+    GUARD(a);
+    GUARD(b);
+    if (a == b) return fail(a, IQCC_ERR_ARG, "the two partitions are one context");
+    if (a->device != b->device || a->n != b->n) return fail(a, IQCC_ERR_ARG, "contexts on different devices or of different qubit counts");
+    if (!gx || !gz || !mx || !mz || !ax || !az) return fail(a, IQCC_ERR_ARG, "null argument");
+    if (!std::isfinite(tau)) return fail(a, IQCC_ERR_ARG, "non-finite amplitude");
+    if (bits_above_n(a, gx) || bits_above_n(a, gz)) return fail(a, IQCC_ERR_ARG, "generator bits above n_qubits");
+    for (int w = 0; w < a->W; ++w)
+        if ((ax[w] & ~mx[w]) || (az[w] & ~mz[w])) return fail(a, IQCC_ERR_ARG, "partition bits outside the masks");
+    uint64_t pk[8], dm[8], dv[8];
+    pad_key(a, gx, gz, pk);
+    pad_key(a, mx, mz, dm);
+    pad_key(a, ax, az, dv);
+    bool identity = true;
+    for (int w = 0; w < 2 * a->Wd; ++w) identity &= pk[w] == 0;
+    if (identity) return IQCC_OK;
+    CK_CTX(a, cudaMemsetAsync(a->counters.p, 0, kCountersClear, a->stream));
+    CK_CTX(b, cudaMemsetAsync(b->counters.p, 0, kCountersClear, b->stream));
+    return dress_pair_impl(a, b, pk, tau, dm, dv);
+}
+
 iqcc_status iqcc_dress(iqcc_ctx* ctx, int n_gen, const uint64_t* gx, const uint64_t* gz, const double* tau,
                        int* n_applied) {
     if (n_applied) *n_applied = 0;
@@ -1449,7 +1606,7 @@ iqcc_status iqcc_prune(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* n_
 // histogram summed over the parts (each part's kernel adds into one
 // histogram), the threshold bucket's rows of all parts ordered together by
 // (|C| desc, canonical key asc), and each part compacted with its own flags.
-iqcc_status prune_parts_impl(iqcc_ctx* const* parts, int np, double eps, int64_t max_terms, int64_t* removed) {
+static iqcc_status prune_parts_impl(iqcc_ctx* const* parts, int np, double eps, int64_t max_terms, int64_t* removed) {
     iqcc_ctx* c0 = parts[0];
     cudaStream_t s0 = c0->stream;
     struct PartArea {
@@ -1653,6 +1810,30 @@ iqcc_status iqcc_generator_abc(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t
     uint64_t pk[8];
     pad_key(ctx, gx, gz, pk);
     return abc_impl(ctx, pk, theta, phi, abc);
+}
+
+iqcc_status iqcc_generator_abc_parts(iqcc_ctx* const* parts, int n_parts, const uint64_t* gx, const uint64_t* gz,
+                                     const double* theta, const double* phi, double abc[3], double* tau) {
+    if (!parts || n_parts <= 0) return fail(nullptr, IQCC_ERR_ARG, "no contexts");
+    for (int p = 0; p < n_parts; ++p) {
+        GUARD(parts[p]);
+        if (parts[p]->n != parts[0]->n) return fail(parts[p], IQCC_ERR_ARG, "contexts of different qubit counts");
+    }
+    iqcc_ctx* ctx = parts[0];
+    if (!gx || !gz || !theta || !phi || !abc) return fail(ctx, IQCC_ERR_ARG, "null argument");
+    if (bits_above_n(ctx, gx) || bits_above_n(ctx, gz)) return fail(ctx, IQCC_ERR_ARG, "generator bits above n_qubits");
+    uint64_t pk[8];
+    pad_key(ctx, gx, gz, pk);
+    double sum[3] = {0.0, 0.0, 0.0};
+    for (int p = 0; p < n_parts; ++p) {  // in part order: the same sum on every call
+        double v[3];
+        iqcc_status st = abc_impl(parts[p], pk, theta, phi, v);
+        if (st) return st;
+        for (int k = 0; k < 3; ++k) sum[k] += v[k];
+    }
+    for (int k = 0; k < 3; ++k) abc[k] = sum[k];
+    if (tau) *tau = (sum[1] == 0.0 && sum[2] == 0.0) ? 0.0 : std::atan2(-sum[2], -sum[1]);
+    return IQCC_OK;
 }
 
 iqcc_status iqcc_energy_gradients(iqcc_ctx* ctx, const uint64_t* gx, const uint64_t* gz, double tau,

@@ -410,6 +410,19 @@ void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const 
                       int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef, const uint32_t* kept,
                       unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s);
 
+// Bins filled from two partitions of one Hamiltonian (one generator, d.gens == nullptr): the join
+// writes each output row to the partition owning its key.  mask, aval: device-layout keys; a key k
+// belongs to partition 0 iff (k & mask) == aval.
+struct PairTwo {
+    uint64_t mask[8], aval[8];
+    uint64_t* rows[2];
+    double* coef[2];
+    const uint32_t* kept[2];
+    unsigned long long* cursor[2];
+};
+void launch_pair_join2(const PairDress& d, const uint64_t* rk, const double* rc, const uint32_t* start,
+                       int log2_bins, uint32_t bins_per_block, const PairTwo& t, DevCounters* ctr, cudaStream_t s);
+
 // k_dress.cu: the key index (partitioned dress only)
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,

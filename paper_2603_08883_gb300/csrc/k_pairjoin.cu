@@ -176,6 +176,43 @@ __global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restr
     }
 }
 
+// Matches the n rows rk[r0, r0 + n) by pair key in a shared-memory table:
+// partner[i] = j for the two members of a present pair, kNoPartner otherwise.
+// Both members of a pair probe the same slot sequence; the first inserts
+// itself at the first empty slot, the second meets it there (every slot
+// before it stays occupied) and links the two.  table (kJoinSlots, all
+// kJoinEmpty) and partner (all kNoPartner) are initialised by the caller.
+template <int W, class G>
+__device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint32_t r0, int n, const G& gen_of,
+                                           uint32_t* table, uint16_t* partner) {
+    volatile uint32_t* vt = table;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
+        const auto& g = gen_of(t);
+        const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
+        const Key<W> q = key_xor<W>(t, g.p);
+        const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
+        const uint32_t mine = tag | (uint32_t)i;
+        uint32_t s = (uint32_t)h & (kJoinSlots - 1);
+        for (int probe = 0; probe < kJoinSlots; ++probe) {
+            uint32_t v = vt[s];
+            if (v == kJoinEmpty) {
+                v = atomicCAS(&table[s], kJoinEmpty, mine);
+                if (v == kJoinEmpty) break;
+            }
+            if ((v & 0xFFFF0000u) == tag) {
+                const int j = (int)(v & 0xFFFFu);
+                if (key_equal<W>(load_key<W>(rk, (int64_t)r0 + j), q)) {
+                    partner[i] = (uint16_t)j;
+                    partner[j] = (uint16_t)i;
+                    break;
+                }
+            }
+            s = (s + 1) & (kJoinSlots - 1);
+        }
+    }
+}
+
 // Block j joins bins [j*bpb, (j+1)*bpb): records [start[b0], start[b1]).
 // WRITE: the dressed rows go to rows/coef from *kept on (the commuting rows
 // end there), each block's at the position it reserves on out_cursor;
@@ -207,35 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
         s_app = 0;
     }
     __syncthreads();
-    // Match by pair key.  Both members of a pair probe the same slot sequence;
-    // the first inserts itself at the first empty slot, the second meets it
-    // there (every slot before it stays occupied) and links the two.
-    volatile uint32_t* vt = table;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
-        const auto& g = gen_of(t);
-        const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
-        const Key<W> q = key_xor<W>(t, g.p);
-        const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
-        const uint32_t mine = tag | (uint32_t)i;
-        uint32_t s = (uint32_t)h & (kJoinSlots - 1);
-        for (int probe = 0; probe < kJoinSlots; ++probe) {
-            uint32_t v = vt[s];
-            if (v == kJoinEmpty) {
-                v = atomicCAS(&table[s], kJoinEmpty, mine);
-                if (v == kJoinEmpty) break;
-            }
-            if ((v & 0xFFFF0000u) == tag) {
-                const int j = (int)(v & 0xFFFFu);
-                if (key_equal<W>(load_key<W>(rk, (int64_t)r0 + j), q)) {
-                    partner[i] = (uint16_t)j;
-                    partner[j] = (uint16_t)i;
-                    break;
-                }
-            }
-            s = (s + 1) & (kJoinSlots - 1);
-        }
-    }
+    pair_match<W>(rk, r0, n, gen_of, table, partner);
     __syncthreads();
     unsigned cnt = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) cnt += partner[i] == kNoPartner;
@@ -269,6 +278,107 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
         }
         store_key<W>(rows, base + i, t);
         coef[base + i] = cn;
+    }
+}
+
+// Which of two partitions a key belongs to: partition 0 holds the keys whose
+// bits under the partition masks equal aval, partition 1 every other key.
+template <int W>
+struct TwoParts {
+    Key<W> mask, aval;
+    uint64_t* rows[2];
+    double* coef[2];
+    const uint32_t* kept[2];        // rows each partition's split kept (its output starts there)
+    unsigned long long* cursor[2];  // zeroed; rows each partition receives from the join
+    __device__ __forceinline__ int owner(const Key<W>& k) const {
+        uint64_t d = 0;
+#pragma unroll
+        for (int j = 0; j < W; ++j) d |= ((k.x[j] & mask.x[j]) ^ aval.x[j]) | ((k.z[j] & mask.z[j]) ^ aval.z[j]);
+        return d != 0;
+    }
+};
+
+// As k_pair_join (WRITE), for bins filled from two partitions of one
+// Hamiltonian: every output row goes to the partition that owns its key (a
+// rotated row stays where it came from; an appended partner T xor P goes to
+// its own partition, the other one when P flips the partition bits).  Each
+// block counts its outputs per partition, reserves both ranges, and places
+// its rows through shared-memory counters.
+template <int W, class G>
+__global__ void __launch_bounds__(kThreads) k_pair_join2(const uint64_t* __restrict__ rk, const double* __restrict__ rc,
+                                                         const uint32_t* __restrict__ start, uint32_t n_bins,
+                                                         uint32_t bins_per_block, G gen_of, TwoParts<W> o,
+                                                         DevCounters* ctr) {
+    __shared__ uint32_t table[kJoinSlots];
+    __shared__ uint16_t partner[kJoinCap];
+    __shared__ unsigned int s_cnt[2], s_cur[2], s_single;
+    __shared__ unsigned long long s_base[2];
+    const uint32_t b0 = blockIdx.x * bins_per_block;
+    const uint32_t b1 = min(b0 + bins_per_block, n_bins);
+    const uint32_t r0 = start[b0];
+    const int n = (int)(start[b1] - r0);
+    if (n <= 0) return;
+    if (n > kJoinCap) {
+        if (threadIdx.x == 0) set_error(ctr, IQCC_ERR_HASH_FULL, 71);
+        return;
+    }
+    for (int s = threadIdx.x; s < kJoinSlots; s += blockDim.x) table[s] = kJoinEmpty;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) partner[s] = kNoPartner;
+    if (threadIdx.x < 2) {
+        s_cnt[threadIdx.x] = 0;
+        s_cur[threadIdx.x] = 0;
+    }
+    if (threadIdx.x == 0) s_single = 0;
+    __syncthreads();
+    pair_match<W>(rk, r0, n, gen_of, table, partner);
+    __syncthreads();
+    unsigned c[2] = {0, 0}, single = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
+        ++c[o.owner(t)];
+        if (partner[i] == kNoPartner) {
+            ++single;
+            ++c[o.owner(key_xor<W>(t, gen_of(t).p))];
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        c[0] += __shfl_down_sync(0xFFFFFFFFu, c[0], off);
+        c[1] += __shfl_down_sync(0xFFFFFFFFu, c[1], off);
+        single += __shfl_down_sync(0xFFFFFFFFu, single, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (c[0]) atomicAdd(&s_cnt[0], c[0]);
+        if (c[1]) atomicAdd(&s_cnt[1], c[1]);
+        if (single) atomicAdd(&s_single, single);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (s_single) atomicAdd(&ctr->n_new, (unsigned long long)s_single);
+        for (int d = 0; d < 2; ++d)
+            s_base[d] = (unsigned long long)*o.kept[d] + atomicAdd(o.cursor[d], (unsigned long long)s_cnt[d]);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
+        const auto& g = gen_of(t);
+        const Key<W> q = key_xor<W>(t, g.p);
+        const double sg = (double)product_sign<W>(t, g.yP, g.p, q);
+        const double ct = rc[r0 + i];
+        const int p = partner[i];
+        const int dt = o.owner(t);
+        const int64_t rt = (int64_t)s_base[dt] + atomicAdd(&s_cur[dt], 1u);
+        if (p != kNoPartner) {
+            store_key<W>(o.rows[dt], rt, t);
+            o.coef[dt][rt] = ct * g.cos_t - sg * rc[r0 + p] * g.sin_t;
+        } else {
+            store_key<W>(o.rows[dt], rt, t);
+            o.coef[dt][rt] = ct * g.cos_t;
+            const int dq = o.owner(q);
+            const int64_t rq = (int64_t)s_base[dq] + atomicAdd(&s_cur[dq], 1u);
+            store_key<W>(o.rows[dq], rq, q);
+            o.coef[dq][rq] = sg * ct * g.sin_t;
+        }
     }
 }
 
@@ -329,6 +439,27 @@ void with_provider(const PairDress& d, F&& f) {
     }
 }
 
+template <int W>
+void join2_launch(const PairDress& d, const uint64_t* rk, const double* rc, const uint32_t* start, uint32_t n_bins,
+                  uint32_t bpb, const PairTwo& t, DevCounters* ctr, cudaStream_t s) {
+    TwoParts<W> o;
+    for (int j = 0; j < W; ++j) {  // device layout: x words, then z words
+        o.mask.x[j] = t.mask[j];
+        o.mask.z[j] = t.mask[W + j];
+        o.aval.x[j] = t.aval[j];
+        o.aval.z[j] = t.aval[W + j];
+    }
+    for (int k = 0; k < 2; ++k) {
+        o.rows[k] = t.rows[k];
+        o.coef[k] = t.coef[k];
+        o.kept[k] = t.kept[k];
+        o.cursor[k] = t.cursor[k];
+    }
+    const unsigned blocks = (n_bins + bpb - 1) / bpb;
+    k_pair_join2<W, OneGen<W>><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb,
+                                                           OneGen<W>{make_gen<W>(d.pkey, d.cos_t, d.sin_t)}, o, ctr);
+}
+
 }  // namespace
 
 // At most 2048 anticommuting rows per bin on average (every row of H
@@ -375,6 +506,17 @@ void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const 
     with_provider(d, [&](auto L, auto g) {
         decltype(L)::join(g, write, rk, rc, start, n_bins, bins_per_block, rows, coef, kept, out_cursor, ctr, s);
     });
+    note_launch();
+}
+
+void launch_pair_join2(const PairDress& d, const uint64_t* rk, const double* rc, const uint32_t* start,
+                       int log2_bins, uint32_t bins_per_block, const PairTwo& t, DevCounters* ctr, cudaStream_t s) {
+    const uint32_t n_bins = 1u << log2_bins;
+    switch (d.Wd) {
+        case 1: join2_launch<1>(d, rk, rc, start, n_bins, bins_per_block, t, ctr, s); break;
+        case 2: join2_launch<2>(d, rk, rc, start, n_bins, bins_per_block, t, ctr, s); break;
+        default: join2_launch<4>(d, rk, rc, start, n_bins, bins_per_block, t, ctr, s); break;
+    }
     note_launch();
 }
 

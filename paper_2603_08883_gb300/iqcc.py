@@ -96,6 +96,15 @@ _prune_learned = _sig("iqcc_prune_learned", _c, [_vp, ctypes.c_double, ctypes.c_
 _dress_sorted = _sig("iqcc_dress_sorted", _c, [_vp, ctypes.c_int, _u64p, _u64p, _f64p, ctypes.c_int,
                                                ctypes.POINTER(ctypes.c_int)])
 _prune = _sig("iqcc_prune", _c, [_vp, ctypes.c_double, ctypes.c_int64, _i64p])
+_dress_pair_raw = _sig("iqcc_dress_pair", _c, [_vp, _vp, _u64p, _u64p, ctypes.c_double, _u64p, _u64p, _u64p, _u64p])
+
+
+def _dress_pair(a, b, gx, gz, mx, mz, ax, az, tau):
+    return _dress_pair_raw(a, b, gx, gz, tau, mx, mz, ax, az)
+
+
+_abc_parts = _sig("iqcc_generator_abc_parts", _c, [ctypes.POINTER(_vp), ctypes.c_int, _u64p, _u64p, _f64p, _f64p,
+                                                   _f64p, _f64p])
 _prune_parts = _sig("iqcc_prune_parts", _c, [ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_double, ctypes.c_int64,
                                                _i64p])
 _energy = _sig("iqcc_qmf_energy", _c, [_vp, _f64p, _f64p, _f64p])
@@ -319,6 +328,36 @@ def iqcc_prune(H: Hamiltonian, eps: float, max_terms: int = 0) -> int:
     removed = ctypes.c_int64(0)
     H._check(_prune(H._h, float(eps), int(max_terms), ctypes.byref(removed)))
     return removed.value
+
+
+def iqcc_dress_pair(A: Hamiltonian, B: Hamiltonian, gx, gz, tau: float, mx, mz, ax, az) -> None:
+    """iqcc_dress_pair: dress two partitions of one Hamiltonian (A's keys have
+    (ax, az) under the masks (mx, mz)) by one generator on the device."""
+    W = A.W
+    arrs = [_u64(v, (W,)) for v in (gx, gz, mx, mz, ax, az)]
+    st = _dress_pair(A._h, B._h, *[p for _, p in arrs], float(tau))
+    if st != 0:
+        msg = _err(A._h).decode()
+        raise IqccError(st, msg if msg != "no error" else _err(B._h).decode())
+
+
+def iqcc_generator_abc_parts(parts, gx, gz, theta, phi):
+    """iqcc_generator_abc_parts: (A, B, C) summed over the parts and the
+    minimising amplitude tau* of the summed E(tau)."""
+    parts = list(parts)
+    W = parts[0].W
+    gxa, gxp = _u64(gx, (W,))
+    gza, gzp = _u64(gz, (W,))
+    ta, tp = _f64(theta, parts[0].n)
+    pa, pp = _f64(phi, parts[0].n)
+    arr = (_vp * len(parts))(*[H._h for H in parts])
+    abc = np.zeros(3)
+    tau = ctypes.c_double(0.0)
+    st = _abc_parts(arr, len(parts), gxp, gzp, tp, pp, abc.ctypes.data_as(_f64p), ctypes.byref(tau))
+    if st != 0:
+        msgs = [_err(H._h).decode() for H in parts if H._h]
+        raise IqccError(st, next((m for m in msgs if m != "no error"), _err(None).decode()))
+    return tuple(float(v) for v in abc), tau.value
 
 
 def iqcc_prune_parts(parts, eps: float, max_terms: int = 0) -> int:

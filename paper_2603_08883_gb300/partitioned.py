@@ -4,16 +4,21 @@ A partition is the set of strings that share the values of chosen key bits
 (``mx`` / ``mz``: masks over the x and z words).  A generator P whose masked
 bits are zero keeps each anticommuting row and its partner T xor P in the same
 partition, so each part is dressed on its own.  Otherwise every anticommuting
-row of partition a has its partner in partition a xor shift(P), and the dress
-takes one exchange per pair of partitions: each side sends its anticommuting
-rows (``iqcc_cross_rows``) and applies the dress to its own rows with the
-other side's (``iqcc_dress_cross``).  A, B, C and the energy are sums over the
-parts (one all-reduce in a multi-process run).
+row of partition a has its partner in partition a xor shift(P).
 
-``PartitionedHamiltonian`` keeps the parts as separate contexts in this
-process (on one GPU).  ``exchange_dress`` and ``reduced_tau`` are the same
-steps for one part per process, moving rows with torch.distributed (the
-engine is anything with the four methods of ``ContextEngine``).
+``PartitionedHamiltonian`` keeps the parts as separate contexts on one GPU and
+runs every step in the library: a crossing generator dresses each pair of
+partitions together (``iqcc_dress_pair``: both parts' anticommuting rows in
+one set of pair bins, every output row to the partition owning its key), A, B,
+C and the energy are summed over the parts (``iqcc_generator_abc_parts``), and
+the term limit is taken over all parts on the device (``iqcc_prune_parts``).
+
+``exchange_dress`` and ``reduced_tau`` are the steps for one part per process
+(a multi-process layout, not built for GPUs here): each side sends its
+anticommuting rows (``iqcc_cross_rows``) and applies the dress to its own rows
+with the other side's (``iqcc_dress_cross``), moving rows with
+torch.distributed; the engine is anything with the four methods of
+``ContextEngine``.
 """
 from __future__ import annotations
 
@@ -105,27 +110,39 @@ class PartitionedHamiltonian:
         return sum(len(H) for H in self.parts)
 
     def energy(self, theta, phi) -> float:
-        return sum(_lib().iqcc_qmf_energy(H, theta, phi) for H in self.parts)
+        zero = np.zeros(self.W, np.uint64)
+        return _lib().iqcc_generator_abc_parts(self.parts, zero, zero, theta, phi)[0][0]
 
     def abc(self, gx, gz, theta, phi):
-        s = np.zeros(3)
-        for H in self.parts:
-            s += np.asarray(_lib().iqcc_generator_abc(H, gx, gz, theta, phi))
-        return tuple(float(v) for v in s)
+        return _lib().iqcc_generator_abc_parts(self.parts, gx, gz, theta, phi)[0]
+
+    def pattern(self, a: int):
+        """Key bits (x words, z words) of partition a under the masks."""
+        px = np.zeros(self.W, np.uint64)
+        pz = np.zeros(self.W, np.uint64)
+        for k, (w, b, which) in enumerate(_mask_bits(self.mx, self.mz, self.W)):
+            if (a >> k) & 1:
+                (pz if which else px)[w] |= np.uint64(1) << np.uint64(b)
+        return px, pz
 
     def dress(self, gx, gz, tau: float) -> None:
+        """One generator: inside each part when P flips no partition bit, else
+        over each pair of partitions (a, a xor shift) on the device
+        (iqcc_dress_pair: one set of pair bins for both, every output row to
+        the partition owning its key)."""
         d = generator_shift(gx, gz, self.mx, self.mz)
         if d == 0:
             for H in self.parts:
                 ContextEngine(H).dress(gx, gz, tau)
             return
-        sent = [_lib().iqcc_cross_rows(H, gx, gz) for H in self.parts]
-        for a, H in enumerate(self.parts):
-            _lib().iqcc_dress_cross(H, gx, gz, tau, *sent[a ^ d])
+        for a in range(len(self.parts)):
+            if a < a ^ d:
+                ax, az = self.pattern(a)
+                _lib().iqcc_dress_pair(self.parts[a], self.parts[a ^ d], gx, gz, tau, self.mx, self.mz, ax, az)
 
     def step(self, gx, gz, theta, phi) -> float:
-        """The closed-form amplitude from the summed A, B, C, then the dress; returns tau."""
-        tau = closed_form_tau(*self.abc(gx, gz, theta, phi))
+        """The closed-form amplitude from the A, B, C summed over the parts, then the dress; returns tau."""
+        _, tau = _lib().iqcc_generator_abc_parts(self.parts, gx, gz, theta, phi)
         self.dress(gx, gz, tau)
         return tau
 

@@ -143,3 +143,57 @@ def test_partitioned_term_limit_matches_the_oracle(n, rows, eps, limit):
     bad = compare(P.export(), o.export())
     assert not bad, bad[:5]
     P.close()
+
+
+def test_dress_pair_matches_the_host_exchange_and_errors_leave_both_unchanged():
+    """iqcc_dress_pair (both partitions' anticommuting rows in one set of bins
+    on the device) against the host exchange (iqcc_cross_rows, then
+    iqcc_dress_cross on each side) and the oracle, for a generator that flips
+    the partition bit; then its argument and capacity errors."""
+    n = 100
+    rng = np.random.Generator(np.random.PCG64(41))
+    _, x, z, c = synth.random_hamiltonian(n, 40_000, 43, density=0.12)
+    mx, mz = _masks(n, 2)
+    gx, gz = synth.random_generator(n, rng, weight=3)
+    gx, gz = gx.copy(), gz.copy()
+    gx[0] |= np.uint64(1 << 3)
+    if sum(bin(int(a & b)).count("1") for a, b in zip(gx, gz)) % 2 == 0:
+        gz[0] ^= np.uint64(1 << 3)
+    assert pt.generator_shift(gx, gz, mx, mz) == 1
+    tau = 0.37
+    P = pt.PartitionedHamiltonian(n, x, z, c, mx, mz)
+    P.dress(gx, gz, tau)                                 # the device pair dress
+    Q = pt.PartitionedHamiltonian(n, x, z, c, mx, mz)    # the host exchange
+    sent = [iqcc.iqcc_cross_rows(H, gx, gz) for H in Q.parts]
+    for a, H in enumerate(Q.parts):
+        iqcc.iqcc_dress_cross(H, gx, gz, tau, *sent[a ^ 1])
+    o = oracle.Oracle(n, x, z, c)
+    o.dress(gx, gz, tau)
+    for got in (P.export(), Q.export()):
+        bad = compare(got, o.export())
+        assert not bad, bad[:5]
+    for a in (0, 1):                                     # every row landed in the partition owning it
+        assert np.all(pt.partition_of(*iqcc.iqcc_export(P.parts[a])[:2], mx, mz) == a)
+    ax, az = P.pattern(0)
+    with pytest.raises(iqcc.IqccError) as e:             # the same context twice
+        iqcc.iqcc_dress_pair(P.parts[0], P.parts[0], gx, gz, tau, mx, mz, ax, az)
+    assert e.value.status == 1
+    bad_ax = ax.copy()
+    bad_ax[1] |= np.uint64(1)                           # a bit outside the masks
+    with pytest.raises(iqcc.IqccError) as e:
+        iqcc.iqcc_dress_pair(P.parts[0], P.parts[1], gx, gz, tau, mx, mz, bad_ax, az)
+    assert e.value.status == 1
+    part = pt.partition_of(x, z, mx, mz)
+    A = iqcc.iqcc_load_hamiltonian(n, x[part == 0], z[part == 0], c[part == 0], capacity=int(np.sum(part == 0)) + 1)
+    B = iqcc.iqcc_load_hamiltonian(n, x[part == 1], z[part == 1], c[part == 1])
+    before = [iqcc.iqcc_export(A), iqcc.iqcc_export(B)]
+    with pytest.raises(iqcc.IqccError) as e:             # A could receive a partner per row of B
+        iqcc.iqcc_dress_pair(A, B, gx, gz, tau, mx, mz, ax, az)
+    assert e.value.status == 4
+    for H, want in zip((A, B), before):
+        for got, w in zip(iqcc.iqcc_export(H), want):
+            assert np.array_equal(got, w)
+    for H in (A, B):
+        H.close()
+    P.close()
+    Q.close()
