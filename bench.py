@@ -345,9 +345,10 @@ def measure_partitioned(iqcc, n, x, z, c, th, ph, n_gen=8, tau=0.1):
     (App. B's bit-wise partitioning on one GPU, paper_2603_08883_gb300/
     partitioned.py), dressed by its top DIS candidates at tau; the qubit is
     the one most of those generators flip, and each generator that flips it
-    exchanges the anticommuting rows of both parts through the host.  Wall
-    time with a device synchronize around the whole sequence, against the
-    same sequence on one context."""
+    dresses both parts through one set of pair bins (iqcc_dress_pair).  Then
+    a term limit of half the terms over both parts (iqcc_prune_parts) against
+    the same limit on one context.  Wall times with a device synchronize
+    around each sequence."""
     import torch
     from paper_2603_08883_gb300 import partitioned as pt
     H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 31)
@@ -358,7 +359,6 @@ def measure_partitioned(iqcc, n, x, z, c, th, ph, n_gen=8, tau=0.1):
     torch.cuda.synchronize()
     t_one = time.perf_counter() - t0
     m_one = len(H)
-    H.close()
     W = (n + 63) // 64
     flips = [sum((int(g[j // 64]) >> (j % 64)) & 1 for g in gx) for j in range(n)]
     qubit = int(np.argmax(flips))
@@ -374,10 +374,23 @@ def measure_partitioned(iqcc, n, x, z, c, th, ph, n_gen=8, tau=0.1):
         P.dress(a, b, tau)
     torch.cuda.synchronize()
     t_two = time.perf_counter() - t0
+    m_two = len(P)
+    limit = m_one // 2
+    t0 = time.perf_counter()
+    iqcc.iqcc_prune(H, 0.0, limit)
+    torch.cuda.synchronize()
+    t_cut_one = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    P.prune(0.0, limit)
+    torch.cuda.synchronize()
+    t_cut_two = time.perf_counter() - t0
     out = {"split": f"x bit of qubit {qubit}", "parts_M0": parts_m0,
            "generators": f"top {len(gx)} DIS candidates of the loaded Hamiltonian, tau = {tau}",
-           "crossing_generators": int(crossing), "M_after": {"one_context": m_one, "partitioned": len(P)},
-           "ms_one_context": round(t_one * 1e3, 2), "ms_partitioned": round(t_two * 1e3, 2)}
+           "crossing_generators": int(crossing), "M_after": {"one_context": m_one, "partitioned": m_two},
+           "ms_one_context": round(t_one * 1e3, 2), "ms_partitioned": round(t_two * 1e3, 2),
+           "term_limit": {"limit": limit, "ms_one_context": round(t_cut_one * 1e3, 2),
+                          "ms_partitioned": round(t_cut_two * 1e3, 2), "M_after": [len(H), len(P)]}}
+    H.close()
     P.close()
     return out
 
