@@ -589,7 +589,7 @@ def run_gpu(args):
             r = iqcc.iqcc_iterate(Hk, th, ph, w.n_gen, w.eps, w.max_terms)
             torch.cuda.synchronize()
             tc = time.perf_counter()
-            ox, oz, oc = iqcc.iqcc_export(Hk, out=dst)
+            ox, oz, oc = iqcc.iqcc_export_rows(Hk, out=dst)
             phases["load_s"] += tb - ta
             phases["iterate_s"] += tc - tb
             phases["export_s"] += time.perf_counter() - tc
@@ -604,8 +604,8 @@ def run_gpu(args):
         e2e = {"value": e_dressed / e_wall, "unit": UNIT, "h2d_bytes_per_step": h2d // args.e2e_steps,
                "d2h_bytes_per_step": d2h // args.e2e_steps, "steps": args.e2e_steps,
                "phases_s_per_step": {k: round(v / args.e2e_steps, 4) for k, v in phases.items()},
-               "path": "per step: iqcc_load_hamiltonian from pinned host arrays, iqcc_iterate, iqcc_export to "
-                       "pinned host arrays (the next step's input); wall clock"}
+               "path": "per step: iqcc_load_hamiltonian from pinned host arrays, iqcc_iterate, iqcc_export_rows "
+                       "(storage order, no sort) to pinned host arrays, the next step's input; wall clock"}
     else:
         H.close()
     batch_variant = None

@@ -304,6 +304,19 @@ iqcc_status iqcc_num_terms(const iqcc_ctx* ctx, int64_t* n_terms);
 iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z,
                         double* coef);
 
+/*
+ * As iqcc_export, in the context's storage order (no particular order; each
+ * string once): no sort, so the copy runs at the host link's rate.  Meant for
+ * moving H out and back in (checkpoints, a host round trip between steps):
+ * iqcc_load_hamiltonian accepts rows in any order and sums repeated strings
+ * without a sort (or with one, when one string repeats thousands of times).
+ * x, z: host [cap][W]; coef: host [cap]; pinned host arrays are written by
+ * the kernel directly.  A pending term-limit cut of iqcc_iterate is applied
+ * first.  Errors: IQCC_ERR_ARG (NULL n, cap < 0, NULL output array with
+ * cap > 0), IQCC_ERR_OOM, IQCC_ERR_CUDA.
+ */
+iqcc_status iqcc_export_rows(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z, double* coef);
+
 /* Running counters of the context (reset by iqcc_reset_stats). */
 typedef struct {
     int64_t n_dress;           /* generators applied */

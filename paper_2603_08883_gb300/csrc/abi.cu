@@ -1061,6 +1061,58 @@ namespace iqcc {
 void set_thread_error(const std::string& msg) { g_last_error = msg; }
 }  // namespace iqcc
 
+// Load of packed rows in any order (k_pairjoin.cu, launch_key_group): the
+// distinct keys with their coefficients summed in input order, non-zero sums
+// kept, written to the row buffer in bin order; ctx->M set.  *done = false
+// (nothing written) when a group of bins holds more rows than one join block
+// can (many copies of one key): the caller sorts instead.
+iqcc_status load_by_groups(iqcc_ctx* ctx, const uint64_t* staged, const double* c_staged, int64_t n, bool* done) {
+    *done = false;
+    const int L = pair_bins_log2(n);
+    const uint32_t NB = 1u << L;
+    const uint32_t bpb = pair_bins_per_block(n, L);
+    const int Wd = ctx->Wd;
+    Carver cv;
+    cv.take<uint32_t>((size_t)NB + 1);
+    cv.take<uint64_t>((size_t)n * 2 * Wd);
+    cv.take<double>(n);
+    cv.take<uint32_t>(n);
+    cv.take<uint32_t>(1024);
+    cv.take<unsigned long long>(1);
+    if (!ensure(ctx, ctx->aux, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->aux.p, 0};
+    uint32_t* counts = cv.take<uint32_t>((size_t)NB + 1);
+    uint64_t* rk = cv.take<uint64_t>((size_t)n * 2 * Wd);
+    double* rc = cv.take<double>(n);
+    uint32_t* ri = cv.take<uint32_t>(n);
+    uint32_t* scan_tmp = cv.take<uint32_t>(1024);
+    unsigned long long* out_cursor = cv.take<unsigned long long>(1);
+    cudaStream_t s = ctx->stream;
+    DevCounters* c = dctr(ctx);
+    CK(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * ((size_t)NB + 1), s));
+    CK(cudaMemsetAsync(out_cursor, 0, sizeof(unsigned long long), s));
+    launch_key_group(Wd, staged, c_staged, n, L, 0, counts, rk, rc, ri, bpb, nullptr, nullptr, out_cursor, c, s);
+    launch_scan_u32_long(counts + 1, NB, scan_tmp, s);
+    CK_LAUNCH();
+    std::vector<uint32_t> h((size_t)NB + 1);
+    CK(cudaMemcpyAsync(h.data(), counts + 1, sizeof(uint32_t) * NB, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    h[NB] = (uint32_t)n;  // h[b]: start of bin b
+    for (uint32_t g = 0; g < NB; g += bpb)
+        if ((int64_t)h[std::min(g + bpb, NB)] - (int64_t)h[g] > kKeyJoinCap) return IQCC_OK;
+    launch_key_group(Wd, staged, c_staged, n, L, 1, counts, rk, rc, ri, bpb, nullptr, nullptr, out_cursor, c, s);
+    launch_key_group(Wd, staged, c_staged, n, L, 2, counts, rk, rc, ri, bpb, ctx->rows(), ctx->c(), out_cursor, c, s);
+    CK_LAUNCH();
+    iqcc_status st = read_counters(ctx);
+    if (st) return st;
+    unsigned long long m = 0;
+    CK(cudaMemcpyAsync(&m, out_cursor, sizeof m, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->M = (int64_t)m;
+    *done = true;
+    return IQCC_OK;
+}
+
 extern "C" {
 
 iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t n_terms, const uint64_t* x,
@@ -1183,6 +1235,14 @@ iqcc_status iqcc_load_hamiltonian(iqcc_ctx** out, const iqcc_opts* opts, int64_t
             if (ctx->h_counters->n_new != 0) {
                 st = fail(ctx, IQCC_ERR_ARG, "key bits set above n_qubits");
                 break;
+            }
+            if (ctx->h_counters->aux != 0) {
+                // rows in any order: repeated keys summed by partition and join (no sort) unless a
+                // group of bins is too large for one join block (many copies of one key)
+                bool done = false;
+                st = load_by_groups(ctx, staged, c_staged, n, &done);
+                if (st) break;
+                if (done) break;
             }
             uint32_t* sorted = sa.a;
             if (ctx->h_counters->aux != 0)
@@ -2053,6 +2113,43 @@ void* pinned_device_view(const void* p) {
 
 extern "C" {
 
+iqcc_status iqcc_export_rows(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z, double* coef) {
+    GUARD(ctx);
+    if (!n) return fail(ctx, IQCC_ERR_ARG, "n is NULL");
+    if (cap < 0) return fail(ctx, IQCC_ERR_ARG, "cap < 0");
+    iqcc_status st = apply_pending_cut(ctx);
+    if (st) return st;
+    *n = ctx->M;
+    const int64_t k = std::min(cap, ctx->M);
+    if (k == 0) return IQCC_OK;
+    if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
+    const int W = ctx->W;
+    uint64_t* dx = (uint64_t*)pinned_device_view(x);
+    uint64_t* dz = (uint64_t*)pinned_device_view(z);
+    double* dc = (double*)pinned_device_view(coef);
+    if (dx && dz && dc) {  // written by the kernel straight into the pinned output arrays
+        launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), nullptr, dx, dz, dc, k, ctx->stream);
+        CK_LAUNCH();
+    } else {
+        Carver cv;
+        cv.take<uint64_t>((size_t)k * W);
+        cv.take<uint64_t>((size_t)k * W);
+        cv.take<double>(k);
+        if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+        cv = Carver{(char*)ctx->scratch.p, 0};
+        uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
+        uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
+        double* sc = cv.take<double>(k);
+        launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), nullptr, sx, sz, sc, k, ctx->stream);
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
 iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uint64_t* z, double* coef) {
     GUARD(ctx);
     if (!n) return fail(ctx, IQCC_ERR_ARG, "n is NULL");
@@ -2661,3 +2758,4 @@ void iqcc_batch_free(iqcc_batch* b) {
 }
 
 }  // extern "C"
+

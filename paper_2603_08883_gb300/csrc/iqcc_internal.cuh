@@ -423,6 +423,18 @@ struct PairTwo {
 void launch_pair_join2(const PairDress& d, const uint64_t* rk, const double* rc, const uint32_t* start,
                        int log2_bins, uint32_t bins_per_block, const PairTwo& t, DevCounters* ctr, cudaStream_t s);
 
+// Load of rows in any order (k_pairjoin.cu): the distinct keys of rows[0, n) with their coefficients
+// summed in input order, non-zero sums written to rows_out / c_out from *out_cursor (zeroed) on, in
+// bin order.  Three phases: 0 counts rows per bin into counts[1..2^L] (zeroed, counts[0] = 0);
+// then the caller scans counts[1..2^L] (bin starts) and checks that no group of bins_per_block bins
+// holds more than 4096 rows; 1 copies rows into their bins (rk [n][2 Wd], rc, ri = input index;
+// counts[1..] advance to bin ends, so counts[b] is bin b's start); 2 joins each group of bins.
+void launch_key_group(int Wd, const uint64_t* rows, const double* coef, int64_t n, int log2_bins, int phase,
+                      uint32_t* counts, uint64_t* rk, double* rc, uint32_t* ri, uint32_t bins_per_block,
+                      uint64_t* rows_out, double* c_out, unsigned long long* out_cursor, DevCounters* ctr,
+                      cudaStream_t s);
+constexpr int kKeyJoinCap = 4096;  // rows one key-join block holds
+
 // k_dress.cu: the key index (partitioned dress only)
 void launch_hash_clear(HashView h, uint64_t slots, cudaStream_t s);
 void launch_hash_insert(int Wd, const uint64_t* rows, int64_t lo, int64_t hi, HashView h,

@@ -33,6 +33,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <type_traits>
 
 #include "iqcc_internal.cuh"
 
@@ -382,6 +384,175 @@ __global__ void __launch_bounds__(kThreads) k_pair_join2(const uint64_t* __restr
     }
 }
 
+// ---------------------------------------------------------------------------
+// Load of rows in any order: repeated keys summed (Eq. 2: one coefficient per
+// distinct string) by the same partition-and-join scheme, keyed on the whole
+// key.  k_key_hist counts rows per bin (top L bits of the key's hash),
+// k_key_split copies each row with its input index into its bin, and
+// k_key_join matches equal keys of a bin group in shared memory; each group
+// of equal keys sums its coefficients in input order (so the result equals a
+// stable sort followed by run sums), and the distinct keys with a non-zero
+// sum are written out in bin order.
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_key_hist(const uint64_t* __restrict__ rows, int64_t n, int shift,
+                                                       uint32_t* counts) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s)
+        atomicAdd(&counts[hash_key<W>(load_key<W>(rows, i)) >> shift], 1u);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_key_split(const uint64_t* __restrict__ rows,
+                                                        const double* __restrict__ coef, int64_t n, int shift,
+                                                        uint32_t* cursor, uint64_t* rk, double* rc, uint32_t* ri) {
+    constexpr int kPer = 4;
+    const int64_t base = ((int64_t)blockIdx.x * kPer) * blockDim.x + threadIdx.x;
+    Key<W> key[kPer];
+    uint32_t pos[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = base + (int64_t)r * blockDim.x;
+        if (i < n) {
+            key[r] = load_key<W>(rows, i);
+            pos[r] = atomicAdd(&cursor[hash_key<W>(key[r]) >> shift], 1u);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = base + (int64_t)r * blockDim.x;
+        if (i < n) {
+            store_key<W>(rk, pos[r], key[r]);
+            rc[pos[r]] = coef[i];
+            ri[pos[r]] = (uint32_t)i;
+        }
+    }
+}
+
+// The sum of the group headed by row h (its other members linked from
+// lst[h] through nxt) in ascending input index.
+__device__ __forceinline__ double key_group_sum(int h, const uint32_t* lst, const uint16_t* nxt,
+                                                const uint32_t* __restrict__ ri, const double* __restrict__ rc,
+                                                uint32_t r0) {
+    if (lst[h] == kJoinEmpty) return rc[r0 + h];
+    double sum = 0.0;
+    uint32_t last = 0;
+    bool first = true;
+    for (;;) {  // repeatedly the smallest input index above the last one taken
+        int best = -1;
+        uint32_t bi = 0xFFFFFFFFu;
+        int m = h;
+        uint32_t link = lst[h];
+        for (;;) {
+            const uint32_t v = ri[r0 + m];
+            if ((first || v > last) && v < bi) {
+                bi = v;
+                best = m;
+            }
+            if (link == kJoinEmpty) break;
+            m = (int)link;
+            link = nxt[m] == kNoPartner ? kJoinEmpty : (uint32_t)nxt[m];
+        }
+        if (best < 0) break;
+        sum += rc[r0 + best];
+        last = bi;
+        first = false;
+    }
+    return sum;
+}
+
+constexpr size_t kKeyJoinSmem = sizeof(uint32_t) * kJoinSlots + sizeof(uint16_t) * kJoinCap +
+                                sizeof(uint32_t) * kJoinCap + sizeof(uint16_t) * kJoinCap;
+
+// Block j: bins [j*bpb, (j+1)*bpb), rows [start[b0], start[b1]) (at most
+// kJoinCap: the caller checks the groups first; a larger one is an error).
+// Writes the distinct keys with non-zero sums to rows_out / c_out at
+// positions reserved on out_cursor.
+template <int W>
+__global__ void __launch_bounds__(kThreads) k_key_join(const uint64_t* __restrict__ rk, const double* __restrict__ rc,
+                                                       const uint32_t* __restrict__ ri,
+                                                       const uint32_t* __restrict__ start, uint32_t n_bins,
+                                                       uint32_t bins_per_block, uint64_t* rows_out, double* c_out,
+                                                       unsigned long long* out_cursor, DevCounters* ctr) {
+    extern __shared__ __align__(16) unsigned char s_dyn[];
+    uint32_t* table = reinterpret_cast<uint32_t*>(s_dyn);
+    uint32_t* lst = table + kJoinSlots;
+    uint16_t* head = reinterpret_cast<uint16_t*>(lst + kJoinCap);
+    uint16_t* nxt = head + kJoinCap;
+    __shared__ unsigned int s_cnt, s_cur;
+    __shared__ unsigned long long s_base;
+    const uint32_t b0 = blockIdx.x * bins_per_block;
+    const uint32_t b1 = min(b0 + bins_per_block, n_bins);
+    const uint32_t r0 = start[b0];
+    const int n = (int)(start[b1] - r0);
+    if (n <= 0) return;
+    if (n > kJoinCap) {
+        if (threadIdx.x == 0) set_error(ctr, IQCC_ERR_HASH_FULL, 72);
+        return;
+    }
+    for (int s = threadIdx.x; s < kJoinSlots; s += blockDim.x) table[s] = kJoinEmpty;
+    for (int s = threadIdx.x; s < n; s += blockDim.x) {
+        lst[s] = kJoinEmpty;
+        nxt[s] = kNoPartner;
+    }
+    if (threadIdx.x == 0) {
+        s_cnt = 0;
+        s_cur = 0;
+    }
+    __syncthreads();
+    // every row finds the first row that claimed its key's slot (its group's head)
+    volatile uint32_t* vt = table;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
+        const uint64_t h = hash_key<W>(t);
+        const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
+        uint32_t s = (uint32_t)h & (kJoinSlots - 1);
+        int hd = i;
+        for (int probe = 0; probe < kJoinSlots; ++probe) {
+            uint32_t v = vt[s];
+            if (v == kJoinEmpty) {
+                v = atomicCAS(&table[s], kJoinEmpty, tag | (uint32_t)i);
+                if (v == kJoinEmpty) break;  // i heads its key's group
+            }
+            if ((v & 0xFFFF0000u) == tag) {
+                const int j = (int)(v & 0xFFFFu);
+                if (key_equal<W>(load_key<W>(rk, (int64_t)r0 + j), t)) {
+                    hd = j;
+                    break;
+                }
+            }
+            s = (s + 1) & (kJoinSlots - 1);
+        }
+        head[i] = (uint16_t)hd;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {  // the other members hang off their head
+        const int h = head[i];
+        if (h != i) {
+            const uint32_t old = atomicExch(&lst[h], (uint32_t)i);
+            nxt[i] = old == kJoinEmpty ? kNoPartner : (uint16_t)old;
+        }
+    }
+    __syncthreads();
+    unsigned cnt = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (head[i] == i && key_group_sum(i, lst, nxt, ri, rc, r0) != 0.0) ++cnt;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_down_sync(0xFFFFFFFFu, cnt, o);
+    if ((threadIdx.x & 31) == 0 && cnt) atomicAdd(&s_cnt, cnt);
+    __syncthreads();
+    if (threadIdx.x == 0) s_base = atomicAdd(out_cursor, (unsigned long long)s_cnt);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (head[i] != i) continue;
+        const double v = key_group_sum(i, lst, nxt, ri, rc, r0);
+        if (v == 0.0) continue;
+        const int64_t q = (int64_t)s_base + atomicAdd(&s_cur, 1u);
+        store_key<W>(rows_out, q, load_key<W>(rk, (int64_t)r0 + i));
+        c_out[q] = v;
+    }
+}
+
 int grid_cap(int64_t items, int per_sm) {
     int64_t want = (items + kThreads - 1) / kThreads;
     const int64_t cap = (int64_t)sm_count() * per_sm;
@@ -516,6 +687,37 @@ void launch_pair_join2(const PairDress& d, const uint64_t* rk, const double* rc,
         case 1: join2_launch<1>(d, rk, rc, start, n_bins, bins_per_block, t, ctr, s); break;
         case 2: join2_launch<2>(d, rk, rc, start, n_bins, bins_per_block, t, ctr, s); break;
         default: join2_launch<4>(d, rk, rc, start, n_bins, bins_per_block, t, ctr, s); break;
+    }
+    note_launch();
+}
+
+void launch_key_group(int Wd, const uint64_t* rows, const double* coef, int64_t n, int log2_bins, int phase,
+                      uint32_t* counts, uint64_t* rk, double* rc, uint32_t* ri, uint32_t bins_per_block,
+                      uint64_t* rows_out, double* c_out, unsigned long long* out_cursor, DevCounters* ctr,
+                      cudaStream_t s) {
+    if (n <= 0) return;
+    const int shift = 64 - log2_bins;
+    const uint32_t n_bins = 1u << log2_bins;
+    auto run = [&](auto wtag) {
+        constexpr int W = decltype(wtag)::value;
+        if (phase == 0) {
+            k_key_hist<W><<<grid_cap(n, 8), kThreads, 0, s>>>(rows, n, shift, counts + 1);
+        } else if (phase == 1) {
+            const unsigned blocks = (unsigned)((n + 4 * kThreads - 1) / (4 * kThreads));
+            k_key_split<W><<<blocks, kThreads, 0, s>>>(rows, coef, n, shift, counts + 1, rk, rc, ri);
+        } else {
+            static std::atomic<unsigned long long> attr{0};
+            if (first_on_device(&attr))
+                cudaFuncSetAttribute(k_key_join<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kKeyJoinSmem);
+            const unsigned blocks = (n_bins + bins_per_block - 1) / bins_per_block;
+            k_key_join<W><<<blocks, kThreads, kKeyJoinSmem, s>>>(rk, rc, ri, counts, n_bins, bins_per_block, rows_out,
+                                                                 c_out, out_cursor, ctr);
+        }
+    };
+    switch (Wd) {
+        case 1: run(std::integral_constant<int, 1>{}); break;
+        case 2: run(std::integral_constant<int, 2>{}); break;
+        default: run(std::integral_constant<int, 4>{}); break;
     }
     note_launch();
 }

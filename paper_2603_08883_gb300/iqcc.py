@@ -117,6 +117,7 @@ _iterate = _sig("iqcc_iterate", _c, [_vp, _f64p, _f64p, ctypes.POINTER(iqcc_iter
                                      ctypes.POINTER(iqcc_iter_result)])
 _num = _sig("iqcc_num_terms", _c, [_vp, _i64p])
 _export = _sig("iqcc_export", _c, [_vp, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
+_export_rows = _sig("iqcc_export_rows", _c, [_vp, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
 _stats = _sig("iqcc_get_stats", _c, [_vp, ctypes.POINTER(iqcc_stats)])
 _reset = _sig("iqcc_reset_stats", _c, [_vp])
 _err = _sig("iqcc_last_error", ctypes.c_char_p, [_vp])
@@ -485,6 +486,23 @@ def iqcc_export(H: Hamiltonian, out=None):
         x, z, c = out
     H._check(_export(H._h, m, ctypes.byref(n), x.ctypes.data_as(_u64p), z.ctypes.data_as(_u64p),
                      c.ctypes.data_as(_f64p)))
+    return x[:m], z[:m], c[:m]
+
+
+def iqcc_export_rows(H: Hamiltonian, out=None):
+    """(x, z, c) in the context's storage order (iqcc_export_rows: no sort);
+    ``out`` as for iqcc_export."""
+    n = ctypes.c_int64(0)
+    H._check(_export_rows(H._h, 0, ctypes.byref(n), None, None, None))
+    m = n.value
+    if out is None:
+        x = np.zeros((max(m, 1), H.W), np.uint64)
+        z = np.zeros((max(m, 1), H.W), np.uint64)
+        c = np.zeros(max(m, 1))
+    else:
+        x, z, c = out
+    H._check(_export_rows(H._h, m, ctypes.byref(n), x.ctypes.data_as(_u64p), z.ctypes.data_as(_u64p),
+                          c.ctypes.data_as(_f64p)))
     return x[:m], z[:m], c[:m]
 
 
