@@ -310,8 +310,8 @@ iqcc_status iqcc_export(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x, uin
  * moving H out and back in (checkpoints, a host round trip between steps):
  * iqcc_load_hamiltonian accepts rows in any order and sums repeated strings
  * without a sort (or with one, when one string repeats thousands of times).
- * x, z: host [cap][W]; coef: host [cap]; pinned host arrays are written by
- * the kernel directly.  A pending term-limit cut of iqcc_iterate is applied
+ * x, z: host [cap][W]; coef: host [cap] (pinned memory copies fastest).
+ * Device scratch: 16 W + 8 bytes per row.  A pending term-limit cut of iqcc_iterate is applied
  * first.  Errors: IQCC_ERR_ARG (NULL n, cap < 0, NULL output array with
  * cap > 0), IQCC_ERR_OOM, IQCC_ERR_CUDA.
  */

@@ -2124,28 +2124,22 @@ iqcc_status iqcc_export_rows(iqcc_ctx* ctx, int64_t cap, int64_t* n, uint64_t* x
     if (k == 0) return IQCC_OK;
     if (!x || !z || !coef) return fail(ctx, IQCC_ERR_ARG, "null output array");
     const int W = ctx->W;
-    uint64_t* dx = (uint64_t*)pinned_device_view(x);
-    uint64_t* dz = (uint64_t*)pinned_device_view(z);
-    double* dc = (double*)pinned_device_view(coef);
-    if (dx && dz && dc) {  // written by the kernel straight into the pinned output arrays
-        launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), nullptr, dx, dz, dc, k, ctx->stream);
-        CK_LAUNCH();
-    } else {
-        Carver cv;
-        cv.take<uint64_t>((size_t)k * W);
-        cv.take<uint64_t>((size_t)k * W);
-        cv.take<double>(k);
-        if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-        cv = Carver{(char*)ctx->scratch.p, 0};
-        uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
-        uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
-        double* sc = cv.take<double>(k);
-        launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), nullptr, sx, sz, sc, k, ctx->stream);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
-    }
+    // unpacked into device scratch, then three copies by the copy engines (faster
+    // over the host link than kernel stores into mapped host memory)
+    Carver cv;
+    cv.take<uint64_t>((size_t)k * W);
+    cv.take<uint64_t>((size_t)k * W);
+    cv.take<double>(k);
+    if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    cv = Carver{(char*)ctx->scratch.p, 0};
+    uint64_t* sx = cv.take<uint64_t>((size_t)k * W);
+    uint64_t* sz = cv.take<uint64_t>((size_t)k * W);
+    double* sc = cv.take<double>(k);
+    launch_unpack_rows(W, ctx->Wd, ctx->rows(), ctx->c(), nullptr, sx, sz, sc, k, ctx->stream);
+    CK_LAUNCH();
+    CK(cudaMemcpyAsync(x, sx, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(z, sz, sizeof(uint64_t) * k * W, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(coef, sc, sizeof(double) * k, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return IQCC_OK;
 }
