@@ -160,22 +160,33 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
         unsigned n_anti = 0;
         const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+            // the tile's rows of this thread in flight together: live flags, then keys
+            constexpr int kPer = kDressTile / kThreads;
+            bool v[kPer], k[kPer];
+            Key<W> t[kPer];
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
+                v[r] = i < M && (!live || live[i]);  // rows dropped by a pending term-limit cut are skipped
+            }
+#pragma unroll
+            for (int r = 0; r < kPer; ++r)
+                if (v[r]) t[r] = load_key<W>(rows, tile * kDressTile + r * kThreads + threadIdx.x);
+#pragma unroll
+            for (int r = 0; r < kPer; ++r) {
+                const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
+                k[r] = false;
+                if (!v[r]) continue;
+                if (abc_row<W, BASIS>(t[r], coef, i, p, yP, occ, s_tab, n_groups, acc)) {
+                    atomicAdd(&pc.counts[pair_hash<W>(t[r], p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
+                    ++n_anti;
+                } else {
+                    k[r] = true;
+                }
+            }
             int kept = 0;
 #pragma unroll
-            for (int r = 0; r < kDressTile / kThreads; ++r) {
-                const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
-                bool k = false;
-                if (i < M && (!live || live[i])) {  // rows dropped by a pending term-limit cut are skipped
-                    const Key<W> t = load_key<W>(rows, i);
-                    if (abc_row<W, BASIS>(t, coef, i, p, yP, occ, s_tab, n_groups, acc)) {
-                        atomicAdd(&pc.counts[pair_hash<W>(t, p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
-                        ++n_anti;
-                    } else {
-                        k = true;
-                    }
-                }
-                kept += __syncthreads_count(k);
-            }
+            for (int r = 0; r < kPer; ++r) kept += __syncthreads_count(k[r]);
             if (threadIdx.x == 0) pc.tile_kept[tile] = (uint32_t)kept;
         }
 #pragma unroll

@@ -76,23 +76,32 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
     unsigned n_anti = 0;
     const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        constexpr int kPer = kDressTile / kThreads;  // the tile's rows of this thread in flight together
+        bool v[kPer], k[kPer];
+        Key<W> t[kPer];
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
+            v[r] = i < M && (!live || live[i]);
+        }
+#pragma unroll
+        for (int r = 0; r < kPer; ++r)
+            if (v[r]) t[r] = load_key<W>(rows, tile * kDressTile + r * kThreads + threadIdx.x);
+#pragma unroll
+        for (int r = 0; r < kPer; ++r) {
+            k[r] = false;
+            if (!v[r]) continue;
+            const auto& g = gen_of(t[r]);
+            if (anticommutes<W>(t[r], g.p)) {
+                atomicAdd(&counts[pair_hash<W>(t[r], g.p, g.top_word, g.top_mask) >> shift], 1u);
+                ++n_anti;
+            } else {
+                k[r] = true;
+            }
+        }
         int kept = 0;
 #pragma unroll
-        for (int r = 0; r < kDressTile / kThreads; ++r) {
-            const int64_t i = tile * kDressTile + r * kThreads + threadIdx.x;
-            bool k = false;
-            if (i < M && (!live || live[i])) {
-                const Key<W> t = load_key<W>(rows, i);
-                const auto& g = gen_of(t);
-                if (anticommutes<W>(t, g.p)) {
-                    atomicAdd(&counts[pair_hash<W>(t, g.p, g.top_word, g.top_mask) >> shift], 1u);
-                    ++n_anti;
-                } else {
-                    k = true;
-                }
-            }
-            kept += __syncthreads_count(k);
-        }
+        for (int r = 0; r < kPer; ++r) kept += __syncthreads_count(k[r]);
         if (threadIdx.x == 0) tile_kept[tile] = (uint32_t)kept;
     }
 #pragma unroll
