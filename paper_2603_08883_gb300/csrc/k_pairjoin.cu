@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
 // its end on exit.  live (may be NULL): rows with live[i] == 0 (dropped by a
 // pending term-limit cut) are neither kept nor copied.
 template <int W, class G, bool COMPACT, bool SCATTER>
-__global__ void __launch_bounds__(kThreads) k_pair_split(const uint64_t* __restrict__ rows,
+__global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 1)) k_pair_split(const uint64_t* __restrict__ rows,
                                                          const double* __restrict__ coef, int64_t n, G gen_of,
                                                          int shift, uint32_t* cursor, uint64_t* rk, double* rc,
                                                          const uint32_t* __restrict__ tile_off, uint64_t* rows_out,
