@@ -391,12 +391,17 @@ iqcc_status apply_pending_cut(iqcc_ctx* ctx);
 // anticommuting rows, split (commuting rows compacted in place, anticommuting
 // ones copied into their bins), join.  On IQCC_ERR_CAPACITY / OOM H is
 // unchanged.  Returns the counts in *n_anti_out / *n_new_out.
-// One dress by pair partition (k_pairjoin.cu): bin and tile counts (taken by
-// the A, B, C pass that preceded the dress, or here), split of H into the
-// other row buffer (commuting rows at offsets known per tile, anticommuting
-// rows copied into their bins), join behind the commuting rows; then the two
-// row buffers swap.  On IQCC_ERR_CAPACITY / OOM H is unchanged.  Returns the
-// counts in *n_anti_out / *n_new_out.
+// One dress by pair partition (k_pairjoin.cu), then the two row buffers swap.
+// When the A, B, C pass that preceded it counted the anticommuting rows and
+// the kept rows per tile (iqcc_iterate), the bins have a fixed size (the
+// mean count with a quarter and 32 rows of slack): the split takes each
+// row's slot in its bin and the join takes one bin per block, with no
+// counting pass.  Should a bin overflow (no hash spreads that unevenly by
+// chance), or without those counts, the bins are counted exactly
+// (k_pair_hist), scanned, and filled and joined as contiguous ranges.  The
+// split copies the commuting rows to the other row buffer at offsets known
+// per tile; the join writes behind them.  On IQCC_ERR_CAPACITY / OOM H is
+// unchanged.  Returns the counts in *n_anti_out / *n_new_out.
 iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, int64_t* n_new_out, float* ms_out) {
     const int64_t M = ctx->M;
     *n_anti_out = *n_new_out = 0;
@@ -408,10 +413,8 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     ctx->pair_ready = false;
     PairCounts pc = pair_counts_layout(ctx, M);
     const uint32_t NB = 1u << pc.log2_bins;
-    if (!ready) {
-        if (!ensure(ctx, ctx->pairbuf, pc.bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-        pc = pair_counts_layout(ctx, M);
-    }
+    if (!ensure(ctx, ctx->pairbuf, pc.bytes)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    pc = pair_counts_layout(ctx, M);
     Carver cv;
     cv.take<uint32_t>(1024);
     cv.take<unsigned long long>(1);
@@ -421,41 +424,86 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     unsigned long long* out_cursor = cv.take<unsigned long long>(1);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
     DevCounters* c = dctr(ctx);
-    CK(cudaMemsetAsync(out_cursor, 0, sizeof(unsigned long long), ctx->stream));
-    CK(cudaEventRecord(ctx->ev0, ctx->stream));
-    if (!ready) {
-        CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), ctx->stream));
-        CK(cudaMemsetAsync(pc.bins, 0, pc.bytes, ctx->stream));
-        launch_pair_hist(d, ctx->rows(), M, pc.log2_bins, pc.bins + 1, pc.tiles, c, ctx->stream, live_flags(ctx));
+    cudaStream_t s = ctx->stream;
+    CK(cudaMemsetAsync(out_cursor, 0, sizeof(unsigned long long), s));
+    CK(cudaEventRecord(ctx->ev0, s));
+    int64_t n_anti = 0;
+    uint32_t cap = 0;  // rows per fixed-size bin; 0: exact counts
+    auto count_exact = [&]() -> iqcc_status {
+        CK(cudaMemsetAsync(c, 0, 4 * sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(pc.bins, 0, pc.bytes, s));
+        launch_pair_hist(d, ctx->rows(), M, pc.log2_bins, pc.bins + 1, pc.tiles, c, s, live_flags(ctx));
+        launch_scan_u32_long(pc.bins + 1, NB, scan_tmp, s);
+        launch_scan_u32_long(pc.tiles, pc.n_tiles + 1, scan_tmp, s);
+        CK_LAUNCH();
+        iqcc_status st2 = read_counters(ctx);
+        if (st2) return st2;
+        n_anti = (int64_t)ctx->h_counters->n_anti;
+        cap = 0;
+        return IQCC_OK;
+    };
+    iqcc_status st = IQCC_OK;
+    if (ready) {
+        n_anti = ctx->pair_n_anti;
+        const double mean = (double)n_anti / (double)NB;
+        const double want = std::ceil(1.25 * mean) + 32.0;
+        if (want * (double)NB < 4.0e9) cap = (uint32_t)want;
+        launch_scan_u32_long(pc.tiles, pc.n_tiles + 1, scan_tmp, s);
+        CK_LAUNCH();
+        if (!cap) {
+            st = count_exact();
+            if (st) return st;
+        }
+    } else {
+        st = count_exact();
+        if (st) return st;
     }
-    launch_scan_u32_long(pc.bins + 1, NB, scan_tmp, ctx->stream);
-    launch_scan_u32_long(pc.tiles, pc.n_tiles + 1, scan_tmp, ctx->stream);
-    CK_LAUNCH();
-    iqcc_status st = read_counters(ctx);
-    if (st) return st;
-    const int64_t n_anti = ready ? ctx->pair_n_anti : (int64_t)ctx->h_counters->n_anti;
     *n_anti_out = n_anti;
     if (n_anti == 0) return apply_pending_cut(ctx);  // P commutes with every term
-    // bin copies of the anticommuting rows
+    // bin copies of the anticommuting rows: fixed-size bins when cap > 0
+    const size_t slots = cap ? (size_t)NB * cap : (size_t)n_anti;
     Carver rv;
-    rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
-    rv.take<double>(n_anti);
+    rv.take<uint64_t>(slots * 2 * ctx->Wd);
+    rv.take<double>(slots);
     if (!ensure(ctx, ctx->aux, rv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     rv = Carver{(char*)ctx->aux.p, 0};
-    uint64_t* rk = rv.take<uint64_t>((size_t)n_anti * 2 * ctx->Wd);
-    double* rc = rv.take<double>(n_anti);
+    uint64_t* rk = rv.take<uint64_t>(slots * 2 * ctx->Wd);
+    double* rc = rv.take<double>(slots);
     if (rv.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    const uint32_t bpb = pair_bins_per_block(n_anti, pc.log2_bins);
     const int64_t live = live_terms(ctx);  // the rows a pending cut keeps: the input of this dress
     const uint32_t* kept = pc.tiles + pc.n_tiles;  // rows the split keeps, after the scan
+    uint32_t* cursor = cap ? pc.bins : pc.bins + 1;   // fixed: per-bin counts from 0; exact: starts -> ends
+    auto bpb_now = [&]() { return cap ? 1u : pair_bins_per_block(n_anti, pc.log2_bins); };
+    // scatter only into the bins; with fixed-size bins an overflow falls back to exact bins
+    auto scatter = [&](bool compact, uint64_t* rows_out, double* coef_out) -> iqcc_status {
+        if (cap) {
+            CK(cudaMemsetAsync(pc.bins, 0, sizeof(uint32_t) * NB, s));
+            CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), s));
+        }
+        launch_pair_split(d, compact, true, ctx->rows(), ctx->c(), M, pc.log2_bins, cursor, cap, rk, rc, pc.tiles,
+                          rows_out, coef_out, c, s, live_flags(ctx));
+        CK_LAUNCH();
+        if (!cap) return IQCC_OK;
+        iqcc_status st2 = read_counters(ctx);
+        if (st2) return st2;
+        if (ctx->h_counters->aux == 0) return IQCC_OK;
+        // a bin overflowed: exact counts, contiguous bins, and the copy again
+        st2 = count_exact();
+        if (st2) return st2;
+        cursor = pc.bins + 1;
+        launch_pair_split(d, compact, true, ctx->rows(), ctx->c(), M, pc.log2_bins, cursor, 0, rk, rc, pc.tiles,
+                          rows_out, coef_out, c, s, live_flags(ctx));
+        CK_LAUNCH();
+        return IQCC_OK;
+    };
     bool scattered = false;
     int64_t need = live + n_anti;
     if (live + n_anti > ctx->capacity) {
         // exact admission: bin copies and a counting join first, H untouched
-        launch_pair_split(d, false, true, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.bins + 1, rk, rc, pc.tiles,
-                          nullptr, nullptr, ctx->stream, live_flags(ctx));
-        launch_pair_join(d, false, rk, rc, pc.bins, pc.log2_bins, bpb, nullptr, nullptr, kept, out_cursor, c,
-                         ctx->stream);
+        st = scatter(false, nullptr, nullptr);
+        if (st) return st;
+        launch_pair_join(d, false, rk, rc, pc.bins, pc.log2_bins, bpb_now(), nullptr, nullptr, kept, out_cursor, c, s,
+                         cap);
         CK_LAUNCH();
         st = read_counters(ctx);
         if (st) return st;
@@ -466,26 +514,32 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
                      (long long)ctx->capacity);
             return fail(ctx, IQCC_ERR_CAPACITY, buf);
         }
-        CK(cudaMemsetAsync(&c->n_new, 0, sizeof(unsigned long long), ctx->stream));
+        CK(cudaMemsetAsync(&c->n_new, 0, sizeof(unsigned long long), s));
         scattered = true;
     }
     st = ensure_second_rows(ctx, std::max<int64_t>(need, 1));
     if (st) return st;
     uint64_t* rows_out = (uint64_t*)ctx->keys2.p;
     double* coef_out = (double*)ctx->coef2.p;
-    launch_pair_split(d, true, !scattered, ctx->rows(), ctx->c(), M, pc.log2_bins, pc.bins + 1, rk, rc, pc.tiles,
-                      rows_out, coef_out, ctx->stream, live_flags(ctx));
-    launch_pair_join(d, true, rk, rc, pc.bins, pc.log2_bins, bpb, rows_out, coef_out, kept, out_cursor, c,
-                     ctx->stream);
+    if (scattered) {
+        launch_pair_split(d, true, false, ctx->rows(), ctx->c(), M, pc.log2_bins, cursor, cap, rk, rc, pc.tiles,
+                          rows_out, coef_out, c, s, live_flags(ctx));
+        CK_LAUNCH();
+    } else {
+        st = scatter(true, rows_out, coef_out);
+        if (st) return st;
+    }
+    launch_pair_join(d, true, rk, rc, pc.bins, pc.log2_bins, bpb_now(), rows_out, coef_out, kept, out_cursor, c, s,
+                     cap);
     CK_LAUNCH();
-    CK(cudaEventRecord(ctx->ev1, ctx->stream));
+    CK(cudaEventRecord(ctx->ev1, s));
     st = read_counters(ctx);
     if (st) return st;
     uint32_t mc = 0;
     unsigned long long oc = 0;
-    CK(cudaMemcpyAsync(&mc, kept, sizeof mc, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaMemcpyAsync(&oc, out_cursor, sizeof oc, cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    CK(cudaMemcpyAsync(&mc, kept, sizeof mc, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&oc, out_cursor, sizeof oc, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
     const int64_t n_new = (int64_t)ctx->h_counters->n_new;
     if ((int64_t)mc + n_anti != live || (int64_t)oc != n_anti + n_new)
         return fail(ctx, IQCC_ERR_STATE, "internal: pair dress row counts disagree");
@@ -1453,11 +1507,11 @@ static iqcc_status dress_pair_impl(iqcc_ctx* a, iqcc_ctx* b, const uint64_t* pk,
     st = ensure_second_rows(b, std::max<int64_t>(need_b, 1));
     if (st) return st;
     if (Ma)
-        launch_pair_split(d, true, true, a->rows(), a->c(), Ma, L, bins + 1, rk, rc, ta, (uint64_t*)a->keys2.p,
-                          (double*)a->coef2.p, s);
+        launch_pair_split(d, true, true, a->rows(), a->c(), Ma, L, bins + 1, 0, rk, rc, ta, (uint64_t*)a->keys2.p,
+                          (double*)a->coef2.p, ca, s);
     if (Mb)
-        launch_pair_split(d, true, true, b->rows(), b->c(), Mb, L, bins + 1, rk, rc, tb, (uint64_t*)b->keys2.p,
-                          (double*)b->coef2.p, s);
+        launch_pair_split(d, true, true, b->rows(), b->c(), Mb, L, bins + 1, 0, rk, rc, tb, (uint64_t*)b->keys2.p,
+                          (double*)b->coef2.p, cb, s);
     PairTwo two{};
     for (int w = 0; w < 2 * a->Wd; ++w) {
         two.mask[w] = dmask[w];

@@ -399,16 +399,20 @@ uint32_t pair_bins_per_block(int64_t n_anti, int log2_bins);
 void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int log2_bins, uint32_t* counts,
                       uint32_t* tile_kept, DevCounters* ctr, cudaStream_t s, const uint8_t* live = nullptr);
 // From rows/coef (M rows) into rows_out/coef_out: the kept rows of tile t from tile_off[t] on (compact);
-// rk [n_anti][2 Wd] keys and rc [n_anti] coefficients of the anticommuting rows, by bin (scatter;
-// cursor: bin starts in, bin ends out).
+// rk [.][2 Wd] keys and rc [.] coefficients of the anticommuting rows, by bin (scatter).  cap == 0:
+// cursor holds the bin starts (scanned exact counts) in, bin ends out.  cap > 0: bins of cap rows
+// (bin b at b cap), cursor zeroed in, rows received per bin out; rows past a full bin are counted in
+// ctr->aux and dropped (the caller then redoes the dress with exact counts).
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
-                       int64_t M, int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
-                       uint64_t* rows_out, double* coef_out, cudaStream_t s, const uint8_t* live = nullptr);
-// start: [2^log2_bins + 1] bin starts; rows without a partner counted in ctr->n_new; with `write` the
-// dressed rows and appended partners are written to rows/coef from row *kept + (*out_cursor, zeroed) on
+                       int64_t M, int log2_bins, uint32_t* cursor, uint32_t cap, uint64_t* rk, double* rc,
+                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
+                       cudaStream_t s, const uint8_t* live = nullptr);
+// start: [2^log2_bins + 1] bin starts (cap == 0) or the rows each fixed-size bin received (cap > 0,
+// one bin per block); rows without a partner counted in ctr->n_new; with `write` the dressed rows and
+// appended partners are written to rows/coef from row *kept + (*out_cursor, zeroed) on
 void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
                       int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef, const uint32_t* kept,
-                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s);
+                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s, uint32_t cap = 0);
 
 // Bins filled from two partitions of one Hamiltonian (one generator, d.gens == nullptr): the join
 // writes each output row to the partition owning its key.  mask, aval: device-layout keys; a key k

@@ -142,8 +142,9 @@ __device__ __forceinline__ bool abc_row(const Key<W>& t, const double* __restric
 
 // A, B, C for generator p (p = 0: energy in A).  HIST: the same pass also
 // counts, for the dress by p that follows (k_pairjoin.cu), the anticommuting
-// rows by dress bin and the commuting rows per tile of kDressTile rows (the
-// blocks then walk whole tiles); one read of the keys for both.
+// rows and the commuting rows per tile of kDressTile rows (the blocks then
+// walk whole tiles); one read of the keys for both.  The dress sizes its bins
+// from the first count and places the commuting rows by the second.
 template <int W, bool BASIS, bool HIST>
 __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ rows,
                                                   const double* __restrict__ coef, int64_t M, Key<W> p,
@@ -178,7 +179,6 @@ __global__ void __launch_bounds__(kThreads) k_abc(const uint64_t* __restrict__ r
                 k[r] = false;
                 if (!v[r]) continue;
                 if (abc_row<W, BASIS>(t[r], coef, i, p, yP, occ, s_tab, n_groups, acc)) {
-                    atomicAdd(&pc.counts[pair_hash<W>(t[r], p, pc.top_word, pc.top_mask) >> pc.shift], 1u);
                     ++n_anti;
                 } else {
                     k[r] = true;

@@ -116,15 +116,20 @@ __global__ void __launch_bounds__(kThreads) k_pair_hist(const uint64_t* __restri
 // those counts, so no block waits on another); SCATTER copies the
 // anticommuting rows (key, coefficient) to their bins, their positions taken
 // first so that the round trips of the four positions of a thread overlap
-// with the ranking of the kept rows.  cursor[b]: the start of bin b on entry,
-// its end on exit.  live (may be NULL): rows with live[i] == 0 (dropped by a
-// pending term-limit cut) are neither kept nor copied.
+// with the ranking of the kept rows.  cap == 0: cursor[b] is the start of
+// bin b on entry (an exclusive scan of exact counts), its end on exit.
+// cap > 0: bins of cap rows each (bin b at [b cap, (b + 1) cap)), cursor
+// zeroed on entry and holding the rows that came to each bin on exit; rows
+// past a full bin are counted in ctr->aux and not copied.  live (may be
+// NULL): rows with live[i] == 0 (dropped by a pending term-limit cut) are
+// neither kept nor copied.
 template <int W, class G, bool COMPACT, bool SCATTER>
 __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 1)) k_pair_split(const uint64_t* __restrict__ rows,
                                                          const double* __restrict__ coef, int64_t n, G gen_of,
-                                                         int shift, uint32_t* cursor, uint64_t* rk, double* rc,
-                                                         const uint32_t* __restrict__ tile_off, uint64_t* rows_out,
-                                                         double* coef_out, const uint8_t* __restrict__ live) {
+                                                         int shift, uint32_t* cursor, uint32_t cap, uint64_t* rk,
+                                                         double* rc, const uint32_t* __restrict__ tile_off,
+                                                         uint64_t* rows_out, double* coef_out,
+                                                         const uint8_t* __restrict__ live, DevCounters* ctr) {
     constexpr int kPer = kDressTile / kThreads;
     __shared__ uint32_t s_w[kThreads / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -152,8 +157,18 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 1)) k_pair_split(const
             const auto& g = gen_of(key[r]);
             anti[r] = anticommutes<W>(key[r], g.p);
             keep[r] = !anti[r];
-            if (SCATTER && anti[r])
-                pos[r] = atomicAdd(&cursor[pair_hash<W>(key[r], g.p, g.top_word, g.top_mask) >> shift], 1u);
+            if (SCATTER && anti[r]) {
+                const uint32_t bin = (uint32_t)(pair_hash<W>(key[r], g.p, g.top_word, g.top_mask) >> shift);
+                pos[r] = atomicAdd(&cursor[bin], 1u);
+                if (cap) {  // fixed-size bins: the bin's slot, or an overflow (the caller redoes the dress)
+                    if (pos[r] < cap) {
+                        pos[r] += bin * cap;
+                    } else {
+                        anti[r] = false;
+                        atomicAdd(&ctr->aux, 1ull);
+                    }
+                }
+            }
         }
     }
     if (COMPACT) {
@@ -195,7 +210,7 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 1)) k_pair_split(const
 // kJoinEmpty) and partner (all kNoPartner) are initialised by the caller.
 template <int W, class G>
 __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint32_t r0, int n, const G& gen_of,
-                                           uint32_t* table, uint16_t* partner) {
+                                           uint32_t* table, uint16_t* partner, uint32_t smask = kJoinSlots - 1) {
     volatile uint32_t* vt = table;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
         const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
@@ -204,8 +219,8 @@ __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint
         const Key<W> q = key_xor<W>(t, g.p);
         const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
         const uint32_t mine = tag | (uint32_t)i;
-        uint32_t s = (uint32_t)h & (kJoinSlots - 1);
-        for (int probe = 0; probe < kJoinSlots; ++probe) {
+        uint32_t s = (uint32_t)h & smask;
+        for (uint32_t probe = 0; probe <= smask; ++probe) {
             uint32_t v = vt[s];
             if (v == kJoinEmpty) {
                 v = atomicCAS(&table[s], kJoinEmpty, mine);
@@ -219,12 +234,14 @@ __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint
                     break;
                 }
             }
-            s = (s + 1) & (kJoinSlots - 1);
+            s = (s + 1) & smask;
         }
     }
 }
 
-// Block j joins bins [j*bpb, (j+1)*bpb): records [start[b0], start[b1]).
+// Block j joins bins [j*bpb, (j+1)*bpb): records [start[b0], start[b1]);
+// with cap > 0 (fixed-size bins) block j joins bin j alone: records
+// [j cap, j cap + min(start[j], cap)).
 // WRITE: the dressed rows go to rows/coef from *kept on (the commuting rows
 // end there), each block's at the position it reserves on out_cursor;
 // appended partners follow the block's own rows.  Always: the number of rows
@@ -234,28 +251,38 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
                                                         const uint32_t* __restrict__ start, uint32_t n_bins,
                                                         uint32_t bins_per_block, G gen_of, uint64_t* rows,
                                                         double* coef, const uint32_t* __restrict__ kept,
-                                                        unsigned long long* out_cursor, DevCounters* ctr) {
+                                                        unsigned long long* out_cursor, DevCounters* ctr,
+                                                        uint32_t cap) {
     __shared__ uint32_t table[kJoinSlots];
     __shared__ uint16_t partner[kJoinCap];
     __shared__ unsigned int s_single, s_app;
     __shared__ unsigned long long s_base;
-    const uint32_t b0 = blockIdx.x * bins_per_block;
-    const uint32_t b1 = min(b0 + bins_per_block, n_bins);
-    const uint32_t r0 = start[b0];
-    const int n = (int)(start[b1] - r0);
+    uint32_t r0;
+    int n;
+    if (cap) {  // fixed-size bins, one per block: start[] holds the rows each bin received
+        r0 = blockIdx.x * cap;
+        n = (int)min(start[blockIdx.x], cap);
+    } else {
+        const uint32_t b0 = blockIdx.x * bins_per_block;
+        const uint32_t b1 = min(b0 + bins_per_block, n_bins);
+        r0 = start[b0];
+        n = (int)(start[b1] - r0);
+    }
     if (n <= 0) return;
     if (n > kJoinCap) {  // far beyond any statistical fluctuation of a hash partition
         if (threadIdx.x == 0) set_error(ctr, IQCC_ERR_HASH_FULL, 70);
         return;
     }
-    for (int s = threadIdx.x; s < kJoinSlots; s += blockDim.x) table[s] = kJoinEmpty;
+    uint32_t slots = 64;  // a table of at least twice the rows, cleared only that far
+    while (slots < 2u * (uint32_t)n && slots < (uint32_t)kJoinSlots) slots *= 2;
+    for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) table[s] = kJoinEmpty;
     for (int s = threadIdx.x; s < n; s += blockDim.x) partner[s] = kNoPartner;
     if (threadIdx.x == 0) {
         s_single = 0;
         s_app = 0;
     }
     __syncthreads();
-    pair_match<W>(rk, r0, n, gen_of, table, partner);
+    pair_match<W>(rk, r0, n, gen_of, table, partner, slots - 1);
     __syncthreads();
     unsigned cnt = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) cnt += partner[i] == kNoPartner;
@@ -579,29 +606,29 @@ struct PairLaunch {
         k_pair_hist<W, G><<<grid, kThreads, 0, s>>>(rows, M, g, shift, counts, tile_kept, ctr, live);
     }
     static void split(const G& g, bool compact, bool scatter, const uint64_t* rows, const double* coef, int64_t M,
-                      int shift, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
-                      uint64_t* rows_out, double* coef_out, const uint8_t* live, cudaStream_t s) {
+                      int shift, uint32_t* cursor, uint32_t cap, uint64_t* rk, double* rc, const uint32_t* tile_off,
+                      uint64_t* rows_out, double* coef_out, const uint8_t* live, DevCounters* ctr, cudaStream_t s) {
         const unsigned nt = (unsigned)((M + kDressTile - 1) / kDressTile);
         if (compact && scatter)
-            k_pair_split<W, G, true, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, tile_off,
-                                                                    rows_out, coef_out, live);
+            k_pair_split<W, G, true, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, cap, rk, rc,
+                                                                    tile_off, rows_out, coef_out, live, ctr);
         else if (compact)
-            k_pair_split<W, G, true, false><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, tile_off,
-                                                                     rows_out, coef_out, live);
+            k_pair_split<W, G, true, false><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, cap, rk, rc,
+                                                                     tile_off, rows_out, coef_out, live, ctr);
         else
-            k_pair_split<W, G, false, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, rk, rc, tile_off,
-                                                                     rows_out, coef_out, live);
+            k_pair_split<W, G, false, true><<<nt, kThreads, 0, s>>>(rows, coef, M, g, shift, cursor, cap, rk, rc,
+                                                                     tile_off, rows_out, coef_out, live, ctr);
     }
     static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
                      uint32_t n_bins, uint32_t bpb, uint64_t* rows, double* coef, const uint32_t* kept,
-                     unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s) {
-        const unsigned blocks = (n_bins + bpb - 1) / bpb;
+                     unsigned long long* out_cursor, DevCounters* ctr, uint32_t cap, cudaStream_t s) {
+        const unsigned blocks = cap ? n_bins : (n_bins + bpb - 1) / bpb;
         if (write)
             k_pair_join<W, G, true><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, kept,
-                                                                 out_cursor, ctr);
+                                                                 out_cursor, ctr, cap);
         else
             k_pair_join<W, G, false><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, kept,
-                                                                  out_cursor, ctr);
+                                                                  out_cursor, ctr, cap);
     }
 };
 
@@ -669,22 +696,23 @@ void launch_pair_hist(const PairDress& d, const uint64_t* rows, int64_t M, int l
 }
 
 void launch_pair_split(const PairDress& d, bool compact, bool scatter, const uint64_t* rows, const double* coef,
-                       int64_t M, int log2_bins, uint32_t* cursor, uint64_t* rk, double* rc, const uint32_t* tile_off,
-                       uint64_t* rows_out, double* coef_out, cudaStream_t s, const uint8_t* live) {
+                       int64_t M, int log2_bins, uint32_t* cursor, uint32_t cap, uint64_t* rk, double* rc,
+                       const uint32_t* tile_off, uint64_t* rows_out, double* coef_out, DevCounters* ctr,
+                       cudaStream_t s, const uint8_t* live) {
     if (M <= 0 || !(compact || scatter)) return;
     with_provider(d, [&](auto L, auto g) {
-        decltype(L)::split(g, compact, scatter, rows, coef, M, 64 - log2_bins, cursor, rk, rc, tile_off, rows_out,
-                           coef_out, live, s);
+        decltype(L)::split(g, compact, scatter, rows, coef, M, 64 - log2_bins, cursor, cap, rk, rc, tile_off,
+                           rows_out, coef_out, live, ctr, s);
     });
     note_launch();
 }
 
 void launch_pair_join(const PairDress& d, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
                       int log2_bins, uint32_t bins_per_block, uint64_t* rows, double* coef, const uint32_t* kept,
-                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s) {
+                      unsigned long long* out_cursor, DevCounters* ctr, cudaStream_t s, uint32_t cap) {
     const uint32_t n_bins = 1u << log2_bins;
     with_provider(d, [&](auto L, auto g) {
-        decltype(L)::join(g, write, rk, rc, start, n_bins, bins_per_block, rows, coef, kept, out_cursor, ctr, s);
+        decltype(L)::join(g, write, rk, rc, start, n_bins, bins_per_block, rows, coef, kept, out_cursor, ctr, cap, s);
     });
     note_launch();
 }
