@@ -341,9 +341,22 @@ typedef struct {
     double screen_ms;          /* device time of that scoring (CUDA events) */
     int words;                 /* device words per x or z vector (1, 2 or 4) */
     int pad;
+    int64_t fixed_bin_dresses; /* dresses whose bins were sized from the A,B,C pass's count */
+    int64_t bin_overflows;     /* of those, dresses redone with exact bins after a bin overflowed */
 } iqcc_stats;
 
 iqcc_status iqcc_get_stats(const iqcc_ctx* ctx, iqcc_stats* out);
+
+/*
+ * Size of the dress's fixed bins inside iqcc_iterate: a bin holds
+ * ceil((1 + frac) * mean) + rows anticommuting rows, mean being the count of
+ * the A,B,C pass over the bins (defaults 0.25 and 32: a bin overflows only
+ * when the hash spreads far more unevenly than chance allows).  A dress whose
+ * bin overflows is redone with exact bins (stats.bin_overflows), so the
+ * result does not depend on these values; small ones trade memory for that
+ * second pass.  Errors: IQCC_ERR_ARG (frac < 0 or not finite, rows < 0).
+ */
+iqcc_status iqcc_set_bin_slack(iqcc_ctx* ctx, double frac, int rows);
 iqcc_status iqcc_reset_stats(iqcc_ctx* ctx);
 
 /*

@@ -446,8 +446,9 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     if (ready) {
         n_anti = ctx->pair_n_anti;
         const double mean = (double)n_anti / (double)NB;
-        const double want = std::ceil(1.25 * mean) + 32.0;
-        if (want * (double)NB < 4.0e9) cap = (uint32_t)want;
+        const double want = std::ceil((1.0 + ctx->bin_slack) * mean) + (double)ctx->bin_slack_rows;
+        if (want * (double)NB < 4.0e9 && want <= 4096.0) cap = (uint32_t)want;
+        if (cap) ctx->stats.fixed_bin_dresses++;
         launch_scan_u32_long(pc.tiles, pc.n_tiles + 1, scan_tmp, s);
         CK_LAUNCH();
         if (!cap) {
@@ -488,6 +489,7 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
         if (st2) return st2;
         if (ctx->h_counters->aux == 0) return IQCC_OK;
         // a bin overflowed: exact counts, contiguous bins, and the copy again
+        ctx->stats.bin_overflows++;
         st2 = count_exact();
         if (st2) return st2;
         cursor = pc.bins + 1;
@@ -2125,6 +2127,14 @@ iqcc_status iqcc_set_wait_limit(iqcc_ctx* ctx, int polls) {
     CK(cudaMemcpyAsync((char*)ctx->counters.p + offsetof(DevCounters, wait_limit), &ctx->h_counters->wait_limit,
                        sizeof(int), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    return IQCC_OK;
+}
+
+iqcc_status iqcc_set_bin_slack(iqcc_ctx* ctx, double frac, int rows) {
+    GUARD(ctx);
+    if (!std::isfinite(frac) || frac < 0.0 || rows < 0) return fail(ctx, IQCC_ERR_ARG, "bin slack out of range");
+    ctx->bin_slack = frac;
+    ctx->bin_slack_rows = rows;
     return IQCC_OK;
 }
 

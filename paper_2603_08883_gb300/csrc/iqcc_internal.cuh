@@ -286,6 +286,8 @@ struct iqcc_ctx {
     iqcc::Buf model;               // learned screening weights (device layout), when set
     iqcc::Buf screen_rank;         // learned screening: per-row keys and the <sigma> table
     double screen_floor = 0.5;     // learned term limit: share kept by largest |C| first
+    double bin_slack = 0.25;       // fixed dress bins: relative slack over the mean count
+    int bin_slack_rows = 32;       //   and rows added to it
 
     uint64_t* rows() const { return (uint64_t*)keys.p; }
     double* c() const { return (double*)coef.p; }

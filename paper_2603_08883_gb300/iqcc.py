@@ -69,7 +69,7 @@ class iqcc_stats(ctypes.Structure):
                 ("hash_slots", ctypes.c_int64), ("kernel_launches", ctypes.c_int64),
                 ("n_sorted_groups", ctypes.c_int64), ("sorted_dress_ms", ctypes.c_double),
                 ("screen_terms", ctypes.c_int64), ("screen_ms", ctypes.c_double), ("words", ctypes.c_int),
-                ("pad", ctypes.c_int)]
+                ("pad", ctypes.c_int), ("fixed_bin_dresses", ctypes.c_int64), ("bin_overflows", ctypes.c_int64)]
 
 
 def _sig(name, res, args):
@@ -118,6 +118,7 @@ _iterate = _sig("iqcc_iterate", _c, [_vp, _f64p, _f64p, ctypes.POINTER(iqcc_iter
 _num = _sig("iqcc_num_terms", _c, [_vp, _i64p])
 _export = _sig("iqcc_export", _c, [_vp, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
 _export_rows = _sig("iqcc_export_rows", _c, [_vp, ctypes.c_int64, _i64p, _u64p, _u64p, _f64p])
+_bin_slack = _sig("iqcc_set_bin_slack", _c, [_vp, ctypes.c_double, ctypes.c_int])
 _stats = _sig("iqcc_get_stats", _c, [_vp, ctypes.POINTER(iqcc_stats)])
 _reset = _sig("iqcc_reset_stats", _c, [_vp])
 _err = _sig("iqcc_last_error", ctypes.c_char_p, [_vp])
@@ -504,6 +505,10 @@ def iqcc_export_rows(H: Hamiltonian, out=None):
     H._check(_export_rows(H._h, m, ctypes.byref(n), x.ctypes.data_as(_u64p), z.ctypes.data_as(_u64p),
                           c.ctypes.data_as(_f64p)))
     return x[:m], z[:m], c[:m]
+
+
+def iqcc_set_bin_slack(H: Hamiltonian, frac: float, rows: int) -> None:
+    H._check(_bin_slack(H._h, float(frac), int(rows)))
 
 
 def iqcc_get_stats(H: Hamiltonian) -> dict:

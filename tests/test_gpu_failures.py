@@ -126,3 +126,31 @@ def test_group_table_full_then_context_refuses():
     assert e.value.status == STATE
     batch.close()
     _fresh_context_still_works()
+
+
+def test_overflowing_fixed_bins_redo_the_dress_exactly():
+    """Inside iqcc_iterate the dress bins are sized from the A,B,C pass's
+    count.  With no slack (each bin holds exactly the mean), bins overflow and
+    the dress is redone with exact bins: the iteration must end on the same
+    Hamiltonian, bit for bit, as with the default slack."""
+    n = 100
+    _, x, z, c = synth.random_hamiltonian(n, 150_000, 61, density=0.15)
+    th, ph = synth.qmf_angles(n, "basis", seed=61)
+    out = []
+    for slack in ((0.25, 32), (0.0, 0)):
+        H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 24)
+        iqcc.iqcc_set_bin_slack(H, *slack)
+        iqcc.iqcc_reset_stats(H)
+        iqcc.iqcc_iterate(H, th, ph, 4, 1e-10, 400_000)
+        st = iqcc.iqcc_get_stats(H)
+        out.append((iqcc.iqcc_export(H), st))
+        H.close()
+    (ref, st0), (got, st1) = out
+    assert st0["fixed_bin_dresses"] > 0 and st0["bin_overflows"] == 0
+    assert st1["bin_overflows"] > 0
+    for a, b in zip(got, ref):
+        assert np.array_equal(a, b)
+    with pytest.raises(iqcc.IqccError) as e:
+        H = iqcc.iqcc_load_hamiltonian(n, x[:10], z[:10], c[:10])
+        iqcc.iqcc_set_bin_slack(H, -0.1, 0)
+    assert e.value.status == 1
