@@ -474,7 +474,14 @@ iqcc_status dress_pairs(iqcc_ctx* ctx, const PairDress& d, int64_t* n_anti_out, 
     const int64_t live = live_terms(ctx);  // the rows a pending cut keeps: the input of this dress
     const uint32_t* kept = pc.tiles + pc.n_tiles;  // rows the split keeps, after the scan
     uint32_t* cursor = cap ? pc.bins : pc.bins + 1;   // fixed: per-bin counts from 0; exact: starts -> ends
-    auto bpb_now = [&]() { return cap ? 1u : pair_bins_per_block(n_anti, pc.log2_bins); };
+    // fixed bins: up to 4 per join block, about 2048 rows and at most 4096 in all
+    auto bpb_now = [&]() {
+        if (!cap) return pair_bins_per_block(n_anti, pc.log2_bins);
+        const double mean = (double)n_anti / (double)NB;
+        uint32_t b = 1;
+        while (b < 4 && 2.0 * b * mean <= 2048.0 && 2 * b * cap <= 4096) b *= 2;
+        return b;
+    };
     // scatter only into the bins; with fixed-size bins an overflow falls back to exact bins
     auto scatter = [&](bool compact, uint64_t* rows_out, double* coef_out) -> iqcc_status {
         if (cap) {

@@ -202,18 +202,35 @@ __global__ void __launch_bounds__(kThreads, (W <= 2 ? 4 : 1)) k_pair_split(const
     }
 }
 
-// Matches the n rows rk[r0, r0 + n) by pair key in a shared-memory table:
+// Where the join's local row i lives in the bin copies: one contiguous range
+// (exact bins), or up to kMaxGroupBins fixed-size bins (range k holds local
+// rows [pre[k], pre[k + 1]) from base[k] on).
+constexpr int kMaxGroupBins = 4;
+struct BinRows {
+    uint32_t base[kMaxGroupBins];
+    uint32_t pre[kMaxGroupBins + 1];
+    int nb;
+    __device__ __forceinline__ int64_t operator()(int i) const {
+        int k = 0;
+#pragma unroll
+        for (int q = 1; q < kMaxGroupBins; ++q) k += (q < nb && (uint32_t)i >= pre[q]) ? 1 : 0;
+        return (int64_t)base[k] + ((uint32_t)i - pre[k]);
+    }
+};
+
+// Matches the n rows rk[at(0)], ..., rk[at(n - 1)] by pair key in a shared-memory table:
 // partner[i] = j for the two members of a present pair, kNoPartner otherwise.
 // Both members of a pair probe the same slot sequence; the first inserts
 // itself at the first empty slot, the second meets it there (every slot
 // before it stays occupied) and links the two.  table (kJoinSlots, all
 // kJoinEmpty) and partner (all kNoPartner) are initialised by the caller.
 template <int W, class G>
-__device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint32_t r0, int n, const G& gen_of,
-                                           uint32_t* table, uint16_t* partner, uint32_t smask = kJoinSlots - 1) {
+__device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, const BinRows& at, int n,
+                                           const G& gen_of, uint32_t* table, uint16_t* partner,
+                                           uint32_t smask = kJoinSlots - 1) {
     volatile uint32_t* vt = table;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
+        const Key<W> t = load_key<W>(rk, at(i));
         const auto& g = gen_of(t);
         const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
         const Key<W> q = key_xor<W>(t, g.p);
@@ -228,7 +245,7 @@ __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint
             }
             if ((v & 0xFFFF0000u) == tag) {
                 const int j = (int)(v & 0xFFFFu);
-                if (key_equal<W>(load_key<W>(rk, (int64_t)r0 + j), q)) {
+                if (key_equal<W>(load_key<W>(rk, at(j)), q)) {
                     partner[i] = (uint16_t)j;
                     partner[j] = (uint16_t)i;
                     break;
@@ -240,8 +257,8 @@ __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, uint
 }
 
 // Block j joins bins [j*bpb, (j+1)*bpb): records [start[b0], start[b1]);
-// with cap > 0 (fixed-size bins) block j joins bin j alone: records
-// [j cap, j cap + min(start[j], cap)).
+// with cap > 0 (fixed-size bins, bpb <= kMaxGroupBins) the records
+// [b cap, b cap + min(start[b], cap)) of each of its bins.
 // WRITE: the dressed rows go to rows/coef from *kept on (the commuting rows
 // end there), each block's at the position it reserves on out_cursor;
 // appended partners follow the block's own rows.  Always: the number of rows
@@ -257,16 +274,25 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
     __shared__ uint16_t partner[kJoinCap];
     __shared__ unsigned int s_single, s_app;
     __shared__ unsigned long long s_base;
-    uint32_t r0;
-    int n;
-    if (cap) {  // fixed-size bins, one per block: start[] holds the rows each bin received
-        r0 = blockIdx.x * cap;
-        n = (int)min(start[blockIdx.x], cap);
+    BinRows at;
+    int n = 0;
+    const uint32_t b0 = blockIdx.x * bins_per_block;
+    const uint32_t b1 = min(b0 + bins_per_block, n_bins);
+    if (cap) {  // fixed-size bins (at most kMaxGroupBins): start[] holds the rows each bin received
+        at.nb = (int)(b1 - b0);
+        for (int k = 0; k < kMaxGroupBins; ++k) {
+            const uint32_t b = b0 + (uint32_t)k;
+            at.pre[k] = (uint32_t)n;
+            at.base[k] = b * cap;
+            if (k < at.nb) n += (int)min(start[b], cap);
+        }
+        at.pre[kMaxGroupBins] = (uint32_t)n;
     } else {
-        const uint32_t b0 = blockIdx.x * bins_per_block;
-        const uint32_t b1 = min(b0 + bins_per_block, n_bins);
-        r0 = start[b0];
-        n = (int)(start[b1] - r0);
+        at.nb = 1;
+        at.base[0] = start[b0];
+        at.pre[0] = 0;
+        n = (int)(start[b1] - start[b0]);
+        for (int k = 1; k <= kMaxGroupBins; ++k) at.pre[k] = (uint32_t)n;
     }
     if (n <= 0) return;
     if (n > kJoinCap) {  // far beyond any statistical fluctuation of a hash partition
@@ -282,7 +308,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
         s_app = 0;
     }
     __syncthreads();
-    pair_match<W>(rk, r0, n, gen_of, table, partner, slots - 1);
+    pair_match<W>(rk, at, n, gen_of, table, partner, slots - 1);
     __syncthreads();
     unsigned cnt = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) cnt += partner[i] == kNoPartner;
@@ -299,15 +325,15 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
     __syncthreads();
     const int64_t base = (int64_t)s_base;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Key<W> t = load_key<W>(rk, (int64_t)r0 + i);
+        const Key<W> t = load_key<W>(rk, at(i));
         const auto& g = gen_of(t);
         const Key<W> q = key_xor<W>(t, g.p);
         const double sg = (double)product_sign<W>(t, g.yP, g.p, q);
-        const double ct = rc[r0 + i];
+        const double ct = rc[at(i)];
         const int p = partner[i];
         double cn;
         if (p != kNoPartner) {
-            cn = ct * g.cos_t - sg * rc[r0 + p] * g.sin_t;
+            cn = ct * g.cos_t - sg * rc[at(p)] * g.sin_t;
         } else {
             cn = ct * g.cos_t;
             const int64_t r = base + n + (int64_t)atomicAdd(&s_app, 1u);
@@ -368,7 +394,11 @@ __global__ void __launch_bounds__(kThreads) k_pair_join2(const uint64_t* __restr
     }
     if (threadIdx.x == 0) s_single = 0;
     __syncthreads();
-    pair_match<W>(rk, r0, n, gen_of, table, partner);
+    BinRows at;
+    at.nb = 1;
+    at.base[0] = r0;
+    for (int k = 0; k <= kMaxGroupBins; ++k) at.pre[k] = k ? (uint32_t)n : 0u;
+    pair_match<W>(rk, at, n, gen_of, table, partner);
     __syncthreads();
     unsigned c[2] = {0, 0}, single = 0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -622,7 +652,7 @@ struct PairLaunch {
     static void join(const G& g, bool write, const uint64_t* rk, const double* rc, const uint32_t* start,
                      uint32_t n_bins, uint32_t bpb, uint64_t* rows, double* coef, const uint32_t* kept,
                      unsigned long long* out_cursor, DevCounters* ctr, uint32_t cap, cudaStream_t s) {
-        const unsigned blocks = cap ? n_bins : (n_bins + bpb - 1) / bpb;
+        const unsigned blocks = (n_bins + bpb - 1) / bpb;
         if (write)
             k_pair_join<W, G, true><<<blocks, kThreads, 0, s>>>(rk, rc, start, n_bins, bpb, g, rows, coef, kept,
                                                                  out_cursor, ctr, cap);
