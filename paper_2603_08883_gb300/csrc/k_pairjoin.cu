@@ -299,8 +299,8 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
         if (threadIdx.x == 0) set_error(ctr, IQCC_ERR_HASH_FULL, 70);
         return;
     }
-    uint32_t slots = 64;  // a table of at least twice the rows, cleared only that far
-    while (slots < 2u * (uint32_t)n && slots < (uint32_t)kJoinSlots) slots *= 2;
+    uint32_t slots = 64;  // a table of at least four times the rows (up to kJoinSlots), cleared only that far
+    while (slots < 4u * (uint32_t)n && slots < (uint32_t)kJoinSlots) slots *= 2;
     for (uint32_t s = threadIdx.x; s < slots; s += blockDim.x) table[s] = kJoinEmpty;
     for (int s = threadIdx.x; s < n; s += blockDim.x) partner[s] = kNoPartner;
     if (threadIdx.x == 0) {
