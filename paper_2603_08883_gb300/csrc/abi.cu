@@ -826,9 +826,7 @@ iqcc_status dis_enumerate(iqcc_ctx* ctx, const double* theta, const double* phi,
     const int nblk = expect_blocks();
     constexpr int64_t kHeadLimit = 1 << 16;  // the top-k path orders at most this many candidates
     ctx->pair_ready = false;                 // the bins below reuse the dress-bin buffer
-    // flip-set bins of at most about 512 rows on average (a quarter of the dress's), so that
-    // a join block's table of 2048 flip sets holds all of them with room to spare
-    const int lb = std::min(pair_bins_log2(M) + 2, 28);
+    const int lb = pair_bins_log2(M);
     const uint32_t NB = 1u << lb;
     Carver cv;
     cv.take<uint32_t>(1024);

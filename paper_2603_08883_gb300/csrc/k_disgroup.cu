@@ -25,8 +25,8 @@ namespace iqcc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSlots = 2048;       // distinct flip sets one join block can hold (at most about 512 expected)
-constexpr int kTarget = 512;       // rows per join block on average: a 32 KB table, six blocks per SM
+constexpr int kSlots = 4096;       // distinct flip sets one join block can hold (about 1024 expected)
+constexpr int kTarget = 1024;      // rows per join block on average
 
 template <int W>
 __device__ __forceinline__ bool has_flips(const Key<W>& t) {
@@ -137,10 +137,9 @@ __global__ void __launch_bounds__(kThreads) k_flip_scatter(const uint64_t* __res
 
 // Block j: bins [j*bpb, (j+1)*bpb), rows [start[b0], start[b1]) of the copies.
 // A group (one flip set) may hold any number of rows, so the shared-memory
-// table bounds the distinct flip sets of a block (at most its rows: about
-// kTarget = kSlots / 4 on average, which the bin sizing keeps), not its rows:
-// every slot holds the first row of its group (tag and index) and the group's
-// sum.
+// table bounds the distinct flip sets of a block (kSlots / 2 on average,
+// which the bin sizing keeps), not its rows: every slot holds the first row of
+// its group (tag and index) and the group's sum.
 template <int W, bool VALUES>
 __global__ void __launch_bounds__(kThreads) k_flip_join(const uint64_t* __restrict__ rr,
                                                         const uint32_t* __restrict__ start, uint32_t n_bins,
