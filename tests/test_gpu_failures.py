@@ -128,14 +128,14 @@ def test_group_table_full_then_context_refuses():
     _fresh_context_still_works()
 
 
-def test_overflowing_fixed_bins_redo_the_dress_exactly():
+@pytest.mark.parametrize("n", [24, 100, 200])
+def test_overflowing_fixed_bins_redo_the_dress_exactly(n):
     """Inside iqcc_iterate the dress bins are sized from the A,B,C pass's
     count.  With no slack (each bin holds exactly the mean), bins overflow and
     the dress is redone with exact bins: the iteration must end on the same
-    Hamiltonian, bit for bit, as with the default slack."""
-    n = 100
-    _, x, z, c = synth.random_hamiltonian(n, 150_000, 61, density=0.15)
-    th, ph = synth.qmf_angles(n, "basis", seed=61)
+    Hamiltonian, bit for bit, as with the default slack (key words 1, 2, 4)."""
+    _, x, z, c = synth.random_hamiltonian(n, 150_000, 61 + n, density=min(0.5, 15 / n))
+    th, ph = synth.qmf_angles(n, "basis", seed=61 + n)
     out = []
     for slack in ((0.25, 32), (0.0, 0)):
         H = iqcc.iqcc_load_hamiltonian(n, x, z, c, capacity=1 << 24)
