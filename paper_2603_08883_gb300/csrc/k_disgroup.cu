@@ -75,11 +75,11 @@ struct Occ {
     uint64_t w[W];
 };
 
-// A bin record: the flip set (W words), the contribution, zero padding to
-// whole 32-byte sectors (W = 1, 2: 32 B; W = 4: 64 B), so that the scattered
-// writes fill whole sectors.
+// A bin record: the flip set (W words), the contribution, the flip set's
+// hash, zero padding to whole 32-byte sectors (W = 1, 2: 32 B; W = 4: 64 B),
+// so that the scattered writes fill whole sectors.
 template <int W>
-constexpr int frec_words() { return (W + 1 + 3) / 4 * 4; }
+constexpr int frec_words() { return (W + 2 + 3) / 4 * 4; }
 
 template <int W>
 __global__ void __launch_bounds__(kThreads) k_flip_hist(const uint64_t* __restrict__ rows, int64_t M, int shift,
@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_scatter(const uint64_t* __res
 #pragma unroll
             for (int j = 0; j < W; ++j) w[j] = t[r].x[j];
             if (VALUES) w[W] = (uint64_t)__double_as_longlong(basis_contribution<W>(t[r], coef[i0 + r], occ.w));
+            w[W + 1] = flip_hash<W>(t[r].x);  // for the join, which would otherwise hash the flip set again
             ulonglong2* d = reinterpret_cast<ulonglong2*>(rr + (size_t)p[r] * R);
 #pragma unroll
             for (int j = 0; j < R / 2; ++j) d[j] = make_ulonglong2(w[2 * j], w[2 * j + 1]);
@@ -168,7 +169,7 @@ __global__ void __launch_bounds__(kThreads) k_flip_join(const uint64_t* __restri
         uint64_t x[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) x[j] = rr[(size_t)(r0 + i) * R + j];
-        const uint64_t h = flip_hash<W>(x);
+        const uint64_t h = rr[(size_t)(r0 + i) * R + W + 1];  // the flip set's hash, stored by the scatter
         const unsigned long long mine = (h & 0xFFFFFFFF00000000ull) | (unsigned long long)(uint32_t)i;
         uint32_t s = (uint32_t)h & (kSlots - 1);
         int probe = 0;
