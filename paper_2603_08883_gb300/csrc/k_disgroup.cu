@@ -85,11 +85,17 @@ template <int W>
 __global__ void __launch_bounds__(kThreads) k_flip_hist(const uint64_t* __restrict__ rows, int64_t M, int shift,
                                                         uint32_t* counts, DevCounters* ctr) {
     unsigned n = 0;
+    constexpr int kU = 4;  // rows per thread whose keys are in flight together
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
-        const Key<W> t = load_key<W>(rows, i);
-        if (has_flips<W>(t)) {
-            atomicAdd(&counts[flip_hash<W>(t.x) >> shift], 1u);
+    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += stride * kU) {
+        Key<W> t[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * stride < M) t[u] = load_key<W>(rows, i0 + u * stride);
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            if (i0 + u * stride >= M || !has_flips<W>(t[u])) continue;
+            atomicAdd(&counts[flip_hash<W>(t[u].x) >> shift], 1u);
             ++n;
         }
     }
