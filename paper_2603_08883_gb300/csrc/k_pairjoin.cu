@@ -229,29 +229,39 @@ __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, cons
                                            const G& gen_of, uint32_t* table, uint16_t* partner,
                                            uint32_t smask = kJoinSlots - 1) {
     volatile uint32_t* vt = table;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Key<W> t = load_key<W>(rk, at(i));
-        const auto& g = gen_of(t);
-        const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
-        const Key<W> q = key_xor<W>(t, g.p);
-        const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
-        const uint32_t mine = tag | (uint32_t)i;
-        uint32_t s = (uint32_t)h & smask;
-        for (uint32_t probe = 0; probe <= smask; ++probe) {
-            uint32_t v = vt[s];
-            if (v == kJoinEmpty) {
-                v = atomicCAS(&table[s], kJoinEmpty, mine);
-                if (v == kJoinEmpty) break;
-            }
-            if ((v & 0xFFFF0000u) == tag) {
-                const int j = (int)(v & 0xFFFFu);
-                if (key_equal<W>(load_key<W>(rk, at(j)), q)) {
-                    partner[i] = (uint16_t)j;
-                    partner[j] = (uint16_t)i;
-                    break;
+    constexpr int kU = 4;  // rows per thread whose keys are in flight together
+    for (int i0 = threadIdx.x; i0 < n; i0 += blockDim.x * kU) {
+        Key<W> tk[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u)
+            if (i0 + u * (int)blockDim.x < n) tk[u] = load_key<W>(rk, at(i0 + u * (int)blockDim.x));
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i >= n) break;
+            const Key<W>& t = tk[u];
+            const auto& g = gen_of(t);
+            const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
+            const Key<W> q = key_xor<W>(t, g.p);
+            const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
+            const uint32_t mine = tag | (uint32_t)i;
+            uint32_t s = (uint32_t)h & smask;
+            for (uint32_t probe = 0; probe <= smask; ++probe) {
+                uint32_t v = vt[s];
+                if (v == kJoinEmpty) {
+                    v = atomicCAS(&table[s], kJoinEmpty, mine);
+                    if (v == kJoinEmpty) break;
                 }
+                if ((v & 0xFFFF0000u) == tag) {
+                    const int j = (int)(v & 0xFFFFu);
+                    if (key_equal<W>(load_key<W>(rk, at(j)), q)) {
+                        partner[i] = (uint16_t)j;
+                        partner[j] = (uint16_t)i;
+                        break;
+                    }
+                }
+                s = (s + 1) & smask;
             }
-            s = (s + 1) & smask;
         }
     }
 }
