@@ -334,24 +334,40 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
     if (!WRITE) return;
     __syncthreads();
     const int64_t base = (int64_t)s_base;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const Key<W> t = load_key<W>(rk, at(i));
-        const auto& g = gen_of(t);
-        const Key<W> q = key_xor<W>(t, g.p);
-        const double sg = (double)product_sign<W>(t, g.yP, g.p, q);
-        const double ct = rc[at(i)];
-        const int p = partner[i];
-        double cn;
-        if (p != kNoPartner) {
-            cn = ct * g.cos_t - sg * rc[at(p)] * g.sin_t;
-        } else {
-            cn = ct * g.cos_t;
-            const int64_t r = base + n + (int64_t)atomicAdd(&s_app, 1u);
-            store_key<W>(rows, r, q);
-            coef[r] = sg * ct * g.sin_t;
+    constexpr int kU = 4;  // rows per thread whose keys and coefficients are in flight together
+    for (int i0 = threadIdx.x; i0 < n; i0 += blockDim.x * kU) {
+        Key<W> tk[kU];
+        double ck[kU], cp[kU];
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i >= n) continue;
+            tk[u] = load_key<W>(rk, at(i));
+            ck[u] = rc[at(i)];
+            const int p = partner[i];
+            cp[u] = p != kNoPartner ? rc[at(p)] : 0.0;
         }
-        store_key<W>(rows, base + i, t);
-        coef[base + i] = cn;
+#pragma unroll
+        for (int u = 0; u < kU; ++u) {
+            const int i = i0 + u * (int)blockDim.x;
+            if (i >= n) break;
+            const Key<W>& t = tk[u];
+            const auto& g = gen_of(t);
+            const Key<W> q = key_xor<W>(t, g.p);
+            const double sg = (double)product_sign<W>(t, g.yP, g.p, q);
+            const double ct = ck[u];
+            double cn;
+            if (partner[i] != kNoPartner) {
+                cn = ct * g.cos_t - sg * cp[u] * g.sin_t;
+            } else {
+                cn = ct * g.cos_t;
+                const int64_t r = base + n + (int64_t)atomicAdd(&s_app, 1u);
+                store_key<W>(rows, r, q);
+                coef[r] = sg * ct * g.sin_t;
+            }
+            store_key<W>(rows, base + i, t);
+            coef[base + i] = cn;
+        }
     }
 }
 
