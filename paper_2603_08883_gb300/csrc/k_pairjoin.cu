@@ -334,7 +334,7 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
     if (!WRITE) return;
     __syncthreads();
     const int64_t base = (int64_t)s_base;
-    constexpr int kU = 4;  // rows per thread whose keys and coefficients are in flight together
+    constexpr int kU = 2;  // rows per thread whose keys and coefficients are in flight together
     for (int i0 = threadIdx.x; i0 < n; i0 += blockDim.x * kU) {
         Key<W> tk[kU];
         double ck[kU], cp[kU];
