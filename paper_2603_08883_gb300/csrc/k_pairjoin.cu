@@ -229,39 +229,29 @@ __device__ __forceinline__ void pair_match(const uint64_t* __restrict__ rk, cons
                                            const G& gen_of, uint32_t* table, uint16_t* partner,
                                            uint32_t smask = kJoinSlots - 1) {
     volatile uint32_t* vt = table;
-    constexpr int kU = 4;  // rows per thread whose keys are in flight together
-    for (int i0 = threadIdx.x; i0 < n; i0 += blockDim.x * kU) {
-        Key<W> tk[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (i0 + u * (int)blockDim.x < n) tk[u] = load_key<W>(rk, at(i0 + u * (int)blockDim.x));
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int i = i0 + u * (int)blockDim.x;
-            if (i >= n) break;
-            const Key<W>& t = tk[u];
-            const auto& g = gen_of(t);
-            const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
-            const Key<W> q = key_xor<W>(t, g.p);
-            const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
-            const uint32_t mine = tag | (uint32_t)i;
-            uint32_t s = (uint32_t)h & smask;
-            for (uint32_t probe = 0; probe <= smask; ++probe) {
-                uint32_t v = vt[s];
-                if (v == kJoinEmpty) {
-                    v = atomicCAS(&table[s], kJoinEmpty, mine);
-                    if (v == kJoinEmpty) break;
-                }
-                if ((v & 0xFFFF0000u) == tag) {
-                    const int j = (int)(v & 0xFFFFu);
-                    if (key_equal<W>(load_key<W>(rk, at(j)), q)) {
-                        partner[i] = (uint16_t)j;
-                        partner[j] = (uint16_t)i;
-                        break;
-                    }
-                }
-                s = (s + 1) & smask;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Key<W> t = load_key<W>(rk, at(i));
+        const auto& g = gen_of(t);
+        const uint64_t h = pair_hash<W>(t, g.p, g.top_word, g.top_mask);
+        const Key<W> q = key_xor<W>(t, g.p);
+        const uint32_t tag = (uint32_t)(h >> 16) & 0xFFFF0000u;
+        const uint32_t mine = tag | (uint32_t)i;
+        uint32_t s = (uint32_t)h & smask;
+        for (uint32_t probe = 0; probe <= smask; ++probe) {
+            uint32_t v = vt[s];
+            if (v == kJoinEmpty) {
+                v = atomicCAS(&table[s], kJoinEmpty, mine);
+                if (v == kJoinEmpty) break;
             }
+            if ((v & 0xFFFF0000u) == tag) {
+                const int j = (int)(v & 0xFFFFu);
+                if (key_equal<W>(load_key<W>(rk, at(j)), q)) {
+                    partner[i] = (uint16_t)j;
+                    partner[j] = (uint16_t)i;
+                    break;
+                }
+            }
+            s = (s + 1) & smask;
         }
     }
 }
@@ -334,40 +324,24 @@ __global__ void __launch_bounds__(kThreads) k_pair_join(const uint64_t* __restri
     if (!WRITE) return;
     __syncthreads();
     const int64_t base = (int64_t)s_base;
-    constexpr int kU = 2;  // rows per thread whose keys and coefficients are in flight together
-    for (int i0 = threadIdx.x; i0 < n; i0 += blockDim.x * kU) {
-        Key<W> tk[kU];
-        double ck[kU], cp[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int i = i0 + u * (int)blockDim.x;
-            if (i >= n) continue;
-            tk[u] = load_key<W>(rk, at(i));
-            ck[u] = rc[at(i)];
-            const int p = partner[i];
-            cp[u] = p != kNoPartner ? rc[at(p)] : 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const Key<W> t = load_key<W>(rk, at(i));
+        const auto& g = gen_of(t);
+        const Key<W> q = key_xor<W>(t, g.p);
+        const double sg = (double)product_sign<W>(t, g.yP, g.p, q);
+        const double ct = rc[at(i)];
+        const int p = partner[i];
+        double cn;
+        if (p != kNoPartner) {
+            cn = ct * g.cos_t - sg * rc[at(p)] * g.sin_t;
+        } else {
+            cn = ct * g.cos_t;
+            const int64_t r = base + n + (int64_t)atomicAdd(&s_app, 1u);
+            store_key<W>(rows, r, q);
+            coef[r] = sg * ct * g.sin_t;
         }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int i = i0 + u * (int)blockDim.x;
-            if (i >= n) break;
-            const Key<W>& t = tk[u];
-            const auto& g = gen_of(t);
-            const Key<W> q = key_xor<W>(t, g.p);
-            const double sg = (double)product_sign<W>(t, g.yP, g.p, q);
-            const double ct = ck[u];
-            double cn;
-            if (partner[i] != kNoPartner) {
-                cn = ct * g.cos_t - sg * cp[u] * g.sin_t;
-            } else {
-                cn = ct * g.cos_t;
-                const int64_t r = base + n + (int64_t)atomicAdd(&s_app, 1u);
-                store_key<W>(rows, r, q);
-                coef[r] = sg * ct * g.sin_t;
-            }
-            store_key<W>(rows, base + i, t);
-            coef[base + i] = cn;
-        }
+        store_key<W>(rows, base + i, t);
+        coef[base + i] = cn;
     }
 }
 
