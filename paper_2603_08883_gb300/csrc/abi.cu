@@ -663,7 +663,9 @@ iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags
 
 // The rows of a term limit's threshold bucket (ties, n_cand of them, with
 // `need` still to keep) kept in order of (key value desc, canonical key asc):
-// their flags set.
+// their flags set.  The bucket is first ordered by the key value alone (a few
+// digit passes); every row above the need-th row's value is kept, and only
+// the rows that tie with that value exactly are ordered by canonical key.
 iqcc_status keep_bucket_head(iqcc_ctx* ctx, const double* key, const uint32_t* ties, int64_t n_cand, int64_t need,
                              uint8_t* flags) {
     if (need >= n_cand) {
@@ -671,25 +673,51 @@ iqcc_status keep_bucket_head(iqcc_ctx* ctx, const double* key, const uint32_t* t
         CK_LAUNCH();
         return IQCC_OK;
     }
+    if (need <= 0) return IQCC_OK;
     const int stride = 2 * ctx->Wd + 1;
     Carver dry;
     dry.take<uint64_t>((size_t)n_cand * stride);
+    dry.take<uint64_t>(n_cand);
+    carve_sort(dry, n_cand);
     carve_sort(dry, n_cand);
     if (!ensure(ctx, ctx->aux, dry.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     Carver cv2{(char*)ctx->aux.p, 0};
     uint64_t* skeys = cv2.take<uint64_t>((size_t)n_cand * stride);
+    uint64_t* first = cv2.take<uint64_t>(n_cand);  // word 0 (the key value) in sorted order
     SortArea ca = carve_sort(cv2, n_cand);
+    SortArea cb = carve_sort(cv2, n_cand);
     if (cv2.off > ctx->aux.bytes) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
-    launch_candidate_keys(ctx->Wd, ctx->rows(), key, ties, n_cand, skeys, ctx->stream);
-    launch_iota(ca.a, n_cand, ctx->stream);
-    SortPlan plan{};
-    plan.n_words = stride;
-    plan.n_order = stride;
-    for (int w = 0; w < stride; ++w) plan.order[w] = w;
+    cudaStream_t s = ctx->stream;
+    launch_candidate_keys(ctx->Wd, ctx->rows(), key, ties, n_cand, skeys, s);
+    launch_iota(ca.a, n_cand, s);
+    SortPlan byval{};
+    byval.n_words = stride;
+    byval.n_order = 1;
+    byval.order[0] = 0;
     uint32_t* sorted = nullptr;
-    radix_sort_indirect(skeys, stride, plan, ca.a, ca.b, n_cand, &sorted, ca.tmp, ca.tmp_bytes, ctx->stream);
+    radix_sort_indirect(skeys, stride, byval, ca.a, ca.b, n_cand, &sorted, ca.tmp, ca.tmp_bytes, s);
+    launch_gather_word(skeys, stride, sorted, n_cand, first, s);
     CK_LAUNCH();
-    launch_set_flags_sorted(ties, sorted, need, flags, ctx->stream);
+    std::vector<uint64_t> h(n_cand);
+    CK(cudaMemcpyAsync(h.data(), first, sizeof(uint64_t) * n_cand, cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const uint64_t v = h[need - 1];
+    int64_t lo = need - 1, hi = need;
+    while (lo > 0 && h[lo - 1] == v) --lo;
+    while (hi < n_cand && h[hi] == v) ++hi;
+    launch_set_flags_sorted(ties, sorted, lo, flags, s);  // every row above the value
+    if (hi - lo == need - lo) {
+        launch_set_flags_sorted(ties, sorted + lo, hi - lo, flags, s);
+    } else {  // the exact ties at the value, in canonical key order
+        CK(cudaMemcpyAsync(cb.a, sorted + lo, sizeof(uint32_t) * (hi - lo), cudaMemcpyDeviceToDevice, s));
+        SortPlan bykey{};
+        bykey.n_words = stride;
+        bykey.n_order = stride - 1;
+        for (int w = 1; w < stride; ++w) bykey.order[w - 1] = w;
+        uint32_t* sorted2 = nullptr;
+        radix_sort_indirect(skeys, stride, bykey, cb.a, cb.b, hi - lo, &sorted2, cb.tmp, cb.tmp_bytes, s);
+        launch_set_flags_sorted(ties, sorted2, need - lo, flags, s);
+    }
     CK_LAUNCH();
     return IQCC_OK;
 }

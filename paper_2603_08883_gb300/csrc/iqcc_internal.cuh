@@ -572,6 +572,9 @@ void launch_cut_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t pr
 void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, const uint32_t* cand, int64_t k,
                            uint64_t* skeys, cudaStream_t s);
 void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s);
+// out[i] = keys[order[i] * stride]: the first word of each key in sorted order
+void launch_gather_word(const uint64_t* keys, int stride, const uint32_t* order, int64_t n, uint64_t* out,
+                        cudaStream_t s);
 // cand: candidates of all parts concatenated (part p's at [offs[p], offs[p + 1])); flags: device array of
 // the parts' flag arrays; the first k in `order` set in their owner's flags.
 void launch_set_flags_sorted_parts(const uint32_t* cand, const uint32_t* order, int64_t k, const int64_t* offs,

@@ -589,6 +589,14 @@ __global__ void k_set_flags_sorted(const uint32_t* __restrict__ cand, const uint
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += s) flags[cand[order[i]]] = 1;
 }
 
+// out[i] = keys[order[i] * stride + 0]: the first word of each key, in sorted order.
+__global__ void k_gather_word(const uint64_t* __restrict__ keys, int stride, const uint32_t* __restrict__ order,
+                              int64_t n, uint64_t* out) {
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s)
+        out[i] = keys[(size_t)order[i] * stride];
+}
+
 // Multi-part term limit: the first k candidates in sorted order, each owned
 // by the part whose range [offs[p], offs[p + 1]) holds its index, flagged in
 // that part's flags.
@@ -907,6 +915,14 @@ void launch_candidate_keys(int Wd, const uint64_t* rows, const double* coef, con
 void launch_set_flags_sorted(const uint32_t* cand, const uint32_t* order, int64_t k, uint8_t* flags, cudaStream_t s) {
     if (k > 0) {
         k_set_flags_sorted<<<grid_stride_blocks(k), kThreads, 0, s>>>(cand, order, k, flags);
+        note_launch();
+    }
+}
+
+void launch_gather_word(const uint64_t* keys, int stride, const uint32_t* order, int64_t n, uint64_t* out,
+                        cudaStream_t s) {
+    if (n > 0) {
+        k_gather_word<<<grid_stride_blocks(n), kThreads, 0, s>>>(keys, stride, order, n, out);
         note_launch();
     }
 }
