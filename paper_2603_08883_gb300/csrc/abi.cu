@@ -789,14 +789,17 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
     if (st) return st;
     const int64_t M = ctx->M;
     if (M == 0) return IQCC_OK;
+    const int64_t n_tiles = (M + kDressTile - 1) / kDressTile;
     Carver cv;
     cv.take<uint8_t>(M);
-    cv.take<char>(compact_inplace_scratch_bytes(M));
+    cv.take<uint32_t>(n_tiles + 1);
+    cv.take<uint32_t>(1024);
     cv.take<uint32_t>(M);  // tie list
     if (!ensure(ctx, ctx->scratch, cv.off)) return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     cv = Carver{(char*)ctx->scratch.p, 0};
     uint8_t* flags = cv.take<uint8_t>(M);
-    char* cscratch = cv.take<char>(compact_inplace_scratch_bytes(M));
+    uint32_t* tiles = cv.take<uint32_t>(n_tiles + 1);
+    uint32_t* scan_tmp = cv.take<uint32_t>(1024);
     uint32_t* ties = cv.take<uint32_t>(M);
     if (!carve_fits(ctx, cv)) return fail(ctx, IQCC_ERR_STATE, "internal: scratch carve exceeds allocation");
 
@@ -824,19 +827,40 @@ iqcc_status compress(iqcc_ctx* ctx, double eps, int64_t max_terms, int64_t* remo
         st = keep_bucket_head(ctx, rank ? rank : ctx->c(), ties, (int64_t)ctx->h_counters->aux, need, flags);
         if (st) return st;
     }
-    CK(cudaMemsetAsync(&c->aux, 0, sizeof(unsigned long long), ctx->stream));
-    launch_compact_inplace(ctx->Wd, flags, ctx->rows(), ctx->c(), M, cscratch, &c->aux, c, ctx->stream);
+    // the kept rows copied into the other row buffer at offsets known per tile (no block waits on
+    // another), then the buffers swap
+    launch_flag_tiles(flags, M, tiles, ctx->stream);
+    CK(cudaMemsetAsync(tiles + n_tiles, 0, sizeof(uint32_t), ctx->stream));
+    launch_scan_u32_long(tiles, n_tiles + 1, scan_tmp, ctx->stream);
     CK_LAUNCH();
+    uint32_t kept_total = 0;
+    CK(cudaMemcpyAsync(&kept_total, tiles + n_tiles, sizeof kept_total, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    const int64_t newM = (int64_t)kept_total;
+    if (newM != M) {
+        st = ensure_second_rows(ctx, std::max<int64_t>(newM, 1));
+        if (st) return st;
+        uint64_t zero[8] = {0};
+        PairDress keep{ctx->Wd, zero, nullptr, 0, 1.0, 0.0};  // no row anticommutes: the flagged rows are kept
+        launch_pair_split(keep, true, false, ctx->rows(), ctx->c(), M, 10, nullptr, 0, nullptr, nullptr, tiles,
+                          (uint64_t*)ctx->keys2.p, (double*)ctx->coef2.p, c, ctx->stream, flags);
+        CK_LAUNCH();
+    }
     CK(cudaEventRecord(ctx->ev1, ctx->stream));
     st = read_counters(ctx);
     if (st) return st;
     float ms = 0;
     cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
     ctx->stats.prune_ms += ms;
-    const int64_t newM = (int64_t)ctx->h_counters->aux;
+    if (newM != M) {
+        std::swap(ctx->keys, ctx->keys2);
+        std::swap(ctx->coef, ctx->coef2);
+        ctx->rows_alloc = (int64_t)std::min(ctx->keys.bytes / row_bytes(ctx), ctx->coef.bytes / 8);
+        ctx->stats.rows_allocated = ctx->rows_alloc;
+        ctx->index_valid = false;  // rows moved: the index (when one is kept) is stale
+    }
     ctx->M = newM;
     *removed = M - newM;
-    if (newM != M) ctx->index_valid = false;  // rows moved: the index (when one is kept) is stale
     return IQCC_OK;
 }
 

@@ -429,6 +429,9 @@ struct PairTwo {
 void launch_pair_join2(const PairDress& d, const uint64_t* rk, const double* rc, const uint32_t* start,
                        int log2_bins, uint32_t bins_per_block, const PairTwo& t, DevCounters* ctr, cudaStream_t s);
 
+// tile_kept[t]: flagged rows in tile t of kDressTile rows (an out-of-place compaction's offsets,
+// after a scan, for launch_pair_split with a zero generator and the flags as live rows).
+void launch_flag_tiles(const uint8_t* flags, int64_t n, uint32_t* tile_kept, cudaStream_t s);
 // Load of rows in any order (k_pairjoin.cu): the distinct keys of rows[0, n) with their coefficients
 // summed in input order, non-zero sums written to rows_out / c_out from *out_cursor (zeroed) on, in
 // bin order.  Three phases: 0 counts rows per bin into counts[1..2^L] (zeroed, counts[0] = 0);

@@ -619,6 +619,23 @@ __global__ void __launch_bounds__(kThreads) k_key_join(const uint64_t* __restric
     }
 }
 
+// Rows flagged in each tile of kDressTile rows (flags only): tile_kept[t].
+__global__ void __launch_bounds__(kThreads) k_flag_tiles(const uint8_t* __restrict__ flags, int64_t n,
+                                                         uint32_t* tile_kept) {
+    constexpr int kPer = kDressTile / kThreads;
+    const int64_t base = (int64_t)blockIdx.x * kDressTile;
+    bool f[kPer];
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) {
+        const int64_t i = base + r * kThreads + threadIdx.x;
+        f[r] = i < n && flags[i];
+    }
+    int kept = 0;
+#pragma unroll
+    for (int r = 0; r < kPer; ++r) kept += __syncthreads_count(f[r]);
+    if (threadIdx.x == 0) tile_kept[blockIdx.x] = (uint32_t)kept;
+}
+
 int grid_cap(int64_t items, int per_sm) {
     int64_t want = (items + kThreads - 1) / kThreads;
     const int64_t cap = (int64_t)sm_count() * per_sm;
@@ -786,6 +803,12 @@ void launch_key_group(int Wd, const uint64_t* rows, const double* coef, int64_t 
         case 2: run(std::integral_constant<int, 2>{}); break;
         default: run(std::integral_constant<int, 4>{}); break;
     }
+    note_launch();
+}
+
+void launch_flag_tiles(const uint8_t* flags, int64_t n, uint32_t* tile_kept, cudaStream_t s) {
+    if (n <= 0) return;
+    k_flag_tiles<<<(unsigned)((n + kDressTile - 1) / kDressTile), kThreads, 0, s>>>(flags, n, tile_kept);
     note_launch();
 }
 
