@@ -85,17 +85,11 @@ template <int W>
 __global__ void __launch_bounds__(kThreads) k_flip_hist(const uint64_t* __restrict__ rows, int64_t M, int shift,
                                                         uint32_t* counts, DevCounters* ctr) {
     unsigned n = 0;
-    constexpr int kU = 4;  // rows per thread whose keys are in flight together
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i0 < M; i0 += stride * kU) {
-        Key<W> t[kU];
-#pragma unroll
-        for (int u = 0; u < kU; ++u)
-            if (i0 + u * stride < M) t[u] = load_key<W>(rows, i0 + u * stride);
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (i0 + u * stride >= M || !has_flips<W>(t[u])) continue;
-            atomicAdd(&counts[flip_hash<W>(t[u].x) >> shift], 1u);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < M; i += stride) {
+        const Key<W> t = load_key<W>(rows, i);
+        if (has_flips<W>(t)) {
+            atomicAdd(&counts[flip_hash<W>(t.x) >> shift], 1u);
             ++n;
         }
     }
@@ -171,50 +165,34 @@ __global__ void __launch_bounds__(kThreads) k_flip_join(const uint64_t* __restri
     __syncthreads();
     volatile unsigned long long* vt = table;
     bool full = false;
-    constexpr int kU = 4;  // rows per thread whose records are in flight together
-    for (int64_t i0 = threadIdx.x; i0 < n; i0 += (int64_t)blockDim.x * kU) {
-        uint64_t x[kU][W], hh[kU], val[kU];
-        bool ok[kU];
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        uint64_t x[W];
 #pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            const int64_t i = i0 + (int64_t)u * blockDim.x;
-            ok[u] = i < n;
-            if (!ok[u]) continue;
-            const uint64_t* rec = rr + (size_t)(r0 + i) * R;
-#pragma unroll
-            for (int j = 0; j < W; ++j) x[u][j] = rec[j];
-            val[u] = rec[W];
-            hh[u] = rec[W + 1];  // the flip set's hash, stored by the scatter
-        }
-#pragma unroll
-        for (int u = 0; u < kU; ++u) {
-            if (!ok[u]) continue;
-            const int64_t i = i0 + (int64_t)u * blockDim.x;
-            const uint64_t h = hh[u];
-            const unsigned long long mine = (h & 0xFFFFFFFF00000000ull) | (unsigned long long)(uint32_t)i;
-            uint32_t s = (uint32_t)h & (kSlots - 1);
-            int probe = 0;
-            for (; probe < kSlots; ++probe) {
-                unsigned long long v = vt[s];
-                if (v == kEmptySlot) {
-                    v = atomicCAS(&table[s], kEmptySlot, mine);
-                    if (v == kEmptySlot) break;  // first row of its group
-                }
-                if ((v >> 32) == (h >> 32)) {
-                    const uint32_t j = (uint32_t)v;
-                    bool same = true;
-#pragma unroll
-                    for (int w = 0; w < W; ++w) same &= rr[(size_t)(r0 + j) * R + w] == x[u][w];
-                    if (same) break;
-                }
-                s = (s + 1) & (kSlots - 1);
+        for (int j = 0; j < W; ++j) x[j] = rr[(size_t)(r0 + i) * R + j];
+        const uint64_t h = rr[(size_t)(r0 + i) * R + W + 1];  // the flip set's hash, stored by the scatter
+        const unsigned long long mine = (h & 0xFFFFFFFF00000000ull) | (unsigned long long)(uint32_t)i;
+        uint32_t s = (uint32_t)h & (kSlots - 1);
+        int probe = 0;
+        for (; probe < kSlots; ++probe) {
+            unsigned long long v = vt[s];
+            if (v == kEmptySlot) {
+                v = atomicCAS(&table[s], kEmptySlot, mine);
+                if (v == kEmptySlot) break;  // first row of its group
             }
-            if (probe == kSlots) {
-                full = true;
-                continue;
+            if ((v >> 32) == (h >> 32)) {
+                const uint32_t j = (uint32_t)v;
+                bool same = true;
+#pragma unroll
+                for (int w = 0; w < W; ++w) same &= rr[(size_t)(r0 + j) * R + w] == x[w];
+                if (same) break;
             }
-            if (VALUES) atomicAdd(&sum[s], __longlong_as_double((long long)val[u]));
+            s = (s + 1) & (kSlots - 1);
         }
+        if (probe == kSlots) {
+            full = true;
+            continue;
+        }
+        if (VALUES) atomicAdd(&sum[s], __longlong_as_double((long long)rr[(size_t)(r0 + i) * R + W]));
     }
     if (full) set_error(ctr, IQCC_ERR_HASH_FULL, 80);  // more distinct flip sets than slots in one block
     __syncthreads();
