@@ -63,11 +63,11 @@ def test_default_wait_limit_is_restored_and_bounded():
 
 
 def test_one_poll_waits_give_up_or_finish_correctly():
-    """A one-poll limit on work that waits for real (the compression's and
-    the dress's in-place compactions of about 10^6 rows in about 1,000 tiles):
-    each call either completes with the right result or fails with
-    IQCC_ERR_TIMEOUT and leaves the context refusing further calls.  Nothing
-    hangs."""
+    """A one-poll wait limit on compression and dress of about 10^6 rows.
+    Both copy rows out of place at offsets known per tile, so no block waits
+    on another and both must finish with the right result; were a wait left
+    in them, the call would have to fail with IQCC_ERR_TIMEOUT and leave the
+    context refusing further calls.  Nothing hangs either way."""
     n = 40
     _, x, z, c = synth.random_hamiltonian(n, 1_200_000, 9, density=0.1)
     x[: len(x) // 2] &= np.uint64(0xF)             # few flip sets: many rows share a DIS group
