@@ -627,34 +627,60 @@ iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags
     int64_t bucket = kept;
     uint64_t prefix = 0, pmask = 0;
     int hi = 63;
-    unsigned long long* hist12 = nullptr;
-    std::vector<unsigned long long> h(4096);
-    while (bucket > kBucketLimit && hi > 0) {
-        const int shift = std::max(0, hi - 12);
-        if (!hist12) {
-            if (!ensure(ctx, ctx->aux, 4096 * sizeof(unsigned long long)))
-                return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
-            hist12 = (unsigned long long*)ctx->aux.p;
-        }
-        CK(cudaMemsetAsync(hist12, 0, 4096 * sizeof(unsigned long long), ctx->stream));
-        launch_abs_digit_hist12(key, flags, M, shift, prefix, pmask, hist12, ctx->stream);
-        CK_LAUNCH();
-        CK(cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
-        CK(cudaStreamSynchronize(ctx->stream));
+    if (!ensure(ctx, ctx->aux, 2 * 4096 * sizeof(unsigned long long)))
+        return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
+    unsigned long long* hist12 = (unsigned long long*)ctx->aux.p;
+    unsigned long long* hist2 = hist12 + 4096;
+    std::vector<unsigned long long> h(4096), h2(4096);
+    // the bucket of digit d of histogram hh holding the *need-th largest
+    auto pick = [&](const std::vector<unsigned long long>& hh) {
         int64_t cum = 0;
         int sel = 0;
         for (int d = 4095; d >= 0; --d) {
-            if (cum + (int64_t)h[d] >= *need) {
+            if (cum + (int64_t)hh[d] >= *need) {
                 sel = d;
                 break;
             }
-            cum += (int64_t)h[d];
+            cum += (int64_t)hh[d];
         }
         *need -= cum;
+        return sel;
+    };
+    bool have2 = false;  // hist2 holds the second level for the chosen first digit
+    while (bucket > kBucketLimit && hi > 0) {
+        const int shift = std::max(0, hi - 12);
+        const bool first = hi == 63;
+        CK(cudaMemsetAsync(hist12, 0, 2 * 4096 * sizeof(unsigned long long), ctx->stream));
+        if (first && ctx->select_guess >= 0 && shift >= 12) {
+            // one pass for two levels when the threshold's first digit is where the last select found it
+            launch_abs_digit_hist12x2(key, flags, M, shift, shift - 12, (unsigned)ctx->select_guess, hist12, hist2,
+                                      ctx->stream);
+        } else {
+            launch_abs_digit_hist12(key, flags, M, shift, prefix, pmask, hist12, ctx->stream);
+        }
+        CK_LAUNCH();
+        CK(cudaMemcpyAsync(h.data(), hist12, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaMemcpyAsync(h2.data(), hist2, 4096 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        const int sel = pick(h);
         bucket = (int64_t)h[sel];
         prefix |= (uint64_t)sel << shift;
         pmask |= (uint64_t)4095 << shift;
         hi = shift;
+        if (first) {
+            have2 = ctx->select_guess == sel && shift >= 12;
+            ctx->select_guess = sel;
+        }
+        if (have2 && bucket > kBucketLimit && hi > 0) {  // the second level from the same pass
+            have2 = false;
+            const int shift2 = hi - 12;
+            const int sel2 = pick(h2);
+            bucket = (int64_t)h2[sel2];
+            prefix |= (uint64_t)sel2 << shift2;
+            pmask |= (uint64_t)4095 << shift2;
+            hi = shift2;
+        }
+        have2 = false;
     }
     *prefix_out = prefix;
     *pmask_out = pmask & 0x7FFFFFFFFFFFFFFFull;

@@ -286,6 +286,7 @@ struct iqcc_ctx {
     iqcc::Buf model;               // learned screening weights (device layout), when set
     iqcc::Buf screen_rank;         // learned screening: per-row keys and the <sigma> table
     double screen_floor = 0.5;     // learned term limit: share kept by largest |C| first
+    int select_guess = -1;         // first-level digit of the last term-limit select (-1: none yet)
     double bin_slack = 0.25;       // fixed dress bins: relative slack over the mean count
     int bin_slack_rows = 32;       //   and rows added to it
 
@@ -560,6 +561,10 @@ void launch_set_flags(const uint32_t* idx, int64_t k, uint8_t* flags, cudaStream
 // term-limit select with 12-bit digits, then an exact sort of the threshold bucket
 void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n, int shift, uint64_t prefix,
                              uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s);
+// The first two select levels in one pass: hist1 (4096, zeroed) of the digit at shift1 of every kept
+// row, hist2 (4096, zeroed) of the digit at shift2 of the kept rows whose first digit is `guess`.
+void launch_abs_digit_hist12x2(const double* coef, const uint8_t* flags, int64_t n, int shift1, int shift2,
+                               unsigned guess, unsigned long long* hist1, unsigned long long* hist2, cudaStream_t s);
 void launch_bucket_flags(const double* coef, uint8_t* flags, int64_t n, uint64_t prefix, uint64_t prefix_mask,
                          uint32_t* cand, unsigned long long* n_cand, cudaStream_t s);
 // |c| bit patterns (as doubles) of the kept rows in a select bucket, appended to

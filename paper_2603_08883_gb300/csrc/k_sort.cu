@@ -515,6 +515,30 @@ __global__ void k_abs_digit_hist12(const double* __restrict__ coef, const uint8_
         if (h[i]) atomicAdd(hist + i, (unsigned long long)h[i]);
 }
 
+// The first two levels of the select in one pass when the first level's digit
+// is guessed: hist1 over the digit at shift1 of every kept row, hist2 over the
+// digit at shift2 of the kept rows whose first digit is `guess`.
+__global__ void k_abs_digit_hist12x2(const double* __restrict__ coef, const uint8_t* __restrict__ flags,
+                                     int64_t n, int shift1, int shift2, unsigned guess, unsigned long long* hist1,
+                                     unsigned long long* hist2) {
+    __shared__ unsigned int h1[4096], h2[4096];
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) h1[i] = h2[i] = 0;
+    __syncthreads();
+    const int64_t s = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += s) {
+        if (flags && !flags[i]) continue;
+        const uint64_t b = abs_bits(coef[i]);
+        const unsigned d1 = (unsigned)(b >> shift1) & 4095u;
+        atomicAdd(&h1[d1], 1u);
+        if (d1 == guess) atomicAdd(&h2[(b >> shift2) & 4095u], 1u);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4096; i += blockDim.x) {
+        if (h1[i]) atomicAdd(hist1 + i, (unsigned long long)h1[i]);
+        if (h2[i]) atomicAdd(hist2 + i, (unsigned long long)h2[i]);
+    }
+}
+
 // |C| of the kept rows inside the bucket (bits under prefix_mask equal prefix),
 // appended to vals (at most cap of them; *n_vals counts them all).
 __global__ void k_bucket_values(const double* __restrict__ coef, const uint8_t* __restrict__ flags, int64_t n,
@@ -864,6 +888,15 @@ void launch_abs_digit_hist12(const double* coef, const uint8_t* flags, int64_t n
                              uint64_t prefix_mask, unsigned long long* hist, cudaStream_t s) {
     if (n > 0) {
         k_abs_digit_hist12<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift, prefix, prefix_mask, hist);
+        note_launch();
+    }
+}
+
+void launch_abs_digit_hist12x2(const double* coef, const uint8_t* flags, int64_t n, int shift1, int shift2,
+                               unsigned guess, unsigned long long* hist1, unsigned long long* hist2, cudaStream_t s) {
+    if (n > 0) {
+        k_abs_digit_hist12x2<<<grid_stride_blocks(n), kThreads, 0, s>>>(coef, flags, n, shift1, shift2, guess, hist1,
+                                                                        hist2);
         note_launch();
     }
 }
