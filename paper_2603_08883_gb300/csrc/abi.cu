@@ -617,16 +617,19 @@ size_t sort_area_bytes(int64_t n) {
 // rank (device [M], may be NULL): the term limit keeps the largest |rank|
 // instead of the largest |C| (the magnitude threshold eps always uses |C|).
 // Radix select on the bit patterns of the non-negative doubles `key` among
-// the rows whose flag is set (`kept` of them), 12 bits at a time from the top,
-// until the bucket that holds the *need-th largest value has at most 65,536
-// rows.  Out: the bucket's bits (*prefix under *pmask) and, in *need, how many
-// of its rows are still needed.
+// the rows whose flag is set (`kept` of them), 12 bits at a time from the top
+// (the first digit is the exponent), until the bucket that holds the *need-th
+// largest value has at most 65,536 rows.  When the first digit is the one the
+// last select chose (consecutive cuts have similar thresholds), the first pass
+// also histograms the second digit of that bucket and the second pass is
+// skipped.  Out: the bucket's bits (*prefix under *pmask) and, in *need, how
+// many of its rows are still needed.
 iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags, int64_t M, int64_t kept,
                           int64_t* need, uint64_t* prefix_out, uint64_t* pmask_out) {
     constexpr int64_t kBucketLimit = 1 << 16;
     int64_t bucket = kept;
     uint64_t prefix = 0, pmask = 0;
-    int hi = 63;
+    int hi = 64;  // first digit: bits 52..63, the exponent (the sign bit is clear)
     if (!ensure(ctx, ctx->aux, 2 * 4096 * sizeof(unsigned long long)))
         return fail(ctx, IQCC_ERR_OOM, "scratch allocation failed");
     unsigned long long* hist12 = (unsigned long long*)ctx->aux.p;
@@ -649,7 +652,7 @@ iqcc_status select_bucket(iqcc_ctx* ctx, const double* key, const uint8_t* flags
     bool have2 = false;  // hist2 holds the second level for the chosen first digit
     while (bucket > kBucketLimit && hi > 0) {
         const int shift = std::max(0, hi - 12);
-        const bool first = hi == 63;
+        const bool first = hi == 64;
         CK(cudaMemsetAsync(hist12, 0, 2 * 4096 * sizeof(unsigned long long), ctx->stream));
         if (first && ctx->select_guess >= 0 && shift >= 12) {
             // one pass for two levels when the threshold's first digit is where the last select found it
