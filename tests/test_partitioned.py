@@ -203,3 +203,27 @@ def test_exchange_with_an_empty_partition():
     assert len(res[1][1][2]) > 0                        # the empty side received and appended partners
     bad = compare(union, o.export())
     assert not bad, bad[:5]
+
+
+@pytest.mark.parametrize("n,parts", [(24, 2), (100, 4), (200, 4)])
+def test_partition_pattern_round_trip(n, parts):
+    """The key bits a partition is given under the masks (the owner rule of
+    the two-partition dress) map back to that partition, and generator shifts
+    combine partitions by xor."""
+    W = (n + 63) // 64
+    mx = np.zeros(W, np.uint64)
+    mz = np.zeros(W, np.uint64)
+    mx[0] = np.uint64(1 << 3)
+    if parts == 4:
+        mz[W - 1] = np.uint64(1 << ((n - 1) % 64))
+    P = object.__new__(pt.PartitionedHamiltonian)   # the bookkeeping only: no contexts
+    P.n, P.W, P.mx, P.mz = n, W, mx, mz
+    for a in range(parts):
+        px, pz = P.pattern(a)
+        assert np.all((px & ~mx) == 0) and np.all((pz & ~mz) == 0)
+        assert pt.partition_of(px.reshape(1, -1), pz.reshape(1, -1), mx, mz)[0] == a
+        for d in range(parts):
+            gx, gz = P.pattern(d)
+            assert pt.generator_shift(gx, gz, mx, mz) == d
+            qx, qz = px ^ gx, pz ^ gz
+            assert pt.partition_of(qx.reshape(1, -1), qz.reshape(1, -1), mx, mz)[0] == a ^ d
