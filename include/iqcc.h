@@ -264,15 +264,22 @@ typedef struct {
  * max_terms is cut to the max_terms largest |C| at once (the term limit of the
  * paper's Tables 2-3 holds after every dress, which bounds device memory by
  * 2 max_terms rows); then iqcc_prune(eps, max_terms) and the energy.  The
- * generators of one iteration come from one screening.
+ * generators of one iteration come from one screening.  A cut is taken as
+ * flags and applied by the next dress while it copies H (none after the last
+ * dress: the final compression applies the same limit); the A, B, C pass of a
+ * generator also counts the rows its dress will keep and bin, so the dress
+ * sizes its bins from that count (iqcc_set_bin_slack) and needs no counting
+ * pass of its own.
  */
 iqcc_status iqcc_iterate(iqcc_ctx* ctx, const double* theta, const double* phi,
                          const iqcc_iter_opts* opts, iqcc_iter_result* out);
 
 /*
- * Device waits.  The stable in-place compactions (the dress's split of the
- * commuting rows, the compression) wait on other blocks: a tile waits for its
- * predecessors' counts (decoupled look-back).  Each wait polls at most
+ * Device waits.  The stable in-place compaction (the load of canonical
+ * input, and a deferred term-limit cut applied outside a dress) waits on other
+ * blocks: a tile waits for its predecessors' counts (decoupled look-back); the
+ * dress and the compression copy rows out of place and do not wait.  Each
+ * wait polls at most
  * `polls` times; then the kernel records IQCC_ERR_TIMEOUT and returns without
  * writing out of bounds, the call that launched it returns IQCC_ERR_TIMEOUT,
  * and the context refuses every later call (IQCC_ERR_STATE).  polls = 0
