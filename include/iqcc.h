@@ -74,8 +74,13 @@ typedef struct {
 /*
  * Create a context holding H = sum_k coef[k] P(x[k], z[k]) (Eq. 2).
  * x, z: host [n_terms][W]; coef: host [n_terms].  Repeated keys are summed in
- * input order, exact zeros are dropped, and the rows are stored in canonical
- * order (device radix sort + segmented sum).  n_terms may be 0.
+ * input order and exact zeros are dropped.  Input already in canonical order
+ * with distinct keys (an iqcc_export) is checked on the device and kept in
+ * that order; other input is grouped by key through a hash partition and a
+ * shared-memory join (rows stored in bin order; a device radix sort instead
+ * when one string repeats thousands of times).  The row order of a context
+ * is not part of its state: iqcc_export returns canonical order regardless.
+ * n_terms may be 0.
  * On success *out owns the context (free with iqcc_free); on failure *out is
  * NULL and iqcc_last_error(NULL) describes the error.
  */
